@@ -1,0 +1,148 @@
+/*
+ * sht.h -- C ABI of libsht, batched spherical harmonic transforms of many
+ * HEALPix maps on one B300 GPU (sm_103a).
+ *
+ * Method: arXiv:2208.10154, "Accelerating spherical harmonic transforms for a
+ * large number of sky maps". For a batch of maps on one pixelisation the
+ * per-m sums over iso-latitude rings become matrix-matrix products
+ * (Sec. 2.1, eq:mm, equ:mm_forward, equ:mm backward; Sec. 2.2 equ:matrix form):
+ *     map2alm:  A_m = P_m T_m        (contract rings, dsigma = 4 pi / Npix)
+ *     alm2map:  T_m = P_m^t A_m      (contract l), then ring FFTs.
+ * Spin 2 (Q,U <-> E,B) follows Sec. 2.3 (Q_lm+iU_lm, equ:alm-eb,
+ * equ:aeab mat form and its transpose). Iteration follows Algorithm 2.
+ *
+ * Conventions shared by every entry point
+ *   - All data pointers are DEVICE pointers owned by the caller (typically
+ *     torch tensors); the library never copies them to the host. Pointers to
+ *     maps/alm must be 16-byte aligned.
+ *   - map layout: double [nmaps][ncomp][npix], HEALPix RING order,
+ *     npix = 12 nside^2. ncomp = 1 (T) for spin 0, 2 (Q, U) for spin 2.
+ *   - alm layout: complex double (re, im interleaved) [nmaps][ncomp][nalm],
+ *     m-major packed: idx(l, m) = m (2 lmax + 1 - m) / 2 + l, 0 <= m <= mmax,
+ *     m <= l <= lmax, nalm = (mmax + 1)(2 lmax + 2 - mmax) / 2.
+ *     ncomp = 1 (T) or 2 (E, B). Only m >= 0 is stored (real fields). The
+ *     imaginary part of every m = 0 coefficient is ignored on input and
+ *     written as 0 on output; for spin 2, l < 2 is ignored / written as 0.
+ *   - map2alm uses the constant pixel weight dsigma = 4 pi / Npix (Sec. 2.1).
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream); nothing synchronises the host.
+ *   - `workspace` is caller-owned device memory of at least
+ *     sht_workspace_bytes(plan, nmaps) bytes, 256-byte aligned. Concurrent
+ *     calls on different streams need distinct workspaces.
+ *   - Errors are returned as status codes, never thrown; the message of the
+ *     last failure on the calling thread is in sht_last_error(). Arguments
+ *     are validated before any launch; on SHT_EINVAL nothing was launched.
+ */
+#ifndef SHT_H_
+#define SHT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan sht_plan;   /* opaque: ring tables, recurrence tables, FFT tables */
+
+typedef enum {
+    SHT_OK = 0,
+    SHT_EINVAL = 1,         /* bad argument (nothing launched)              */
+    SHT_ENOMEM = 2,         /* a device or host allocation failed          */
+    SHT_ECUDA = 3,          /* a CUDA runtime call or launch failed        */
+    SHT_EUNSUPPORTED = 4,   /* valid request outside what this build does  */
+    SHT_ETIMEOUT = 5        /* a bounded device wait gave up               */
+} sht_status;
+
+typedef enum {
+    /* Every step in FP64 (FFT, lambda recurrence, contraction). */
+    SHT_FP64 = 0,
+    /* Contraction on BF16 tensor cores (tcgen05, FP32 TMEM accumulation):
+     * each operand = exact integer main slice + BF16 residual pieces, the
+     * main products accumulate exactly; lambda recurrence in FP64; ring
+     * FFTs in FP32; final accumulation into a_lm in FP64. */
+    SHT_SPLIT_BF16 = 1
+} sht_precision;
+
+/* Create a plan for HEALPix resolution `nside` (>= 1), band limit `lmax`
+ * (>= 0), `mmax` (0..lmax; pass -1 for lmax), `spin` (0 or 2) and
+ * `precision` (sht_precision) on CUDA device `device`. Builds the ring
+ * geometry (standard HEALPix RING layout), the lambda_lm recurrence tables
+ * (Sec. 2.1 footnote: lambda_lm, normalised as |lambda| = |Y|) and the FFT
+ * tables on the host, and uploads them once (resident until destroy).
+ * Synchronous. On success *out receives the plan. */
+sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precision,
+                           int device, sht_plan** out);
+
+/* Release a plan and its device tables. NULL is ignored. Synchronous. */
+void sht_plan_destroy(sht_plan* plan);
+
+/* Device workspace (bytes) needed by one call on `nmaps` maps. Used for
+ * HBM admission by the serving loop. Returns 0 for a NULL plan or nmaps < 1. */
+size_t sht_workspace_bytes(const sht_plan* plan, int nmaps);
+
+/* Workspace for sht_map2alm with `niter` > 0 refinement steps of
+ * Algorithm 2 (adds a residual map buffer and a coefficient increment
+ * buffer). Equal to sht_workspace_bytes for niter = 0. */
+size_t sht_workspace_bytes_iter(const sht_plan* plan, int nmaps, int niter);
+
+/* Plan properties. */
+int       sht_plan_nside(const sht_plan* plan);
+int       sht_plan_lmax(const sht_plan* plan);
+int       sht_plan_mmax(const sht_plan* plan);
+int       sht_plan_spin(const sht_plan* plan);
+int       sht_plan_precision(const sht_plan* plan);
+long long sht_plan_npix(const sht_plan* plan);
+long long sht_plan_nalm(const sht_plan* plan);
+
+/* Backward transform (Sec. 2.1 equ:backward equ, equ:mm backward; spin 2:
+ * equ:aeab mat form inv). alm [nmaps][ncomp][nalm] (complex double, device)
+ * -> map [nmaps][ncomp][npix] (double, device). Real field:
+ *   T = sum_l a_l0 lambda_l0 + 2 Re sum_{m>0} sum_l a_lm lambda_lm e^{i m phi}.
+ * Spin 2: Q +- iU = sum a_{+-2,lm} +-2Y_lm with a_{+-2} = -(a_E +- i a_B). */
+sht_status sht_alm2map(sht_plan* plan, const void* alm, void* map, int nmaps,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Forward transform (Sec. 2.1 Eq. 1, eq:mm, equ:mm_forward; spin 2:
+ * equ:alm-eb, equ:aeab mat form). map -> alm, layouts as above, with
+ * `niter` >= 0 refinement steps of Algorithm 2 (0 = plain quadrature):
+ *   a^0 = map2alm(T), a^{n+1} = a^n + map2alm(T - alm2map(a^n)).
+ * niter > 0 needs sht_workspace_bytes_iter(plan, nmaps, niter) bytes. */
+sht_status sht_map2alm(sht_plan* plan, const void* map, void* alm, int nmaps, int niter,
+                       void* workspace, size_t workspace_bytes, void* stream);
+
+/* Adjoints in real parameters (Re a_l0; Re, Im a_lm for m > 0), used by the
+ * autograd wrappers. The paper has no adjoints; these are the exact
+ * transposes of the two linear maps above:
+ *   alm2map_adjoint(h)_lm = (Npix / 4 pi) map2alm(h)_lm * (1 if m = 0 [real
+ *                           part only], 2 if m > 0)
+ *   map2alm_adjoint(g)    = (4 pi / Npix) alm2map(g'), g'_l0 = Re g_l0,
+ *                           g'_lm = g_lm / 2 (m > 0).
+ * Same layouts and conventions as the forward calls. */
+sht_status sht_alm2map_adjoint(sht_plan* plan, const void* map, void* alm, int nmaps,
+                               void* workspace, size_t workspace_bytes, void* stream);
+sht_status sht_map2alm_adjoint(sht_plan* plan, const void* alm, void* map, int nmaps,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
+/* End-to-end variants on HOST buffers (pageable or pinned): the library
+ * stages the batch through its own pinned buffers in chunks and returns
+ * after the result is back in host memory (synchronous on `stream`).
+ * Same layouts as above. The staging buffers are owned by the plan. */
+sht_status sht_alm2map_host(sht_plan* plan, const void* alm_host, void* map_host, int nmaps,
+                            void* stream);
+sht_status sht_map2alm_host(sht_plan* plan, const void* map_host, void* alm_host, int nmaps,
+                            int niter, void* stream);
+
+/* Number of kernel launches the most recent call on this thread issued
+ * (for the benchmark's launch accounting). */
+int sht_last_launch_count(void);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* sht_last_error(void);
+
+/* Library version string. */
+const char* sht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHT_H_ */

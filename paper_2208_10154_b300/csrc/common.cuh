@@ -1,0 +1,139 @@
+// common.cuh -- internal types shared by the libsht translation units.
+//
+// Internal data layout (HBM). The Legendre step works per (m, slot q) on the
+// "FFT-mapped" ring spectra of Sec. 2.1 (the matrices T_m of equ:mat form def),
+// stored m-major so that every (m, q) block is one dense [pair][col] matrix:
+//
+//   T[m][q][p][c]   m = 0..mmax, q = 0/1, p = ring pair 0..R-1, c = column
+//
+// Ring pair p joins north ring p+1 and its mirror 4 nside - 1 - p (same
+// length and phase offset); pair R-1 = 2 nside - 1 is the equator ring alone.
+// With lambda_lm(pi - theta) = (-1)^{l+m} lambda_lm(theta), the ring sum of
+// eq:mm splits into  E = T_north + T_south  (slot 0, rows with l+m even) and
+// O = T_north - T_south (slot 1, rows with l+m odd). For spin 2 the slot is
+// the parity of the output row for F+ (F- has the opposite parity, Sec. 2.3).
+// A column c = (map, comp, re/im): c = (map * ncomp + comp) * 2 + reim.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/sht.h"
+
+namespace sht {
+
+// Per ring-pair geometry (north ring of the pair).
+struct PairGeom {
+    double x;          // cos(theta) of the north ring (>= 0)
+    double s;          // sin(theta)
+    double phi0;       // phi of the first pixel (0 or pi/N; same for both rings)
+    long long start_n; // first pixel of the north ring
+    long long start_s; // first pixel of the south ring (-1 for the equator pair)
+    int n;             // pixels per ring
+    int fft;           // index into the FFT length table
+};
+
+// One distinct ring length and its FFT recipe.
+struct FftLen {
+    int n;             // ring length N
+    int m;             // power-of-two FFT size used (N itself or the Bluestein size)
+    int bluestein;     // 1 if N is not a power of two
+    long long chirp;   // offset of w_n = exp(-i pi n^2 / N) (n < N) in the chirp table
+    long long bhat;    // offset of FFT_M(conj chirp, circular) (bit-reversed order)
+};
+
+struct DevTables {
+    PairGeom* pairs = nullptr;      // [R]
+    FftLen* fft = nullptr;          // [nfft]
+    double2* twiddle = nullptr;     // [fft_max/2]  exp(-2 pi i k / fft_max)
+    double2* chirp = nullptr;       // Bluestein chirps
+    double2* bhat = nullptr;        // Bluestein filter spectra
+    float2* twiddle_f = nullptr;    // FP32 copies for the split form
+    float2* chirp_f = nullptr;
+    float2* bhat_f = nullptr;
+    // lambda seeds: value at the first row of each chain, per pair, as
+    // mantissa * 2^exponent. Spin 0: [m][q][p] (l0 = m + q);
+    // spin 2: [m][s = +2, -2][p] at l0 = max(m, 2).
+    double* seed_mant = nullptr;
+    int* seed_exp = nullptr;
+    // spin-0 two-step recurrence (same parity), per (m, l) at packed index
+    // idx(l,m): lambda_{l+2} = (alpha x^2 + beta) lambda_l + gamma lambda_{l-2}
+    double* rec_a = nullptr;
+    double* rec_b = nullptr;
+    double* rec_c = nullptr;
+    // spin-2 three-term recurrence for s = +2 / -2 (Wigner d), per (m, l):
+    // sl_l = (A x + AB) sl_{l-1} - C sl_{l-2}
+    double* w_A[2] = {nullptr, nullptr};
+    double* w_AB[2] = {nullptr, nullptr};
+    double* w_C[2] = {nullptr, nullptr};
+};
+
+}  // namespace sht
+
+struct sht_plan {
+    int nside = 0, lmax = 0, mmax = 0, spin = 0, precision = 0, device = 0;
+    int ncomp = 1;
+    long long npix = 0, nalm = 0;
+    int R = 0;                  // ring pairs = 2 nside
+    int fft_max = 0;            // largest power-of-two FFT size
+    int nfft = 0;
+    sht::DevTables t;
+    std::vector<sht::PairGeom> h_pairs;
+    std::vector<sht::FftLen> h_fft;
+    size_t table_bytes = 0;
+    // Legendre work lists (m, q, tile, 0) for the FP64 kernels
+    int4* work_m2a = nullptr; int nwork_m2a = 0;
+    int4* work_a2m = nullptr; int nwork_a2m = 0;
+    // staging for the host-buffer entry points (allocated lazily)
+    void* pin_in = nullptr;
+    void* pin_out = nullptr;
+    size_t pin_in_bytes = 0, pin_out_bytes = 0;
+    void* host_ws = nullptr;
+    size_t host_ws_bytes = 0;
+    void* host_dev_in = nullptr;
+    void* host_dev_out = nullptr;
+    size_t host_dev_in_bytes = 0, host_dev_out_bytes = 0;
+};
+
+namespace sht {
+
+// thread-local error message and launch counter
+void set_error(const std::string& msg);
+void count_launch(int n = 1);
+void reset_launches();
+
+inline long long alm_index(int lmax, int l, int m)
+{
+    return (long long)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+// columns of the GEMMs for a batch
+inline long long ncols(const sht_plan* p, int nmaps) { return (long long)nmaps * p->ncomp * 2; }
+
+// workspace: the T / G buffer [m][q][p][c] in the compute precision
+size_t tbuf_bytes(const sht_plan* p, int nmaps);
+
+// kernels (launchers), return cudaSuccess or the launch error
+cudaError_t launch_fft_forward_f64(const sht_plan* p, const double* map, double* T, int nmaps,
+                                   cudaStream_t st);
+cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* map, int nmaps,
+                                    cudaStream_t st);
+cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                    double scale0, double scale, cudaStream_t st);
+cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
+                                    double scale0, double scale, cudaStream_t st);
+int legendre_f64_row_tile();
+int legendre_f64_pair_tile();
+
+}  // namespace sht
+
+#define SHT_CUDA_TRY(call)                                                              \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            sht::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));         \
+            return SHT_ECUDA;                                                           \
+        }                                                                               \
+    } while (0)

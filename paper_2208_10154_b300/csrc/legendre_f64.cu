@@ -1,0 +1,408 @@
+// legendre_f64.cu -- FP64 form of the Legendre contraction (Sec. 2.2
+// equ:matrix form; spin 2: Sec. 2.3 equ:aeab mat form and its transpose),
+// with lambda generated on the fly per (m, ring tile) from resident seeds and
+// recurrence coefficients, so the Legendre matrix never lands in HBM.
+//
+// Slot convention (see common.cuh): for spin 0, slot q holds rows / K entries
+// with (l - m) % 2 == q and uses T_q. For spin 2 (F+- = -(2lambda +- -2lambda)/2):
+//   map2alm  slot q rows (l-m)%2 == q:  A = F+ T_q + F- perm(T_{1-q})
+//   alm2map  slot q:  G_q = sum_{(l-m)%2==q} F+ a + sum_{(l-m)%2!=q} F- perm(a)
+// with perm(Qr,Qi,Ur,Ui) = (-Ui,Ur,Qi,-Qr) (E/B coupling through i U, Sec. 2.3).
+#include "common.cuh"
+
+namespace sht {
+
+// v * 2^E as a double (0 far below the double range)
+__device__ __forceinline__ double scale2(double v, int E)
+{
+    if (E >= -1022) {
+        if (E > 1023) E = 1023;
+        return v * __longlong_as_double((long long)(E + 1023) << 52);
+    }
+    if (E < -2100) return 0.0;
+    double t = v * __longlong_as_double((long long)(-1000 + 1023) << 52);
+    int E2 = E + 1000;
+    if (E2 < -1022) return 0.0;
+    return t * __longlong_as_double((long long)(E2 + 1023) << 52);
+}
+
+constexpr double RESCALE_UP = 0x1p500;
+constexpr double RESCALE_DN = 0x1p-500;
+
+struct LegArgs {
+    const int4* work;            // (m, q, tile, 0)
+    const PairGeom* pairs;
+    const double* seed_mant;
+    const int* seed_exp;
+    const double *ra, *rb, *rc;
+    const double *wA0, *wAB0, *wC0, *wA1, *wAB1, *wC1;
+    int spin, lmax, mmax, R;
+    long long ncol, nalm;
+    int ncomp;
+    double scale;      // output scale for m > 0
+    double scale0;     // output scale for m = 0
+};
+
+__device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
+{
+    return (long long)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+// ---------------------------------------------------------------------------
+// map2alm: a[l, c] (rows l = m + q + 2 r) = sum_k Lambda[l, k] B[k, c]
+// CTA tile: 128 rows x 32 cols, K chunk = 32 ring pairs.
+// grid.x = work item (m, q, row tile), grid.y = column tile
+// ---------------------------------------------------------------------------
+constexpr int M2A_TL = 128, M2A_TN = 32, M2A_TK = 32;
+
+__global__ void __launch_bounds__(256)
+k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    double* lam = sm;                                   // [2][TK][TL]
+    double* dat = sm + 2 * M2A_TK * M2A_TL;             // [2][TK][TN]
+    const int4 w = a.work[blockIdx.x];
+    const int m = w.x, q = w.y, rt = w.z;
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.y * M2A_TN;
+    const int l_first = m + q;
+    const int nrows = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
+    const int r0 = rt * M2A_TL;
+    const int ntypes = a.spin ? 2 : 1;
+    const long long qstride = (long long)a.R * a.ncol;
+    const double* Tq = T + ((long long)m * 2 + q) * qstride;
+    const double* To = T + ((long long)m * 2 + (1 - q)) * qstride;
+    const int tx = tid & 7, ty = tid >> 3;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    for (int k0 = 0; k0 < a.R; k0 += M2A_TK) {
+        // ---- lambda tile: warp 0, one ring pair per lane, walk rows ----
+        if (tid < 32) {
+            const int p = k0 + tid;
+            const bool valid = p < a.R;
+            const double x = valid ? a.pairs[p].x : 0.0;
+            if (a.spin == 0) {
+                double cur = 0.0, prev = 0.0;
+                int E = 0;
+                if (valid) {
+                    long long si = ((long long)m * 2 + q) * a.R + p;
+                    cur = a.seed_mant[si];
+                    E = a.seed_exp[si];
+                }
+                const double x2 = x * x;
+                for (int r = 0; r < r0 + M2A_TL; r++) {
+                    if (r >= r0) lam[tid * M2A_TL + (r - r0)] = (r < nrows) ? scale2(cur, E) : 0.0;
+                    if (r + 1 < nrows) {
+                        int l = l_first + 2 * r;
+                        long long ci = d_alm_index(a.lmax, l, m);
+                        double t = fma(a.ra[ci], x2, a.rb[ci]);
+                        double nxt = fma(t, cur, a.rc[ci] * prev);
+                        prev = cur;
+                        cur = nxt;
+                        if (fabs(cur) > RESCALE_UP) { cur *= RESCALE_DN; prev *= RESCALE_DN; E += 500; }
+                    }
+                }
+            } else {
+                // spin 2: walk every l from l0 = max(m,2); rows are l with (l-m)%2 == q
+                const int l0 = m > 2 ? m : 2;
+                double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;   // s=+2: cur, prev; s=-2: cur, prev
+                int E2 = 0, E3 = 0;
+                if (valid) {
+                    long long si = ((long long)m * 2 + 0) * a.R + p;
+                    c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
+                    si = ((long long)m * 2 + 1) * a.R + p;
+                    c3 = a.seed_mant[si]; E3 = a.seed_exp[si];
+                }
+                const int rlast = r0 + M2A_TL - 1;
+                const int lend = min(a.lmax, l_first + 2 * rlast);
+                for (int l = l0; l <= lend; l++) {
+                    if (l > l0) {
+                        long long ci = d_alm_index(a.lmax, l, m);
+                        double t = fma(a.wA0[ci], x, a.wAB0[ci]);
+                        double n2 = fma(t, c2, -a.wC0[ci] * p2);
+                        p2 = c2; c2 = n2;
+                        t = fma(a.wA1[ci], x, a.wAB1[ci]);
+                        double n3 = fma(t, c3, -a.wC1[ci] * p3);
+                        p3 = c3; c3 = n3;
+                        if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
+                        if (fabs(c3) > RESCALE_UP) { c3 *= RESCALE_DN; p3 *= RESCALE_DN; E3 += 500; }
+                    }
+                    if (((l - m) & 1) == q && l >= l_first) {
+                        int r = (l - l_first) >> 1;
+                        if (r >= r0) {
+                            double v2 = scale2(c2, E2), v3 = scale2(c3, E3);
+                            lam[(0 * M2A_TK + tid) * M2A_TL + (r - r0)] = -0.5 * (v2 + v3);
+                            lam[(1 * M2A_TK + tid) * M2A_TL + (r - r0)] = -0.5 * (v2 - v3);
+                        }
+                    }
+                }
+                // rows not produced above (l < l0 or beyond lmax) are zero
+                for (int r = r0; r < r0 + M2A_TL; r++) {
+                    int l = l_first + 2 * r;
+                    if (l < l0 || l > a.lmax || !valid) {
+                        lam[(0 * M2A_TK + tid) * M2A_TL + (r - r0)] = 0.0;
+                        lam[(1 * M2A_TK + tid) * M2A_TL + (r - r0)] = 0.0;
+                    }
+                }
+            }
+        }
+        // ---- data tile ----
+        for (int i = tid; i < M2A_TK * M2A_TN; i += blockDim.x) {
+            int k = i / M2A_TN, c = i % M2A_TN;
+            int p = k0 + k;
+            long long cg = c0 + c;
+            double v0 = 0.0, v1 = 0.0;
+            if (p < a.R && cg < a.ncol) {
+                v0 = Tq[(long long)p * a.ncol + cg];
+                if (a.spin) {
+                    long long base = cg & ~3LL;
+                    int wsel = (int)(cg & 3);
+                    const double* o = To + (long long)p * a.ncol + base;
+                    v1 = (wsel == 0) ? -o[3] : (wsel == 1) ? o[2] : (wsel == 2) ? o[1] : -o[0];
+                }
+            }
+            dat[k * M2A_TN + c] = v0;
+            dat[(M2A_TK + k) * M2A_TN + c] = v1;
+        }
+        __syncthreads();
+        for (int t = 0; t < ntypes; t++) {
+            const double* L = lam + t * M2A_TK * M2A_TL;
+            const double* D = dat + t * M2A_TK * M2A_TN;
+#pragma unroll 4
+            for (int k = 0; k < M2A_TK; k++) {
+                double lv[4], dv[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) lv[i] = L[k * M2A_TL + ty + 32 * i];
+#pragma unroll
+                for (int j = 0; j < 4; j++) dv[j] = D[k * M2A_TN + tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+            }
+        }
+        __syncthreads();
+    }
+    // ---- write a_lm ----
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int r = r0 + ty + 32 * i;
+        if (r >= nrows) continue;
+        int l = l_first + 2 * r;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            long long cg = c0 + tx * 4 + j;
+            if (cg >= a.ncol) continue;
+            long long mc = cg >> 1;           // map * ncomp + comp
+            int reim = (int)(cg & 1);
+            double v = (m == 0 ? a.scale0 : a.scale) * acc[i][j];
+            if ((m == 0 && reim) || (a.spin && l < 2)) v = 0.0;
+            alm[(mc * a.nalm + d_alm_index(a.lmax, l, m)) * 2 + reim] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// alm2map: G[m][q][p][c] = sum_k Lambda[k, p] B[k, c]
+// CTA tile: 64 ring pairs x 64 cols, K chunk = 32 values of l.
+// grid.x = work item (m, q, pair tile), grid.y = column tile
+// ---------------------------------------------------------------------------
+constexpr int A2M_TP = 64, A2M_TN = 64, A2M_TK = 32;
+
+__global__ void __launch_bounds__(256)
+k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
+{
+    extern __shared__ __align__(16) double sm[];
+    double* lam = sm;                        // [TK][TP]
+    double* dat = sm + A2M_TK * A2M_TP;      // [TK][TN]
+    const int4 w = a.work[blockIdx.x];
+    const int m = w.x, q = w.y, pt = w.z;
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.y * A2M_TN;
+    const int p0 = pt * A2M_TP;
+    const long long qstride = (long long)a.R * a.ncol;
+    const int tx = tid & 15, ty = tid >> 4;     // 16 col groups of 4, 16 pair groups of 4
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+
+    int lk0, lstep, K;
+    if (a.spin == 0) {
+        lk0 = m + q; lstep = 2;
+        K = (a.lmax >= lk0) ? (a.lmax - lk0) / 2 + 1 : 0;
+    } else {
+        lk0 = m > 2 ? m : 2; lstep = 1;
+        K = (a.lmax >= lk0) ? a.lmax - lk0 + 1 : 0;
+    }
+    // chain state (threads 0..63: one ring pair each)
+    double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;
+    int E2 = 0, E3 = 0;
+    double x = 0.0;
+    const int myp = p0 + tid;
+    if (tid < A2M_TP && myp < a.R) {
+        x = a.pairs[myp].x;
+        if (a.spin == 0) {
+            long long si = ((long long)m * 2 + q) * a.R + myp;
+            c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
+        } else {
+            long long si = ((long long)m * 2 + 0) * a.R + myp;
+            c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
+            si = ((long long)m * 2 + 1) * a.R + myp;
+            c3 = a.seed_mant[si]; E3 = a.seed_exp[si];
+        }
+    }
+    const double x2 = x * x;
+    for (int k0 = 0; k0 < K; k0 += A2M_TK) {
+        if (tid < A2M_TP) {
+            const bool valid = myp < a.R;
+            for (int kk = 0; kk < A2M_TK; kk++) {
+                int k = k0 + kk;
+                double v = 0.0;
+                if (k < K && valid) {
+                    int l = lk0 + lstep * k;
+                    if (a.spin == 0) {
+                        v = scale2(c2, E2);
+                        if (k + 1 < K) {
+                            long long ci = d_alm_index(a.lmax, l, m);
+                            double t = fma(a.ra[ci], x2, a.rb[ci]);
+                            double nxt = fma(t, c2, a.rc[ci] * p2);
+                            p2 = c2; c2 = nxt;
+                            if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
+                        }
+                    } else {
+                        if (k > 0) {
+                            long long ci = d_alm_index(a.lmax, l, m);
+                            double t = fma(a.wA0[ci], x, a.wAB0[ci]);
+                            double n2 = fma(t, c2, -a.wC0[ci] * p2);
+                            p2 = c2; c2 = n2;
+                            t = fma(a.wA1[ci], x, a.wAB1[ci]);
+                            double n3 = fma(t, c3, -a.wC1[ci] * p3);
+                            p3 = c3; c3 = n3;
+                            if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
+                            if (fabs(c3) > RESCALE_UP) { c3 *= RESCALE_DN; p3 *= RESCALE_DN; E3 += 500; }
+                        }
+                        double v2 = scale2(c2, E2), v3 = scale2(c3, E3);
+                        v = (((l - m) & 1) == q) ? -0.5 * (v2 + v3) : -0.5 * (v2 - v3);
+                    }
+                }
+                lam[kk * A2M_TP + tid] = v;
+            }
+        }
+        // data tile: a[l][c] (or perm(a) for spin-2 rows of the other parity)
+        for (int i = tid; i < A2M_TK * A2M_TN; i += blockDim.x) {
+            int kk = i / A2M_TN, c = i % A2M_TN;
+            int k = k0 + kk;
+            long long cg = c0 + c;
+            double v = 0.0;
+            if (k < K && cg < a.ncol) {
+                int l = lk0 + lstep * k;
+                long long li = d_alm_index(a.lmax, l, m);
+                if (a.spin == 0) {
+                    long long mc = cg >> 1;
+                    int reim = (int)(cg & 1);
+                    v = (m == 0 && reim) ? 0.0 : alm[(mc * a.nalm + li) * 2 + reim];
+                } else {
+                    long long mp = cg >> 2;
+                    int wsel = (int)(cg & 3);
+                    bool perm = ((l - m) & 1) != q;
+                    int src = wsel; double sg = 1.0;
+                    if (perm) {   // (Er, Ei, Br, Bi) -> (-Bi, Br, Ei, -Er)
+                        src = 3 - wsel;
+                        sg = (wsel == 0 || wsel == 3) ? -1.0 : 1.0;
+                    }
+                    int comp = src >> 1, reim = src & 1;
+                    v = (m == 0 && reim) ? 0.0
+                        : sg * alm[((mp * 2 + comp) * a.nalm + li) * 2 + reim];
+                }
+            }
+            dat[kk * A2M_TN + c] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < A2M_TK; kk++) {
+            double lv[4], dv[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) lv[i] = lam[kk * A2M_TP + ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) dv[j] = dat[kk * A2M_TN + tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double* Gq = G + ((long long)m * 2 + q) * qstride;
+    const double gs = (m == 0) ? a.scale0 : a.scale;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int p = p0 + ty + 16 * i;
+        if (p >= a.R) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            long long cg = c0 + tx * 4 + j;
+            if (cg < a.ncol) Gq[(long long)p * a.ncol + cg] = gs * acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double scale, const int4* work)
+{
+    LegArgs a;
+    a.work = work;
+    a.pairs = p->t.pairs;
+    a.seed_mant = p->t.seed_mant;
+    a.seed_exp = p->t.seed_exp;
+    a.ra = p->t.rec_a; a.rb = p->t.rec_b; a.rc = p->t.rec_c;
+    a.wA0 = p->t.w_A[0]; a.wAB0 = p->t.w_AB[0]; a.wC0 = p->t.w_C[0];
+    a.wA1 = p->t.w_A[1]; a.wAB1 = p->t.w_AB[1]; a.wC1 = p->t.w_C[1];
+    a.spin = p->spin; a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;
+    a.ncol = ncols(p, nmaps); a.nalm = p->nalm; a.ncomp = p->ncomp;
+    a.scale = scale;
+    a.scale0 = scale0;
+    return a;
+}
+
+cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                    double scale0, double scale, cudaStream_t st)
+{
+    const int4* work = p->work_m2a;
+    int nwork = p->nwork_m2a;
+    if (nwork == 0) return cudaSuccess;
+    size_t sm = (size_t)(2 * M2A_TK * M2A_TL + 2 * M2A_TK * M2A_TN) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long nc = ncols(p, nmaps);
+    dim3 grid((unsigned)nwork, (unsigned)((nc + M2A_TN - 1) / M2A_TN));
+    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, make_args(p, nmaps, scale0, scale, work));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
+                                    double scale0, double scale, cudaStream_t st)
+{
+    const int4* work = p->work_a2m;
+    int nwork = p->nwork_a2m;
+    if (nwork == 0) return cudaSuccess;
+    size_t sm = (size_t)(A2M_TK * A2M_TP + A2M_TK * A2M_TN) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_a2m_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long nc = ncols(p, nmaps);
+    dim3 grid((unsigned)nwork, (unsigned)((nc + A2M_TN - 1) / A2M_TN));
+    k_leg_a2m_f64<<<grid, 256, sm, st>>>(alm, G, make_args(p, nmaps, scale0, scale, work));
+    count_launch();
+    return cudaGetLastError();
+}
+
+int legendre_f64_row_tile() { return M2A_TL; }
+int legendre_f64_pair_tile() { return A2M_TP; }
+
+}  // namespace sht

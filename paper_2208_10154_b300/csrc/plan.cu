@@ -1,0 +1,624 @@
+// plan.cu -- plan creation (ring geometry, lambda recurrence tables, FFT
+// tables), workspace accounting, argument validation and the C ABI of
+// include/sht.h. Tables are built once on the host in long double and stay
+// resident on the device (the paper likewise separates this init overhead
+// from the transform time, Sec. 3.3).
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <map>
+
+#include "common.cuh"
+
+namespace sht {
+
+static thread_local std::string t_err;
+static thread_local int t_launches = 0;
+void set_error(const std::string& msg) { t_err = msg; }
+void count_launch(int n) { t_launches += n; }
+void reset_launches() { t_launches = 0; }
+
+typedef long double ld;
+static const ld PI_L = 3.141592653589793238462643383279502884L;
+static const double PI_D = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// HEALPix RING geometry of ring i (1-based): z, sin(theta), pixels, phi0
+// shift flag, first pixel. Caps take sin(theta) from the exact 1 -+ z.
+// ---------------------------------------------------------------------------
+struct RingH { ld z, s; int n; bool shifted; long long start; };
+
+static RingH ring_h(int nside, int i)
+{
+    RingH r;
+    long long npix = 12LL * nside * nside;
+    ld ns = nside;
+    if (i < nside) {
+        ld omz = (ld)i * i / (3 * ns * ns);
+        r.z = 1 - omz; r.s = sqrtl(omz * (2 - omz));
+        r.n = 4 * i; r.shifted = true; r.start = 2LL * i * (i - 1);
+    } else if (i <= 3 * nside) {
+        ld z = (ld)(4 * nside - 2 * i) / (3 * ns);
+        r.z = z; r.s = sqrtl((1 - z) * (1 + z));
+        r.n = 4 * nside; r.shifted = ((i - nside) % 2 == 0);
+        r.start = 2LL * nside * (nside - 1) + 4LL * nside * (i - nside);
+    } else {
+        int ip = 4 * nside - i;
+        ld opz = (ld)ip * ip / (3 * ns * ns);
+        r.z = opz - 1; r.s = sqrtl(opz * (2 - opz));
+        r.n = 4 * ip; r.shifted = true; r.start = npix - 2LL * ip * (ip + 1);
+    }
+    return r;
+}
+
+static int next_pow2(int v) { int p = 1; while (p < v) p <<= 1; return p; }
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// in-place iterative radix-2 FFT (host, double), forward sign e^{-2 pi i}
+static void host_fft(std::vector<double>& re, std::vector<double>& im)
+{
+    int n = (int)re.size();
+    for (int i = 1, j = 0; i < n; i++) {
+        int bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { std::swap(re[i], re[j]); std::swap(im[i], im[j]); }
+    }
+    for (int len = 2; len <= n; len <<= 1) {
+        int h = len / 2;
+        for (int k = 0; k < h; k++) {
+            ld a = -2 * PI_L * k / len;
+            double wr = (double)cosl(a), wi = (double)sinl(a);
+            for (int i = k; i < n; i += len) {
+                double xr = re[i + h] * wr - im[i + h] * wi;
+                double xi = re[i + h] * wi + im[i + h] * wr;
+                re[i + h] = re[i] - xr; im[i + h] = im[i] - xi;
+                re[i] += xr; im[i] += xi;
+            }
+        }
+    }
+}
+
+static int bitrev(int i, int logm)
+{
+    int r = 0;
+    for (int b = 0; b < logm; b++) if (i & (1 << b)) r |= 1 << (logm - 1 - b);
+    return r;
+}
+
+// scaled long-double value: mant * 2^exp
+struct Scaled { ld v; long e; };
+static Scaled snorm(ld v, long e)
+{
+    if (v == 0) return {0, 0};
+    int ex; ld f = frexpl(v, &ex);
+    return {f, e + ex};
+}
+static Scaled smul(Scaled a, ld b) { return snorm(a.v * b, a.e); }
+static Scaled spow(ld x, int n)   // x >= 0
+{
+    if (n == 0) return {0.5L, 1};
+    if (x == 0) return {0, 0};
+    int ex; ld f = frexpl(x, &ex);
+    return snorm(powl(f, (ld)n), (long)ex * n);
+}
+static Scaled sprod(Scaled a, Scaled b) { return snorm(a.v * b.v, a.e + b.e); }
+
+template <typename T>
+static cudaError_t upload(T** d, const std::vector<T>& h, size_t* acc)
+{
+    size_t b = h.size() * sizeof(T);
+    if (b == 0) { *d = nullptr; return cudaSuccess; }
+    cudaError_t e = cudaMalloc((void**)d, b);
+    if (e != cudaSuccess) return e;
+    *acc += b;
+    return cudaMemcpy(*d, h.data(), b, cudaMemcpyHostToDevice);
+}
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+static cudaError_t build_tables(sht_plan* p)
+{
+    const int nside = p->nside, lmax = p->lmax, mmax = p->mmax, R = p->R;
+    size_t acc = 0;
+    cudaError_t e;
+    // ---- rings and FFT lengths ----
+    std::map<int, int> len_index;
+    p->h_pairs.resize(R);
+    std::vector<ld> zs(R), ss(R);
+    for (int q = 0; q < R; q++) {
+        int i = q + 1;
+        RingH r = ring_h(nside, i);
+        RingH rs = ring_h(nside, 4 * nside - i);
+        PairGeom g;
+        g.x = (double)r.z; g.s = (double)r.s;
+        g.phi0 = r.shifted ? (double)(PI_L / r.n) : 0.0;
+        g.start_n = r.start;
+        g.start_s = (i == 2 * nside) ? -1 : rs.start;
+        g.n = r.n;
+        if (!len_index.count(r.n)) { int k = (int)len_index.size(); len_index[r.n] = k; }
+        g.fft = len_index[r.n];
+        p->h_pairs[q] = g;
+        zs[q] = r.z; ss[q] = r.s;
+    }
+    p->nfft = (int)len_index.size();
+    p->h_fft.resize(p->nfft);
+    std::vector<double2> chirp, bhat;
+    int fftmax = 2;
+    for (auto& kv : len_index) {
+        int N = kv.first;
+        FftLen f;
+        f.n = N;
+        f.bluestein = is_pow2(N) ? 0 : 1;
+        f.m = f.bluestein ? next_pow2(2 * N - 1) : N;
+        f.chirp = (long long)chirp.size();
+        f.bhat = (long long)bhat.size();
+        if (f.bluestein) {
+            std::vector<double2> w(N);
+            for (int n = 0; n < N; n++) {
+                long long n2 = ((long long)n * n) % (2LL * N);
+                ld a = -PI_L * (ld)n2 / N;
+                w[n] = make_double2((double)cosl(a), (double)sinl(a));
+                chirp.push_back(w[n]);
+            }
+            int M = f.m, logm = 0;
+            while ((1 << logm) < M) logm++;
+            std::vector<double> br(M, 0.0), bi(M, 0.0);
+            for (int j = 0; j < N; j++) {
+                br[j] = w[j].x; bi[j] = -w[j].y;
+                if (j > 0) { br[M - j] = w[j].x; bi[M - j] = -w[j].y; }
+            }
+            host_fft(br, bi);
+            std::vector<double2> b(M);
+            for (int i = 0; i < M; i++) { int s = bitrev(i, logm); b[i] = make_double2(br[s], bi[s]); }
+            bhat.insert(bhat.end(), b.begin(), b.end());
+        }
+        fftmax = std::max(fftmax, f.m);
+        p->h_fft[kv.second] = f;
+    }
+    p->fft_max = fftmax;
+    std::vector<double2> tw(fftmax / 2);
+    for (int t = 0; t < fftmax / 2; t++) {
+        ld a = -2 * PI_L * t / fftmax;
+        tw[t] = make_double2((double)cosl(a), (double)sinl(a));
+    }
+    if ((e = upload(&p->t.pairs, p->h_pairs, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->t.fft, p->h_fft, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->t.twiddle, tw, &acc)) != cudaSuccess) return e;
+    if (chirp.empty()) chirp.push_back(make_double2(1, 0));
+    if (bhat.empty()) bhat.push_back(make_double2(1, 0));
+    if ((e = upload(&p->t.chirp, chirp, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->t.bhat, bhat, &acc)) != cudaSuccess) return e;
+    {
+        std::vector<float2> twf(tw.size()), chf(chirp.size()), bhf(bhat.size());
+        for (size_t i = 0; i < tw.size(); i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+        for (size_t i = 0; i < chirp.size(); i++) chf[i] = make_float2((float)chirp[i].x, (float)chirp[i].y);
+        for (size_t i = 0; i < bhat.size(); i++) bhf[i] = make_float2((float)bhat[i].x, (float)bhat[i].y);
+        if ((e = upload(&p->t.twiddle_f, twf, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->t.chirp_f, chf, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->t.bhat_f, bhf, &acc)) != cudaSuccess) return e;
+    }
+
+    // ---- lambda seeds ----
+    std::vector<double> smant((size_t)(mmax + 1) * 2 * R);
+    std::vector<int> sexp((size_t)(mmax + 1) * 2 * R);
+    if (p->spin == 0) {
+        // lambda_mm = (-1)^m sqrt((2m+1)/4pi prod_{k<=m} (2k-1)/(2k)) sin^m,
+        // lambda_{m+1,m} = sqrt(2m+3) cos lambda_mm  (Condon-Shortley phase)
+        for (int q = 0; q < R; q++) {
+            Scaled v = snorm(1.0L / sqrtl(4 * PI_L), 0);
+            for (int m = 0; m <= mmax; m++) {
+                if (m > 0) v = smul(v, sqrtl((ld)(2 * m - 1) / (2 * m)) * ss[q]);
+                Scaled lmm = smul(v, sqrtl((ld)(2 * m + 1)) * ((m & 1) ? -1 : 1));
+                Scaled lm1 = smul(lmm, sqrtl((ld)(2 * m + 3)) * zs[q]);
+                size_t i0 = ((size_t)m * 2 + 0) * R + q, i1 = ((size_t)m * 2 + 1) * R + q;
+                smant[i0] = (double)lmm.v; sexp[i0] = (int)lmm.e;
+                smant[i1] = (double)lm1.v; sexp[i1] = (int)lm1.e;
+            }
+        }
+    } else {
+        // s lambda at l0 = max(m,2): (-1)^m sqrt((2 l0+1)/4pi) d^{l0}_{-m,s}(theta)
+        //   m >= 2: d^m_{-m,s}  = sqrt(C(2m, m-s)) cos^{m-s}(t/2) sin^{m+s}(t/2)
+        //   m <  2: d^2_{-m,2}  = sqrt(C(4, 2-m)) cos^{2-m}(t/2) sin^{2+m}(t/2)
+        //           d^2_{-m,-2} = (-1)^{2-m} sqrt(C(4, 2+m)) cos^{2+m}(t/2) sin^{2-m}(t/2)
+        for (int m = 0; m <= mmax; m++) {
+            int l0 = m > 2 ? m : 2;
+            for (int si = 0; si < 2; si++) {
+                int s = si == 0 ? 2 : -2;
+                int kbin, pc, ps; ld sign = 1;
+                if (m >= 2) { kbin = m - s; pc = m - s; ps = m + s; }
+                else if (s == 2) { kbin = 2 - m; pc = 2 - m; ps = 2 + m; }
+                else { kbin = 2 + m; pc = 2 + m; ps = 2 - m; sign = ((2 - m) & 1) ? -1 : 1; }
+                int kk = std::min(kbin, 2 * l0 - kbin);
+                Scaled c = {0.5L, 1};
+                for (int i = 1; i <= kk; i++) c = smul(c, (ld)(2 * l0 - kk + i) / i);
+                if (c.e & 1) { c.v *= 2; c.e -= 1; }
+                c.v = sqrtl(c.v); c.e /= 2;
+                ld pre = sign * ((m & 1) ? -1 : 1) * sqrtl((2 * l0 + 1) / (4 * PI_L));
+                c = smul(c, pre);
+                for (int q = 0; q < R; q++) {
+                    ld ch = sqrtl((1 + zs[q]) / 2), sh = sqrtl((1 - zs[q]) / 2);
+                    if (zs[q] > 0.5L) sh = sqrtl((ss[q] * ss[q]) / (2 * (1 + zs[q])));
+                    Scaled v = sprod(c, sprod(spow(ch, pc), spow(sh, ps)));
+                    size_t i0 = ((size_t)m * 2 + si) * R + q;
+                    smant[i0] = (double)v.v; sexp[i0] = (int)v.e;
+                }
+            }
+        }
+    }
+    if ((e = upload(&p->t.seed_mant, smant, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->t.seed_exp, sexp, &acc)) != cudaSuccess) return e;
+
+    // ---- recurrence coefficients ----
+    const long long nalm = p->nalm;
+    if (p->spin == 0) {
+        // a_l = sqrt((4l^2-1)/(l^2-m^2)), 1/a_m := 0; two-step same-parity form
+        //   lambda_{l+2} = (alpha_l x^2 + beta_l) lambda_l + gamma_l lambda_{l-2}
+        //   alpha_l = a_{l+2} a_{l+1}
+        //   beta_l  = -a_{l+2} (a_{l+1} / a_l^2 + 1 / a_{l+1})
+        //   gamma_l = -a_{l+2} a_{l+1} / (a_l a_{l-1})
+        std::vector<double> ra(nalm, 0.0), rb(nalm, 0.0), rc(nalm, 0.0);
+        for (int m = 0; m <= mmax; m++) {
+            auto ainv = [&](int l) -> ld {
+                if (l <= m) return 0;
+                ld L = l, M = m;
+                return sqrtl((L * L - M * M) / (4 * L * L - 1));
+            };
+            auto aa = [&](int l) -> ld {
+                ld L = l, M = m;
+                return sqrtl((4 * L * L - 1) / (L * L - M * M));
+            };
+            for (int l = m; l <= lmax; l++) {
+                long long ci = alm_index(lmax, l, m);
+                ld a1 = aa(l + 1), a2 = aa(l + 2);
+                ld ia0 = ainv(l), iam = ainv(l - 1);
+                ra[ci] = (double)(a2 * a1);
+                rb[ci] = (double)(-a2 * (a1 * ia0 * ia0 + 1 / a1));
+                rc[ci] = (double)(-a2 * a1 * ia0 * iam);
+            }
+        }
+        if ((e = upload(&p->t.rec_a, ra, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->t.rec_b, rb, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->t.rec_c, rc, &acc)) != cudaSuccess) return e;
+    } else {
+        // s lambda_l = (A_l x + A_l B_l) s lambda_{l-1} - C_l s lambda_{l-2}
+        //   A_l = l sqrt((2l+1)(2l-1)) / sqrt((l^2-m^2)(l^2-s^2)),  B_l = m s / (l(l-1))
+        //   C_l = (l/(l-1)) sqrt((2l+1)/(2l-3)) sqrt(((l-1)^2-m^2)((l-1)^2-s^2) / ((l^2-m^2)(l^2-s^2)))
+        for (int si = 0; si < 2; si++) {
+            ld s = si == 0 ? 2 : -2;
+            std::vector<double> A(nalm, 0.0), AB(nalm, 0.0), C(nalm, 0.0);
+            for (int m = 0; m <= mmax; m++) {
+                int l0 = m > 2 ? m : 2;
+                for (int l = l0 + 1; l <= lmax; l++) {
+                    long long ci = alm_index(lmax, l, m);
+                    ld L = l, M = m;
+                    ld den = (L * L - M * M) * (L * L - s * s);
+                    ld Al = L * sqrtl((2 * L + 1) * (2 * L - 1)) / sqrtl(den);
+                    ld Bl = M * s / (L * (L - 1));
+                    ld num = ((L - 1) * (L - 1) - M * M) * ((L - 1) * (L - 1) - s * s);
+                    ld Cl = (L / (L - 1)) * sqrtl((2 * L + 1) / (2 * L - 3)) * sqrtl(num / den);
+                    A[ci] = (double)Al; AB[ci] = (double)(Al * Bl); C[ci] = (double)Cl;
+                }
+            }
+            if ((e = upload(&p->t.w_A[si], A, &acc)) != cudaSuccess) return e;
+            if ((e = upload(&p->t.w_AB[si], AB, &acc)) != cudaSuccess) return e;
+            if ((e = upload(&p->t.w_C[si], C, &acc)) != cudaSuccess) return e;
+        }
+    }
+
+    // ---- FP64 Legendre work lists ----
+    {
+        int TL = legendre_f64_row_tile(), TP = legendre_f64_pair_tile();
+        std::vector<int4> w1, w2;
+        for (int m = 0; m <= mmax; m++)
+            for (int q = 0; q < 2; q++) {
+                int lf = m + q;
+                int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
+                for (int t = 0; t * TL < nrows; t++) w1.push_back(make_int4(m, q, t, 0));
+                for (int t = 0; t * TP < R; t++) w2.push_back(make_int4(m, q, t, 0));
+            }
+        p->nwork_m2a = (int)w1.size();
+        p->nwork_a2m = (int)w2.size();
+        if ((e = upload(&p->work_m2a, w1, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->work_a2m, w2, &acc)) != cudaSuccess) return e;
+    }
+    p->table_bytes = acc;
+    return cudaSuccess;
+}
+
+static void free_tables(sht_plan* p)
+{
+    void* ptrs[] = {p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp, p->t.bhat, p->t.twiddle_f,
+                    p->t.chirp_f, p->t.bhat_f, p->t.seed_mant, p->t.seed_exp, p->t.rec_a, p->t.rec_b,
+                    p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
+                    p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
+    for (void* q : ptrs) if (q) cudaFree(q);
+    if (p->pin_in) cudaFreeHost(p->pin_in);
+    if (p->pin_out) cudaFreeHost(p->pin_out);
+}
+
+size_t tbuf_bytes(const sht_plan* p, int nmaps)
+{
+    size_t el = p->precision == SHT_FP64 ? sizeof(double) : sizeof(float);
+    return (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * el;
+}
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// workspace layout: [T/G buffer][residual map][delta alm] (the last two only
+// for map2alm with niter > 0)
+static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
+{
+    size_t b = round_up(tbuf_bytes(p, nmaps), 256);
+    if (niter > 0) {
+        b += round_up((size_t)nmaps * p->ncomp * (size_t)p->npix * sizeof(double), 256);
+        b += round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
+    }
+    return b;
+}
+
+// elementwise helpers for the iteration (Algorithm 2)
+__global__ void k_sub(double* __restrict__ r, const double* __restrict__ a, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long st = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += st) r[i] = a[i] - r[i];
+}
+__global__ void k_add(double* __restrict__ a, const double* __restrict__ d, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long st = (long long)gridDim.x * blockDim.x;
+    for (; i < n; i += st) a[i] += d[i];
+}
+static int ew_grid(long long n) { long long b = (n + 255) / 256; return (int)std::min<long long>(b, 148 * 16); }
+
+}  // namespace sht
+
+using namespace sht;
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sht_last_error(void) { return t_err.c_str(); }
+int sht_last_launch_count(void) { return t_launches; }
+const char* sht_version(void) { return "libsht 0.1 (sm_103a)"; }
+
+sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precision, int device,
+                           sht_plan** out)
+{
+    t_err.clear();
+    if (!out) { set_error("out is NULL"); return SHT_EINVAL; }
+    *out = nullptr;
+    if (mmax < 0) mmax = lmax;
+    if (nside < 1 || nside > 8192) { set_error("nside must be in [1, 8192]"); return SHT_EINVAL; }
+    if (lmax < 0 || lmax > 4 * 8192) { set_error("lmax out of range"); return SHT_EINVAL; }
+    if (mmax > lmax) { set_error("mmax must be <= lmax"); return SHT_EINVAL; }
+    if (spin != 0 && spin != 2) { set_error("spin must be 0 or 2"); return SHT_EINVAL; }
+    if (precision != SHT_FP64 && precision != SHT_SPLIT_BF16) { set_error("unknown precision"); return SHT_EINVAL; }
+    if (precision == SHT_SPLIT_BF16) {
+        set_error("SHT_SPLIT_BF16 is not available in this build");
+        return SHT_EUNSUPPORTED;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        set_error("no such CUDA device");
+        return SHT_EINVAL;
+    }
+    SHT_CUDA_TRY(cudaSetDevice(device));
+    sht_plan* p = new sht_plan();
+    p->nside = nside; p->lmax = lmax; p->mmax = mmax; p->spin = spin;
+    p->precision = precision; p->device = device;
+    p->ncomp = spin ? 2 : 1;
+    p->npix = 12LL * nside * nside;
+    p->nalm = (long long)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
+    p->R = 2 * nside;
+    cudaError_t e = build_tables(p);
+    if (e != cudaSuccess) {
+        set_error(std::string("plan tables: ") + cudaGetErrorString(e));
+        free_tables(p);
+        delete p;
+        return e == cudaErrorMemoryAllocation ? SHT_ENOMEM : SHT_ECUDA;
+    }
+    *out = p;
+    return SHT_OK;
+}
+
+void sht_plan_destroy(sht_plan* p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    free_tables(p);
+    delete p;
+}
+
+size_t sht_workspace_bytes(const sht_plan* p, int nmaps)
+{
+    if (!p || nmaps < 1) return 0;
+    return ws_bytes(p, nmaps, 0);
+}
+
+size_t sht_workspace_bytes_iter(const sht_plan* p, int nmaps, int niter)
+{
+    if (!p || nmaps < 1) return 0;
+    return ws_bytes(p, nmaps, niter);
+}
+
+int sht_plan_nside(const sht_plan* p) { return p ? p->nside : 0; }
+int sht_plan_lmax(const sht_plan* p) { return p ? p->lmax : 0; }
+int sht_plan_mmax(const sht_plan* p) { return p ? p->mmax : 0; }
+int sht_plan_spin(const sht_plan* p) { return p ? p->spin : 0; }
+int sht_plan_precision(const sht_plan* p) { return p ? p->precision : 0; }
+long long sht_plan_npix(const sht_plan* p) { return p ? p->npix : 0; }
+long long sht_plan_nalm(const sht_plan* p) { return p ? p->nalm : 0; }
+
+static sht_status check_call(const sht_plan* p, const void* in, const void* out, int nmaps,
+                             void* ws, size_t wsb, int niter)
+{
+    t_err.clear();
+    reset_launches();
+    if (!p) { set_error("plan is NULL"); return SHT_EINVAL; }
+    if (nmaps < 1) { set_error("nmaps must be >= 1"); return SHT_EINVAL; }
+    if (!in || !out) { set_error("data pointer is NULL"); return SHT_EINVAL; }
+    if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) { set_error("data pointers must be 16-byte aligned"); return SHT_EINVAL; }
+    if (niter < 0) { set_error("niter must be >= 0"); return SHT_EINVAL; }
+    size_t need = ws_bytes(p, nmaps, niter);
+    if (!ws || wsb < need) {
+        set_error("workspace too small: need " + std::to_string(need) + " bytes");
+        return SHT_EINVAL;
+    }
+    if ((uintptr_t)ws & 255) { set_error("workspace must be 256-byte aligned"); return SHT_EINVAL; }
+    return SHT_OK;
+}
+
+static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nmaps, void* ws,
+                             double s0, double s1, cudaStream_t st)
+{
+    double* G = (double*)ws;
+    cudaError_t e = launch_legendre_a2m_f64(p, alm, G, nmaps, s0, s1, st);
+    if (e == cudaSuccess) e = launch_fft_backward_f64(p, G, map, nmaps, st);
+    if (e != cudaSuccess) { set_error(std::string("alm2map launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    return SHT_OK;
+}
+
+static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nmaps, void* ws,
+                             double s0, double s1, cudaStream_t st)
+{
+    double* T = (double*)ws;
+    cudaError_t e = launch_fft_forward_f64(p, map, T, nmaps, st);
+    if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, T, alm, nmaps, s0, s1, st);
+    if (e != cudaSuccess) { set_error(std::string("map2alm launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    return SHT_OK;
+}
+
+sht_status sht_alm2map(sht_plan* p, const void* alm, void* map, int nmaps, void* ws, size_t wsb,
+                       void* stream)
+{
+    sht_status s = check_call(p, alm, map, nmaps, ws, wsb, 0);
+    if (s != SHT_OK) return s;
+    cudaSetDevice(p->device);
+    return do_alm2map(p, (const double*)alm, (double*)map, nmaps, ws, 1.0, 1.0, (cudaStream_t)stream);
+}
+
+sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int niter, void* ws,
+                       size_t wsb, void* stream)
+{
+    sht_status s = check_call(p, map, alm, nmaps, ws, wsb, niter);
+    if (s != SHT_OK) return s;
+    cudaSetDevice(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double dsig = 4.0 * PI_D / (double)p->npix;
+    s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
+    if (s != SHT_OK || niter == 0) return s;
+    // Algorithm 2: a += map2alm(T - alm2map(a)), niter times
+    size_t off = round_up(tbuf_bytes(p, nmaps), 256);
+    double* res = (double*)((char*)ws + off);
+    long long nm = (long long)nmaps * p->ncomp * p->npix;
+    off += round_up((size_t)nm * sizeof(double), 256);
+    double* da = (double*)((char*)ws + off);
+    long long na = (long long)nmaps * p->ncomp * p->nalm * 2;
+    for (int it = 0; it < niter; it++) {
+        s = do_alm2map(p, (const double*)alm, res, nmaps, ws, 1.0, 1.0, st);
+        if (s != SHT_OK) return s;
+        k_sub<<<ew_grid(nm), 256, 0, st>>>(res, (const double*)map, nm);
+        count_launch();
+        s = do_map2alm(p, res, da, nmaps, ws, dsig, dsig, st);
+        if (s != SHT_OK) return s;
+        k_add<<<ew_grid(na), 256, 0, st>>>((double*)alm, da, na);
+        count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return SHT_ECUDA; }
+    }
+    return SHT_OK;
+}
+
+sht_status sht_alm2map_adjoint(sht_plan* p, const void* map, void* alm, int nmaps, void* ws,
+                               size_t wsb, void* stream)
+{
+    // (Npix/4pi) map2alm(h) * w_m: the dsigma of map2alm cancels
+    sht_status s = check_call(p, map, alm, nmaps, ws, wsb, 0);
+    if (s != SHT_OK) return s;
+    cudaSetDevice(p->device);
+    return do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, 1.0, 2.0, (cudaStream_t)stream);
+}
+
+sht_status sht_map2alm_adjoint(sht_plan* p, const void* alm, void* map, int nmaps, void* ws,
+                               size_t wsb, void* stream)
+{
+    // (4pi/Npix) alm2map(g'), g'_l0 = Re g_l0, g'_lm = g_lm / 2
+    sht_status s = check_call(p, alm, map, nmaps, ws, wsb, 0);
+    if (s != SHT_OK) return s;
+    cudaSetDevice(p->device);
+    const double dsig = 4.0 * PI_D / (double)p->npix;
+    return do_alm2map(p, (const double*)alm, (double*)map, nmaps, ws, dsig, 0.5 * dsig,
+                      (cudaStream_t)stream);
+}
+
+// ---- host-buffer entry points: chunked through pinned staging ----
+static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, int nmaps, int niter,
+                            bool to_map, cudaStream_t st)
+{
+    t_err.clear();
+    if (!p || !in_host || !out_host || nmaps < 1 || niter < 0) { set_error("bad argument"); return SHT_EINVAL; }
+    cudaSetDevice(p->device);
+    const size_t map_b = (size_t)p->ncomp * p->npix * sizeof(double);
+    const size_t alm_b = (size_t)p->ncomp * p->nalm * 2 * sizeof(double);
+    const size_t in_b = to_map ? alm_b : map_b, out_b = to_map ? map_b : alm_b;
+    int chunk = nmaps;
+    const size_t cap = (size_t)8 << 30;
+    while (chunk > 1 && (size_t)chunk * (in_b + out_b) + ws_bytes(p, chunk, niter) > cap) chunk = (chunk + 1) / 2;
+    size_t need_in = (size_t)chunk * in_b, need_out = (size_t)chunk * out_b;
+    size_t need_ws = ws_bytes(p, chunk, niter);
+    auto grow_dev = [&](void** ptr, size_t* have, size_t need) -> cudaError_t {
+        if (*have >= need) return cudaSuccess;
+        if (*ptr) cudaFree(*ptr);
+        *ptr = nullptr; *have = 0;
+        cudaError_t e = cudaMalloc(ptr, need);
+        if (e == cudaSuccess) *have = need;
+        return e;
+    };
+    auto grow_pin = [&](void** ptr, size_t* have, size_t need) -> cudaError_t {
+        if (*have >= need) return cudaSuccess;
+        if (*ptr) cudaFreeHost(*ptr);
+        *ptr = nullptr; *have = 0;
+        cudaError_t e = cudaMallocHost(ptr, need);
+        if (e == cudaSuccess) *have = need;
+        return e;
+    };
+    SHT_CUDA_TRY(grow_dev(&p->host_dev_in, &p->host_dev_in_bytes, need_in));
+    SHT_CUDA_TRY(grow_dev(&p->host_dev_out, &p->host_dev_out_bytes, need_out));
+    SHT_CUDA_TRY(grow_dev(&p->host_ws, &p->host_ws_bytes, need_ws));
+    SHT_CUDA_TRY(grow_pin(&p->pin_in, &p->pin_in_bytes, need_in));
+    SHT_CUDA_TRY(grow_pin(&p->pin_out, &p->pin_out_bytes, need_out));
+    int launches = 0;
+    for (int b0 = 0; b0 < nmaps; b0 += chunk) {
+        int nb = std::min(chunk, nmaps - b0);
+        memcpy(p->pin_in, (const char*)in_host + (size_t)b0 * in_b, (size_t)nb * in_b);
+        SHT_CUDA_TRY(cudaMemcpyAsync(p->host_dev_in, p->pin_in, (size_t)nb * in_b, cudaMemcpyHostToDevice, st));
+        sht_status s = to_map
+            ? sht_alm2map(p, p->host_dev_in, p->host_dev_out, nb, p->host_ws, p->host_ws_bytes, st)
+            : sht_map2alm(p, p->host_dev_in, p->host_dev_out, nb, niter, p->host_ws, p->host_ws_bytes, st);
+        if (s != SHT_OK) return s;
+        launches += t_launches;
+        SHT_CUDA_TRY(cudaMemcpyAsync(p->pin_out, p->host_dev_out, (size_t)nb * out_b, cudaMemcpyDeviceToHost, st));
+        SHT_CUDA_TRY(cudaStreamSynchronize(st));
+        memcpy((char*)out_host + (size_t)b0 * out_b, p->pin_out, (size_t)nb * out_b);
+    }
+    t_launches = launches;
+    return SHT_OK;
+}
+
+sht_status sht_alm2map_host(sht_plan* p, const void* alm_host, void* map_host, int nmaps, void* stream)
+{
+    return host_call(p, alm_host, map_host, nmaps, 0, true, (cudaStream_t)stream);
+}
+
+sht_status sht_map2alm_host(sht_plan* p, const void* map_host, void* alm_host, int nmaps, int niter,
+                            void* stream)
+{
+    return host_call(p, map_host, alm_host, nmaps, niter, false, (cudaStream_t)stream);
+}
+
+}  // extern "C"
