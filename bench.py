@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Benchmark: batched HEALPix spherical harmonic transforms on B300.
+
+One step = alm2map + map2alm (spin 0) of one batch of maps at nside 512,
+lmax 1023, 1000 maps per GPU (the paper's batched-SHT scheme, Sec. 2.1-2.2),
+on synthetic Gaussian skies with C_l = 1/(l(l+1)) plus 1% white noise.
+Prints ONE JSON line (rank 0). With N > 1 (torchrun), every rank transforms
+its own batch (maps are independent columns: weak scaling, no collective on
+the data path); the timed region is bracketed by barriers and the slowest
+rank's time is used.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision auto|fp64|split]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "maps/s batched vs per-map on one B300 at <=1e-6 rel err; served p50/p99 latency"
+WORKLOAD = "t_nside512"
+FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (recipe table); probe measured 1.13 at 2032 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "split"])
+    ap.add_argument("--nside", type=int, default=512)
+    ap.add_argument("--lmax", type=int, default=None)
+    ap.add_argument("--nmaps", type=int, default=1000)
+    ap.add_argument("--per-map-samples", type=int, default=4)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.lmax is None:
+        a.lmax = 2 * a.nside - 1
+    return a
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def algorithmic_flops(nside, lmax, nmaps, spin=0):
+    """Legendre contraction flops per transform (4 per (l, m, ring pair) per map
+    for spin 0; x4 for a spin-2 Q/U pair)."""
+    R = 2 * nside
+    nalm = (lmax + 1) * (lmax + 2) // 2
+    return 4.0 * R * nalm * nmaps * (4 if spin else 1)
+
+
+# ----------------------------------------------------------------------------
+def run_reference(a):
+    """The CPU oracle (plain FP64, separable tier) on a bounded sample: one map
+    per step at the benchmark's nside/lmax (the oracle is timed as it stands)."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_2208_10154_b300 import inputs
+    oracle.build()
+    nside, lmax = a.nside, a.lmax
+    alm = inputs.gaussian_alm(1, 1, 1, lmax, cls=inputs.cl_inv_llp1(lmax))
+    maps = oracle.alm2map(alm, nside, lmax)
+    def step():
+        oracle.alm2map(alm, nside, lmax)
+        oracle.map2alm(maps, nside, lmax)
+    for _ in range(min(a.warmup, 1)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = a.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * dt / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": ref_config(a),
+        "cpu_baseline": {"value": value, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"1 map per step (alm2map + map2alm, nside {nside}, lmax {lmax})"},
+        "e2e": {"value": value, "unit": "maps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ref_config(a):
+    return {"workload": f"{WORKLOAD}: spin-0 alm2map + map2alm, nside {a.nside}, lmax {a.lmax}, "
+                        f"{a.nmaps} maps per GPU, C_l = 1/(l(l+1)) + 1% white noise",
+            "nside": a.nside, "lmax": a.lmax, "nmaps": a.nmaps, "spin": 0}
+
+
+# ----------------------------------------------------------------------------
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2208_10154_b300 import build, sht
+    rank, world, local = dist_info()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    sht.load()
+    nside, lmax, nmaps = a.nside, a.lmax, a.nmaps
+    precision = a.precision
+    if precision == "auto":
+        try:
+            p = sht.Plan(4, 7, None, 0, "split")
+            p.close()
+            precision = "split"
+        except sht.ShtError:
+            precision = "fp64"
+
+    # ---- inputs: Gaussian a_lm (seed 1 + rank), maps = alm2map(a) + 1% noise ----
+    t0 = time.perf_counter()
+    plan64 = sht.Plan(nside, lmax, None, 0, "fp64")
+    plan = plan64 if precision == "fp64" else sht.Plan(nside, lmax, None, 0, precision)
+    plan_s = time.perf_counter() - t0
+    from paper_2208_10154_b300 import inputs
+    ls, ms = inputs.lm_arrays(lmax)
+    cl = inputs.cl_inv_llp1(lmax)[ls]
+    sd = torch.from_numpy(np.where(ms == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1 + rank)
+    re = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
+    im = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
+    im[..., torch.from_numpy(ms == 0).cuda()] = 0.0
+    alm = torch.complex(re, im).contiguous()
+    del re, im
+    maps_in = plan64.alm2map(alm)
+    rms = maps_in.square().mean(dim=-1, keepdim=True).sqrt()
+    maps_in += 0.01 * rms * torch.randn(maps_in.shape, generator=g, dtype=torch.float64, device="cuda")
+    plan64._ws = None
+    maps_out = torch.empty_like(maps_in)
+    alm_out = torch.empty_like(alm)
+    wsb = max(plan.workspace_bytes(nmaps), 1)
+    ws = torch.empty(wsb + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    torch.cuda.synchronize()
+
+    launches = [0]
+
+    def step():
+        plan.alm2map(alm, out=maps_out, workspace=ws)
+        launches[0] += sht.sht_last_launch_count()
+        plan.map2alm(maps_in, out=alm_out, workspace=ws)
+        launches[0] += sht.sht_last_launch_count()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches[0] = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sht.sht_profile_begin()
+    with ClockSampler(dev) as clk:
+        e0.record()
+        for _ in range(a.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+    prof = sht.sht_profile_end()
+    if world > 1:
+        dist.barrier()
+    ms_step = e0.elapsed_time(e1) / a.steps
+    t_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step = float(t_max.item())
+    value = world * nmaps / (ms_step / 1e3)
+    gpu_launches = launches[0]
+
+    # ---- per-map FP64 form (the paper's "one map at a time" baseline) ----
+    per_map = None
+    if a.per_map_samples > 0:
+        plan1 = plan64
+        P = min(a.per_map_samples, nmaps)
+        for i in range(1):
+            plan1.alm2map(alm[i:i + 1].contiguous())
+            plan1.map2alm(maps_in[i:i + 1].contiguous())
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        views = [(alm[i:i + 1].contiguous(), maps_in[i:i + 1].contiguous()) for i in range(P)]
+        s0.record()
+        for av, mv in views:
+            plan1.alm2map(av)
+            plan1.map2alm(mv)
+        s1.record()
+        torch.cuda.synchronize()
+        per_map = {"value": P / (s0.elapsed_time(s1) / 1e3), "unit": "maps/s", "form": "fp64, nmaps=1",
+                   "samples": P}
+        plan1._ws = None
+
+    # ---- roofline of the dominant kernel ----
+    peaks, peak_src = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roofline = None
+    if dom:
+        name, rec = dom
+        avg_ms = rec["ms"] / max(rec["launches"], 1)
+        flops = algorithmic_flops(nside, lmax, nmaps)
+        if "leg" in name and "f64" in name:
+            ach = flops / (avg_ms / 1e3) / 1e12
+            roofline = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                        "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)",
+                        "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
+        elif "leg" in name:
+            ach = flops / (avg_ms / 1e3) / 1e12
+            pk = peaks.get("bf16_tflops_sustained", 1400.0)
+            roofline = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                        "frac": ach / pk, "traffic": None, "peak_source": f"bf16 sustained, {peak_src}",
+                        "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
+        else:
+            byts = 8.0 * nmaps * plan.npix * 2
+            ach = byts / (avg_ms / 1e3) / 1e9
+            roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                        "peak_source": peak_src, "avg_launch_ms": avg_ms}
+
+    # ---- end to end through the host-buffer C-ABI entry points ----
+    e2e = None
+    if not a.no_e2e:
+        alm_h = torch.empty(alm.shape, dtype=torch.complex128, pin_memory=True)
+        alm_h.copy_(alm)
+        maps_h = torch.empty(maps_in.shape, dtype=torch.float64, pin_memory=True)
+        maps_h.copy_(maps_in)
+        mo_h = torch.empty(maps_in.shape, dtype=torch.float64, pin_memory=True)
+        ao_h = torch.empty(alm.shape, dtype=torch.complex128, pin_memory=True)
+        del maps_out, alm_out, ws
+        torch.cuda.empty_cache()
+        plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
+        plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ke = max(1, min(a.steps, 2))
+        for _ in range(ke):
+            plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
+            plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
+        dt = (time.perf_counter() - t0) / ke
+        td = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(td, op=dist.ReduceOp.MAX)
+        dt = float(td.item())
+        nb_alm = alm_h.numel() * 16
+        nb_map = maps_h.numel() * 8
+        e2e = {"value": world * nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
+               "d2h_bytes_per_step": nb_map + nb_alm, "api": "sht_alm2map_host + sht_map2alm_host"}
+
+    # ---- CPU baseline: the oracle on one map ----
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        a1 = alm[:1].cpu().numpy()
+        m1 = maps_in[:1].cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.alm2map(a1, nside, lmax)
+        oracle.map2alm(m1, nside, lmax)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"1 map (alm2map + map2alm, nside {nside}, lmax {lmax}), separable tier"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16+f64",
+            "data": "synthetic",
+            "config": dict(ref_config(a), precision=precision, direction="alm2map+map2alm per step",
+                           l2="inputs larger than L2 (maps 25.2 GB per GPU), no flush",
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
+            "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
+            "kernels": prof, "plan_create_s": plan_s,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

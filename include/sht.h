@@ -136,6 +136,15 @@ sht_status sht_map2alm_host(sht_plan* plan, const void* map_host, void* alm_host
  * (for the benchmark's launch accounting). */
 int sht_last_launch_count(void);
 
+/* Per-kernel timing for benchmarks (no counterpart in the paper). After
+ * sht_profile_begin(), every kernel this thread launches is bracketed by
+ * CUDA events recorded on its launching stream. sht_profile_end() waits for
+ * those events, writes {"kernel": {"launches": n, "ms": t}, ...} as a
+ * NUL-terminated JSON string into buf (up to cap bytes), stops recording and
+ * returns the length the full string needs including the NUL. */
+void sht_profile_begin(void);
+int  sht_profile_end(char* buf, int cap);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* sht_last_error(void);
 

@@ -103,6 +103,10 @@ namespace sht {
 void set_error(const std::string& msg);
 void count_launch(int n = 1);
 void reset_launches();
+// optional per-kernel timing (sht_profile_begin / sht_profile_end): CUDA events
+// recorded on the launching stream around each launch
+void prof_start(const char* name, cudaStream_t st);
+void prof_stop(cudaStream_t st);
 
 inline long long alm_index(int lmax, int l, int m)
 {

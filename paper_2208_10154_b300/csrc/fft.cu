@@ -242,9 +242,11 @@ cudaError_t launch_fft_forward_f64(const sht_plan* p, const double* map, double*
     cudaError_t e = cudaFuncSetAttribute(k_fft_forward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid(p->R, nmaps * p->ncomp);
+    prof_start("k_fft_forward_f64", st);
     k_fft_forward<double><<<grid, 256, sm, st>>>(map, T, p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp,
                                                   p->t.bhat, p->fft_max, p->R, p->mmax, p->npix,
                                                   ncols(p, nmaps));
+    prof_stop(st);
     count_launch();
     return cudaGetLastError();
 }
@@ -256,9 +258,11 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
     cudaError_t e = cudaFuncSetAttribute(k_fft_backward<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     dim3 grid(p->R, nmaps * p->ncomp);
+    prof_start("k_fft_backward_f64", st);
     k_fft_backward<double><<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp,
                                                    p->t.bhat, p->fft_max, p->R, p->mmax, p->npix,
                                                    ncols(p, nmaps));
+    prof_stop(st);
     count_launch();
     return cudaGetLastError();
 }

@@ -381,7 +381,9 @@ cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* 
     if (e != cudaSuccess) return e;
     long long nc = ncols(p, nmaps);
     dim3 grid((unsigned)nwork, (unsigned)((nc + M2A_TN - 1) / M2A_TN));
+    prof_start("k_leg_m2a_f64", st);
     k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, make_args(p, nmaps, scale0, scale, work));
+    prof_stop(st);
     count_launch();
     return cudaGetLastError();
 }
@@ -397,7 +399,9 @@ cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double
     if (e != cudaSuccess) return e;
     long long nc = ncols(p, nmaps);
     dim3 grid((unsigned)nwork, (unsigned)((nc + A2M_TN - 1) / A2M_TN));
+    prof_start("k_leg_a2m_f64", st);
     k_leg_a2m_f64<<<grid, 256, sm, st>>>(alm, G, make_args(p, nmaps, scale0, scale, work));
+    prof_stop(st);
     count_launch();
     return cudaGetLastError();
 }

@@ -18,6 +18,24 @@ void set_error(const std::string& msg) { t_err = msg; }
 void count_launch(int n) { t_launches += n; }
 void reset_launches() { t_launches = 0; }
 
+struct ProfRec { std::string name; cudaEvent_t a, b; };
+static thread_local bool t_prof = false;
+static thread_local std::vector<ProfRec> t_recs;
+void prof_start(const char* name, cudaStream_t st)
+{
+    if (!t_prof) return;
+    ProfRec r; r.name = name;
+    if (cudaEventCreate(&r.a) != cudaSuccess) return;
+    if (cudaEventCreate(&r.b) != cudaSuccess) { cudaEventDestroy(r.a); return; }
+    cudaEventRecord(r.a, st);
+    t_recs.push_back(r);
+}
+void prof_stop(cudaStream_t st)
+{
+    if (!t_prof || t_recs.empty()) return;
+    cudaEventRecord(t_recs.back().b, st);
+}
+
 typedef long double ld;
 static const ld PI_L = 3.141592653589793238462643383279502884L;
 static const double PI_D = 3.14159265358979323846;
@@ -386,6 +404,47 @@ const char* sht_last_error(void) { return t_err.c_str(); }
 int sht_last_launch_count(void) { return t_launches; }
 const char* sht_version(void) { return "libsht 0.1 (sm_103a)"; }
 
+void sht_profile_begin(void)
+{
+    for (auto& r : t_recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    t_recs.clear();
+    t_prof = true;
+}
+
+int sht_profile_end(char* buf, int cap)
+{
+    t_prof = false;
+    std::map<std::string, std::pair<int, double>> agg;
+    for (auto& r : t_recs) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            auto& v = agg[r.name];
+            v.first += 1;
+            v.second += ms;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    t_recs.clear();
+    std::string js = "{";
+    bool first = true;
+    for (auto& kv : agg) {
+        char tmp[256];
+        snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"launches\": %d, \"ms\": %.6f}", first ? "" : ", ",
+                 kv.first.c_str(), kv.second.first, kv.second.second);
+        js += tmp;
+        first = false;
+    }
+    js += "}";
+    if (buf && cap > 0) {
+        int n = (int)std::min<size_t>(js.size(), (size_t)cap - 1);
+        memcpy(buf, js.data(), n);
+        buf[n] = 0;
+    }
+    return (int)js.size() + 1;
+}
+
 sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precision, int device,
                            sht_plan** out)
 {
@@ -522,11 +581,15 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     for (int it = 0; it < niter; it++) {
         s = do_alm2map(p, (const double*)alm, res, nmaps, ws, 1.0, 1.0, st);
         if (s != SHT_OK) return s;
+        prof_start("k_sub", st);
         k_sub<<<ew_grid(nm), 256, 0, st>>>(res, (const double*)map, nm);
+        prof_stop(st);
         count_launch();
         s = do_map2alm(p, res, da, nmaps, ws, dsig, dsig, st);
         if (s != SHT_OK) return s;
+        prof_start("k_add", st);
         k_add<<<ew_grid(na), 256, 0, st>>>((double*)alm, da, na);
+        prof_stop(st);
         count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return SHT_ECUDA; }
@@ -592,19 +655,30 @@ static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, in
     SHT_CUDA_TRY(grow_dev(&p->host_ws, &p->host_ws_bytes, need_ws));
     SHT_CUDA_TRY(grow_pin(&p->pin_in, &p->pin_in_bytes, need_in));
     SHT_CUDA_TRY(grow_pin(&p->pin_out, &p->pin_out_bytes, need_out));
+    // pinned (page-locked) caller buffers are copied directly; pageable ones
+    // are staged through the plan's pinned buffers
+    auto is_pinned = [](const void* ptr) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+        return at.type == cudaMemoryTypeHost;
+    };
+    const bool in_pinned = is_pinned(in_host), out_pinned = is_pinned(out_host);
     int launches = 0;
     for (int b0 = 0; b0 < nmaps; b0 += chunk) {
         int nb = std::min(chunk, nmaps - b0);
-        memcpy(p->pin_in, (const char*)in_host + (size_t)b0 * in_b, (size_t)nb * in_b);
-        SHT_CUDA_TRY(cudaMemcpyAsync(p->host_dev_in, p->pin_in, (size_t)nb * in_b, cudaMemcpyHostToDevice, st));
+        const char* src = (const char*)in_host + (size_t)b0 * in_b;
+        if (!in_pinned) { memcpy(p->pin_in, src, (size_t)nb * in_b); src = (const char*)p->pin_in; }
+        SHT_CUDA_TRY(cudaMemcpyAsync(p->host_dev_in, src, (size_t)nb * in_b, cudaMemcpyHostToDevice, st));
         sht_status s = to_map
             ? sht_alm2map(p, p->host_dev_in, p->host_dev_out, nb, p->host_ws, p->host_ws_bytes, st)
             : sht_map2alm(p, p->host_dev_in, p->host_dev_out, nb, niter, p->host_ws, p->host_ws_bytes, st);
         if (s != SHT_OK) return s;
         launches += t_launches;
-        SHT_CUDA_TRY(cudaMemcpyAsync(p->pin_out, p->host_dev_out, (size_t)nb * out_b, cudaMemcpyDeviceToHost, st));
+        char* dst = (char*)out_host + (size_t)b0 * out_b;
+        SHT_CUDA_TRY(cudaMemcpyAsync(out_pinned ? dst : (char*)p->pin_out, p->host_dev_out, (size_t)nb * out_b,
+                                     cudaMemcpyDeviceToHost, st));
         SHT_CUDA_TRY(cudaStreamSynchronize(st));
-        memcpy((char*)out_host + (size_t)b0 * out_b, p->pin_out, (size_t)nb * out_b);
+        if (!out_pinned) memcpy(dst, p->pin_out, (size_t)nb * out_b);
     }
     t_launches = launches;
     return SHT_OK;

@@ -73,6 +73,9 @@ def load() -> ctypes.CDLL:
         lib.sht_last_error.restype = ctypes.c_char_p
         lib.sht_last_launch_count.restype = I
         lib.sht_version.restype = ctypes.c_char_p
+        lib.sht_profile_begin.restype = None
+        lib.sht_profile_end.argtypes = [ctypes.c_char_p, I]
+        lib.sht_profile_end.restype = I
         _lib = lib
         return lib
 
@@ -88,6 +91,21 @@ def sht_last_error() -> str:
 
 def sht_last_launch_count() -> int:
     return load().sht_last_launch_count()
+
+
+def sht_profile_begin() -> None:
+    load().sht_profile_begin()
+
+
+def sht_profile_end() -> dict:
+    """Per-kernel {name: {"launches": n, "ms": total}} since sht_profile_begin()."""
+    import json
+    lib = load()
+    buf = ctypes.create_string_buffer(1 << 16)
+    n = lib.sht_profile_end(buf, len(buf))
+    if n > len(buf):
+        raise RuntimeError("profile buffer too small")
+    return json.loads(buf.value.decode())
 
 
 def sht_plan_create(nside, lmax, mmax=-1, spin=0, precision=SHT_FP64, device=0):
