@@ -132,6 +132,25 @@ sht_status sht_alm2map_host(sht_plan* plan, const void* alm_host, void* map_host
 sht_status sht_map2alm_host(sht_plan* plan, const void* map_host, void* alm_host, int nmaps,
                             int niter, void* stream);
 
+/* alm2map without any device allocation (the paper has no counterpart; this
+ * is a library convenience). For callers that cannot allocate device memory
+ * while they run -- code inside a CUDA-graph capture region, a serving loop
+ * that must not touch the allocator, or a host framework that owns all GPU
+ * memory -- and so cannot provide the workspace sht_alm2map needs. Same
+ * transform, layouts and stream semantics as sht_alm2map on an SHT_FP64 plan
+ * (other precisions return SHT_EUNSUPPORTED); the caller passes only the
+ * inputs and outputs. The intermediate matrix lives in one static device
+ * array of sht_noalloc_scratch_bytes() bytes (64 MiB) that every GPU loading
+ * the library keeps until the process exits; a call that needs more returns
+ * SHT_EINVAL with both sizes in sht_last_error(). All calls on a device share
+ * that array (nothing in it needs to start at zero), so calls that overlap
+ * on the GPU race: serialise them. The first call on each device looks up
+ * the array's address (cudaGetSymbolAddress); make it before any stream
+ * capture begins. */
+sht_status sht_alm2map_noalloc(sht_plan* plan, const void* alm, void* map, int nmaps,
+                               void* stream);
+size_t     sht_noalloc_scratch_bytes(void);
+
 /* Number of kernel launches the most recent call on this thread issued
  * (for the benchmark's launch accounting). */
 int sht_last_launch_count(void);
