@@ -70,6 +70,21 @@ struct DevTables {
     double* w_C[2] = {nullptr, nullptr};
 };
 
+// tables of the split-precision (tensor-core) form
+struct SplitTables {
+    double* nA = nullptr;          // normalised recurrence per packed (l, m):
+    double* nB = nullptr;          //   mu_{l+2} = (nA x^2 + nB) mu_l + mu_{l-2}
+    float* nc = nullptr;           //   lambda_l = nc * mu_l
+    double2* ck = nullptr;         // map2alm row-tile checkpoints [block][p]
+    int* ck_exp = nullptr;
+    unsigned int* rowmax_bits = nullptr;   // max_p |lambda_lm| per packed (l, m) (float bits)
+    float* pairmax = nullptr;      // max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
+    int* err = nullptr;            // device error word of the bounded waits
+    int4* work_m2a = nullptr; int nwork_m2a = 0;
+    int4* work_a2m = nullptr; int nwork_a2m = 0;
+    float Q_m2a = 0.0f, Q_a2m = 0.0f;
+};
+
 }  // namespace sht
 
 struct sht_plan {
@@ -80,6 +95,7 @@ struct sht_plan {
     int fft_max = 0;            // largest power-of-two FFT size
     int nfft = 0;
     sht::DevTables t;
+    sht::SplitTables s;
     std::vector<sht::PairGeom> h_pairs;
     std::vector<sht::FftLen> h_fft;
     size_t table_bytes = 0;
@@ -130,6 +146,18 @@ cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double
                                     double scale0, double scale, cudaStream_t st);
 int legendre_f64_row_tile();
 int legendre_f64_pair_tile();
+// split (tensor-core) form
+cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, unsigned int* colmax,
+                                     int nmaps, cudaStream_t st);
+cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* colmax, double* alm,
+                                   int nmaps, float s0, float s1, cudaStream_t st);
+cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const double* alm, const float* colmax, float* G,
+                                   int nmaps, float s0, float s1, cudaStream_t st);
+cudaError_t launch_alm_colmax(const sht_plan* p, const double* alm, float* colmax, int nmaps, cudaStream_t st);
+cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base);
+int split_row_tile();
+int split_col_tile();
 
 }  // namespace sht
 

@@ -24,6 +24,17 @@ template <typename C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
+// (cos, sin) of pi * num / den
+template <typename R> __device__ __forceinline__ void sincospi_r(int num, int den, R* sn, R* cs);
+template <> __device__ __forceinline__ void sincospi_r<double>(int num, int den, double* sn, double* cs)
+{
+    sincospi((double)num / (double)den, sn, cs);
+}
+template <> __device__ __forceinline__ void sincospi_r<float>(int num, int den, float* sn, float* cs)
+{
+    sincospif((float)num / (float)den, sn, cs);
+}
+
 __device__ __forceinline__ int brev(int i, int logm) { return (int)(__brev((unsigned)i) >> (32 - logm)); }
 
 // Decimation in frequency: natural-order input -> bit-reversed output.
@@ -147,9 +158,9 @@ k_fft_forward(const double* __restrict__ map, R* __restrict__ T, const PairGeom*
         Xs.x = (R)0.5 * (a.y + b.y); Xs.y = (R)0.5 * (b.x - a.x);
         if (g.phi0 != 0.0) {
             // e^{-i m phi0}, phi0 = pi / N: exact reduction of m mod 2N
-            double sn, cs;
-            sincospi(-(double)(m % (2 * N)) / (double)N, &sn, &cs);
-            C ph; ph.x = (R)cs; ph.y = (R)sn;
+            R sn, cs;
+            sincospi_r<R>(-(m % (2 * N)), N, &sn, &cs);
+            C ph; ph.x = cs; ph.y = sn;
             Xn = cmul(Xn, ph);
             Xs = cmul(Xs, ph);
         }
@@ -198,9 +209,9 @@ k_fft_backward(const R* __restrict__ G, double* __restrict__ map, const PairGeom
                 C tn = cadd(E, O), ts = csub(E, O);
                 R w = m ? (R)2 : (R)1;
                 if (g.phi0 != 0.0) {
-                    double sv, cv;
-                    sincospi((double)(m % (2 * N)) / (double)N, &sv, &cv);
-                    C ph; ph.x = (R)cv; ph.y = (R)sv;
+                    R sv, cv;
+                    sincospi_r<R>(m % (2 * N), N, &sv, &cv);
+                    C ph; ph.x = cv; ph.y = sv;
                     tn = cmul(tn, ph);
                     ts = cmul(ts, ph);
                 }
@@ -262,6 +273,121 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
     k_fft_backward<double><<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp,
                                                    p->t.bhat, p->fft_max, p->R, p->mmax, p->npix,
                                                    ncols(p, nmaps));
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP32 forward transform for the split form: one CTA handles a block of ring
+// pairs of one (map, component) in turn, and tracks per (m, slot, column) the
+// largest |value| it wrote; one atomicMax per entry and block merges the
+// blocks (the column quanta of the tensor-core contraction need the maximum
+// over all ring pairs). grid.x = pair block, grid.y = map * ncomp + comp.
+// ---------------------------------------------------------------------------
+constexpr int FWD_PB = 64;          // ring pairs per CTA
+constexpr int FWD_MJ = 8;           // m values per thread (mmax + 1 <= 8 * 256)
+
+__global__ void __launch_bounds__(256)
+k_fft_forward_split(const double* __restrict__ map, float* __restrict__ T, unsigned int* __restrict__ colmax,
+                    const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts,
+                    const float2* __restrict__ tw, const float2* __restrict__ chirp, const float2* __restrict__ bhat,
+                    int fftmax, int R_, int mmax, long long npix, long long ncol)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    const int mc = blockIdx.y;
+    const long long col = (long long)mc * 2;
+    const long long qstride = (long long)R_ * ncol;
+    float mx[FWD_MJ][4];
+#pragma unroll
+    for (int j = 0; j < FWD_MJ; j++) mx[j][0] = mx[j][1] = mx[j][2] = mx[j][3] = 0.0f;
+    const int pend = min(R_, (blockIdx.x + 1) * FWD_PB);
+    for (int p = blockIdx.x * FWD_PB; p < pend; p++) {
+        const PairGeom g = pairs[p];
+        const FftLen f = ffts[g.fft];
+        const int N = g.n;
+        const double* xn = map + (long long)mc * npix + g.start_n;
+        const double* xs = g.start_s >= 0 ? map + (long long)mc * npix + g.start_s : nullptr;
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            float2 z;
+            z.x = (float)xn[n];
+            z.y = xs ? (float)xs[n] : 0.0f;
+            if (f.bluestein) z = cmul(z, chirp[f.chirp + n]);
+            buf[place_index(f, n)] = z;
+        }
+        zero_tail(buf, f);
+        __syncthreads();
+        dft_forward(buf, f, fftmax, tw, chirp + f.chirp, bhat + f.bhat);
+#pragma unroll
+        for (int jj = 0; jj < FWD_MJ; jj++) {
+            const int m = threadIdx.x + jj * 256;
+            if (m > mmax) break;
+            int j = m % N;
+            int jm = (N - j) % N;
+            float2 a = buf[j], b = buf[jm];
+            float2 Xn, Xs;
+            Xn.x = 0.5f * (a.x + b.x); Xn.y = 0.5f * (a.y - b.y);
+            Xs.x = 0.5f * (a.y + b.y); Xs.y = 0.5f * (b.x - a.x);
+            if (g.phi0 != 0.0) {
+                float sn, cs;
+                sincospi_r<float>(-(m % (2 * N)), N, &sn, &cs);
+                float2 ph = make_float2(cs, sn);
+                Xn = cmul(Xn, ph);
+                Xs = cmul(Xs, ph);
+            }
+            float2 E = cadd(Xn, Xs), O = csub(Xn, Xs);
+            float* t0 = T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
+            *reinterpret_cast<float2*>(t0) = E;
+            *reinterpret_cast<float2*>(t0 + qstride) = O;
+            mx[jj][0] = fmaxf(mx[jj][0], fabsf(E.x));
+            mx[jj][1] = fmaxf(mx[jj][1], fabsf(E.y));
+            mx[jj][2] = fmaxf(mx[jj][2], fabsf(O.x));
+            mx[jj][3] = fmaxf(mx[jj][3], fabsf(O.y));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int jj = 0; jj < FWD_MJ; jj++) {
+        const int m = threadIdx.x + jj * 256;
+        if (m > mmax) break;
+        unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
+        unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
+        if (mx[jj][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][0]));
+        if (mx[jj][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][1]));
+        if (mx[jj][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][2]));
+        if (mx[jj][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][3]));
+    }
+}
+
+cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, unsigned int* colmax,
+                                     int nmaps, cudaStream_t st)
+{
+    size_t sm = (size_t)p->fft_max * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_forward_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long nc = ncols(p, nmaps);
+    e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p->R + FWD_PB - 1) / FWD_PB, nmaps * p->ncomp);
+    prof_start("k_fft_forward_split", st);
+    k_fft_forward_split<<<grid, 256, sm, st>>>(map, T, colmax, p->t.pairs, p->t.fft, p->t.twiddle_f, p->t.chirp_f,
+                                               p->t.bhat_f, p->fft_max, p->R, p->mmax, p->npix, nc);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
+{
+    size_t sm = (size_t)p->fft_max * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_backward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid(p->R, nmaps * p->ncomp);
+    prof_start("k_fft_backward_f32", st);
+    k_fft_backward<float><<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, p->t.twiddle_f, p->t.chirp_f,
+                                                  p->t.bhat_f, p->fft_max, p->R, p->mmax, p->npix,
+                                                  ncols(p, nmaps));
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

@@ -345,6 +345,89 @@ static cudaError_t build_tables(sht_plan* p)
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// split-form tables: normalised two-step recurrence (2 FP64 ops per lambda),
+// plan-time checkpoints of the map2alm row tiles and lambda maxima
+// ---------------------------------------------------------------------------
+static cudaError_t build_split_tables(sht_plan* p)
+{
+    const int lmax = p->lmax, mmax = p->mmax, R = p->R;
+    const long long nalm = p->nalm;
+    size_t acc = 0;
+    cudaError_t e;
+    // lambda_{l+2} = (alpha x^2 + beta) lambda_l + gamma lambda_{l-2} (see build_tables);
+    // with lambda_l = c_l mu_l and c_{l+2} = gamma_l c_{l-2} the chain becomes
+    // mu_{l+2} = (A x^2 + B) mu_l + mu_{l-2}, A = alpha c_l / c_{l+2}, B = beta c_l / c_{l+2};
+    // each parity chain starts with c_{l0} = c_{l0+2} = 1 (gamma_{l0} = 0).
+    std::vector<double> nA(nalm, 0.0), nB(nalm, 0.0);
+    std::vector<float> nc(nalm, 0.0f);
+    for (int m = 0; m <= mmax; m++) {
+        auto ainv = [&](int l) -> ld { if (l <= m) return 0; ld L = l, M = m; return sqrtl((L * L - M * M) / (4 * L * L - 1)); };
+        auto aa = [&](int l) -> ld { ld L = l, M = m; return sqrtl((4 * L * L - 1) / (L * L - M * M)); };
+        for (int q = 0; q < 2; q++) {
+            int l0 = m + q;
+            if (l0 > lmax) continue;
+            std::vector<ld> c;       // c for l = l0 + 2j
+            c.push_back(1.0L);
+            for (int l = l0; l <= lmax; l += 2) {
+                ld a1 = aa(l + 1), a2 = aa(l + 2);
+                ld alpha = a2 * a1;
+                ld beta = -a2 * (a1 * ainv(l) * ainv(l) + 1 / a1);
+                ld gamma = -a2 * a1 * ainv(l) * ainv(l - 1);
+                size_t j = (l - l0) / 2;
+                ld cn = (l == l0) ? 1.0L : gamma * c[j - 1];
+                c.push_back(cn);
+                long long ci = alm_index(lmax, l, m);
+                nA[ci] = (double)(alpha * c[j] / cn);
+                nB[ci] = (double)(beta * c[j] / cn);
+                nc[ci] = (float)c[j];
+            }
+        }
+    }
+    if ((e = upload(&p->s.nA, nA, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.nB, nB, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.nc, nc, &acc)) != cudaSuccess) return e;
+    // work lists and checkpoint blocks
+    const int TM = split_row_tile();
+    std::vector<int4> w1, w2;
+    std::vector<int> base((size_t)(mmax + 1) * 2);
+    int nblk = 0;
+    for (int m = 0; m <= mmax; m++)
+        for (int q = 0; q < 2; q++) {
+            int lf = m + q;
+            int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
+            base[m * 2 + q] = nblk;
+            for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk + t));
+            nblk += (nrows + TM - 1) / TM;
+            for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, 0));
+        }
+    p->s.nwork_m2a = (int)w1.size();
+    p->s.nwork_a2m = (int)w2.size();
+    if ((e = upload(&p->s.work_m2a, w1, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.work_a2m, w2, &acc)) != cudaSuccess) return e;
+    int* d_base = nullptr;
+    if ((e = upload(&d_base, base, &acc)) != cudaSuccess) return e;
+    size_t nck = (size_t)std::max(nblk, 1) * R;
+    if ((e = cudaMalloc(&p->s.ck, nck * sizeof(double2))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.ck_exp, nck * sizeof(int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.rowmax_bits, (size_t)nalm * sizeof(unsigned int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.pairmax, (size_t)(mmax + 1) * 2 * R * sizeof(float))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.err, sizeof(int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    acc += nck * (sizeof(double2) + sizeof(int)) + (size_t)nalm * 4 + (size_t)(mmax + 1) * 2 * R * 4 + 4;
+    cudaMemset(p->s.rowmax_bits, 0, (size_t)nalm * sizeof(unsigned int));
+    cudaMemset(p->s.pairmax, 0, (size_t)(mmax + 1) * 2 * R * sizeof(float));
+    cudaMemset(p->s.err, 0, sizeof(int));
+    e = run_split_tables(p, d_base);
+    cudaFree(d_base);
+    if (e != cudaSuccess) return e;
+    // integer ranges of the exact main slices: Q^2 K <= 2^24 (and Q <= 256)
+    auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 256.0); };
+    p->s.Q_m2a = qfor((double)R);
+    p->s.Q_a2m = qfor((double)(lmax / 2 + 1));
+    p->table_bytes += acc;
+    return cudaSuccess;
+}
+
 static void free_tables(sht_plan* p)
 {
     void* ptrs[] = {p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp, p->t.bhat, p->t.twiddle_f,
@@ -352,6 +435,9 @@ static void free_tables(sht_plan* p)
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
                     p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
+    void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
+                  p->s.work_m2a, p->s.work_a2m};
+    for (void* q : sp) if (q) cudaFree(q);
     if (p->pin_in) cudaFreeHost(p->pin_in);
     if (p->pin_out) cudaFreeHost(p->pin_out);
 }
@@ -366,9 +452,14 @@ static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // workspace layout: [T/G buffer][residual map][delta alm] (the last two only
 // for map2alm with niter > 0)
+static size_t colmax_bytes(const sht_plan* p, int nmaps)
+{
+    return p->precision == SHT_FP64 ? 0 : (size_t)(p->mmax + 1) * 2 * (size_t)ncols(p, nmaps) * sizeof(float);
+}
+
 static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
 {
-    size_t b = round_up(tbuf_bytes(p, nmaps), 256);
+    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
     if (niter > 0) {
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->npix * sizeof(double), 256);
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
@@ -457,8 +548,12 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     if (mmax > lmax) { set_error("mmax must be <= lmax"); return SHT_EINVAL; }
     if (spin != 0 && spin != 2) { set_error("spin must be 0 or 2"); return SHT_EINVAL; }
     if (precision != SHT_FP64 && precision != SHT_SPLIT_BF16) { set_error("unknown precision"); return SHT_EINVAL; }
-    if (precision == SHT_SPLIT_BF16) {
-        set_error("SHT_SPLIT_BF16 is not available in this build");
+    if (precision == SHT_SPLIT_BF16 && mmax > 2047) {
+        set_error("SHT_SPLIT_BF16 supports mmax <= 2047");
+        return SHT_EUNSUPPORTED;
+    }
+    if (precision == SHT_SPLIT_BF16 && spin != 0) {
+        set_error("SHT_SPLIT_BF16 supports spin 0 in this build");
         return SHT_EUNSUPPORTED;
     }
     int ndev = 0;
@@ -475,6 +570,7 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     p->nalm = (long long)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
     p->R = 2 * nside;
     cudaError_t e = build_tables(p);
+    if (e == cudaSuccess && precision == SHT_SPLIT_BF16) e = build_split_tables(p);
     if (e != cudaSuccess) {
         set_error(std::string("plan tables: ") + cudaGetErrorString(e));
         free_tables(p);
@@ -535,9 +631,18 @@ static sht_status check_call(const sht_plan* p, const void* in, const void* out,
 static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nmaps, void* ws,
                              double s0, double s1, cudaStream_t st)
 {
-    double* G = (double*)ws;
-    cudaError_t e = launch_legendre_a2m_f64(p, alm, G, nmaps, s0, s1, st);
-    if (e == cudaSuccess) e = launch_fft_backward_f64(p, G, map, nmaps, st);
+    cudaError_t e;
+    if (p->precision == SHT_FP64) {
+        double* G = (double*)ws;
+        e = launch_legendre_a2m_f64(p, alm, G, nmaps, s0, s1, st);
+        if (e == cudaSuccess) e = launch_fft_backward_f64(p, G, map, nmaps, st);
+    } else {
+        float* G = (float*)ws;
+        float* cm = (float*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
+        e = launch_alm_colmax(p, alm, cm, nmaps, st);
+        if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, alm, cm, G, nmaps, (float)s0, (float)s1, st);
+        if (e == cudaSuccess) e = launch_fft_backward_f32(p, G, map, nmaps, st);
+    }
     if (e != cudaSuccess) { set_error(std::string("alm2map launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
 }
@@ -545,9 +650,20 @@ static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nm
 static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nmaps, void* ws,
                              double s0, double s1, cudaStream_t st)
 {
-    double* T = (double*)ws;
-    cudaError_t e = launch_fft_forward_f64(p, map, T, nmaps, st);
-    if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, T, alm, nmaps, s0, s1, st);
+    cudaError_t e;
+    if (p->precision == SHT_FP64) {
+        double* T = (double*)ws;
+        e = launch_fft_forward_f64(p, map, T, nmaps, st);
+        if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, T, alm, nmaps, s0, s1, st);
+    } else {
+        // the split kernel folds dsigma into lambda: s0, s1 are relative to map2alm
+        const double dsig = 4.0 * PI_D / (double)p->npix;
+        float* T = (float*)ws;
+        unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
+        e = launch_fft_forward_split(p, map, T, cm, nmaps, st);
+        if (e == cudaSuccess)
+            e = launch_legendre_m2a_tc(p, T, (const float*)cm, alm, nmaps, (float)(s0 / dsig), (float)(s1 / dsig), st);
+    }
     if (e != cudaSuccess) { set_error(std::string("map2alm launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
 }
@@ -572,7 +688,7 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
     if (s != SHT_OK || niter == 0) return s;
     // Algorithm 2: a += map2alm(T - alm2map(a)), niter times
-    size_t off = round_up(tbuf_bytes(p, nmaps), 256);
+    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
     double* res = (double*)((char*)ws + off);
     long long nm = (long long)nmaps * p->ncomp * p->npix;
     off += round_up((size_t)nm * sizeof(double), 256);

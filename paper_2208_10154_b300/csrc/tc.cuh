@@ -1,0 +1,192 @@
+// tc.cuh -- inline-PTX helpers for the sm_103a tensor-core path: mbarriers,
+// tensor memory (TMEM) allocation and loads, UMMA shared-memory descriptors and
+// tcgen05.mma (kind::f16 with BF16 operands, FP32 accumulation in TMEM).
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace sht {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}"
+                 :: "r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^22 polls (each poll may itself suspend for a
+// while), records `code` in *err and returns false. Every spin in the
+// tensor-core kernels goes through here, so a kernel can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, int code)
+{
+    for (int it = 0; it < (1 << 22); it++)
+        if (mbar_try_wait(b, parity)) return true;
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+// ------------------------------------------------------------------- fences
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// --------------------------------------------------------------------- TMEM
+// executed by one full warp
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(slot)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(taddr), "r"(ncols) : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns; warp w may only touch lanes 32*(w%4)..
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                   "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- UMMA
+// K-major operand tile in the 64-byte swizzle layout: rows of 32 BF16 (64 B),
+// 8-row atoms of 512 B, 16-byte chunk c of row r stored at chunk c ^ ((r>>1)&3).
+// The tile base must be 512-byte aligned; the K = 16 half of a row starts 32 B in.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset: 8-row atom
+    d |= (uint64_t)1 << 46;                   // descriptor version (tcgen05)
+    d |= (uint64_t)4 << 61;                   // SWIZZLE_64B
+    return d;
+}
+// byte offset of element (r, k) (k < 32) in such a tile
+__device__ __forceinline__ uint32_t sw64_off(int r, int k)
+{
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((((k >> 3)) ^ ((r >> 1) & 3)) << 4) + (k & 7) * 2);
+}
+// byte offset of the 16-byte chunk holding k = 8j..8j+7 of row r
+__device__ __forceinline__ uint32_t sw64_chunk(int r, int j)
+{
+    return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((j ^ ((r >> 1) & 3)) << 4));
+}
+
+// instruction descriptor: kind::f16, A = B = BF16, D = F32, K-major A and B
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+// arrive on an mbarrier once all previously issued tcgen05 ops of this thread completed
+__device__ __forceinline__ void umma_commit(uint64_t* b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(b)) : "memory");
+}
+
+// ------------------------------------------------------- number conversions
+// The FP64 pipe of this GPU is ~2 lanes/clk/SM, and cvt between FP64 and FP32
+// runs on it too, so FP64 <-> FP32 conversions are done with integer ops.
+//
+// FP64 value v times 2^sh as an FP32 (round to nearest on the 29 dropped bits,
+// results below the FP32 normal range flush to 0; |v 2^sh| must stay < 2^127).
+__device__ __forceinline__ float f64_to_f32_scaled(double v, int sh)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned int hi = (unsigned int)(b >> 32);
+    int e = (int)((hi >> 20) & 0x7FF);
+    if (e == 0) return 0.0f;
+    unsigned long long mr = (b & 0x000FFFFFFFFFFFFFull) + (1ull << 28);   // round mantissa to 23 bits
+    int carry = (int)(mr >> 52);
+    unsigned int m23 = (unsigned int)((mr >> 29) & 0x7FFFFF);
+    int ef = e - 1023 + 127 + sh + carry;
+    if (ef <= 0) return 0.0f;
+    unsigned int f = (hi & 0x80000000u) | ((unsigned int)ef << 23) | m23;
+    return __uint_as_float(f);
+}
+// exact FP32 -> FP64 (normal inputs; zero and subnormals give 0)
+__device__ __forceinline__ double f32_to_f64(float x)
+{
+    unsigned int u = __float_as_uint(x);
+    unsigned int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                           ((unsigned long long)(e - 127 + 1023) << 52) |
+                           ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+// x * 2^k for an FP64 x (exact; 0 stays 0)
+__device__ __forceinline__ double ldexp_fast(double x, int k)
+{
+    long long b = __double_as_longlong(x);
+    if ((b & 0x7FF0000000000000ll) == 0) return 0.0;
+    return __longlong_as_double(b + ((long long)k << 52));
+}
+// x * 2^k for an FP32 x (exact when the result stays normal; flushes below)
+__device__ __forceinline__ float ldexpf_fast(float x, int k)
+{
+    int u = __float_as_int(x);
+    int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0f;
+    int en = e + k;
+    if (en <= 0) return 0.0f;
+    return __int_as_float((u & ~0x7F800000) | (en << 23));
+}
+
+// Slice v (|v| <= Q <= 256, in units of the quantum) into an exact integer main
+// part and two BF16 residual pieces: v ~ q + r0 + r1, |v - q - r0 - r1| <= 2^-19.
+struct Slices { __nv_bfloat16 q, r0, r1; };
+__device__ __forceinline__ void slice3(float v, float& q, float& r0, float& r1)
+{
+    const float magic = 12582912.0f;            // 1.5 * 2^23: round to nearest integer
+    q = (v + magic) - magic;
+    float r = v - q;                             // exact, |r| <= 0.5
+    r0 = __bfloat162float(__float2bfloat16_rn(r));
+    r1 = __bfloat162float(__float2bfloat16_rn(r - r0));
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+}  // namespace tc
+}  // namespace sht
