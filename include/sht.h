@@ -56,10 +56,11 @@ typedef enum {
 typedef enum {
     /* Every step in FP64 (FFT, lambda recurrence, contraction). */
     SHT_FP64 = 0,
-    /* Contraction on BF16 tensor cores (tcgen05, FP32 TMEM accumulation):
-     * each operand = exact integer main slice + BF16 residual pieces, the
-     * main products accumulate exactly; lambda recurrence in FP64; ring
-     * FFTs in FP32; final accumulation into a_lm in FP64. */
+    /* Contraction on the 16-bit tensor cores (tcgen05 kind::f16 with FP16
+     * operands, FP32 TMEM accumulation): each operand = exact integer main
+     * slice + two FP16 residual pieces, the main products accumulate exactly;
+     * lambda recurrence in FP64; ring FFTs in compensated FP32; final
+     * accumulation into a_lm in FP64. */
     SHT_SPLIT_BF16 = 1
 } sht_precision;
 

@@ -70,11 +70,22 @@ struct DevTables {
     double* w_C[2] = {nullptr, nullptr};
 };
 
+// lo parts of the FP32 FFT tables and hi/lo ring phase tables (compensated FFT)
+struct CompTables {
+    float2* twiddle_l = nullptr;
+    float2* chirp_l = nullptr;
+    float2* bhat_l = nullptr;
+    float2* phase_h = nullptr;     // exp(+i pi k / N), k < 2N, per ring length
+    float2* phase_l = nullptr;
+    long long* phase_off = nullptr;
+};
+
 // tables of the split-precision (tensor-core) form
 struct SplitTables {
     double* nA = nullptr;          // normalised recurrence per packed (l, m):
     double* nB = nullptr;          //   mu_{l+2} = (nA x^2 + nB) mu_l + mu_{l-2}
     float* nc = nullptr;           //   lambda_l = nc * mu_l
+    double* nc64 = nullptr;        //   the same factor in FP64
     double2* ck = nullptr;         // map2alm row-tile checkpoints [block][p]
     int* ck_exp = nullptr;
     unsigned int* rowmax_bits = nullptr;   // max_p |lambda_lm| per packed (l, m) (float bits)
@@ -83,6 +94,7 @@ struct SplitTables {
     int4* work_m2a = nullptr; int nwork_m2a = 0;
     int4* work_a2m = nullptr; int nwork_a2m = 0;
     float Q_m2a = 0.0f, Q_a2m = 0.0f;
+    int mlo = 0;                   // map2alm keeps an FP32 remainder of T for m < mlo
 };
 
 }  // namespace sht
@@ -96,6 +108,7 @@ struct sht_plan {
     int nfft = 0;
     sht::DevTables t;
     sht::SplitTables s;
+    sht::CompTables c;
     std::vector<sht::PairGeom> h_pairs;
     std::vector<sht::FftLen> h_fft;
     size_t table_bytes = 0;
@@ -147,11 +160,11 @@ cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double
 int legendre_f64_row_tile();
 int legendre_f64_pair_tile();
 // split (tensor-core) form
-cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, unsigned int* colmax,
-                                     int nmaps, cudaStream_t st);
+cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, float* Tlo,
+                                     unsigned int* colmax, int nmaps, cudaStream_t st);
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
-cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* colmax, double* alm,
-                                   int nmaps, float s0, float s1, cudaStream_t st);
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* Tlo, const float* colmax, double* alm,
+                                   int nmaps, double fs0, double fs1, cudaStream_t st);
 cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const double* alm, const float* colmax, float* G,
                                    int nmaps, float s0, float s1, cudaStream_t st);
 cudaError_t launch_alm_colmax(const sht_plan* p, const double* alm, float* colmax, int nmaps, cudaStream_t st);

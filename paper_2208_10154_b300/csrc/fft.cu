@@ -278,119 +278,4 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// FP32 forward transform for the split form: one CTA handles a block of ring
-// pairs of one (map, component) in turn, and tracks per (m, slot, column) the
-// largest |value| it wrote; one atomicMax per entry and block merges the
-// blocks (the column quanta of the tensor-core contraction need the maximum
-// over all ring pairs). grid.x = pair block, grid.y = map * ncomp + comp.
-// ---------------------------------------------------------------------------
-constexpr int FWD_PB = 64;          // ring pairs per CTA
-constexpr int FWD_MJ = 8;           // m values per thread (mmax + 1 <= 8 * 256)
-
-__global__ void __launch_bounds__(256)
-k_fft_forward_split(const double* __restrict__ map, float* __restrict__ T, unsigned int* __restrict__ colmax,
-                    const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts,
-                    const float2* __restrict__ tw, const float2* __restrict__ chirp, const float2* __restrict__ bhat,
-                    int fftmax, int R_, int mmax, long long npix, long long ncol)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* buf = reinterpret_cast<float2*>(smem_raw);
-    const int mc = blockIdx.y;
-    const long long col = (long long)mc * 2;
-    const long long qstride = (long long)R_ * ncol;
-    float mx[FWD_MJ][4];
-#pragma unroll
-    for (int j = 0; j < FWD_MJ; j++) mx[j][0] = mx[j][1] = mx[j][2] = mx[j][3] = 0.0f;
-    const int pend = min(R_, (blockIdx.x + 1) * FWD_PB);
-    for (int p = blockIdx.x * FWD_PB; p < pend; p++) {
-        const PairGeom g = pairs[p];
-        const FftLen f = ffts[g.fft];
-        const int N = g.n;
-        const double* xn = map + (long long)mc * npix + g.start_n;
-        const double* xs = g.start_s >= 0 ? map + (long long)mc * npix + g.start_s : nullptr;
-        for (int n = threadIdx.x; n < N; n += blockDim.x) {
-            float2 z;
-            z.x = (float)xn[n];
-            z.y = xs ? (float)xs[n] : 0.0f;
-            if (f.bluestein) z = cmul(z, chirp[f.chirp + n]);
-            buf[place_index(f, n)] = z;
-        }
-        zero_tail(buf, f);
-        __syncthreads();
-        dft_forward(buf, f, fftmax, tw, chirp + f.chirp, bhat + f.bhat);
-#pragma unroll
-        for (int jj = 0; jj < FWD_MJ; jj++) {
-            const int m = threadIdx.x + jj * 256;
-            if (m > mmax) break;
-            int j = m % N;
-            int jm = (N - j) % N;
-            float2 a = buf[j], b = buf[jm];
-            float2 Xn, Xs;
-            Xn.x = 0.5f * (a.x + b.x); Xn.y = 0.5f * (a.y - b.y);
-            Xs.x = 0.5f * (a.y + b.y); Xs.y = 0.5f * (b.x - a.x);
-            if (g.phi0 != 0.0) {
-                float sn, cs;
-                sincospi_r<float>(-(m % (2 * N)), N, &sn, &cs);
-                float2 ph = make_float2(cs, sn);
-                Xn = cmul(Xn, ph);
-                Xs = cmul(Xs, ph);
-            }
-            float2 E = cadd(Xn, Xs), O = csub(Xn, Xs);
-            float* t0 = T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
-            *reinterpret_cast<float2*>(t0) = E;
-            *reinterpret_cast<float2*>(t0 + qstride) = O;
-            mx[jj][0] = fmaxf(mx[jj][0], fabsf(E.x));
-            mx[jj][1] = fmaxf(mx[jj][1], fabsf(E.y));
-            mx[jj][2] = fmaxf(mx[jj][2], fabsf(O.x));
-            mx[jj][3] = fmaxf(mx[jj][3], fabsf(O.y));
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int jj = 0; jj < FWD_MJ; jj++) {
-        const int m = threadIdx.x + jj * 256;
-        if (m > mmax) break;
-        unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
-        unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
-        if (mx[jj][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][0]));
-        if (mx[jj][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][1]));
-        if (mx[jj][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][2]));
-        if (mx[jj][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][3]));
-    }
-}
-
-cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, unsigned int* colmax,
-                                     int nmaps, cudaStream_t st)
-{
-    size_t sm = (size_t)p->fft_max * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_forward_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    long long nc = ncols(p, nmaps);
-    e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
-    if (e != cudaSuccess) return e;
-    dim3 grid((p->R + FWD_PB - 1) / FWD_PB, nmaps * p->ncomp);
-    prof_start("k_fft_forward_split", st);
-    k_fft_forward_split<<<grid, 256, sm, st>>>(map, T, colmax, p->t.pairs, p->t.fft, p->t.twiddle_f, p->t.chirp_f,
-                                               p->t.bhat_f, p->fft_max, p->R, p->mmax, p->npix, nc);
-    prof_stop(st);
-    count_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
-{
-    size_t sm = (size_t)p->fft_max * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_fft_backward<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid(p->R, nmaps * p->ncomp);
-    prof_start("k_fft_backward_f32", st);
-    k_fft_backward<float><<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, p->t.twiddle_f, p->t.chirp_f,
-                                                  p->t.bhat_f, p->fft_max, p->R, p->mmax, p->npix,
-                                                  ncols(p, nmaps));
-    prof_stop(st);
-    count_launch();
-    return cudaGetLastError();
-}
-
 }  // namespace sht

@@ -1,5 +1,5 @@
 // legendre_tc.cu -- split-precision Legendre contraction on the B300 tensor
-// cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulation in TMEM).
+// cores (tcgen05.mma kind::f16, FP16 operands, FP32 accumulation in TMEM).
 //
 // The paper's per-m GEMMs (Sec. 2.2 equ:matrix form: A_m = P_m T_m and
 // T_m = P_m^t A_m) are evaluated per (m, slot q) with lambda generated on the
@@ -10,7 +10,9 @@
 // which would cost ~1e-6 over K = 1024. Instead each operand x is written, per
 // row (lambda) or column (data), in units of a power-of-two quantum u with
 // |x/u| <= Q, Q^2 K <= 2^24, as
-//     x/u = q + r0 + r1,   q integer (exact in BF16), r0, r1 BF16 residuals.
+//     x/u = q + r0 + r1,   q integer (exact in FP16), r0, r1 FP16 residuals
+// (FP16 rather than BF16: the residual keeps 22 bits relative to itself, so
+// elements far below their row / column maximum stay accurate).
 // The products q_a q_b are integers and their sum over K stays below 2^24, so
 // the main accumulator is EXACT whatever the rounding mode. The five residual
 // products (q r0', q r1', r0 q', r1 q', r0 r0') go to a second accumulator
@@ -37,7 +39,7 @@ constexpr int TM = 128, TN = 256, KC = 32, NST = 3;
 constexpr int A_PLANE = TM * KC * 2;                 // 8 KB
 constexpr int B_PLANE = TN * KC * 2;                 // 16 KB
 constexpr int STAGE_BYTES = 3 * A_PLANE + 3 * B_PLANE;   // 72 KB
-constexpr uint32_t IDESC = idesc_bf16(TM, TN);
+constexpr uint32_t IDESC = idesc_f16(TM, TN);
 
 struct TcArgs {
     const int4* work;          // (m, q, tile, index of its checkpoint block)
@@ -47,17 +49,18 @@ struct TcArgs {
     const double* nA;          // normalised recurrence: mu_{l+2} = (A x^2 + B) mu_l + mu_{l-2}
     const double* nB;
     const float* nc;           // lambda_l = c_l mu_l
+    const double* nc64;        // the same c_l in FP64 (map2alm applies it per output row)
     const double2* ck;         // map2alm checkpoints [block][p] (mu at row r0, mu at row r0-1)
     const int* ck_exp;
-    const float* rowmax;       // map2alm: max_p |lambda_lm| per packed (l, m)
+    const float* rowmax;       // map2alm: max_p |mu_l(theta_p) 2^E| per packed (l, m)
     const float* pairmax;      // alm2map: max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
     const float* colmax;       // data: max |x| per [m][q][col]
     int* err;
-    int lmax, mmax, R;
+    int lmax, mmax, R, mlo;
     long long ncol, nalm;
     float Q;                   // integer range of the main slices
-    float dsig;                // map2alm pixel weight (folded into lambda)
-    float s0, s1;              // extra output scale for m = 0 / m > 0
+    double fs0, fs1;           // map2alm: output factor (dsigma times any adjoint weight), m = 0 / m > 0
+    float s0, s1;              // alm2map: extra output scale for m = 0 / m > 0
 };
 
 // quantum exponent: smallest e with max / 2^e <= Q
@@ -80,9 +83,9 @@ __device__ __forceinline__ void put3(uint8_t* planes, int plane_bytes, int row, 
     float q, r0, r1;
     slice3(v, q, r0, r1);
     uint32_t off = sw64_off(row, k);
-    *reinterpret_cast<__nv_bfloat16*>(planes + off) = __float2bfloat16_rn(q);
-    *reinterpret_cast<__nv_bfloat16*>(planes + plane_bytes + off) = __float2bfloat16_rn(r0);
-    *reinterpret_cast<__nv_bfloat16*>(planes + 2 * plane_bytes + off) = __float2bfloat16_rn(r1);
+    *reinterpret_cast<__half*>(planes + off) = __float2half_rn(q);
+    *reinterpret_cast<__half*>(planes + plane_bytes + off) = __float2half_rn(r0);
+    *reinterpret_cast<__half*>(planes + 2 * plane_bytes + off) = __float2half_rn(r1);
 }
 
 // write 8 consecutive k (chunk j) of one row into the three planes
@@ -94,9 +97,29 @@ __device__ __forceinline__ void put3x8(uint8_t* planes, int plane_bytes, int row
         float q0, x0, y0, q1, x1, y1;
         slice3(v[2 * i], q0, x0, y0);
         slice3(v[2 * i + 1], q1, x1, y1);
-        qq[i] = pack_bf16x2(q0, q1);
-        a[i] = pack_bf16x2(x0, x1);
-        b[i] = pack_bf16x2(y0, y1);
+        qq[i] = pack_h2(q0, q1);
+        a[i] = pack_h2(x0, x1);
+        b[i] = pack_h2(y0, y1);
+    }
+    uint32_t off = sw64_chunk(row, j);
+    *reinterpret_cast<uint4*>(planes + off) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
+    *reinterpret_cast<uint4*>(planes + plane_bytes + off) = make_uint4(a[0], a[1], a[2], a[3]);
+    *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = make_uint4(b[0], b[1], b[2], b[3]);
+}
+
+// the same with FP32 remainders vl (value = v + vl)
+__device__ __forceinline__ void put3x8l(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
+                                        const float (&vl)[8])
+{
+    uint32_t qq[4], a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float q0, x0, y0, q1, x1, y1;
+        slice3x(v[2 * i], vl[2 * i], q0, x0, y0);
+        slice3x(v[2 * i + 1], vl[2 * i + 1], q1, x1, y1);
+        qq[i] = pack_h2(q0, q1);
+        a[i] = pack_h2(x0, x1);
+        b[i] = pack_h2(y0, y1);
     }
     uint32_t off = sw64_chunk(row, j);
     *reinterpret_cast<uint4*>(planes + off) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
@@ -112,12 +135,12 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint32_t stage_addr, 
     for (int kk = 0; kk < 2; kk++) {
         const uint32_t o = kk * 32;
         const uint32_t acc = (first && kk == 0) ? 0u : 1u;
-        umma_bf16(tmem, desc_sw64(A0 + o), desc_sw64(B0 + o), IDESC, acc);             // main: q q'
-        umma_bf16(tmem + TN, desc_sw64(A0 + o), desc_sw64(B1 + o), IDESC, acc);        // q r0'
-        umma_bf16(tmem + TN, desc_sw64(A0 + o), desc_sw64(B2 + o), IDESC, 1u);         // q r1'
-        umma_bf16(tmem + TN, desc_sw64(A1 + o), desc_sw64(B0 + o), IDESC, 1u);         // r0 q'
-        umma_bf16(tmem + TN, desc_sw64(A2 + o), desc_sw64(B0 + o), IDESC, 1u);         // r1 q'
-        umma_bf16(tmem + TN, desc_sw64(A1 + o), desc_sw64(B1 + o), IDESC, 1u);         // r0 r0'
+        umma_f16(tmem, desc_sw64(A0 + o), desc_sw64(B0 + o), IDESC, acc);             // main: q q'
+        umma_f16(tmem + TN, desc_sw64(A0 + o), desc_sw64(B1 + o), IDESC, acc);        // q r0'
+        umma_f16(tmem + TN, desc_sw64(A0 + o), desc_sw64(B2 + o), IDESC, 1u);         // q r1'
+        umma_f16(tmem + TN, desc_sw64(A1 + o), desc_sw64(B0 + o), IDESC, 1u);         // r0 q'
+        umma_f16(tmem + TN, desc_sw64(A2 + o), desc_sw64(B0 + o), IDESC, 1u);         // r1 q'
+        umma_f16(tmem + TN, desc_sw64(A1 + o), desc_sw64(B1 + o), IDESC, 1u);         // r0 r0'
     }
 }
 
@@ -129,7 +152,7 @@ struct TcShared {
     int colexp[TN];
     int rowexp[TM];
     double cA[TM], cB[TM];
-    float cfac[TM];
+    float2 rfac[TM];           // map2alm: c_l * factor as an FP32 hi/lo pair
 };
 constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
 
@@ -137,7 +160,7 @@ constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
 // map2alm: a[l, c] = sum_p lambda_lm(theta_p) dsig T[p, c]   (rows l = m + q + 2r)
 // ===========================================================================
 __global__ void __launch_bounds__(256, 1)
-k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
+k_leg_m2a_tc(const float* __restrict__ T, const float* __restrict__ Tlo, double* __restrict__ alm, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -152,6 +175,7 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
     const int nch = (a.R + KC - 1) / KC;
     const long long qstride = (long long)a.R * a.ncol;
     const float* Tq = T + ((long long)m * 2 + q) * qstride;
+    const float* Tlq = (m < a.mlo) ? Tlo + ((long long)m * 2 + q) * qstride : nullptr;
 
     // per-row constants and scales
     for (int r = tid; r < TM; r += blockDim.x) {
@@ -161,11 +185,14 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
             long long ci = a_idx(a.lmax, l, m);
             sh.cA[r] = a.nA[ci];
             sh.cB[r] = a.nB[ci];
-            int e = quantum_exp(a.rowmax[ci] * a.dsig, a.Q);
-            sh.rowexp[r] = e;
-            sh.cfac[r] = a.nc[ci] * a.dsig;
+            sh.rowexp[r] = quantum_exp(a.rowmax[ci], a.Q);
+            // the row factor c_l * dsigma is applied once per output, in
+            // double-float, so its rounding is not a coherent error on the row
+            double f = a.nc64[ci] * (m == 0 ? a.fs0 : a.fs1);
+            float fh = (float)f;
+            sh.rfac[r] = make_float2(fh, (float)(f - (double)fh));
         } else {
-            sh.cA[r] = 0.0; sh.cB[r] = 0.0; sh.rowexp[r] = 0; sh.cfac[r] = 0.0f;
+            sh.cA[r] = 0.0; sh.cB[r] = 0.0; sh.rowexp[r] = 0; sh.rfac[r] = make_float2(0.0f, 0.0f);
         }
     }
     for (int c = tid; c < TN; c += blockDim.x) {
@@ -216,7 +243,7 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
             for (int r = 0; r < TM; r++) {
                 float v = 0.0f;
                 if (r0 + r < nrows) {
-                    v = f64_to_f32_scaled(cur, E - sh.rowexp[r]) * sh.cfac[r];
+                    v = f64_to_f32_scaled(cur, E - sh.rowexp[r]);
                     double t = fma(sh.cA[r], x2, sh.cB[r]);
                     double nxt = fma(t, cur, prev);
                     prev = cur;
@@ -243,18 +270,22 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
             uint8_t* B = smem + s * STAGE_BYTES + 3 * A_PLANE;
 #pragma unroll
             for (int j = 0; j < KC / 8; j++) {
-                float va[8], vb[8];
+                float va[8], vb[8], la[8], lb[8];
 #pragma unroll
                 for (int i = 0; i < 8; i++) {
                     int p = kc * KC + j * 8 + i;
-                    float2 x = make_float2(0.0f, 0.0f);
-                    if (p < a.R && cg < a.ncol)
+                    float2 x = make_float2(0.0f, 0.0f), xl = make_float2(0.0f, 0.0f);
+                    if (p < a.R && cg < a.ncol) {
                         x = *reinterpret_cast<const float2*>(Tq + (long long)p * a.ncol + cg);
+                        if (Tlq) xl = *reinterpret_cast<const float2*>(Tlq + (long long)p * a.ncol + cg);
+                    }
                     va[i] = ldexpf_fast(x.x, -e0);
                     vb[i] = ldexpf_fast(x.y, -e1);
+                    la[i] = ldexpf_fast(xl.x, -e0);
+                    lb[i] = ldexpf_fast(xl.y, -e1);
                 }
-                put3x8(B, B_PLANE, cl, j, va);
-                put3x8(B, B_PLANE, cl + 1, j, vb);
+                put3x8l(B, B_PLANE, cl, j, va, la);
+                put3x8l(B, B_PLANE, cl + 1, j, vb, lb);
             }
             fence_proxy_async_smem();
             mbar_arrive(&sh.full[s]);
@@ -267,8 +298,8 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
         tc_fence_after();
         const int l = l_first + 2 * row;
         const bool live = ok && row < nrows;
-        const double sc = (m == 0) ? a.s0 : a.s1;
         const long long li = live ? a_idx(a.lmax, l, m) : 0;
+        const float2 F = sh.rfac[r];
         for (int c = 0; c < TN; c += 16) {
             uint32_t vm[16], vc[16];
             const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -280,12 +311,21 @@ k_leg_m2a_tc(const float* __restrict__ T, double* __restrict__ alm, TcArgs a)
             for (int j = 0; j < 16; j += 2) {
                 long long cgj = c0 + c + j;
                 if (cgj >= a.ncol) break;
-                double re = f32_to_f64(__uint_as_float(vm[j])) + f32_to_f64(__uint_as_float(vc[j]));
-                double im = f32_to_f64(__uint_as_float(vm[j + 1])) + f32_to_f64(__uint_as_float(vc[j + 1]));
-                re = sc * ldexp_fast(re, sh.rowexp[r] + sh.colexp[c + j]);
-                im = (m == 0) ? 0.0 : sc * ldexp_fast(im, sh.rowexp[r] + sh.colexp[c + j + 1]);
+                double out[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    // (main + corr) * (Fh + Fl): main is an exact integer, the
+                    // product error of main * Fh is recovered with an FMA
+                    const float mn = __uint_as_float(vm[j + h]), cr = __uint_as_float(vc[j + h]);
+                    const float p1 = mn * F.x;
+                    const float e1 = fmaf(mn, F.x, -p1);
+                    const float lo = e1 + cr * F.x + (mn + cr) * F.y;
+                    double v = f32_to_f64(p1) + f32_to_f64(lo);          // final FP64 accumulation
+                    out[h] = ldexp_fast(v, sh.rowexp[r] + sh.colexp[c + j + h]);
+                }
+                if (m == 0) out[1] = 0.0;
                 long long mc = cgj >> 1;
-                *reinterpret_cast<double2*>(alm + (mc * a.nalm + li) * 2) = make_double2(re, im);
+                *reinterpret_cast<double2*>(alm + (mc * a.nalm + li) * 2) = make_double2(out[0], out[1]);
             }
         }
     }
@@ -497,10 +537,11 @@ k_split_tables(TcArgs a, const int* __restrict__ ck_base, double2* __restrict__ 
             }
             int l = l_first + 2 * row;
             long long ci = a_idx(a.lmax, l, m);
-            float v = 0.0f;
+            float v = 0.0f, vmu = 0.0f;
             if (valid) {
-                // |lambda| = |c_l mu 2^E| (FP64 product then a scaled conversion)
-                v = fabsf(f64_to_f32_scaled(cur, E) * a.nc[ci]);
+                // |mu 2^E| for the map2alm row quanta; |lambda| = |c_l mu 2^E| for alm2map
+                vmu = fabsf(f64_to_f32_scaled(cur, E));
+                v = vmu * fabsf(a.nc[ci]);
                 double t = fma(a.nA[ci], x2, a.nB[ci]);
                 double nxt = fma(t, cur, prev);
                 prev = cur;
@@ -511,7 +552,7 @@ k_split_tables(TcArgs a, const int* __restrict__ ck_base, double2* __restrict__ 
             }
             pmax = fmaxf(pmax, v);
             // max over the ring pairs of this warp, then one atomic per warp
-            float wv = v;
+            float wv = vmu;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) wv = fmaxf(wv, __shfl_xor_sync(0xffffffffu, wv, o));
             if ((threadIdx.x & 31) == 0 && wv > 0.0f) atomicMax(rowmax_bits + ci, __float_as_uint(wv));
@@ -553,33 +594,34 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.pairs = p->t.pairs;
     a.seed_mant = p->t.seed_mant;
     a.seed_exp = p->t.seed_exp;
-    a.nA = p->s.nA; a.nB = p->s.nB; a.nc = p->s.nc;
+    a.nA = p->s.nA; a.nB = p->s.nB; a.nc = p->s.nc; a.nc64 = p->s.nc64;
     a.ck = p->s.ck; a.ck_exp = p->s.ck_exp;
     a.rowmax = (const float*)p->s.rowmax_bits;
     a.pairmax = p->s.pairmax;
     a.colmax = colmax;
     a.err = p->s.err;
-    a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;
+    a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R; a.mlo = p->s.mlo;
     a.ncol = ncols(p, nmaps); a.nalm = p->nalm;
     a.Q = Q;
-    a.dsig = (float)(4.0 * 3.14159265358979323846 / (double)p->npix);
+    a.fs0 = a.fs1 = 1.0;
     a.s0 = s0; a.s1 = s1;
     a.work = nullptr;
     return a;
 }
 
-cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* colmax, double* alm,
-                                   int nmaps, float s0, float s1, cudaStream_t st)
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* Tlo, const float* colmax, double* alm,
+                                   int nmaps, double fs0, double fs1, cudaStream_t st)
 {
     if (p->s.nwork_m2a == 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
     if (e != cudaSuccess) return e;
-    TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_m2a, s0, s1);
+    TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_m2a, 1.0f, 1.0f);
+    a.fs0 = fs0; a.fs1 = fs1;
     a.work = p->s.work_m2a;
     long long nc = ncols(p, nmaps);
     dim3 grid((unsigned)p->s.nwork_m2a, (unsigned)((nc + TN - 1) / TN));
     prof_start("k_leg_m2a_tc", st);
-    k_leg_m2a_tc<<<grid, 256, SMEM_TC, st>>>(T, alm, a);
+    k_leg_m2a_tc<<<grid, 256, SMEM_TC, st>>>(T, Tlo, alm, a);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

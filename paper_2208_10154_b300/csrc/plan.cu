@@ -208,14 +208,43 @@ static cudaError_t build_tables(sht_plan* p)
     if (bhat.empty()) bhat.push_back(make_double2(1, 0));
     if ((e = upload(&p->t.chirp, chirp, &acc)) != cudaSuccess) return e;
     if ((e = upload(&p->t.bhat, bhat, &acc)) != cudaSuccess) return e;
-    {
-        std::vector<float2> twf(tw.size()), chf(chirp.size()), bhf(bhat.size());
-        for (size_t i = 0; i < tw.size(); i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-        for (size_t i = 0; i < chirp.size(); i++) chf[i] = make_float2((float)chirp[i].x, (float)chirp[i].y);
-        for (size_t i = 0; i < bhat.size(); i++) bhf[i] = make_float2((float)bhat[i].x, (float)bhat[i].y);
-        if ((e = upload(&p->t.twiddle_f, twf, &acc)) != cudaSuccess) return e;
-        if ((e = upload(&p->t.chirp_f, chf, &acc)) != cudaSuccess) return e;
-        if ((e = upload(&p->t.bhat_f, bhf, &acc)) != cudaSuccess) return e;
+    if (p->precision != SHT_FP64) {
+        // FP32 hi/lo pairs of every FFT table for the compensated FFT
+        auto split = [](const std::vector<double2>& v, std::vector<float2>& h, std::vector<float2>& l) {
+            h.resize(v.size()); l.resize(v.size());
+            for (size_t i = 0; i < v.size(); i++) {
+                float hx = (float)v[i].x, hy = (float)v[i].y;
+                h[i] = make_float2(hx, hy);
+                l[i] = make_float2((float)(v[i].x - (double)hx), (float)(v[i].y - (double)hy));
+            }
+        };
+        std::vector<float2> h, l;
+        split(tw, h, l);
+        if ((e = upload(&p->t.twiddle_f, h, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.twiddle_l, l, &acc)) != cudaSuccess) return e;
+        split(chirp, h, l);
+        if ((e = upload(&p->t.chirp_f, h, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.chirp_l, l, &acc)) != cudaSuccess) return e;
+        split(bhat, h, l);
+        if ((e = upload(&p->t.bhat_f, h, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.bhat_l, l, &acc)) != cudaSuccess) return e;
+        // exp(+i pi k / N), k < 2N, for every distinct ring length (long double)
+        std::vector<float2> ph, pl;
+        std::vector<long long> off(p->nfft);
+        for (auto& kv : len_index) {
+            int N = kv.first;
+            off[kv.second] = (long long)ph.size();
+            for (int k = 0; k < 2 * N; k++) {
+                ld a = PI_L * k / N;
+                ld c = cosl(a), sn = sinl(a);
+                float hc = (float)c, hs = (float)sn;
+                ph.push_back(make_float2(hc, hs));
+                pl.push_back(make_float2((float)(c - hc), (float)(sn - hs)));
+            }
+        }
+        if ((e = upload(&p->c.phase_h, ph, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.phase_l, pl, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.phase_off, off, &acc)) != cudaSuccess) return e;
     }
 
     // ---- lambda seeds ----
@@ -361,6 +390,7 @@ static cudaError_t build_split_tables(sht_plan* p)
     // each parity chain starts with c_{l0} = c_{l0+2} = 1 (gamma_{l0} = 0).
     std::vector<double> nA(nalm, 0.0), nB(nalm, 0.0);
     std::vector<float> nc(nalm, 0.0f);
+    std::vector<double> nc64(nalm, 0.0);
     for (int m = 0; m <= mmax; m++) {
         auto ainv = [&](int l) -> ld { if (l <= m) return 0; ld L = l, M = m; return sqrtl((L * L - M * M) / (4 * L * L - 1)); };
         auto aa = [&](int l) -> ld { ld L = l, M = m; return sqrtl((4 * L * L - 1) / (L * L - M * M)); };
@@ -381,12 +411,14 @@ static cudaError_t build_split_tables(sht_plan* p)
                 nA[ci] = (double)(alpha * c[j] / cn);
                 nB[ci] = (double)(beta * c[j] / cn);
                 nc[ci] = (float)c[j];
+                nc64[ci] = (double)c[j];
             }
         }
     }
     if ((e = upload(&p->s.nA, nA, &acc)) != cudaSuccess) return e;
     if ((e = upload(&p->s.nB, nB, &acc)) != cudaSuccess) return e;
     if ((e = upload(&p->s.nc, nc, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.nc64, nc64, &acc)) != cudaSuccess) return e;
     // work lists and checkpoint blocks
     const int TM = split_row_tile();
     std::vector<int4> w1, w2;
@@ -424,6 +456,7 @@ static cudaError_t build_split_tables(sht_plan* p)
     auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 256.0); };
     p->s.Q_m2a = qfor((double)R);
     p->s.Q_a2m = qfor((double)(lmax / 2 + 1));
+    p->s.mlo = std::min(mmax + 1, std::max(64, (mmax + 1) / 16));
     p->table_bytes += acc;
     return cudaSuccess;
 }
@@ -435,7 +468,9 @@ static void free_tables(sht_plan* p)
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
                     p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
-    void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
+    void* cp[] = {p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
+    for (void* q : cp) if (q) cudaFree(q);
+    void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m};
     for (void* q : sp) if (q) cudaFree(q);
     if (p->pin_in) cudaFreeHost(p->pin_in);
@@ -457,9 +492,16 @@ static size_t colmax_bytes(const sht_plan* p, int nmaps)
     return p->precision == SHT_FP64 ? 0 : (size_t)(p->mmax + 1) * 2 * (size_t)ncols(p, nmaps) * sizeof(float);
 }
 
+// split form: FP32 remainder of T for the lowest m
+static size_t tlo_bytes(const sht_plan* p, int nmaps)
+{
+    return p->precision == SHT_FP64 ? 0 : (size_t)p->s.mlo * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * sizeof(float);
+}
+
 static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
 {
-    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
+    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256) +
+               round_up(tlo_bytes(p, nmaps), 256);
     if (niter > 0) {
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->npix * sizeof(double), 256);
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
@@ -656,13 +698,13 @@ static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nm
         e = launch_fft_forward_f64(p, map, T, nmaps, st);
         if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, T, alm, nmaps, s0, s1, st);
     } else {
-        // the split kernel folds dsigma into lambda: s0, s1 are relative to map2alm
-        const double dsig = 4.0 * PI_D / (double)p->npix;
+        // s0, s1 are the complete output factors (dsigma for map2alm)
         float* T = (float*)ws;
         unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
-        e = launch_fft_forward_split(p, map, T, cm, nmaps, st);
+        float* Tlo = (float*)((char*)cm + round_up(colmax_bytes(p, nmaps), 256));
+        e = launch_fft_forward_split(p, map, T, Tlo, cm, nmaps, st);
         if (e == cudaSuccess)
-            e = launch_legendre_m2a_tc(p, T, (const float*)cm, alm, nmaps, (float)(s0 / dsig), (float)(s1 / dsig), st);
+            e = launch_legendre_m2a_tc(p, T, Tlo, (const float*)cm, alm, nmaps, s0, s1, st);
     }
     if (e != cudaSuccess) { set_error(std::string("map2alm launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
@@ -688,7 +730,8 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
     if (s != SHT_OK || niter == 0) return s;
     // Algorithm 2: a += map2alm(T - alm2map(a)), niter times
-    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
+    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256) +
+                 round_up(tlo_bytes(p, nmaps), 256);
     double* res = (double*)((char*)ws + off);
     long long nm = (long long)nmaps * p->ncomp * p->npix;
     off += round_up((size_t)nm * sizeof(double), 256);

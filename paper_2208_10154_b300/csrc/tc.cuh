@@ -1,9 +1,10 @@
 // tc.cuh -- inline-PTX helpers for the sm_103a tensor-core path: mbarriers,
 // tensor memory (TMEM) allocation and loads, UMMA shared-memory descriptors and
-// tcgen05.mma (kind::f16 with BF16 operands, FP32 accumulation in TMEM).
+// tcgen05.mma (kind::f16 with FP16 operands, FP32 accumulation in TMEM).
 #pragma once
 #include <cstdint>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace sht {
 namespace tc {
@@ -78,7 +79,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- UMMA
-// K-major operand tile in the 64-byte swizzle layout: rows of 32 BF16 (64 B),
+// K-major operand tile in the 64-byte swizzle layout: rows of 32 16-bit values (64 B),
 // 8-row atoms of 512 B, 16-byte chunk c of row r stored at chunk c ^ ((r>>1)&3).
 // The tile base must be 512-byte aligned; the K = 16 half of a row starts 32 B in.
 __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr)
@@ -107,8 +108,13 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// instruction descriptor: kind::f16, A = B = FP16, D = F32, K-major A and B
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -142,6 +148,29 @@ __device__ __forceinline__ float f64_to_f32_scaled(double v, int sh)
     unsigned int f = (hi & 0x80000000u) | ((unsigned int)ef << 23) | m23;
     return __uint_as_float(f);
 }
+__device__ __forceinline__ float ldexpf_fast_i(float x, int k)
+{
+    int u = __float_as_int(x);
+    int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0f;
+    int en = e + k;
+    if (en <= 0) return 0.0f;
+    return __int_as_float((u & ~0x7F800000) | (en << 23));
+}
+// FP64 v as an unevaluated FP32 pair hi + lo (hi = v rounded to nearest as in
+// f64_to_f32_scaled, lo = the residual rounded to FP32), integer ops only.
+__device__ __forceinline__ void f64_split(double v, float& hi, float& lo)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned int h32 = (unsigned int)(b >> 32);
+    int e = (int)((h32 >> 20) & 0x7FF);
+    hi = f64_to_f32_scaled(v, 0);
+    if (e == 0 || hi == 0.0f) { lo = 0.0f; return; }
+    int r = (int)(b & ((1ull << 29) - 1));              // the 29 dropped mantissa bits
+    if (r >= (1 << 28)) r -= (1 << 29);                 // hi was rounded up
+    if (h32 & 0x80000000u) r = -r;
+    lo = (r == 0) ? 0.0f : ldexpf_fast_i(__int2float_rn(r), e - 1075);
+}
 // exact FP32 -> FP64 (normal inputs; zero and subnormals give 0)
 __device__ __forceinline__ double f32_to_f64(float x)
 {
@@ -172,19 +201,29 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
 }
 
 // Slice v (|v| <= Q <= 256, in units of the quantum) into an exact integer main
-// part and two BF16 residual pieces: v ~ q + r0 + r1, |v - q - r0 - r1| <= 2^-19.
-struct Slices { __nv_bfloat16 q, r0, r1; };
+// part and two FP16 residual pieces: v ~ q + r0 + r1 with |v - q - r0 - r1| <=
+// 2^-22 |v - q| (the integer q is exact in FP16). The residual keeps ~22 bits
+// relative to itself, so elements far below the quantum stay accurate.
 __device__ __forceinline__ void slice3(float v, float& q, float& r0, float& r1)
 {
     const float magic = 12582912.0f;            // 1.5 * 2^23: round to nearest integer
     q = (v + magic) - magic;
     float r = v - q;                             // exact, |r| <= 0.5
-    r0 = __bfloat162float(__float2bfloat16_rn(r));
-    r1 = __bfloat162float(__float2bfloat16_rn(r - r0));
+    r0 = __half2float(__float2half_rn(r));
+    r1 = __half2float(__float2half_rn(r - r0));
 }
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+// the same for an FP32 pair v + vl (|vl| <= 2^-24 |v|): the residual keeps vl
+__device__ __forceinline__ void slice3x(float v, float vl, float& q, float& r0, float& r1)
 {
-    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    const float magic = 12582912.0f;
+    q = (v + magic) - magic;
+    float r = (v - q) + vl;
+    r0 = __half2float(__float2half_rn(r));
+    r1 = __half2float(__float2half_rn(r - r0));
+}
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
+{
+    __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
