@@ -86,15 +86,15 @@ struct SplitTables {
     double* nB = nullptr;          //   mu_{l+2} = (nA x^2 + nB) mu_l + mu_{l-2}
     float* nc = nullptr;           //   lambda_l = nc * mu_l
     double* nc64 = nullptr;        //   the same factor in FP64
-    double2* ck = nullptr;         // map2alm row-tile checkpoints [block][p]
+    float2* nc2 = nullptr;         //   and as an FP32 hi/lo pair
+    double2* ck = nullptr;         // recurrence checkpoints every 32 rows [block][p]
     int* ck_exp = nullptr;
     unsigned int* rowmax_bits = nullptr;   // max_p |lambda_lm| per packed (l, m) (float bits)
     float* pairmax = nullptr;      // max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
     int* err = nullptr;            // device error word of the bounded waits
     int4* work_m2a = nullptr; int nwork_m2a = 0;
     int4* work_a2m = nullptr; int nwork_a2m = 0;
-    float Q_m2a = 0.0f, Q_a2m = 0.0f;
-    int mlo = 0;                   // map2alm keeps an FP32 remainder of T for m < mlo
+    float Q_m2a = 0.0f, Q_a2m = 0.0f;   // integer range of the main slices (K Q^2 <= 2^24)
 };
 
 }  // namespace sht
@@ -160,16 +160,17 @@ cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double
 int legendre_f64_row_tile();
 int legendre_f64_pair_tile();
 // split (tensor-core) form
-cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, float* Tlo,
+cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st);
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
-cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float* T, const float* Tlo, const float* colmax, double* alm,
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, double* alm,
                                    int nmaps, double fs0, double fs1, cudaStream_t st);
 cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const double* alm, const float* colmax, float* G,
                                    int nmaps, float s0, float s1, cudaStream_t st);
 cudaError_t launch_alm_colmax(const sht_plan* p, const double* alm, float* colmax, int nmaps, cudaStream_t st);
 cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base);
 int split_row_tile();
+int split_ck_rows();
 int split_col_tile();
 
 }  // namespace sht

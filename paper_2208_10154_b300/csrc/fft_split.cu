@@ -25,14 +25,26 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-// x * w with w = wh + wl (hi/lo twiddle)
+// x * w with w = wh + wl (hi/lo twiddle); the products of the hi parts are
+// error-free (FMA residuals) and their sum a TwoSum, so only the lo terms round
 __device__ __forceinline__ cx cmulc(const cx& x, float2 wh, float2 wl)
 {
     cx t;
-    t.hr = fmaf(x.hr, wh.x, -(x.hi * wh.y));
-    t.hi = fmaf(x.hr, wh.y, x.hi * wh.x);
-    t.lr = (x.lr * wh.x - x.li * wh.y) + (x.hr * wl.x - x.hi * wl.y);
-    t.li = (x.lr * wh.y + x.li * wh.x) + (x.hr * wl.y + x.hi * wl.x);
+    float s, e;
+    {
+        const float p1 = __fmul_rn(x.hr, wh.x), p2 = __fmul_rn(x.hi, wh.y);
+        const float e1 = fmaf(x.hr, wh.x, -p1), e2 = fmaf(x.hi, wh.y, -p2);
+        two_sum(p1, -p2, s, e);
+        t.hr = s;
+        t.lr = (e + (e1 - e2)) + (x.lr * wh.x - x.li * wh.y) + (x.hr * wl.x - x.hi * wl.y);
+    }
+    {
+        const float p1 = __fmul_rn(x.hr, wh.y), p2 = __fmul_rn(x.hi, wh.x);
+        const float e1 = fmaf(x.hr, wh.y, -p1), e2 = fmaf(x.hi, wh.x, -p2);
+        two_sum(p1, p2, s, e);
+        t.hi = s;
+        t.li = (e + (e1 + e2)) + (x.lr * wh.y + x.li * wh.x) + (x.hr * wl.y + x.hi * wl.x);
+    }
     return t;
 }
 __device__ __forceinline__ cx caddc(const cx& a, const cx& b)
@@ -143,7 +155,7 @@ __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m,
 }
 
 // ---------------------------------------------------------------------------
-// forward: maps -> T[m][q][p][c] (FP32, rounded once from hi + lo) and the
+// forward: maps -> T[m][q][p][c] (FP32 hi/lo pairs) and the
 // per (m, slot, column) maxima used for the tensor-core column quanta.
 // grid.x = block of FWD_PB ring pairs, grid.y = map * ncomp + comp
 // ---------------------------------------------------------------------------
@@ -151,8 +163,7 @@ constexpr int FWD_PB = 64;
 constexpr int FWD_MJ = 8;
 
 __global__ void __launch_bounds__(256)
-k_fftc_forward(const double* __restrict__ map, float* __restrict__ T, float* __restrict__ Tlo, int mlo,
-               unsigned int* __restrict__ colmax,
+k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned int* __restrict__ colmax,
                const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb,
                int fftmax, int R_, int mmax, long long npix, long long ncol)
 {
@@ -201,14 +212,10 @@ k_fftc_forward(const double* __restrict__ map, float* __restrict__ T, float* __r
             float2 e2, o2, el, ol;
             two_sum(E.hr, E.lr, e2.x, el.x); two_sum(E.hi, E.li, e2.y, el.y);
             two_sum(O.hr, O.lr, o2.x, ol.x); two_sum(O.hi, O.li, o2.y, ol.y);
-            float* t0 = T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
-            *reinterpret_cast<float2*>(t0) = e2;
-            *reinterpret_cast<float2*>(t0 + qstride) = o2;
-            if (m < mlo) {     // low m: keep the FP32 remainder too (see the Legendre slicer)
-                float* l0 = Tlo + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
-                *reinterpret_cast<float2*>(l0) = el;
-                *reinterpret_cast<float2*>(l0 + qstride) = ol;
-            }
+            // T keeps hi and lo: (Re hi, Re lo, Im hi, Im lo) per complex column
+            float2* t0 = T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
+            *reinterpret_cast<float4*>(t0) = make_float4(e2.x, el.x, e2.y, el.y);
+            *reinterpret_cast<float4*>(t0 + qstride) = make_float4(o2.x, ol.x, o2.y, ol.y);
             mx[jj][0] = fmaxf(mx[jj][0], fabsf(e2.x));
             mx[jj][1] = fmaxf(mx[jj][1], fabsf(e2.y));
             mx[jj][2] = fmaxf(mx[jj][2], fabsf(o2.x));
@@ -309,7 +316,7 @@ static FftTabsF tabs(const sht_plan* p)
     return t;
 }
 
-cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float* T, float* Tlo,
+cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st)
 {
     size_t sm = (size_t)p->fft_max * sizeof(cx);
@@ -320,7 +327,7 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
     if (e != cudaSuccess) return e;
     dim3 grid((p->R + FWD_PB - 1) / FWD_PB, nmaps * p->ncomp);
     prof_start("k_fftc_forward", st);
-    k_fftc_forward<<<grid, 256, sm, st>>>(map, T, Tlo, p->s.mlo, colmax, p->t.pairs, p->t.fft, tabs(p), p->fft_max, p->R,
+    k_fftc_forward<<<grid, 256, sm, st>>>(map, T, colmax, p->t.pairs, p->t.fft, tabs(p), p->fft_max, p->R,
                                           p->mmax, p->npix, nc);
     prof_stop(st);
     count_launch();

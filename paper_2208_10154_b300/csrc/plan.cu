@@ -391,6 +391,7 @@ static cudaError_t build_split_tables(sht_plan* p)
     std::vector<double> nA(nalm, 0.0), nB(nalm, 0.0);
     std::vector<float> nc(nalm, 0.0f);
     std::vector<double> nc64(nalm, 0.0);
+    std::vector<float2> nc2(nalm, make_float2(0.0f, 0.0f));
     for (int m = 0; m <= mmax; m++) {
         auto ainv = [&](int l) -> ld { if (l <= m) return 0; ld L = l, M = m; return sqrtl((L * L - M * M) / (4 * L * L - 1)); };
         auto aa = [&](int l) -> ld { ld L = l, M = m; return sqrtl((4 * L * L - 1) / (L * L - M * M)); };
@@ -412,6 +413,8 @@ static cudaError_t build_split_tables(sht_plan* p)
                 nB[ci] = (double)(beta * c[j] / cn);
                 nc[ci] = (float)c[j];
                 nc64[ci] = (double)c[j];
+                const float ch = (float)c[j];
+                nc2[ci] = make_float2(ch, (float)(c[j] - (ld)ch));
             }
         }
     }
@@ -419,8 +422,9 @@ static cudaError_t build_split_tables(sht_plan* p)
     if ((e = upload(&p->s.nB, nB, &acc)) != cudaSuccess) return e;
     if ((e = upload(&p->s.nc, nc, &acc)) != cudaSuccess) return e;
     if ((e = upload(&p->s.nc64, nc64, &acc)) != cudaSuccess) return e;
-    // work lists and checkpoint blocks
-    const int TM = split_row_tile();
+    if ((e = upload(&p->s.nc2, nc2, &acc)) != cudaSuccess) return e;
+    // work lists and checkpoint blocks (one block every CKR rows of a chain)
+    const int TM = split_row_tile(), CKR = split_ck_rows();
     std::vector<int4> w1, w2;
     std::vector<int> base((size_t)(mmax + 1) * 2);
     int nblk = 0;
@@ -429,9 +433,9 @@ static cudaError_t build_split_tables(sht_plan* p)
             int lf = m + q;
             int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
             base[m * 2 + q] = nblk;
-            for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk + t));
-            nblk += (nrows + TM - 1) / TM;
-            for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, 0));
+            for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk));
+            for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, nblk));
+            nblk += (nrows + CKR - 1) / CKR;
         }
     p->s.nwork_m2a = (int)w1.size();
     p->s.nwork_a2m = (int)w2.size();
@@ -456,7 +460,6 @@ static cudaError_t build_split_tables(sht_plan* p)
     auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 256.0); };
     p->s.Q_m2a = qfor((double)R);
     p->s.Q_a2m = qfor((double)(lmax / 2 + 1));
-    p->s.mlo = std::min(mmax + 1, std::max(64, (mmax + 1) / 16));
     p->table_bytes += acc;
     return cudaSuccess;
 }
@@ -470,7 +473,7 @@ static void free_tables(sht_plan* p)
     for (void* q : ptrs) if (q) cudaFree(q);
     void* cp[] = {p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
     for (void* q : cp) if (q) cudaFree(q);
-    void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
+    void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m};
     for (void* q : sp) if (q) cudaFree(q);
     if (p->pin_in) cudaFreeHost(p->pin_in);
@@ -479,7 +482,8 @@ static void free_tables(sht_plan* p)
 
 size_t tbuf_bytes(const sht_plan* p, int nmaps)
 {
-    size_t el = p->precision == SHT_FP64 ? sizeof(double) : sizeof(float);
+    // FP64 form: T / G in FP64; split form: T as an FP32 hi/lo pair (G uses half of it)
+    size_t el = p->precision == SHT_FP64 ? sizeof(double) : sizeof(float2);
     return (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * el;
 }
 
@@ -492,16 +496,9 @@ static size_t colmax_bytes(const sht_plan* p, int nmaps)
     return p->precision == SHT_FP64 ? 0 : (size_t)(p->mmax + 1) * 2 * (size_t)ncols(p, nmaps) * sizeof(float);
 }
 
-// split form: FP32 remainder of T for the lowest m
-static size_t tlo_bytes(const sht_plan* p, int nmaps)
-{
-    return p->precision == SHT_FP64 ? 0 : (size_t)p->s.mlo * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * sizeof(float);
-}
-
 static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
 {
-    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256) +
-               round_up(tlo_bytes(p, nmaps), 256);
+    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
     if (niter > 0) {
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->npix * sizeof(double), 256);
         b += round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
@@ -699,12 +696,11 @@ static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nm
         if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, T, alm, nmaps, s0, s1, st);
     } else {
         // s0, s1 are the complete output factors (dsigma for map2alm)
-        float* T = (float*)ws;
+        float2* T = (float2*)ws;
         unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
-        float* Tlo = (float*)((char*)cm + round_up(colmax_bytes(p, nmaps), 256));
-        e = launch_fft_forward_split(p, map, T, Tlo, cm, nmaps, st);
+        e = launch_fft_forward_split(p, map, T, cm, nmaps, st);
         if (e == cudaSuccess)
-            e = launch_legendre_m2a_tc(p, T, Tlo, (const float*)cm, alm, nmaps, s0, s1, st);
+            e = launch_legendre_m2a_tc(p, T, (const float*)cm, alm, nmaps, s0, s1, st);
     }
     if (e != cudaSuccess) { set_error(std::string("map2alm launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
@@ -730,8 +726,7 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
     if (s != SHT_OK || niter == 0) return s;
     // Algorithm 2: a += map2alm(T - alm2map(a)), niter times
-    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256) +
-                 round_up(tlo_bytes(p, nmaps), 256);
+    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
     double* res = (double*)((char*)ws + off);
     long long nm = (long long)nmaps * p->ncomp * p->npix;
     off += round_up((size_t)nm * sizeof(double), 256);

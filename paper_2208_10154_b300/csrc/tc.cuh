@@ -46,6 +46,61 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
     return false;
 }
 
+// acquire at cluster scope: for barriers that other CTAs of the cluster arrive on
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity, int* err, int code)
+{
+    for (int it = 0; it < (1 << 22); it++)
+        if (mbar_try_wait_cl(b, parity)) return true;
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+// ------------------------------------------------------------------ clusters
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_nctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// all threads of all CTAs of the cluster (also a CTA-wide barrier)
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same shared-memory location in CTA `rank`
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+// arrive on a (possibly remote) mbarrier and announce `tx` bytes that an async copy will deliver
+__device__ __forceinline__ void mbar_arrive_expect_tx_cl(uint32_t mbar_cl, uint32_t tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;"
+                 :: "r"(mbar_cl), "r"(tx) : "memory");
+}
+// bulk copy from this CTA's shared memory into the shared memory of a CTA of the
+// cluster; completion is signalled on that CTA's mbarrier (complete_tx)
+__device__ __forceinline__ void bulk_copy_s2cluster(uint32_t dst_cl, uint32_t src, uint32_t bytes, uint32_t mbar_cl)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst_cl), "r"(src), "r"(bytes), "r"(mbar_cl) : "memory");
+}
+
 // ------------------------------------------------------------------- fences
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
@@ -74,6 +129,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                    "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
                    "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+// 32 lanes x 32 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                   "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                   "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                   "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                  : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -128,6 +196,13 @@ __device__ __forceinline__ void umma_commit(uint64_t* b)
                  :: "r"(smem_u32(b)) : "memory");
 }
 
+// the same arrival on the mbarrier at this offset in every CTA of `mask`
+__device__ __forceinline__ void umma_commit_mc(uint64_t* b, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 :: "r"(smem_u32(b)), "h"(mask) : "memory");
+}
+
 // ------------------------------------------------------- number conversions
 // The FP64 pipe of this GPU is ~2 lanes/clk/SM, and cvt between FP64 and FP32
 // runs on it too, so FP64 <-> FP32 conversions are done with integer ops.
@@ -171,6 +246,20 @@ __device__ __forceinline__ void f64_split(double v, float& hi, float& lo)
     if (h32 & 0x80000000u) r = -r;
     lo = (r == 0) ? 0.0f : ldexpf_fast_i(__int2float_rn(r), e - 1075);
 }
+// v * 2^sh as an FP32 pair hi + lo (|v 2^sh| < 2^127; parts below the FP32
+// normal range flush to 0)
+__device__ __forceinline__ void f64_split_scaled(double v, int sh, float& hi, float& lo)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned int h32 = (unsigned int)(b >> 32);
+    int e = (int)((h32 >> 20) & 0x7FF);
+    hi = f64_to_f32_scaled(v, sh);
+    if (e == 0 || hi == 0.0f) { lo = 0.0f; return; }
+    int r = (int)(b & ((1ull << 29) - 1));
+    if (r >= (1 << 28)) r -= (1 << 29);
+    if (h32 & 0x80000000u) r = -r;
+    lo = (r == 0) ? 0.0f : ldexpf_fast_i(__int2float_rn(r), e - 1075 + sh);
+}
 // exact FP32 -> FP64 (normal inputs; zero and subnormals give 0)
 __device__ __forceinline__ double f32_to_f64(float x)
 {
@@ -200,26 +289,20 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
     return __int_as_float((u & ~0x7F800000) | (en << 23));
 }
 
-// Slice v (|v| <= Q <= 256, in units of the quantum) into an exact integer main
-// part and two FP16 residual pieces: v ~ q + r0 + r1 with |v - q - r0 - r1| <=
-// 2^-22 |v - q| (the integer q is exact in FP16). The residual keeps ~22 bits
-// relative to itself, so elements far below the quantum stay accurate.
-__device__ __forceinline__ void slice3(float v, float& q, float& r0, float& r1)
+// Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into
+//     q  = nearest integer                     (exact in FP16 for Q <= 2048)
+//     r0 = v + vl - q rounded to 11 significant bits (Dekker's split; exact in FP16)
+//     r1 = the rest (<= 2^-12 |r0|, 13 bits; the FP16 packing keeps 11 of them)
+// so v + vl = q + r0 + r1 to ~2^-24 |v + vl - q|: ~30 bits of the row / column
+// maximum for large elements, ~22 bits of the element itself for small ones.
+__device__ __forceinline__ void slice3d(float v, float vl, float& q, float& r0, float& r1)
 {
-    const float magic = 12582912.0f;            // 1.5 * 2^23: round to nearest integer
+    const float magic = 12582912.0f;             // 1.5 * 2^23: round to nearest integer
     q = (v + magic) - magic;
-    float r = v - q;                             // exact, |r| <= 0.5
-    r0 = __half2float(__float2half_rn(r));
-    r1 = __half2float(__float2half_rn(r - r0));
-}
-// the same for an FP32 pair v + vl (|vl| <= 2^-24 |v|): the residual keeps vl
-__device__ __forceinline__ void slice3x(float v, float vl, float& q, float& r0, float& r1)
-{
-    const float magic = 12582912.0f;
-    q = (v + magic) - magic;
-    float r = (v - q) + vl;
-    r0 = __half2float(__float2half_rn(r));
-    r1 = __half2float(__float2half_rn(r - r0));
+    const float r = (v - q) + vl;
+    const float c = __fmul_rn(r, 8193.0f);       // 2^13 + 1; __fmul_rn keeps it out of an FMA
+    r0 = c - (c - r);
+    r1 = r - r0;
 }
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
 {

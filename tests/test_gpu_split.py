@@ -1,6 +1,7 @@
-"""GPU parity of the split-precision tensor-core form (BF16 slices on tcgen05,
-FP32 TMEM accumulation, FP64 lambda recurrence) against the CPU oracle, at the
-split-form bar: max |err| / RMS(output) <= 1e-6 per map column."""
+"""GPU parity of the split-precision tensor-core form (FP16 slices on tcgen05,
+FP32 TMEM accumulation, FP64 lambda recurrence, lambda shared across a
+thread-block cluster) against the CPU oracle, at the split-form bar:
+max |err| / RMS(output) <= 1e-6 per map column."""
 import numpy as np
 import pytest
 import torch
@@ -37,6 +38,8 @@ CASES = [
     (1, 3, 3, 2, "flat"),               # smallest grid
     (64, 127, 127, 130, "inv_llp1"),    # two column tiles, ragged
     (128, 300, 300, 7, "inv_llp1"),     # several row / pair tiles
+    (16, 40, 40, 300, "inv_llp1"),      # 5 column tiles: one cluster of 5 CTAs
+    (8, 23, 23, 520, "flat"),           # 9 column tiles: clusters of 5, one padded tile
 ]
 
 
