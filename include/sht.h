@@ -152,6 +152,16 @@ sht_status sht_alm2map_noalloc(sht_plan* plan, const void* alm, void* map, int n
                                void* stream);
 size_t     sht_noalloc_scratch_bytes(void);
 
+/* Device-side status of a plan's tensor-core kernels (no counterpart in the
+ * paper). Every wait inside those kernels is bounded; one that gives up
+ * records a nonzero code (which wait) in a per-plan device word, skips the
+ * rest of its work and lets the kernel finish, so the outputs of that call
+ * are invalid. This call synchronises the plan's device, reads the word into
+ * *code (if code is not NULL), clears it, and returns SHT_ETIMEOUT if it was
+ * set, SHT_OK otherwise (SHT_EINVAL for a NULL plan, SHT_ECUDA on a CUDA
+ * error). FP64 plans always report SHT_OK. */
+sht_status sht_plan_device_status(sht_plan* plan, int* code);
+
 /* Number of kernel launches the most recent call on this thread issued
  * (for the benchmark's launch accounting). */
 int sht_last_launch_count(void);

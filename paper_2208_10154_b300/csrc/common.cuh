@@ -165,9 +165,12 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
 cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, double* alm,
                                    int nmaps, double fs0, double fs1, cudaStream_t st);
-cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const double* alm, const float* colmax, float* G,
+cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, float* G,
                                    int nmaps, float s0, float s1, cudaStream_t st);
-cudaError_t launch_alm_colmax(const sht_plan* p, const double* alm, float* colmax, int nmaps, cudaStream_t st);
+cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,
+                            cudaStream_t st);
+// split form, alm2map: offset of the transposed a_lm (A2) inside the T / G buffer
+size_t split_a2_offset(const sht_plan* p, int nmaps);
 cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base);
 int split_row_tile();
 int split_ck_rows();

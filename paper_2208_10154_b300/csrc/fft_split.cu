@@ -184,8 +184,8 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         const double* xs = g.start_s >= 0 ? map + (long long)mc * npix + g.start_s : nullptr;
         for (int n = threadIdx.x; n < N; n += blockDim.x) {
             cx z = czero();
-            tc::f64_split(xn[n], z.hr, z.lr);
-            if (xs) tc::f64_split(xs[n], z.hi, z.li);
+            tc::f64_split_scaled(xn[n], 0, z.hr, z.lr);
+            if (xs) tc::f64_split_scaled(xs[n], 0, z.hi, z.li);
             buf[placec(f, n)] = chirp_in(f, tb, z, n);
         }
         if (f.bluestein)

@@ -39,6 +39,7 @@
 //   warps 1-3    lambda pieces (32 ring pairs x 32 rows / steps each)
 //   warps 4-7    slice the data (one map column per thread), then the epilogue
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -50,12 +51,14 @@ using namespace tc;
 constexpr int TC_M = 128;                        // map columns per CTA (MMA M)
 constexpr int TC_N = 128;                        // lambda rows per CTA (MMA N, max)
 constexpr int KC = 32;                           // K per pipeline stage (2 MMA K-steps)
-constexpr int NST = 4;                           // pipeline stages
+constexpr int NST = 3;                           // pipeline stages
 constexpr int PR = 32;                           // rows per lambda piece
 constexpr int A_PLANE = TC_M * KC * 2;           // 8 KB (data, one slice)
 constexpr int B_PLANE = TC_N * KC * 2;           // 8 KB (lambda, one slice)
 constexpr int PIECE_BYTES = PR * KC * 2;         // 2 KB of one B plane
 constexpr int STAGE_BYTES = 3 * A_PLANE + 3 * B_PLANE;   // 48 KB
+constexpr int STG_ROW = TC_M * 8;                // one K row of raw data (FP32 hi/lo per column): 1 KB
+constexpr int STG_BYTES = KC * STG_ROW;          // 32 KB: one K chunk of raw data for the CTA's columns
 constexpr uint32_t CORR0 = 128;                  // TMEM columns of the corr ping-pong pair (128 each)
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
 constexpr int MAX_CLUSTER = 8;
@@ -143,20 +146,32 @@ struct TcShared {
     uint64_t accf;             // all MMAs of this CTA done
     uint64_t cdone[2];         // corr accumulator b holds a finished chunk
     uint64_t cfree[2];         // corr accumulator b drained (4 epilogue warps)
+    uint64_t sfull[2];         // raw-data staging buffer b filled (bulk copies)
+    int released;              // highest chunk whose stage is free in every CTA of the cluster
     uint32_t tmem;
     int colexp[TC_M];
     int rowexp[TC_N];          // quantum exponent per lambda row (l or ring pair)
     double cA[TC_N], cB[TC_N]; // map2alm: recurrence coefficients of the tile's rows
     float2 rfac[TC_N];         // map2alm: c_l * factor as an FP32 hi/lo pair
 };
-constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
+constexpr int SMEM_TC = NST * STAGE_BYTES + 2 * STG_BYTES + (int)sizeof(TcShared) + 1024;
 
-// rescale of the scaled-exponent recurrence (mu 2^E)
+// x * 2^-500 by exponent arithmetic (x is either 0 or has a biased exponent
+// above 500 here, or is flushed to 0 if it does not)
+__device__ __forceinline__ double down500(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    return e > 500 ? __longlong_as_double(b - (500ll << 52)) : 0.0;
+}
+// rescale of the scaled-exponent recurrence (mu 2^E). Integer exponent
+// arithmetic instead of an FP64 multiply: FP64 latency is ~185 cycles on
+// this GPU and the rescale test sits on the recurrence's critical path.
 __device__ __forceinline__ void rescale(double& cur, double& prev, int& E)
 {
     if (((__double2hiint(cur) >> 20) & 0x7FF) > 1023 + 500) {
-        cur *= 0x1p-500;
-        prev *= 0x1p-500;
+        cur = down500(cur);
+        prev = down500(prev);
         E += 500;
     }
 }
@@ -172,7 +187,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES);
+    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES + 2 * STG_BYTES);
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, tile = w.z, ckb = w.w;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -219,7 +234,12 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             mbar_init(&sh.empty[s], csize);
         }
         mbar_init(&sh.accf, 1);
-        for (int b = 0; b < 2; b++) { mbar_init(&sh.cdone[b], 1); mbar_init(&sh.cfree[b], 4); }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&sh.cdone[b], 1);
+            mbar_init(&sh.cfree[b], 4);
+            mbar_init(&sh.sfull[b], 1);
+        }
+        sh.released = NST - 1;
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&sh.tmem, 512);
@@ -245,21 +265,18 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 umma_commit(&sh.cdone[kc & 1]);
             }
             umma_commit(&sh.accf);
-            // every CTA of the cluster arrives on this CTA's stage barriers once
-            // per chunk; wait for the last of those arrivals so that none of
-            // them can land after this CTA has exited
-            for (int s = 0; s < NST && s < nch; s++)
-                mbar_wait_cl(&sh.empty[s], ((nch - 1 - s) / NST) & 1, a.err, 7);
         }
     } else if (warp < 4) {
         // ---------------- lambda pieces ----------------
+        // A piece is computed into registers first (32 recurrence steps, ~one
+        // FP64 FMA latency each) and only then does the warp wait for its stage
+        // to be released, so the recurrence overlaps the MMAs of earlier chunks.
         const int total = nch * npieces;
         for (int g = (int)crank + (int)csize * (warp - 1); g < total; g += (int)csize * 3) {
             const int kc = g / npieces, j = g - kc * npieces;
             const int s = kc % NST;
-            const uint32_t u = kc / NST;
-            if (u >= 1 && !__all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 2))) break;
-            uint8_t* B = smem + s * STAGE_BYTES + 3 * A_PLANE;
+            float hb[PR], lb[PR];
+            int prow;                                   // row of the B tile this lane writes (alm2map)
             if (M2A) {
                 // lane = ring pair (k), walking the 32 l rows of piece j
                 const int p = kc * KC + lane;
@@ -274,26 +291,27 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     const double x = a.pairs[p].x;
                     x2 = x * x;
                 }
+                const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
+                double tn = fma(sh.cA[j * PR], x2, sh.cB[j * PR]);
+#pragma unroll
                 for (int i = 0; i < PR; i++) {
-                    const int r = j * PR + i;
-                    float h = 0.0f, lo = 0.0f;
-                    if (live && r < nrows) {
-                        f64_split_scaled(cur, E - sh.rowexp[r], h, lo);
-                        const double t = fma(sh.cA[r], x2, sh.cB[r]);
+                    hb[i] = 0.0f; lb[i] = 0.0f;
+                    if (i < rn) {
+                        const int r = j * PR + i;
+                        if (live) f64_split_scaled(cur, E - sh.rowexp[r], hb[i], lb[i]);
+                        const double t = tn;            // coefficient FMA one step ahead
+                        if (i + 1 < rn) tn = fma(sh.cA[r + 1], x2, sh.cB[r + 1]);
                         const double nxt = fma(t, cur, prev);
                         prev = cur;
                         cur = nxt;
                         rescale(cur, prev, E);
                     }
-                    float q0, q1, q2;
-                    slice3d(h, lo, q0, q1, q2);
-                    const uint32_t off = sw64_off(r, lane);
-                    *reinterpret_cast<__half*>(B + off) = __float2half_rn(q0);
-                    *reinterpret_cast<__half*>(B + B_PLANE + off) = __float2half_rn(q1);
-                    *reinterpret_cast<__half*>(B + 2 * B_PLANE + off) = __float2half_rn(q2);
                 }
+                prow = 0;
             } else {
-                // lane = ring pair (row), walking the 32 l of stage kc
+                // lane = ring pair (row), walking the 32 l of stage kc; the
+                // coefficients of those 32 l are loaded once (lane k holds l_k)
+                // and broadcast with shuffles
                 const int r = j * PR + lane;
                 const int p = n0 + r;
                 const bool live = r < nrows;
@@ -308,37 +326,73 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     x2 = x * x;
                     pe = sh.rowexp[r];
                 }
-#pragma unroll 1
+                double cAk = 0.0, cBk = 0.0;
+                float2 cck = make_float2(0.0f, 0.0f);
+                {
+                    const int k = kc * KC + lane;
+                    if (k < K) {
+                        const long long ci = a_idx(a.lmax, l_first + 2 * k, m);
+                        cAk = a.nA[ci]; cBk = a.nB[ci]; cck = a.nc2[ci];
+                    }
+                }
+                const int kn = min(KC, K - kc * KC);    // valid l of this chunk (warp-uniform)
+                double tn = fma(__shfl_sync(0xffffffffu, cAk, 0), x2, __shfl_sync(0xffffffffu, cBk, 0));
+#pragma unroll
+                for (int i = 0; i < PR; i++) {
+                    hb[i] = 0.0f; lb[i] = 0.0f;
+                    const float c0_ = __shfl_sync(0xffffffffu, cck.x, i);
+                    const float c1_ = __shfl_sync(0xffffffffu, cck.y, i);
+                    const double cAn = __shfl_sync(0xffffffffu, cAk, (i + 1) & (PR - 1));
+                    const double cBn = __shfl_sync(0xffffffffu, cBk, (i + 1) & (PR - 1));
+                    if (i < kn) {
+                        float h = 0.0f, lo = 0.0f;
+                        if (live) f64_split_scaled(cur, E - pe, h, lo);
+                        const float p1 = h * c0_;               // lambda = c_l mu in double-float
+                        hb[i] = p1;
+                        lb[i] = fmaf(h, c0_, -p1) + (h * c1_ + lo * c0_);
+                        const double t = tn;
+                        if (i + 1 < kn) tn = fma(cAn, x2, cBn);
+                        const double nxt = fma(t, cur, prev);
+                        prev = cur;
+                        cur = nxt;
+                        rescale(cur, prev, E);
+                    }
+                }
+                prow = r;
+            }
+            // A warp's pieces can be several chunks apart, more than the parity
+            // of the stage barrier can tell apart, so it waits on the monotonic
+            // count of released chunks that the data warps publish instead.
+            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
+            uint8_t* B = smem + s * STAGE_BYTES + 3 * A_PLANE;
+            if (M2A) {
+#pragma unroll
+                for (int i = 0; i < PR; i++) {
+                    float q0, q1, q2;
+                    slice3d(hb[i], lb[i], q0, q1, q2);
+                    const uint32_t off = sw64_off(j * PR + i, lane);
+                    *reinterpret_cast<__half*>(B + off) = __float2half_rn(q0);
+                    *reinterpret_cast<__half*>(B + B_PLANE + off) = __float2half_rn(q1);
+                    *reinterpret_cast<__half*>(B + 2 * B_PLANE + off) = __float2half_rn(q2);
+                }
+            } else {
+#pragma unroll
                 for (int jj = 0; jj < KC / 8; jj++) {
                     float hv[8], lv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int k = kc * KC + jj * 8 + i;
-                        hv[i] = 0.0f; lv[i] = 0.0f;
-                        if (live && k < K) {
-                            const long long ci = a_idx(a.lmax, l_first + 2 * k, m);
-                            float h, lo;
-                            f64_split_scaled(cur, E - pe, h, lo);
-                            const float2 c = a.nc2[ci];           // lambda = c_l mu in double-float
-                            const float p1 = h * c.x;
-                            hv[i] = p1;
-                            lv[i] = fmaf(h, c.x, -p1) + (h * c.y + lo * c.x);
-                            const double t = fma(a.nA[ci], x2, a.nB[ci]);
-                            const double nxt = fma(t, cur, prev);
-                            prev = cur;
-                            cur = nxt;
-                            rescale(cur, prev, E);
-                        }
-                    }
-                    put3x8(B, B_PLANE, r, jj, hv, lv);
+                    for (int i = 0; i < 8; i++) { hv[i] = hb[jj * 8 + i]; lv[i] = lb[jj * 8 + i]; }
+                    put3x8(B, B_PLANE, prow, jj, hv, lv);
                 }
             }
             fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) {
-                const uint32_t src0 = smem_u32(B) + j * PIECE_BYTES;
-                for (uint32_t d = 0; d < csize; d++) {
-                    if (d == crank) continue;
+            // lane d sends the piece to CTA d of the cluster (its own CTA: a plain arrival)
+            if (lane < (int)csize) {
+                const uint32_t d = (uint32_t)lane;
+                if (d == crank) {
+                    mbar_arrive(&sh.full[s]);
+                } else {
+                    const uint32_t src0 = smem_u32(B) + j * PIECE_BYTES;
                     const uint32_t fb = mapa_shared(smem_u32(&sh.full[s]), d);
                     mbar_arrive_expect_tx_cl(fb, 3 * PIECE_BYTES);
 #pragma unroll
@@ -347,7 +401,6 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                         bulk_copy_s2cluster(mapa_shared(sa, d), sa, PIECE_BYTES, fb);
                     }
                 }
-                mbar_arrive(&sh.full[s]);
             }
         }
     } else {
@@ -381,48 +434,79 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.cfree[b]);
         };
+        // Raw data: K row kc of the CTA's 128 columns is contiguous in global
+        // memory (T[m][q][p][c] for map2alm, the transposed a_lm A2[l,m][c] for
+        // alm2map, both FP32 hi/lo pairs), so one thread moves each chunk with
+        // 32 bulk copies (1 KB each) into staging buffer kc & 1.
+        const int ncv = (int)max(0ll, min((long long)TC_M, a.ncol - c0));   // valid columns of the tile
+        const float2* raw = (const float2*)src;
+        auto fetch = [&](int c) {
+            const int b = c & 1;
+            const int i1 = min(KC, K - c * KC);
+            const uint32_t rowb = (uint32_t)ncv * 8u;
+            mbar_arrive_expect_tx(&sh.sfull[b], rowb * (uint32_t)max(i1, 0));
+            if (rowb == 0) return;
+            const uint32_t dst = smem_u32(smem + NST * STAGE_BYTES + b * STG_BYTES);
+            for (int i = 0; i < i1; i++) {
+                const int k = c * KC + i;
+                const long long row = M2A ? ((long long)m * 2 + q) * a.R + k : a_idx(a.lmax, l_first + 2 * k, m);
+                bulk_copy_g2s(dst + i * STG_ROW, raw + row * a.ncol + c0, rowb, &sh.sfull[b]);
+            }
+        };
+        const bool issuer = (warp == 4 && lane == 0);
+        if (issuer) {
+            if (nch > 0) fetch(0);
+            if (nch > 1) fetch(1);
+        }
+        // the quantum 2^ce as an FP32 factor (exact scaling)
+        const float csc = __int_as_float((127 - ce) << 23);
+        // (a wait that gives up turns dok off; the loop still runs to the end so
+        // that all four data warps keep meeting at the named barrier)
         for (int kc = 0; kc < nch; kc++) {
             const int s = kc % NST;
             const uint32_t u = kc / NST;
-            if (u >= 1 && !__all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 3))) {
-                dok = false;
-                break;
+            if (dok && u >= 1) {
+                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 3));
+                // stage s is free in every CTA of the cluster: release it to the lambda warps
+                if (dok && issuer) publish_counter(&sh.released, kc);
             }
-            uint8_t* A = smem + s * STAGE_BYTES;
+            if (dok) dok = __all_sync(0xffffffffu, mbar_wait(&sh.sfull[kc & 1], (kc >> 1) & 1, a.err, 8));
+            if (dok) {
+                const float2* stg =
+                    reinterpret_cast<const float2*>(smem + NST * STAGE_BYTES + (kc & 1) * STG_BYTES) + t;
+                const int kv = K - kc * KC;             // valid rows of this chunk
+                uint8_t* A = smem + s * STAGE_BYTES;
 #pragma unroll 1
-            for (int jj = 0; jj < KC / 8; jj++) {
-                float hv[8], lv[8];
-                if (M2A) {
-                    const float2* Tq = (const float2*)src + ((long long)m * 2 + q) * qstride;
+                for (int jj = 0; jj < KC / 8; jj++) {
+                    float hv[8], lv[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
-                        const int p = kc * KC + jj * 8 + i;
+                        const int r = jj * 8 + i;
                         float2 x = make_float2(0.0f, 0.0f);
-                        if (cok && p < a.R) x = Tq[(long long)p * a.ncol + cg];
-                        hv[i] = ldexpf_fast(x.x, -ce);
-                        lv[i] = ldexpf_fast(x.y, -ce);
+                        if (cok && r < kv) x = stg[r * TC_M];
+                        hv[i] = x.x * csc;
+                        lv[i] = x.y * csc;
                     }
-                } else {
-                    const double* alm = (const double*)src;
-                    const long long mp = cg >> 1;
-                    const int reim = (int)(cg & 1);
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int k = kc * KC + jj * 8 + i;
-                        double x = 0.0;
-                        if (cok && k < K && !(m == 0 && reim)) {
-                            const int l = l_first + 2 * k;
-                            x = alm[(mp * a.nalm + a_idx(a.lmax, l, m)) * 2 + reim];
-                        }
-                        f64_split_scaled(x, -ce, hv[i], lv[i]);
-                    }
+                    put3x8(A, A_PLANE, t, jj, hv, lv);
                 }
-                put3x8(A, A_PLANE, t, jj, hv, lv);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.full[s]);
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.full[s]);
+            // all four data warps are done with staging buffer kc & 1: refill it
+            named_bar_sync(1, 128);
+            if (dok && issuer && kc + 2 < nch) fetch(kc + 2);
             if (kc >= 2 && dok) drain(kc - 2);
+        }
+        // Tail: wait until every CTA of the cluster has consumed the last use of
+        // each stage. All their MMA commits then have arrived on this CTA's
+        // barriers, so none can land after it exits. (These waits continue the
+        // sequential phase walk of the loop above.)
+        for (int kc = nch; kc < nch + NST && dok; kc++) {
+            const int s = kc % NST;
+            const uint32_t u = kc / NST;
+            if (u >= 1)
+                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 7));
         }
         if (dok) {
             for (int c = (nch >= 2 ? nch - 2 : 0); c < nch; c++) drain(c);
@@ -544,27 +628,58 @@ k_split_tables(TcArgs a, const int* __restrict__ ck_base, double2* __restrict__ 
 }
 
 // ===========================================================================
-// alm2map data scales: max over l in slot q of |a_lm| per column
-// grid = (mmax+1, ceil(ncol/256)); thread = column
+// alm2map input preparation: the a_lm of the batch, transposed to
+// A2[idx(l, m)][col] (col = (map, component, Re/Im)) as FP32 hi/lo pairs, so
+// each K row of the contraction is contiguous, plus the column maxima per
+// (m, slot q, col) for the quanta. Block: 64 l x 32 map-components of one m.
+// grid = (ceil((lmax+1)/64), mmax+1, ceil(nmaps ncomp / 32))
 // ===========================================================================
+constexpr int PREP_L = 64, PREP_M = 32;
 __global__ void __launch_bounds__(256)
-k_alm_colmax(const double* __restrict__ alm, float* __restrict__ colmax, int lmax, long long nalm, long long ncol)
+k_alm_prep(const double* __restrict__ alm, float2* __restrict__ A2, unsigned int* __restrict__ colmax,
+           int lmax, long long nalm, long long ncol)
 {
-    const int m = blockIdx.x;
-    const long long c = (long long)blockIdx.y * blockDim.x + threadIdx.x;
-    if (c >= ncol) return;
-    const long long mc = c >> 1;
-    const int reim = (int)(c & 1);
-    float mx[2] = {0.0f, 0.0f};
-    const double* base = alm + (mc * nalm + a_idx(lmax, m, m)) * 2 + reim;
-    for (int l = m; l <= lmax; l++) {
-        double v = base[(long long)(l - m) * 2];
-        if (m == 0 && reim) v = 0.0;
-        const float f = fabsf(f64_to_f32_scaled(v, 0));
-        mx[(l - m) & 1] = fmaxf(mx[(l - m) & 1], f * 1.0000003f);
+    __shared__ double2 tile[PREP_L][PREP_M + 1];
+    __shared__ float cmx[2][2 * PREP_M];
+    const int m = blockIdx.y;
+    const int l0 = m + blockIdx.x * PREP_L;
+    if (l0 > lmax) return;
+    const long long nmc = ncol / 2;
+    const long long mp0 = (long long)blockIdx.z * PREP_M;
+    const int tid = threadIdx.x;
+    if (tid < 4 * PREP_M) cmx[tid / (2 * PREP_M)][tid % (2 * PREP_M)] = 0.0f;
+    const long long base = a_idx(lmax, l0, m);
+    for (int e = tid; e < PREP_L * PREP_M; e += blockDim.x) {
+        const int j = e / PREP_L, li = e % PREP_L;            // consecutive threads: consecutive l
+        double2 v = make_double2(0.0, 0.0);
+        if (l0 + li <= lmax && mp0 + j < nmc) {
+            v = reinterpret_cast<const double2*>(alm)[(mp0 + j) * nalm + base + li];
+            if (m == 0) v.y = 0.0;
+        }
+        tile[li][j] = v;
     }
-    colmax[((long long)m * 2 + 0) * ncol + c] = mx[0];
-    colmax[((long long)m * 2 + 1) * ncol + c] = mx[1];
+    __syncthreads();
+    const int cc = tid % (2 * PREP_M);                        // column within the block (fixed per thread)
+    float mx[2] = {0.0f, 0.0f};
+    for (int e = tid; e < PREP_L * 2 * PREP_M; e += blockDim.x) {
+        const int li = e / (2 * PREP_M);
+        const long long col = mp0 * 2 + cc;
+        if (l0 + li > lmax || col >= ncol) continue;
+        const double2 v = tile[li][cc >> 1];
+        float h, lo;
+        f64_split_scaled((cc & 1) ? v.y : v.x, 0, h, lo);
+        A2[(base + li) * ncol + col] = make_float2(h, lo);
+        mx[(l0 + li - m) & 1] = fmaxf(mx[(l0 + li - m) & 1], fabsf(h));
+    }
+    for (int qq = 0; qq < 2; qq++)
+        if (mx[qq] > 0.0f) atomicMax(reinterpret_cast<unsigned int*>(&cmx[qq][cc]), __float_as_uint(mx[qq]));
+    __syncthreads();
+    if (tid < 4 * PREP_M) {
+        const int qq = tid / (2 * PREP_M), c = tid % (2 * PREP_M);
+        const long long col = mp0 * 2 + c;
+        const float v = cmx[qq][c];
+        if (col < ncol && v > 0.0f) atomicMax(colmax + ((long long)m * 2 + qq) * ncol + col, __float_as_uint(v));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -589,14 +704,27 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     return a;
 }
 
-// cluster size along the column tiles: all of them up to 8, else the size in
-// 4..8 that wastes the fewest padded tiles (ties: the larger)
+// largest cluster: 8 (portable limit), or SHT_MAX_CLUSTER from the environment
+static int max_cluster()
+{
+    static int mc = [] {
+        const char* e = std::getenv("SHT_MAX_CLUSTER");
+        int v = e ? std::atoi(e) : MAX_CLUSTER;
+        return std::max(1, std::min(v, MAX_CLUSTER));
+    }();
+    return mc;
+}
+
+// cluster size along the column tiles: all of them up to the largest size,
+// else the size in [largest/2, largest] that wastes the fewest padded tiles
+// (ties: the larger)
 static int pick_cluster(long long ntiles)
 {
-    if (ntiles <= MAX_CLUSTER) return (int)std::max(1ll, ntiles);
-    int best = MAX_CLUSTER;
-    long long waste = (MAX_CLUSTER - ntiles % MAX_CLUSTER) % MAX_CLUSTER;
-    for (int c = MAX_CLUSTER - 1; c >= 4; c--) {
+    const int cmax = max_cluster();
+    if (ntiles <= cmax) return (int)std::max(1ll, ntiles);
+    int best = cmax;
+    long long waste = (cmax - ntiles % cmax) % cmax;
+    for (int c = cmax - 1; c >= std::max(1, cmax / 2); c--) {
         long long wc = (c - ntiles % c) % c;
         if (wc < waste) { waste = wc; best = c; }
     }
@@ -648,22 +776,26 @@ cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const flo
     return launch_tc<true>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc", st);
 }
 
-cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const double* alm, const float* colmax, float* G,
+cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, float* G,
                                    int nmaps, float s0, float s1, cudaStream_t st)
 {
     if (p->s.nwork_a2m == 0) return cudaSuccess;
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_a2m);
     a.s0 = s0; a.s1 = s1;
     a.work = p->s.work_a2m;
-    return launch_tc<false>(p, p->s.nwork_a2m, alm, G, a, "k_leg_a2m_tc", st);
+    return launch_tc<false>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc", st);
 }
 
-cudaError_t launch_alm_colmax(const sht_plan* p, const double* alm, float* colmax, int nmaps, cudaStream_t st)
+cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,
+                            cudaStream_t st)
 {
     const long long nc = ncols(p, nmaps);
-    dim3 grid((unsigned)(p->mmax + 1), (unsigned)((nc + 255) / 256));
-    prof_start("k_alm_colmax", st);
-    k_alm_colmax<<<grid, 256, 0, st>>>(alm, colmax, p->lmax, p->nalm, nc);
+    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((p->lmax + PREP_L) / PREP_L), (unsigned)(p->mmax + 1),
+              (unsigned)((nc / 2 + PREP_M - 1) / PREP_M));
+    prof_start("k_alm_prep", st);
+    k_alm_prep<<<grid, 256, 0, st>>>(alm, A2, colmax, p->lmax, p->nalm, nc);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

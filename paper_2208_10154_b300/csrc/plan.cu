@@ -480,14 +480,22 @@ static void free_tables(sht_plan* p)
     if (p->pin_out) cudaFreeHost(p->pin_out);
 }
 
-size_t tbuf_bytes(const sht_plan* p, int nmaps)
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// split form, alm2map: G (FP32) first, then the transposed a_lm A2 (FP32 hi/lo)
+size_t split_a2_offset(const sht_plan* p, int nmaps)
 {
-    // FP64 form: T / G in FP64; split form: T as an FP32 hi/lo pair (G uses half of it)
-    size_t el = p->precision == SHT_FP64 ? sizeof(double) : sizeof(float2);
-    return (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * el;
+    return round_up((size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * sizeof(float), 256);
 }
 
-static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+size_t tbuf_bytes(const sht_plan* p, int nmaps)
+{
+    const size_t n = (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps);
+    if (p->precision == SHT_FP64) return n * sizeof(double);
+    // split form: map2alm keeps T as FP32 hi/lo pairs; alm2map holds G (FP32) and A2
+    const size_t a2 = (size_t)p->nalm * (size_t)ncols(p, nmaps) * sizeof(float2);
+    return std::max(n * sizeof(float2), split_a2_offset(p, nmaps) + a2);
+}
 
 // workspace layout: [T/G buffer][residual map][delta alm] (the last two only
 // for map2alm with niter > 0)
@@ -532,6 +540,25 @@ extern "C" {
 
 const char* sht_last_error(void) { return t_err.c_str(); }
 int sht_last_launch_count(void) { return t_launches; }
+
+sht_status sht_plan_device_status(sht_plan* p, int* code)
+{
+    t_err.clear();
+    if (code) *code = 0;
+    if (!p) { set_error("plan is NULL"); return SHT_EINVAL; }
+    if (!p->s.err) return SHT_OK;
+    SHT_CUDA_TRY(cudaSetDevice(p->device));
+    SHT_CUDA_TRY(cudaDeviceSynchronize());
+    int v = 0;
+    SHT_CUDA_TRY(cudaMemcpy(&v, p->s.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (v != 0) SHT_CUDA_TRY(cudaMemset(p->s.err, 0, sizeof(int)));
+    if (code) *code = v;
+    if (v != 0) {
+        set_error("a bounded device wait gave up (code " + std::to_string(v) + ")");
+        return SHT_ETIMEOUT;
+    }
+    return SHT_OK;
+}
 const char* sht_version(void) { return "libsht 0.1 (sm_103a)"; }
 
 void sht_profile_begin(void)
@@ -677,9 +704,10 @@ static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nm
         if (e == cudaSuccess) e = launch_fft_backward_f64(p, G, map, nmaps, st);
     } else {
         float* G = (float*)ws;
-        float* cm = (float*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
-        e = launch_alm_colmax(p, alm, cm, nmaps, st);
-        if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, alm, cm, G, nmaps, (float)s0, (float)s1, st);
+        float2* A2 = (float2*)((char*)ws + split_a2_offset(p, nmaps));
+        unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
+        e = launch_alm_prep(p, alm, A2, cm, nmaps, st);
+        if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, A2, (const float*)cm, G, nmaps, (float)s0, (float)s1, st);
         if (e == cudaSuccess) e = launch_fft_backward_f32(p, G, map, nmaps, st);
     }
     if (e != cudaSuccess) { set_error(std::string("alm2map launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }

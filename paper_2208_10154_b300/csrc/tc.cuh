@@ -62,6 +62,24 @@ __device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity, int* 
     return false;
 }
 
+// Bounded wait until a monotonic shared-memory counter reaches `target`
+// (acquire); records `code` in *err and returns false after ~2^22 polls.
+__device__ __forceinline__ bool wait_counter(const int* ctr, int target, int* err, int code)
+{
+    for (int it = 0; it < (1 << 22); it++) {
+        int v;
+        asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ctr)) : "memory");
+        if (v >= target) return true;
+        __nanosleep(32);
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+__device__ __forceinline__ void publish_counter(int* ctr, int v)
+{
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(ctr)), "r"(v) : "memory");
+}
+
 // ------------------------------------------------------------------ clusters
 __device__ __forceinline__ uint32_t cluster_ctarank()
 {
@@ -100,6 +118,35 @@ __device__ __forceinline__ void bulk_copy_s2cluster(uint32_t dst_cl, uint32_t sr
     asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  :: "r"(dst_cl), "r"(src), "r"(bytes), "r"(mbar_cl) : "memory");
 }
+
+// arrive on this CTA's mbarrier and announce `tx` bytes of async copies
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t tx)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(b)), "r"(tx) : "memory");
+}
+// 1-D bulk copy global -> this CTA's shared memory (16-byte aligned, size a
+// multiple of 16), completing on an mbarrier of this CTA
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
+// named barrier over `n` threads (id 1..15; id 0 is __syncthreads)
+__device__ __forceinline__ void named_bar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(n) : "memory");
+}
+
+// ------------------------------------------------------ cp.async (LDGSTS)
+// 8-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
 
 // ------------------------------------------------------------------- fences
 __device__ __forceinline__ void fence_proxy_async_smem()
@@ -232,33 +279,24 @@ __device__ __forceinline__ float ldexpf_fast_i(float x, int k)
     if (en <= 0) return 0.0f;
     return __int_as_float((u & ~0x7F800000) | (en << 23));
 }
-// FP64 v as an unevaluated FP32 pair hi + lo (hi = v rounded to nearest as in
-// f64_to_f32_scaled, lo = the residual rounded to FP32), integer ops only.
-__device__ __forceinline__ void f64_split(double v, float& hi, float& lo)
-{
-    unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    unsigned int h32 = (unsigned int)(b >> 32);
-    int e = (int)((h32 >> 20) & 0x7FF);
-    hi = f64_to_f32_scaled(v, 0);
-    if (e == 0 || hi == 0.0f) { lo = 0.0f; return; }
-    int r = (int)(b & ((1ull << 29) - 1));              // the 29 dropped mantissa bits
-    if (r >= (1 << 28)) r -= (1 << 29);                 // hi was rounded up
-    if (h32 & 0x80000000u) r = -r;
-    lo = (r == 0) ? 0.0f : ldexpf_fast_i(__int2float_rn(r), e - 1075);
-}
 // v * 2^sh as an FP32 pair hi + lo (|v 2^sh| < 2^127; parts below the FP32
-// normal range flush to 0)
+// normal range flush to 0). Integer and FP32 operations only: the 29 mantissa
+// bits below hi become lo through the 1.5 * 2^23 magic constant (their lowest
+// 6 bits are dropped, a 2^-46 relative error), with no int-to-float
+// conversion instruction.
 __device__ __forceinline__ void f64_split_scaled(double v, int sh, float& hi, float& lo)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    unsigned int h32 = (unsigned int)(b >> 32);
-    int e = (int)((h32 >> 20) & 0x7FF);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned int h32 = (unsigned int)(b >> 32);
+    const int e = (int)((h32 >> 20) & 0x7FF);
     hi = f64_to_f32_scaled(v, sh);
-    if (e == 0 || hi == 0.0f) { lo = 0.0f; return; }
-    int r = (int)(b & ((1ull << 29) - 1));
-    if (r >= (1 << 28)) r -= (1 << 29);
-    if (h32 & 0x80000000u) r = -r;
-    lo = (r == 0) ? 0.0f : ldexpf_fast_i(__int2float_rn(r), e - 1075 + sh);
+    int r = (int)(b & ((1ull << 29) - 1));              // the 29 dropped mantissa bits
+    r -= (r >= (1 << 28)) ? (1 << 29) : 0;              // hi was rounded up
+    // (r >> 6) 2^-22, exact (|r >> 6| <= 2^22), then times 2^(e - 1075 + 28 + sh)
+    const float fr = (__int_as_float(0x4B400000 + (r >> 6)) - 12582912.0f) * 2.384185791015625e-07f;
+    const int es = e - 1075 + 28 + sh + 127;
+    const float sc = (es > 0 && es < 255 && e != 0) ? __int_as_float(es << 23) : 0.0f;
+    lo = (h32 & 0x80000000u) ? -(fr * sc) : fr * sc;
 }
 // exact FP32 -> FP64 (normal inputs; zero and subnormals give 0)
 __device__ __forceinline__ double f32_to_f64(float x)

@@ -72,6 +72,8 @@ def load() -> ctypes.CDLL:
             f.restype = I
         lib.sht_last_error.restype = ctypes.c_char_p
         lib.sht_last_launch_count.restype = I
+        lib.sht_plan_device_status.argtypes = [P, ctypes.POINTER(I)]
+        lib.sht_plan_device_status.restype = I
         lib.sht_version.restype = ctypes.c_char_p
         lib.sht_profile_begin.restype = None
         lib.sht_profile_end.argtypes = [ctypes.c_char_p, I]
@@ -91,6 +93,13 @@ def sht_last_error() -> str:
 
 def sht_last_launch_count() -> int:
     return load().sht_last_launch_count()
+
+
+def sht_plan_device_status(h) -> int:
+    """Device word of the plan's bounded waits (0 = fine); raises ShtError on a timeout."""
+    code = ctypes.c_int(0)
+    _check(load().sht_plan_device_status(h, ctypes.byref(code)))
+    return code.value
 
 
 def sht_profile_begin() -> None:
@@ -185,6 +194,10 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def device_status(self) -> int:
+        """0 if every bounded device wait of this plan's kernels succeeded; raises otherwise."""
+        return sht_plan_device_status(self.handle)
 
     def workspace_bytes(self, nmaps: int, niter: int = 0) -> int:
         return sht_workspace_bytes(self.handle, nmaps, niter)

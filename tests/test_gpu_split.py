@@ -82,3 +82,19 @@ def test_split_adjoints_and_iteration(orc, sht):
                   orc.map2alm_adjoint(g, nside, lmax)) < TOL
     assert colerr(plan.map2alm(torch.from_numpy(h).cuda(), niter=2).cpu().numpy(),
                   orc.map2alm(h, nside, lmax, niter=2)) < TOL
+
+
+@pytest.mark.parametrize("nside,lmax,nmaps", [(128, 300, 300), (64, 160, 1100)])
+def test_split_clusters_many_chunks(orc, sht, nside, lmax, nmaps):
+    """Several column tiles per cluster and more K chunks than pipeline stages
+    (stage reuse across the cluster); the oracle checks a few maps spread over
+    the column tiles (map columns are independent)."""
+    a = inputs.gaussian_alm(nside + 5, nmaps, 1, lmax, cls=inputs.cl_inv_llp1(lmax))
+    plan = sht.Plan(nside, lmax, None, 0, "split")
+    pick = [0, nmaps // 2 + 1, nmaps - 1]
+    got = plan.alm2map(torch.from_numpy(a).cuda()).cpu().numpy()
+    assert colerr(got[pick], orc.alm2map(a[pick], nside, lmax)) < TOL
+    rng = np.random.default_rng(nside)
+    T = got + 0.01 * np.sqrt(np.mean(got ** 2, axis=-1, keepdims=True)) * rng.standard_normal(got.shape)
+    ga = plan.map2alm(torch.from_numpy(T).cuda()).cpu().numpy()
+    assert colerr(ga[pick], orc.map2alm(T[pick], nside, lmax)) < TOL
