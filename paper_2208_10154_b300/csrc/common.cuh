@@ -71,7 +71,14 @@ struct DevTables {
 };
 
 // lo parts of the FP32 FFT tables and hi/lo ring phase tables (compensated FFT)
+// ring pairs grouped by FFT size (split form: one launch per class)
+struct FftClass {
+    int m;             // FFT size of the class
+    int off, cnt;      // its ring pairs: cls_pairs[off .. off + cnt)
+};
+
 struct CompTables {
+    int* cls_pairs = nullptr;      // ring pair indices ordered by FFT size class
     float2* twiddle_l = nullptr;
     float2* chirp_l = nullptr;
     float2* bhat_l = nullptr;
@@ -111,6 +118,7 @@ struct sht_plan {
     sht::CompTables c;
     std::vector<sht::PairGeom> h_pairs;
     std::vector<sht::FftLen> h_fft;
+    std::vector<sht::FftClass> h_fcls;
     size_t table_bytes = 0;
     // Legendre work lists (m, q, tile, 0) for the FP64 kernels
     int4* work_m2a = nullptr; int nwork_m2a = 0;

@@ -10,8 +10,14 @@
 // Phases e^{+-i pi m / N} come from a hi/lo table per ring length.
 //
 // Structure (Sec. 2.1 eq:mm; Appendix A.1 for m -> bin m mod N) is that of
-// fft.cu: one complex FFT of x_north + i x_south per ring pair, radix-2 in
-// shared memory for power-of-two N, Bluestein otherwise.
+// fft.cu: one complex FFT of x_north + i x_south per ring pair, power-of-two
+// sizes directly, Bluestein's chirp convolution otherwise. Each CTA transforms
+// one ring pair for two map columns at once (so a T / G row write covers 32
+// contiguous bytes) with radix-4 passes (two radix-2 stages per shared-memory
+// round trip), and the rings are launched in classes of equal FFT size so the
+// shared-memory footprint and thread count fit each size.
+#include <algorithm>
+
 #include "common.cuh"
 #include "tc.cuh"
 
@@ -69,70 +75,135 @@ __device__ __forceinline__ float cim(const cx& a) { return a.hi + a.li; }
 
 __device__ __forceinline__ int brev_c(int i, int logm) { return (int)(__brev((unsigned)i) >> (32 - logm)); }
 
-__device__ __forceinline__ void twid(const float2* twh, const float2* twl, int k, bool inv, float2& wh, float2& wl)
-{
-    wh = twh[k]; wl = twl[k];
-    if (inv) { wh.y = -wh.y; wl.y = -wl.y; }
-}
-
-__device__ void fftc_dif(cx* buf, int M, int fftmax, const float2* twh, const float2* twl, bool inv)
-{
-    for (int h = M >> 1; h >= 1; h >>= 1) {
-        int step = fftmax / (2 * h);
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-            int k = b & (h - 1);
-            int i0 = ((b - k) << 1) + k, i1 = i0 + h;
-            float2 wh, wl;
-            twid(twh, twl, k * step, inv, wh, wl);
-            cx a = buf[i0], c = buf[i1];
-            buf[i0] = caddc(a, c);
-            buf[i1] = cmulc(csubc(a, c), wh, wl);
-        }
-        __syncthreads();
-    }
-}
-
-__device__ void fftc_dit(cx* buf, int M, int fftmax, const float2* twh, const float2* twl, bool inv)
-{
-    for (int h = 1; h < M; h <<= 1) {
-        int step = fftmax / (2 * h);
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-            int k = b & (h - 1);
-            int i0 = ((b - k) << 1) + k, i1 = i0 + h;
-            float2 wh, wl;
-            twid(twh, twl, k * step, inv, wh, wl);
-            cx t = cmulc(buf[i1], wh, wl);
-            cx a = buf[i0];
-            buf[i0] = caddc(a, t);
-            buf[i1] = csubc(a, t);
-        }
-        __syncthreads();
-    }
-}
+// a * (-i) and a * (+i): component swaps, exact
+__device__ __forceinline__ cx cmul_mi(const cx& a) { cx r; r.hr = a.hi; r.lr = a.li; r.hi = -a.hr; r.li = -a.lr; return r; }
+__device__ __forceinline__ cx cmul_pi(const cx& a) { cx r; r.hr = -a.hi; r.lr = -a.li; r.hi = a.hr; r.li = a.lr; return r; }
 
 struct FftTabsF {
-    const float2 *twh, *twl;      // exp(-2 pi i t / fftmax), hi / lo
+    const float2 *twh, *twl;      // exp(-2 pi i t / fftmax), t < fftmax / 2, hi / lo
     const float2 *chh, *chl;      // Bluestein chirp, hi / lo
     const float2 *bhh, *bhl;      // Bluestein filter spectrum (bit-reversed), hi / lo
     const float2 *phh, *phl;      // exp(+i pi k / N), k < 2N, per ring length, hi / lo
     const long long* phoff;       // offset of each ring length's phase table
 };
 
-// forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of data placed by placec()
-__device__ void dftc_forward(cx* buf, const FftLen& f, int fftmax, const FftTabsF& t)
+__device__ __forceinline__ void twid(const FftTabsF& t, int idx, bool inv, float2& wh, float2& wl)
 {
-    int M = f.m;
+    wh = t.twh[idx]; wl = t.twl[idx];
+    if (inv) { wh.y = -wh.y; wl.y = -wl.y; }
+}
+
+// In-place decimation-in-time FFTs of nb sequences of M = 2^L points stored
+// back to back in buf, input in bit-reversed order, output natural. Two
+// radix-2 stages (spans h and 2h) per pass; W = exp(-+2 pi i / M).
+__device__ void fft_dit(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, bool inv)
+{
+    const int M = 1 << L;
+    int lh = 0;
+    if (L & 1) {                                     // one radix-2 stage of span 1 (twiddle 1)
+        for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
+            cx* x = buf + 2 * b;
+            const cx a = x[0], c = x[1];
+            x[0] = caddc(a, c);
+            x[1] = csubc(a, c);
+        }
+        __syncthreads();
+        lh = 1;
+    }
+    for (; lh + 2 <= L; lh += 2) {
+        const int h = 1 << lh;
+        const int s1 = fftmax >> (lh + 1), s2 = fftmax >> (lh + 2);
+        const int ng = M >> 2;                       // groups per sequence
+        for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
+            const int f = b >> (L - 2), g = b & (ng - 1);
+            const int k = g & (h - 1);
+            cx* y = buf + f * M + ((g - k) << 2) + k;
+            cx x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
+            if (k != 0) {
+                float2 w1h, w1l, w2h, w2l;
+                twid(t, k * s1, inv, w1h, w1l);
+                twid(t, k * s2, inv, w2h, w2l);
+                x1 = cmulc(x1, w1h, w1l);
+                x3 = cmulc(x3, w1h, w1l);
+                const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
+                const cx u2 = cmulc(b2, w2h, w2l);
+                const cx u3 = inv ? cmul_pi(cmulc(b3, w2h, w2l)) : cmul_mi(cmulc(b3, w2h, w2l));
+                y[0] = caddc(b0, u2); y[2 * h] = csubc(b0, u2);
+                y[h] = caddc(b1, u3); y[3 * h] = csubc(b1, u3);
+            } else {
+                const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
+                const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
+                y[0] = caddc(b0, b2); y[2 * h] = csubc(b0, b2);
+                y[h] = caddc(b1, u3); y[3 * h] = csubc(b1, u3);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// In-place decimation-in-frequency FFTs (natural input, bit-reversed output),
+// two radix-2 stages (spans h and h/2) per pass.
+__device__ void fft_dif(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, bool inv)
+{
+    const int M = 1 << L;
+    int lh = L - 1;
+    for (; lh >= 1; lh -= 2) {
+        const int h = 1 << lh, hq = h >> 1;
+        const int s1 = fftmax >> (lh + 1), s2 = fftmax >> lh;
+        const int ng = M >> 2;
+        for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
+            const int f = b >> (L - 2), g = b & (ng - 1);
+            const int k = g & (hq - 1);
+            cx* y = buf + f * M + ((g - k) << 2) + k;
+            const cx x0 = y[0], x1 = y[hq], x2 = y[h], x3 = y[h + hq];
+            cx c0 = caddc(x0, x2), c2 = csubc(x0, x2), c1 = caddc(x1, x3), c3 = csubc(x1, x3);
+            c3 = inv ? cmul_pi(c3) : cmul_mi(c3);
+            if (k != 0) {
+                float2 v1h, v1l, v2h, v2l;
+                twid(t, k * s1, inv, v1h, v1l);
+                twid(t, k * s2, inv, v2h, v2l);
+                c2 = cmulc(c2, v1h, v1l);
+                c3 = cmulc(c3, v1h, v1l);
+                y[0] = caddc(c0, c1); y[hq] = cmulc(csubc(c0, c1), v2h, v2l);
+                y[h] = caddc(c2, c3); y[h + hq] = cmulc(csubc(c2, c3), v2h, v2l);
+            } else {
+                y[0] = caddc(c0, c1); y[hq] = csubc(c0, c1);
+                y[h] = caddc(c2, c3); y[h + hq] = csubc(c2, c3);
+            }
+        }
+        __syncthreads();
+    }
+    if (lh == 0) {                                   // last radix-2 stage of span 1
+        for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
+            cx* x = buf + 2 * b;
+            const cx a = x[0], c = x[1];
+            x[0] = caddc(a, c);
+            x[1] = csubc(a, c);
+        }
+        __syncthreads();
+    }
+}
+
+// forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of nb sequences placed by placec()
+__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, int fftmax, const FftTabsF& t)
+{
+    const int M = f.m, L = 31 - __clz(M);
     if (!f.bluestein) {
-        fftc_dit(buf, M, fftmax, t.twh, t.twl, false);
+        fft_dit(buf, nb, L, fftmax, t, false);
         return;
     }
-    fftc_dif(buf, M, fftmax, t.twh, t.twl, false);
-    for (int i = threadIdx.x; i < M; i += blockDim.x) buf[i] = cmulc(buf[i], t.bhh[f.bhat + i], t.bhl[f.bhat + i]);
+    fft_dif(buf, nb, L, fftmax, t, false);
+    for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
+        const int ii = i & (M - 1);
+        buf[i] = cmulc(buf[i], t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
+    }
     __syncthreads();
-    fftc_dit(buf, M, fftmax, t.twh, t.twl, true);
+    fft_dit(buf, nb, L, fftmax, t, true);
     const float inv = 1.0f / (float)M;
-    for (int k = threadIdx.x; k < f.n; k += blockDim.x)
-        buf[k] = cscale(cmulc(buf[k], t.chh[f.chirp + k], t.chl[f.chirp + k]), inv);
+    for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
+        const int s = i / f.n, k = i - s * f.n;
+        buf[s * M + k] = cscale(cmulc(buf[s * M + k], t.chh[f.chirp + k], t.chl[f.chirp + k]), inv);
+    }
     __syncthreads();
 }
 
@@ -155,153 +226,199 @@ __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m,
 }
 
 // ---------------------------------------------------------------------------
-// forward: maps -> T[m][q][p][c] (FP32 hi/lo pairs) and the
-// per (m, slot, column) maxima used for the tensor-core column quanta.
-// grid.x = block of FWD_PB ring pairs, grid.y = map * ncomp + comp
+// forward: maps -> T[m][q][p][c] (FP32 hi/lo pairs) and the per (m, slot,
+// column) maxima used for the tensor-core column quanta. One launch per FFT
+// size class; grid.x = block of FWD_PB ring pairs of the class, grid.y = pair
+// of map columns (map * ncomp + comp).
 // ---------------------------------------------------------------------------
 constexpr int FWD_PB = 64;
-constexpr int FWD_MJ = 8;
 
-__global__ void __launch_bounds__(256)
+// NT threads; each thread owns m = threadIdx.x + jj NT, jj < 4 (mmax < 4 NT)
+template <int NT>
+__global__ void __launch_bounds__(NT)
 k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned int* __restrict__ colmax,
-               const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb,
-               int fftmax, int R_, int mmax, long long npix, long long ncol)
+               const int* __restrict__ cls, int ncls, const PairGeom* __restrict__ pairs,
+               const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax, int M, int R_, int mmax,
+               long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    const int mc = blockIdx.y;
-    const long long col = (long long)mc * 2;
+    const int mc0 = blockIdx.y * mpc;
+    const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
-    float mx[FWD_MJ][4];
+    constexpr int FWD_MJ = 4;
+    float mx[FWD_MJ][2][4];
 #pragma unroll
-    for (int j = 0; j < FWD_MJ; j++) mx[j][0] = mx[j][1] = mx[j][2] = mx[j][3] = 0.0f;
-    const int pend = min(R_, (blockIdx.x + 1) * FWD_PB);
-    for (int p = blockIdx.x * FWD_PB; p < pend; p++) {
+    for (int j = 0; j < FWD_MJ; j++)
+#pragma unroll
+        for (int s = 0; s < 2; s++) mx[j][s][0] = mx[j][s][1] = mx[j][s][2] = mx[j][s][3] = 0.0f;
+    const int iend = min(ncls, (int)(blockIdx.x + 1) * FWD_PB);
+    for (int ip = blockIdx.x * FWD_PB; ip < iend; ip++) {
+        const int p = cls[ip];
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
         const int N = g.n;
-        const double* xn = map + (long long)mc * npix + g.start_n;
-        const double* xs = g.start_s >= 0 ? map + (long long)mc * npix + g.start_s : nullptr;
-        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        for (int e = threadIdx.x; e < nb * N; e += NT) {
+            const int s = e / N, n = e - s * N;
+            const double* mp = map + (long long)(mc0 + s) * npix;
             cx z = czero();
-            tc::f64_split_scaled(xn[n], 0, z.hr, z.lr);
-            if (xs) tc::f64_split_scaled(xs[n], 0, z.hi, z.li);
-            buf[placec(f, n)] = chirp_in(f, tb, z, n);
+            tc::f64_split_scaled(mp[g.start_n + n], 0, z.hr, z.lr);
+            if (g.start_s >= 0) tc::f64_split_scaled(mp[g.start_s + n], 0, z.hi, z.li);
+            buf[s * M + placec(f, n)] = chirp_in(f, tb, z, n);
         }
         if (f.bluestein)
-            for (int i = f.n + threadIdx.x; i < f.m; i += blockDim.x) buf[i] = czero();
+            for (int e = threadIdx.x; e < nb * (M - N); e += NT) {
+                const int s = e / (M - N), i = e - s * (M - N);
+                buf[s * M + N + i] = czero();
+            }
         __syncthreads();
-        dftc_forward(buf, f, fftmax, tb);
+        dftc_forward(buf, nb, f, fftmax, tb);
 #pragma unroll
         for (int jj = 0; jj < FWD_MJ; jj++) {
-            const int m = threadIdx.x + jj * 256;
+            const int m = threadIdx.x + jj * NT;
             if (m > mmax) break;
-            const int j = m % N, jm = (N - j) % N;
-            const cx a = buf[j], b = cconjc(buf[jm]);
-            // Xn = (a + conj b)/2, Xs = (a - conj b)/(2i)
-            cx Xn = cscale(caddc(a, b), 0.5f);
-            cx d = cscale(csubc(a, b), 0.5f);
-            cx Xs; Xs.hr = d.hi; Xs.lr = d.li; Xs.hi = -d.hr; Xs.li = -d.lr;
-            if (g.phi0 != 0.0) {
-                float2 ph, pl;
-                phase(tb, g.fft, N, m, true, ph, pl);
-                Xn = cmulc(Xn, ph, pl);
-                Xs = cmulc(Xs, ph, pl);
+            const int j = m % N, jm = j ? N - j : 0;
+            float2 ph, pl;
+            if (g.phi0 != 0.0) phase(tb, g.fft, N, m, true, ph, pl);
+            float4 ev[2], ov[2];
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                if (s >= nb) break;
+                const cx a = buf[s * M + j], b = cconjc(buf[s * M + jm]);
+                // Xn = (a + conj b)/2, Xs = (a - conj b)/(2i)
+                cx Xn = cscale(caddc(a, b), 0.5f);
+                const cx d = cscale(csubc(a, b), 0.5f);
+                cx Xs; Xs.hr = d.hi; Xs.lr = d.li; Xs.hi = -d.hr; Xs.li = -d.lr;
+                if (g.phi0 != 0.0) { Xn = cmulc(Xn, ph, pl); Xs = cmulc(Xs, ph, pl); }
+                const cx E = caddc(Xn, Xs), O = csubc(Xn, Xs);
+                float2 e2, o2, el, ol;
+                two_sum(E.hr, E.lr, e2.x, el.x); two_sum(E.hi, E.li, e2.y, el.y);
+                two_sum(O.hr, O.lr, o2.x, ol.x); two_sum(O.hi, O.li, o2.y, ol.y);
+                // T keeps hi and lo: (Re hi, Re lo, Im hi, Im lo) per complex column
+                ev[s] = make_float4(e2.x, el.x, e2.y, el.y);
+                ov[s] = make_float4(o2.x, ol.x, o2.y, ol.y);
+                mx[jj][s][0] = fmaxf(mx[jj][s][0], fabsf(e2.x));
+                mx[jj][s][1] = fmaxf(mx[jj][s][1], fabsf(e2.y));
+                mx[jj][s][2] = fmaxf(mx[jj][s][2], fabsf(o2.x));
+                mx[jj][s][3] = fmaxf(mx[jj][s][3], fabsf(o2.y));
             }
-            const cx E = caddc(Xn, Xs), O = csubc(Xn, Xs);
-            float2 e2, o2, el, ol;
-            two_sum(E.hr, E.lr, e2.x, el.x); two_sum(E.hi, E.li, e2.y, el.y);
-            two_sum(O.hr, O.lr, o2.x, ol.x); two_sum(O.hi, O.li, o2.y, ol.y);
-            // T keeps hi and lo: (Re hi, Re lo, Im hi, Im lo) per complex column
-            float2* t0 = T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + col;
-            *reinterpret_cast<float4*>(t0) = make_float4(e2.x, el.x, e2.y, el.y);
-            *reinterpret_cast<float4*>(t0 + qstride) = make_float4(o2.x, ol.x, o2.y, ol.y);
-            mx[jj][0] = fmaxf(mx[jj][0], fabsf(e2.x));
-            mx[jj][1] = fmaxf(mx[jj][1], fabsf(e2.y));
-            mx[jj][2] = fmaxf(mx[jj][2], fabsf(o2.x));
-            mx[jj][3] = fmaxf(mx[jj][3], fabsf(o2.y));
+            float4* t0 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + mc0 * 2);
+            float4* t1 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 1) * qstride + (long long)p * ncol + mc0 * 2);
+            t0[0] = ev[0];
+            t1[0] = ov[0];
+            if (nb == 2) { t0[1] = ev[1]; t1[1] = ov[1]; }
         }
         __syncthreads();
     }
 #pragma unroll
     for (int jj = 0; jj < FWD_MJ; jj++) {
-        const int m = threadIdx.x + jj * 256;
+        const int m = threadIdx.x + jj * NT;
         if (m > mmax) break;
-        unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
-        unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
-        if (mx[jj][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][0]));
-        if (mx[jj][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][1]));
-        if (mx[jj][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][2]));
-        if (mx[jj][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][3]));
+#pragma unroll
+        for (int s = 0; s < 2; s++) {
+            if (s >= nb) break;
+            const long long col = (long long)(mc0 + s) * 2;
+            unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
+            unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
+            if (mx[jj][s][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][s][0]));
+            if (mx[jj][s][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][s][1]));
+            if (mx[jj][s][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][s][2]));
+            if (mx[jj][s][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][s][3]));
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // backward: G[m][q][p][c] (FP32) -> maps. Every m is folded onto bin m mod N
 // with weight w_0 = 1, w_{m>0} = 2 and phase e^{+i m phi0}; the real ring is
-// the IDFT of the Hermitian part. grid.x = ring pair, grid.y = map * ncomp + comp.
+// the IDFT of the Hermitian part. One launch per FFT size class; grid.x = ring
+// pair of the class, grid.y = pair of map columns.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const PairGeom* __restrict__ pairs,
-                const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax, int R_, int mmax, long long npix,
-                long long ncol)
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls,
+                const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax,
+                int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    const int p = blockIdx.x;
-    const int mc = blockIdx.y;
+    const int p = cls[blockIdx.x];
+    const int mc0 = blockIdx.y * mpc;
+    const int nb = min(mpc, nmc - mc0);
     const PairGeom g = pairs[p];
     const FftLen f = ffts[g.fft];
     const int N = g.n;
-    const long long col = (long long)mc * 2;
     const long long qstride = (long long)R_ * ncol;
-    const float* g0 = G + (long long)p * ncol + col;
-    for (int j = threadIdx.x; j <= N / 2; j += blockDim.x) {
-        int jj[2] = {j, (N - j) % N};
-        cx Bn[2], Bs[2];
+    const float* g0 = G + (long long)p * ncol + mc0 * 2;
+    for (int j = threadIdx.x; j <= N / 2; j += NT) {
+        const int jj[2] = {j, (N - j) % N};
+        cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][map]
+#pragma unroll
         for (int t = 0; t < 2; t++) {
-            cx sn = czero(), ss = czero();
+            cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
             for (int m = jj[t]; m <= mmax; m += N) {
                 const float* e = g0 + (long long)m * 2 * qstride;
-                const float2 E = *reinterpret_cast<const float2*>(e);
-                const float2 O = *reinterpret_cast<const float2*>(e + qstride);
-                const float w = m ? 2.0f : 1.0f;
-                cx tn, ts;
-                two_sum(E.x, O.x, tn.hr, tn.lr); two_sum(E.y, O.y, tn.hi, tn.li);
-                two_sum(E.x, -O.x, ts.hr, ts.lr); two_sum(E.y, -O.y, ts.hi, ts.li);
-                tn = cscale(tn, w); ts = cscale(ts, w);
-                if (g.phi0 != 0.0) {
-                    float2 ph, pl;
-                    phase(tb, g.fft, N, m, false, ph, pl);
-                    tn = cmulc(tn, ph, pl);
-                    ts = cmulc(ts, ph, pl);
+                float4 E4, O4;
+                if (nb == 2 && (ncol & 3) == 0) {          // 16-byte aligned: ncol a multiple of 4
+                    E4 = *reinterpret_cast<const float4*>(e);
+                    O4 = *reinterpret_cast<const float4*>(e + qstride);
+                } else if (nb == 2) {
+                    const float2 a0 = *reinterpret_cast<const float2*>(e), a1 = *reinterpret_cast<const float2*>(e + 2);
+                    const float2 b0 = *reinterpret_cast<const float2*>(e + qstride);
+                    const float2 b1 = *reinterpret_cast<const float2*>(e + qstride + 2);
+                    E4 = make_float4(a0.x, a0.y, a1.x, a1.y);
+                    O4 = make_float4(b0.x, b0.y, b1.x, b1.y);
+                } else {
+                    const float2 E2 = *reinterpret_cast<const float2*>(e), O2 = *reinterpret_cast<const float2*>(e + qstride);
+                    E4 = make_float4(E2.x, E2.y, 0.0f, 0.0f);
+                    O4 = make_float4(O2.x, O2.y, 0.0f, 0.0f);
                 }
-                sn = caddc(sn, tn);
-                ss = caddc(ss, ts);
+                const float w = m ? 2.0f : 1.0f;
+                float2 ph, pl;
+                if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, ph, pl);
+#pragma unroll
+                for (int s = 0; s < 2; s++) {
+                    const float er = s ? E4.z : E4.x, ei = s ? E4.w : E4.y;
+                    const float orr = s ? O4.z : O4.x, oi = s ? O4.w : O4.y;
+                    cx tn, ts;
+                    two_sum(er, orr, tn.hr, tn.lr); two_sum(ei, oi, tn.hi, tn.li);
+                    two_sum(er, -orr, ts.hr, ts.lr); two_sum(ei, -oi, ts.hi, ts.li);
+                    tn = cscale(tn, w); ts = cscale(ts, w);
+                    if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
+                    sn[s] = caddc(sn[s], tn);
+                    ss[s] = caddc(ss[s], ts);
+                }
             }
-            Bn[t] = sn; Bs[t] = ss;
+            Bn[t][0] = sn[0]; Bn[t][1] = sn[1]; Bs[t][0] = ss[0]; Bs[t][1] = ss[1];
         }
+#pragma unroll
         for (int t = 0; t < 2; t++) {
-            int jt = jj[t];
+            const int jt = jj[t];
             if (t == 1 && jt == jj[0]) break;
-            // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
-            cx hn = cscale(caddc(Bn[t], cconjc(Bn[1 - t])), 0.5f);
-            cx hs = cscale(caddc(Bs[t], cconjc(Bs[1 - t])), 0.5f);
-            cx ihs; ihs.hr = -hs.hi; ihs.lr = -hs.li; ihs.hi = hs.hr; ihs.li = hs.lr;
-            cx z = cconjc(caddc(hn, ihs));
-            buf[placec(f, jt)] = chirp_in(f, tb, z, jt);
+#pragma unroll
+            for (int s = 0; s < 2; s++) {
+                if (s >= nb) break;
+                // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
+                const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
+                const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
+                const cx z = cconjc(caddc(hn, cmul_pi(hs)));
+                buf[s * M + placec(f, jt)] = chirp_in(f, tb, z, jt);
+            }
         }
     }
     if (f.bluestein)
-        for (int i = f.n + threadIdx.x; i < f.m; i += blockDim.x) buf[i] = czero();
+        for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
+            const int s = e / (M - N), i = e - s * (M - N);
+            buf[s * M + N + i] = czero();
+        }
     __syncthreads();
-    dftc_forward(buf, f, fftmax, tb);
-    double* xn = map + (long long)mc * npix + g.start_n;
-    double* xs = g.start_s >= 0 ? map + (long long)mc * npix + g.start_s : nullptr;
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        const cx z = buf[n];                 // conj of the inverse transform
-        xn[n] = tc::f32_to_f64(cre(z));
-        if (xs) xs[n] = -tc::f32_to_f64(cim(z));
+    dftc_forward(buf, nb, f, fftmax, tb);
+    for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
+        const int s = e / N, n = e - s * N;
+        const cx z = buf[s * M + n];               // conj of the inverse transform
+        double* mp = map + (long long)(mc0 + s) * npix;
+        mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
+        if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi) + tc::f32_to_f64(z.li));
     }
 }
 
@@ -316,35 +433,77 @@ static FftTabsF tabs(const sht_plan* p)
     return t;
 }
 
+// FFT size classes of the plan: launch configuration per class (two map
+// columns per CTA while their buffers fit in 128 KB of shared memory)
+static void class_cfg(int M, int mmax, int& nt, int& mpc, size_t& sm)
+{
+    nt = (M >= 4096 || mmax >= 1024) ? 512 : 256;
+    mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
+    sm = (size_t)mpc * M * sizeof(cx);
+}
+
+static cudaError_t set_smem(const void* fn, const sht_plan* p)
+{
+    size_t mx = 0;
+    for (const FftClass& c : p->h_fcls) {
+        int nt, mpc; size_t sm;
+        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        mx = std::max(mx, sm);
+    }
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+}
+
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st)
 {
-    size_t sm = (size_t)p->fft_max * sizeof(cx);
-    cudaError_t e = cudaFuncSetAttribute(k_fftc_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = set_smem((const void*)k_fftc_forward<256>, p);
+    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_forward<512>, p);
     if (e != cudaSuccess) return e;
-    long long nc = ncols(p, nmaps);
+    const long long nc = ncols(p, nmaps);
+    const int nmc = nmaps * p->ncomp;
     e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    dim3 grid((p->R + FWD_PB - 1) / FWD_PB, nmaps * p->ncomp);
-    prof_start("k_fftc_forward", st);
-    k_fftc_forward<<<grid, 256, sm, st>>>(map, T, colmax, p->t.pairs, p->t.fft, tabs(p), p->fft_max, p->R,
-                                          p->mmax, p->npix, nc);
-    prof_stop(st);
-    count_launch();
+    for (const FftClass& c : p->h_fcls) {
+        int nt, mpc; size_t sm;
+        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        dim3 grid((c.cnt + FWD_PB - 1) / FWD_PB, (nmc + mpc - 1) / mpc);
+        prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
+        if (nt == 512)
+            k_fftc_forward<512><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+                                                      p->t.fft, tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix, nc,
+                                                      nmc, mpc);
+        else
+            k_fftc_forward<256><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+                                                      p->t.fft, tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix, nc,
+                                                      nmc, mpc);
+        prof_stop(st);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
 {
-    size_t sm = (size_t)p->fft_max * sizeof(cx);
-    cudaError_t e = cudaFuncSetAttribute(k_fftc_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = set_smem((const void*)k_fftc_backward<256>, p);
+    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_backward<512>, p);
     if (e != cudaSuccess) return e;
-    dim3 grid(p->R, nmaps * p->ncomp);
-    prof_start("k_fftc_backward", st);
-    k_fftc_backward<<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, tabs(p), p->fft_max, p->R, p->mmax,
-                                           p->npix, ncols(p, nmaps));
-    prof_stop(st);
-    count_launch();
+    const int nmc = nmaps * p->ncomp;
+    for (const FftClass& c : p->h_fcls) {
+        int nt, mpc; size_t sm;
+        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        dim3 grid(c.cnt, (nmc + mpc - 1) / mpc);
+        prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
+        if (nt == 512)
+            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, p->t.pairs, p->t.fft, tabs(p),
+                                                       p->fft_max, c.m, p->R, p->mmax, p->npix, ncols(p, nmaps),
+                                                       nmc, mpc);
+        else
+            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, p->t.pairs, p->t.fft, tabs(p),
+                                                       p->fft_max, c.m, p->R, p->mmax, p->npix, ncols(p, nmaps),
+                                                       nmc, mpc);
+        prof_stop(st);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

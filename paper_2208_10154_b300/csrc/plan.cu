@@ -245,6 +245,19 @@ static cudaError_t build_tables(sht_plan* p)
         if ((e = upload(&p->c.phase_h, ph, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.phase_l, pl, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.phase_off, off, &acc)) != cudaSuccess) return e;
+        // ring pairs grouped by FFT size (one launch per size in the split FFTs)
+        std::map<int, std::vector<int>> bym;
+        for (int q = 0; q < R; q++) bym[p->h_fft[p->h_pairs[q].fft].m].push_back(q);
+        std::vector<int> cls;
+        for (auto& kv : bym) {
+            sht::FftClass c;
+            c.m = kv.first;
+            c.off = (int)cls.size();
+            c.cnt = (int)kv.second.size();
+            cls.insert(cls.end(), kv.second.begin(), kv.second.end());
+            p->h_fcls.push_back(c);
+        }
+        if ((e = upload(&p->c.cls_pairs, cls, &acc)) != cudaSuccess) return e;
     }
 
     // ---- lambda seeds ----
@@ -471,7 +484,7 @@ static void free_tables(sht_plan* p)
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
                     p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
-    void* cp[] = {p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
+    void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m};
