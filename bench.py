@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--per-map-samples", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the serving measurement (0: skip)")
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load of the open-loop serving run, as a fraction of closed-loop saturation")
     a = ap.parse_args()
     if a.lmax is None:
         a.lmax = 2 * a.nside - 1
@@ -56,6 +60,27 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (replicas: the job ends when the last one does)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(rank: int) -> int:
+    """Input seed of a replica: seed 1 of the workload, offset by the rank."""
+    return 1 + rank
+
+
+def job_throughput(nmaps_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job maps/s: the maps all ranks processed over the slowest rank's time."""
+    return world * nmaps_per_rank / seconds
 
 
 class ClockSampler:
@@ -173,6 +198,84 @@ def ref_config(a):
 
 
 # ----------------------------------------------------------------------------
+# Serving: a Poisson stream of mixed requests through the continuous-batching
+# server. Request mix of the serving workload, scaled to finish in seconds:
+# alm2map / map2alm 50/50, nside {64, 128, 256, 512} with weights
+# {0.3, 0.3, 0.2, 0.15} (renormalised), spin 2 for 30% of the nside <= 128
+# requests, maps per request uniform in 1..64, seed 3. Spin-0 requests run in
+# the split form, spin-2 in the FP64 form (the split form is spin 0 only).
+SERVE_NSIDES = [64, 128, 256, 512]
+SERVE_W = [0.3, 0.3, 0.2, 0.15]
+
+
+def run_serving(n_req, load, device):
+    import numpy as np
+    import torch
+    from paper_2208_10154_b300.serving import GpuExecutor, Request, Server
+    rng = np.random.default_rng(3)
+    w = np.array(SERVE_W) / np.sum(SERVE_W)
+    spec = []
+    for _ in range(n_req):
+        nside = int(rng.choice(SERVE_NSIDES, p=w))
+        spin = 2 if (nside <= 128 and rng.random() < 0.3) else 0
+        op = "alm2map" if rng.random() < 0.5 else "map2alm"
+        spec.append((op, nside, spin, int(rng.integers(1, 65))))
+    # one input pool per (op, nside, spin) of 64 maps; a request takes its first n
+    pool = {}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    for op, nside, spin, _ in spec:
+        k = (op, nside, spin)
+        if k in pool:
+            continue
+        ncomp = 2 if spin else 1
+        lmax = 2 * nside - 1
+        if op == "alm2map":
+            nalm = (lmax + 1) * (lmax + 2) // 2
+            x = torch.randn((64, ncomp, nalm, 2), generator=g, dtype=torch.float64, device="cuda")
+            pool[k] = torch.view_as_complex(x).contiguous()
+        else:
+            pool[k] = torch.randn((64, ncomp, 12 * nside * nside), generator=g, dtype=torch.float64, device="cuda")
+    ex = GpuExecutor(device=device, slots=4)
+    srv = Server(ex, hbm_budget=150e9, max_batch_maps=256, slots=4)
+    for op, nside, spin, _ in spec:                       # plans and kernels warm
+        srv.submit(Request(op=op, nside=nside, spin=spin, data=pool[(op, nside, spin)][:1]))
+    srv.run_until_idle()
+    torch.cuda.synchronize()
+
+    def run(arrivals):
+        srv.completed.clear()
+        srv.nbatches = 0
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(spec) or not srv.idle():
+            now = time.perf_counter() - t0
+            while i < len(spec) and arrivals[i] <= now:
+                op, nside, spin, n = spec[i]
+                srv.submit(Request(op=op, nside=nside, spin=spin, data=pool[(op, nside, spin)][:n],
+                                   t_arrival=t0 + arrivals[i]))
+                i += 1
+            if not srv.step():
+                time.sleep(1e-4)
+        torch.cuda.synchronize()
+        return srv.stats()
+
+    closed = run(np.zeros(len(spec)))                      # all at once: saturation
+    # requests/s at saturation = maps/s / mean maps per request
+    mean_maps = sum(s[3] for s in spec) / len(spec)
+    rate = load * closed["maps_per_s"] / mean_maps
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(spec)))
+    opened = run(arrivals)
+    return {"requests": opened["requests"], "offered_load": load,
+            "offered_requests_per_s": rate, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"],
+            "maps_per_s": opened["maps_per_s"], "batches": opened["batches"],
+            "saturation_maps_per_s": closed["maps_per_s"], "errors": opened["errors"] + closed["errors"],
+            "peak_admitted_gb": srv.peak_used / 1e9,
+            "workload": "Poisson stream; alm2map/map2alm 50/50; nside 64/128/256/512 (0.3/0.3/0.2/0.15); "
+                        "spin 2 in 30% of nside<=128; 1-64 maps per request; split form for spin 0, FP64 for spin 2"}
+
+
+# ----------------------------------------------------------------------------
 def main():
     a = parse()
     if a.impl == "reference":
@@ -213,7 +316,7 @@ def main():
     cl = inputs.cl_inv_llp1(lmax)[ls]
     sd = torch.from_numpy(np.where(ms == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda()
     g = torch.Generator(device="cuda")
-    g.manual_seed(1 + rank)
+    g.manual_seed(rank_seed(rank))
     re = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
     im = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
     im[..., torch.from_numpy(ms == 0).cuda()] = 0.0
@@ -257,12 +360,8 @@ def main():
     prof = sht.sht_profile_end()
     if world > 1:
         dist.barrier()
-    ms_step = e0.elapsed_time(e1) / a.steps
-    t_max = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step = float(t_max.item())
-    value = world * nmaps / (ms_step / 1e3)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, "cuda")
+    value = job_throughput(nmaps, world, ms_step / 1e3)
     gpu_launches = launches[0]
 
     # ---- per-map FP64 form (the paper's "one map at a time" baseline) ----
@@ -339,11 +438,7 @@ def main():
         for _ in range(ke):
             plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
             plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
-        dt = (time.perf_counter() - t0) / ke
-        td = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(td, op=dist.ReduceOp.MAX)
-        dt = float(td.item())
+        dt = max_over_ranks((time.perf_counter() - t0) / ke, world, "cuda")
         nb_alm = alm_h.numel() * 16
         nb_map = maps_h.numel() * 8
         e2e = {"value": world * nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
@@ -363,6 +458,12 @@ def main():
         cpu = {"value": 1.0 / dt, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"1 map (alm2map + map2alm, nside {nside}, lmax {lmax}), separable tier"}
 
+    serving = None
+    if rank == 0 and a.serve_requests > 0:
+        del alm, maps_in
+        torch.cuda.empty_cache()
+        serving = run_serving(a.serve_requests, a.serve_load, dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
@@ -375,7 +476,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
             "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
-            "kernels": prof, "plan_create_s": plan_s,
+            "kernels": prof, "plan_create_s": plan_s, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
