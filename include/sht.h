@@ -58,9 +58,11 @@ typedef enum {
     SHT_FP64 = 0,
     /* Contraction on the 16-bit tensor cores (tcgen05 kind::f16 with FP16
      * operands, FP32 TMEM accumulation): each operand = exact integer main
-     * slice + two FP16 residual pieces, the main products accumulate exactly;
-     * lambda recurrence in FP64; ring FFTs in compensated FP32; final
-     * accumulation into a_lm in FP64. */
+     * slice + a slice on the 2^-12 grid + an FP16 residual; the main and
+     * integer-grid products accumulate exactly; lambda recurrence in FP64;
+     * ring FFTs in compensated FP32; final accumulation into a_lm in FP64.
+     * Supported for spin 0, mmax <= 2047, nside <= 4096, lmax <= 16383
+     * (SHT_EUNSUPPORTED otherwise). */
     SHT_SPLIT_BF16 = 1
 } sht_precision;
 

@@ -13,17 +13,21 @@
 // contraction: ring pairs (map2alm) or l (alm2map).
 //
 // Accuracy. Every operand x is written, per row or column, in units of a
-// power-of-two quantum u with |x/u| <= Q (K Q^2 <= 2^24) as three FP16 slices
-// q + r0 + r1 (tc::slice3d: integer, 11-bit and 11-bit parts, ~30 bits).
-// Eight products per K step, in two kinds of TMEM accumulator:
-//     main = sum q q'            integers below 2^24: exact whatever the rounding
-//     corr = q r0' + r0 q' + q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'
-// The TMEM accumulator truncates toward zero on every MMA; over the whole of K
-// that bias reaches ~1e-6 of the output once the sums cancel. So corr lives in
-// two ping-pong accumulators: the MMAs of each 32-wide K chunk start a fresh
-// one, and the epilogue warps drain it into FP32 registers (round to nearest)
-// while the next chunk runs. Only r1 r1' (~2^-35 of the largest product) is
-// dropped.
+// power-of-two quantum u with |x/u| <= Q (K Q^2 <= 2^24, Q <= 127) as three
+// FP16 slices q + r0 + r1 (tc::slice3d: integer, a multiple of 2^-12, and the
+// rest below 2^-13). Eight products per K step, in three TMEM accumulators:
+//     main = sum q q'                        integers below 2^24: exact
+//     ex   = q r0' + r0 q'                   multiples of 2^-12 below 2^12 per
+//                                            32-wide K chunk: exact
+//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'     below ~9 per chunk
+// The TMEM accumulator truncates toward zero on every MMA, so a sum that is not
+// exact picks up a bias that grows with its magnitude and length. After every
+// 32-wide K chunk the epilogue warps drain both into an exact integer count of
+// 2^-12 kept in a fourth TMEM region: all of ex (which the next chunk
+// restarts), and sm rounded to the 2^-12 grid, leaving in sm only its residual
+// (below 2^-13) for the next chunk to accumulate onto. sm thus never grows past
+// one chunk's worth, and nothing but the truncation of those small partial sums
+// and the dropped r1 r1' (< 2^-26) is lost.
 //
 // Cluster sharing of lambda. The FP64 recurrence is the costly part (FP64 runs
 // at ~1/64 of FP32 here), so the CTAs of a thread-block cluster, which work on
@@ -59,7 +63,9 @@ constexpr int PIECE_BYTES = PR * KC * 2;         // 2 KB of one B plane
 constexpr int STAGE_BYTES = 3 * A_PLANE + 3 * B_PLANE;   // 48 KB
 constexpr int STG_ROW = TC_M * 8;                // one K row of raw data (FP32 hi/lo per column): 1 KB
 constexpr int STG_BYTES = KC * STG_ROW;          // 32 KB: one K chunk of raw data for the CTA's columns
-constexpr uint32_t CORR0 = 128;                  // TMEM columns of the corr ping-pong pair (128 each)
+constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
+constexpr uint32_t ACC_SM = 256;                 //   small corrections (+ the residual of earlier chunks)
+constexpr uint32_t ACC_HX = 384;                 //   int32 count of 2^-12 drained so far
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
 constexpr int MAX_CLUSTER = 8;
 
@@ -118,25 +124,35 @@ __device__ __forceinline__ void put3x8(uint8_t* planes, int plane_bytes, int row
     *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = make_uint4(b[0], b[1], b[2], b[3]);
 }
 
-// one stage (two MMA K-steps): main into TMEM column 0, the seven correction
-// products into the corr accumulator `cb` (restarted by this stage); A = data,
-// B = lambda
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first, uint32_t cb)
+// one stage (two MMA K-steps), A = data, B = lambda: the main products into
+// TMEM column 0 (accumulated over the whole of K) ...
+__device__ __forceinline__ void issue_main(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
 {
-    const uint32_t A0 = st_addr, A1 = A0 + A_PLANE, A2 = A1 + A_PLANE;
-    const uint32_t B0 = st_addr + 3 * A_PLANE, B1 = B0 + B_PLANE, B2 = B1 + B_PLANE;
+    const uint32_t A0 = st_addr, B0 = st_addr + 3 * A_PLANE;
 #pragma unroll
     for (int kk = 0; kk < 2; kk++) {
         const uint32_t o = kk * 32;
         umma_f16(tmem, desc_sw64(A0 + o), desc_sw64(B0 + o), idesc, (first && kk == 0) ? 0u : 1u);   // q q'
-        const uint32_t c = tmem + cb;
-        umma_f16(c, desc_sw64(A0 + o), desc_sw64(B1 + o), idesc, kk == 0 ? 0u : 1u);                 // q r0'
-        umma_f16(c, desc_sw64(A1 + o), desc_sw64(B0 + o), idesc, 1u);                                // r0 q'
-        umma_f16(c, desc_sw64(A0 + o), desc_sw64(B2 + o), idesc, 1u);                                // q r1'
-        umma_f16(c, desc_sw64(A2 + o), desc_sw64(B0 + o), idesc, 1u);                                // r1 q'
-        umma_f16(c, desc_sw64(A1 + o), desc_sw64(B1 + o), idesc, 1u);                                // r0 r0'
-        umma_f16(c, desc_sw64(A1 + o), desc_sw64(B2 + o), idesc, 1u);                                // r0 r1'
-        umma_f16(c, desc_sw64(A2 + o), desc_sw64(B1 + o), idesc, 1u);                                // r1 r0'
+    }
+}
+// ... and the seven correction products into the ex accumulator, which this
+// stage restarts, and the sm accumulator, which only the first stage restarts
+__device__ __forceinline__ void issue_corr(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
+{
+    const uint32_t A0 = st_addr, A1 = A0 + A_PLANE, A2 = A1 + A_PLANE;
+    const uint32_t B0 = st_addr + 3 * A_PLANE, B1 = B0 + B_PLANE, B2 = B1 + B_PLANE;
+    const uint32_t ex = tmem + ACC_EX, sm = tmem + ACC_SM;
+#pragma unroll
+    for (int kk = 0; kk < 2; kk++) {
+        const uint32_t o = kk * 32;
+        const uint32_t acc = kk == 0 ? 0u : 1u;
+        umma_f16(ex, desc_sw64(A0 + o), desc_sw64(B1 + o), idesc, acc);                              // q r0'
+        umma_f16(ex, desc_sw64(A1 + o), desc_sw64(B0 + o), idesc, 1u);                               // r0 q'
+        umma_f16(sm, desc_sw64(A0 + o), desc_sw64(B2 + o), idesc, (first && kk == 0) ? 0u : 1u);     // q r1'
+        umma_f16(sm, desc_sw64(A2 + o), desc_sw64(B0 + o), idesc, 1u);                               // r1 q'
+        umma_f16(sm, desc_sw64(A1 + o), desc_sw64(B1 + o), idesc, 1u);                               // r0 r0'
+        umma_f16(sm, desc_sw64(A1 + o), desc_sw64(B2 + o), idesc, 1u);                               // r0 r1'
+        umma_f16(sm, desc_sw64(A2 + o), desc_sw64(B1 + o), idesc, 1u);                               // r1 r0'
     }
 }
 
@@ -144,8 +160,8 @@ struct TcShared {
     uint64_t full[NST];        // stage filled: 4 data warps + one arrival per lambda piece
     uint64_t empty[NST];       // stage consumed by the MMAs of every CTA of the cluster
     uint64_t accf;             // all MMAs of this CTA done
-    uint64_t cdone[2];         // corr accumulator b holds a finished chunk
-    uint64_t cfree[2];         // corr accumulator b drained (4 epilogue warps)
+    uint64_t cdone;            // the correction accumulators hold a finished chunk
+    uint64_t cfree;            // the correction accumulators drained (4 epilogue warps)
     uint64_t sfull[2];         // raw-data staging buffer b filled (bulk copies)
     int released;              // highest chunk whose stage is free in every CTA of the cluster
     uint32_t tmem;
@@ -234,11 +250,9 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             mbar_init(&sh.empty[s], csize);
         }
         mbar_init(&sh.accf, 1);
-        for (int b = 0; b < 2; b++) {
-            mbar_init(&sh.cdone[b], 1);
-            mbar_init(&sh.cfree[b], 4);
-            mbar_init(&sh.sfull[b], 1);
-        }
+        mbar_init(&sh.cdone, 1);
+        mbar_init(&sh.cfree, 4);
+        for (int b = 0; b < 2; b++) mbar_init(&sh.sfull[b], 1);
         sh.released = NST - 1;
         mbar_fence_init();
     }
@@ -257,12 +271,14 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 const int s = kc % NST;
                 const uint32_t u = kc / NST;
                 if (!mbar_wait_cl(&sh.full[s], u & 1, a.err, 1)) break;
-                // the corr accumulator of chunk kc - 2 must have been drained
-                if (kc >= 2 && !mbar_wait_cl(&sh.cfree[kc & 1], ((kc - 2) >> 1) & 1, a.err, 5)) break;
                 tc_fence_after();
-                issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0, CORR0 + (kc & 1) * TC_N);
+                issue_main(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
+                // the correction accumulators of chunk kc - 1 must have been drained
+                if (kc >= 1 && !mbar_wait_cl(&sh.cfree, (kc - 1) & 1, a.err, 5)) break;
+                tc_fence_after();
+                issue_corr(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
                 umma_commit_mc(&sh.empty[s], mask);
-                umma_commit(&sh.cdone[kc & 1]);
+                umma_commit(&sh.cdone);
             }
             umma_commit(&sh.accf);
         }
@@ -411,28 +427,61 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         const int ce = sh.colexp[t];
         const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
-        float csum[TC_N];                             // drained corr, one per lambda row
-#pragma unroll
-        for (int i = 0; i < TC_N; i++) csum[i] = 0.0f;
         bool dok = true;
-        // add the corr accumulator of chunk c into csum and hand it back to the MMA
-        auto drain = [&](int c) {
-            const int b = c & 1;
-            dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone[b], (c >> 1) & 1, a.err, 6));
-            tc_fence_after();
+        // Move chunk c's corrections into the 2^-12 count and hand the
+        // accumulators back to the MMA. Per chunk |ex| <= 32 Q (1 + 2^-11) and
+        // |sm| < 10 + Q / 128, so the count stays below 2^12 (K Q (1 + 2^-11) +
+        // 11 nch) < 2^31 for K Q^2 <= 2^24 and K <= 8192.
+        // (A rolled loop: this runs once per chunk between other code, and a
+        // short body stays in the instruction cache.)
+        auto drain_cols = [&](uint32_t (&ve)[32], uint32_t (&vs)[32], uint32_t (&vh)[32], int n, bool first) {
 #pragma unroll
-            for (int g = 0; g < TC_N / 32; g++) {
-                if (g * 32 < nmma) {
-                    uint32_t v[32];
-                    tmem_ld32(tl + CORR0 + b * TC_N + g * 32, v);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int i = 0; i < 32; i++) csum[g * 32 + i] += __uint_as_float(v[i]);
+            for (int i = 0; i < 32; i++) {
+                if (i < n) {
+                    // ex: a multiple of 2^-12 below 2^12, so ex 2^12 is an exact integer
+                    const int ne = __float2int_rn(__uint_as_float(ve[i]) * 4096.0f);
+                    // sm to the nearest multiple of 2^-12 (|sm| 2^12 < 2^22) and its exact residual
+                    const float v = __uint_as_float(vs[i]);
+                    const float y = fmaf(v, 4096.0f, 12582912.0f);
+                    const int ns = __float_as_int(y) - 0x4B400000;
+                    vs[i] = __float_as_uint(fmaf(y - 12582912.0f, -1.0f / 4096.0f, v));
+                    vh[i] = (uint32_t)((first ? 0 : (int)vh[i]) + ne + ns);
                 }
             }
+        };
+        auto drain = [&](int c) {
+            dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, c & 1, a.err, 6));
+            tc_fence_after();
+            uint32_t ve[32], vs[32], vh[32];
+#pragma unroll 1
+            for (int g = 0; g + 32 <= nmma; g += 32) {
+                tmem_ld32(tl + ACC_EX + g, ve);
+                tmem_ld32(tl + ACC_SM + g, vs);
+                tmem_ld32(tl + ACC_HX + g, vh);
+                tmem_wait_ld();
+                drain_cols(ve, vs, vh, 32, c == 0);
+                tmem_st32(tl + ACC_SM + g, vs);
+                tmem_st32(tl + ACC_HX + g, vh);
+            }
+            if (nmma & 16) {                          // a last group of 16 columns
+                const int g = nmma - 16;
+                uint32_t e16[16], s16[16], h16[16];
+                tmem_ld16(tl + ACC_EX + g, e16);
+                tmem_ld16(tl + ACC_SM + g, s16);
+                tmem_ld16(tl + ACC_HX + g, h16);
+                tmem_wait_ld();
+#pragma unroll
+                for (int i = 0; i < 16; i++) { ve[i] = e16[i]; vs[i] = s16[i]; vh[i] = h16[i]; }
+                drain_cols(ve, vs, vh, 16, c == 0);
+#pragma unroll
+                for (int i = 0; i < 16; i++) { s16[i] = vs[i]; h16[i] = vh[i]; }
+                tmem_st16(tl + ACC_SM + g, s16);
+                tmem_st16(tl + ACC_HX + g, h16);
+            }
+            tmem_wait_st();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sh.cfree[b]);
+            if (lane == 0) mbar_arrive(&sh.cfree);
         };
         // Raw data: K row kc of the CTA's 128 columns is contiguous in global
         // memory (T[m][q][p][c] for map2alm, the transposed a_lm A2[l,m][c] for
@@ -462,14 +511,10 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         const float csc = __int_as_float((127 - ce) << 23);
         // (a wait that gives up turns dok off; the loop still runs to the end so
         // that all four data warps keep meeting at the named barrier)
+        // (the stage of chunk kc is free: one of the first NST, or released at
+        // the end of iteration kc - 1)
         for (int kc = 0; kc < nch; kc++) {
             const int s = kc % NST;
-            const uint32_t u = kc / NST;
-            if (dok && u >= 1) {
-                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 3));
-                // stage s is free in every CTA of the cluster: release it to the lambda warps
-                if (dok && issuer) publish_counter(&sh.released, kc);
-            }
             if (dok) dok = __all_sync(0xffffffffu, mbar_wait(&sh.sfull[kc & 1], (kc >> 1) & 1, a.err, 8));
             if (dok) {
                 const float2* stg =
@@ -496,7 +541,14 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             // all four data warps are done with staging buffer kc & 1: refill it
             named_bar_sync(1, 128);
             if (dok && issuer && kc + 2 < nch) fetch(kc + 2);
-            if (kc >= 2 && dok) drain(kc - 2);
+            // once every CTA of the cluster has consumed the previous use of the
+            // stage of chunk kc + 1, release it to the lambda warps
+            const int kn = kc + 1;
+            if (dok && kn < nch && kn >= NST) {
+                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[kn % NST], (kn / NST - 1) & 1, a.err, 3));
+                if (dok && issuer) publish_counter(&sh.released, kn);
+            }
+            if (kc >= 1 && dok) drain(kc - 1);
         }
         // Tail: wait until every CTA of the cluster has consumed the last use of
         // each stage. All their MMA commits then have arrived on this CTA's
@@ -508,19 +560,19 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             if (u >= 1)
                 dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 7));
         }
-        if (dok) {
-            for (int c = (nch >= 2 ? nch - 2 : 0); c < nch; c++) drain(c);
-        }
+        if (dok && nch >= 1) drain(nch - 1);
 
-        // ---------------- epilogue: out = (main + csum) * scales ----------------
+        // ---------------- epilogue: out = (main + ex + sm) * scales ----------------
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
         tc_fence_after();
 #pragma unroll
         for (int g = 0; g < TC_N / 32; g++) {
             if (g * 32 >= nmma) continue;
-            uint32_t v0[32];
+            uint32_t v0[32], vh[32], vr[32];
             if (nch > 0) {
                 tmem_ld32(tl + g * 32, v0);
+                tmem_ld32(tl + ACC_HX + g * 32, vh);
+                tmem_ld32(tl + ACC_SM + g * 32, vr);
                 tmem_wait_ld();
             }
             if (!ok || !cok) continue;
@@ -532,11 +584,19 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 for (int i = 0; i < 32; i++) {
                     const int r = g * 32 + i;
                     if (r < nrows) {
-                        // main (exact integer) + csum as an exact FP32 pair, times c_l f (hi/lo)
-                        const float x0 = __uint_as_float(v0[i]), x1 = csum[g * 32 + i];
-                        const float sm = x0 + x1;
-                        const float bb = sm - x0;
-                        const float er = (x0 - (sm - bb)) + (x1 - bb);
+                        // main + the count (integer and 2^-12 parts) + the residual as
+                        // an FP32 pair (two TwoSums), times c_l f (hi/lo)
+                        const float x0 = __uint_as_float(v0[i]);
+                        const int hc = (int)vh[i];
+                        const float eh = (float)(hc >> 12);                        // exact, < 2^19
+                        const float el = (float)(hc & 4095) * (1.0f / 4096.0f);    // exact
+                        const float s1 = x0 + eh;
+                        const float b1 = s1 - x0;
+                        const float e1 = (x0 - (s1 - b1)) + (eh - b1);             // exact (an integer)
+                        const float t1 = (el + e1) + __uint_as_float(vr[i]);
+                        const float sm = s1 + t1;
+                        const float bb = sm - s1;
+                        const float er = (s1 - (sm - bb)) + (t1 - bb);
                         const float2 F = sh.rfac[r];
                         const float p1 = __fmul_rn(sm, F.x);
                         const float lo = fmaf(sm, F.x, -p1) + er * F.x + sm * F.y;
@@ -555,8 +615,12 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     const int r = g * 32 + i;
                     if (r < nrows) {
                         float gv = 0.0f;
-                        if (nch > 0)
-                            gv = sc * ldexpf_fast(__uint_as_float(v0[i]) + csum[g * 32 + i], sh.rowexp[r] + ce);
+                        if (nch > 0) {
+                            const int hc = (int)vh[i];
+                            const float x = (__uint_as_float(v0[i]) + (float)(hc >> 12)) +
+                                            ((float)(hc & 4095) * (1.0f / 4096.0f) + __uint_as_float(vr[i]));
+                            gv = sc * ldexpf_fast(x, sh.rowexp[r] + ce);
+                        }
                         Gq[(long long)(n0 + r) * a.ncol] = gv;
                     }
                 }

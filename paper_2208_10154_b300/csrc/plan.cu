@@ -469,8 +469,10 @@ static cudaError_t build_split_tables(sht_plan* p)
     e = run_split_tables(p, d_base);
     cudaFree(d_base);
     if (e != cudaSuccess) return e;
-    // integer ranges of the exact main slices: Q^2 K <= 2^24 (and Q <= 256)
-    auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 256.0); };
+    // integer ranges of the slices: Q^2 K <= 2^24 keeps the main sums exact, and
+    // Q <= 127 keeps a 32-wide chunk of q r0' + r0 q' (multiples of 2^-12, at most
+    // 32 Q (1 + 2^-11)) below 2^12, where FP32 holds it exactly
+    auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 127.0); };
     p->s.Q_m2a = qfor((double)R);
     p->s.Q_a2m = qfor((double)(lmax / 2 + 1));
     p->table_bytes += acc;
@@ -629,6 +631,12 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     if (precision != SHT_FP64 && precision != SHT_SPLIT_BF16) { set_error("unknown precision"); return SHT_EINVAL; }
     if (precision == SHT_SPLIT_BF16 && mmax > 2047) {
         set_error("SHT_SPLIT_BF16 supports mmax <= 2047");
+        return SHT_EUNSUPPORTED;
+    }
+    // the contraction lengths (ring pairs, l of one parity) bound the exact
+    // integer sums of the tensor-core form
+    if (precision == SHT_SPLIT_BF16 && (2 * nside > 8192 || lmax / 2 + 1 > 8192)) {
+        set_error("SHT_SPLIT_BF16 supports nside <= 4096 and lmax <= 16383");
         return SHT_EUNSUPPORTED;
     }
     if (precision == SHT_SPLIT_BF16 && spin != 0) {

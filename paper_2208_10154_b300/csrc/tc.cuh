@@ -192,6 +192,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
                  : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 lanes x 16 consecutive 32-bit columns, stored
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                    "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                    "r"(v[15])
+                 : "memory");
+}
+// 32 lanes x 32 consecutive 32-bit columns, stored
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                 "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                 :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                    "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                    "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+                    "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+                    "r"(v[29]), "r"(v[30]), "r"(v[31])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- UMMA
 // K-major operand tile in the 64-byte swizzle layout: rows of 32 16-bit values (64 B),
@@ -328,18 +352,17 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
 }
 
 // Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into
-//     q  = nearest integer                     (exact in FP16 for Q <= 2048)
-//     r0 = v + vl - q rounded to 11 significant bits (Dekker's split; exact in FP16)
-//     r1 = the rest (<= 2^-12 |r0|, 13 bits; the FP16 packing keeps 11 of them)
-// so v + vl = q + r0 + r1 to ~2^-24 |v + vl - q|: ~30 bits of the row / column
-// maximum for large elements, ~22 bits of the element itself for small ones.
+//     q  = nearest integer                          (exact in FP16 for Q <= 2048)
+//     r0 = v + vl - q rounded to the grid 2^-12     (|r0| <= 1/2 + 2^-12: exact in FP16)
+//     r1 = the rest                                 (|r1| <= 2^-13; FP16 keeps it to 2^-25)
+// so v + vl = q + r0 + r1 to ~2^-25 of the quantum. The fixed grid of r0 makes
+// every product q r0' a multiple of 2^-12, so sums of them are exact in FP32
+// while they stay below 2^12.
 __device__ __forceinline__ void slice3d(float v, float vl, float& q, float& r0, float& r1)
 {
-    const float magic = 12582912.0f;             // 1.5 * 2^23: round to nearest integer
-    q = (v + magic) - magic;
-    const float r = (v - q) + vl;
-    const float c = __fmul_rn(r, 8193.0f);       // 2^13 + 1; __fmul_rn keeps it out of an FMA
-    r0 = c - (c - r);
+    q = __fadd_rn(__fadd_rn(v, 12582912.0f), -12582912.0f);   // 1.5 * 2^23: nearest integer
+    const float r = __fadd_rn(v - q, vl);
+    r0 = __fadd_rn(__fadd_rn(r, 3072.0f), -3072.0f);          // 1.5 * 2^11: ulp 2^-12
     r1 = r - r0;
 }
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
