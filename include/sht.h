@@ -61,8 +61,8 @@ typedef enum {
      * slice + a slice on the 2^-12 grid + an FP16 residual; the main and
      * integer-grid products accumulate exactly; lambda recurrence in FP64;
      * ring FFTs in compensated FP32; final accumulation into a_lm in FP64.
-     * Supported for spin 0, mmax <= 2047, nside <= 4096, lmax <= 16383
-     * (SHT_EUNSUPPORTED otherwise). */
+     * Supported for mmax <= 2047 with nside <= 4096, lmax <= 16383 (spin 0)
+     * or nside <= 2048, lmax <= 4095 (spin 2); SHT_EUNSUPPORTED otherwise. */
     SHT_SPLIT_BF16 = 1
 } sht_precision;
 

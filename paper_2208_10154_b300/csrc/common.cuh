@@ -95,9 +95,15 @@ struct SplitTables {
     double* nc64 = nullptr;        //   the same factor in FP64
     float2* nc2 = nullptr;         //   and as an FP32 hi/lo pair
     double2* ck = nullptr;         // recurrence checkpoints every 32 rows [block][p]
-    int* ck_exp = nullptr;
+    int* ck_exp = nullptr;         //   (spin 2: every 32 l, [block][s][p])
     unsigned int* rowmax_bits = nullptr;   // max_p |lambda_lm| per packed (l, m) (float bits)
     float* pairmax = nullptr;      // max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
+    // spin 2: normalised Wigner recurrences mu_l = (s2A x + s2B) mu_{l-1} - mu_{l-2}
+    // per s = +2 / -2, with s lambda_l = d_l mu_l (d_l the same for both s)
+    double* s2A[2] = {nullptr, nullptr};
+    double* s2B[2] = {nullptr, nullptr};
+    float2* s2d2 = nullptr;
+    double* s2d64 = nullptr;
     int* err = nullptr;            // device error word of the bounded waits
     int4* work_m2a = nullptr; int nwork_m2a = 0;
     int4* work_a2m = nullptr; int nwork_a2m = 0;

@@ -13,21 +13,22 @@
 // contraction: ring pairs (map2alm) or l (alm2map).
 //
 // Accuracy. Every operand x is written, per row or column, in units of a
-// power-of-two quantum u with |x/u| <= Q (K Q^2 <= 2^24, Q <= 127) as three
-// FP16 slices q + r0 + r1 (tc::slice3d: integer, a multiple of 2^-12, and the
-// rest below 2^-13). Eight products per K step, in three TMEM accumulators:
-//     main = sum q q'                        integers below 2^24: exact
-//     ex   = q r0' + r0 q'                   multiples of 2^-12 below 2^12 per
-//                                            32-wide K chunk: exact
-//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'     below ~9 per chunk
+// power-of-two quantum u with |x/u| <= Q (Q (Q + 1) K + 12 K / 32 <= 2^24,
+// Q <= 127) as four FP16 slices q + r0 + r1 + 2^-12 r2s (tc::slice4d: integer,
+// a multiple of 2^-12, the next 11 bits and the 11 after, ~2^-36 of u). Ten
+// products per K step, in four TMEM accumulators:
+//     main = sum q q'                              integers: exact
+//     ex   = q r0' + r0 q'                         multiples of 2^-12 below 2^12
+//                                                  per 32-wide K chunk: exact
+//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'        below ~10 per chunk
+//     fn   = q r2s' + r2s q'                       (2^12 times their value)
 // The TMEM accumulator truncates toward zero on every MMA, so a sum that is not
-// exact picks up a bias that grows with its magnitude and length. After every
-// 32-wide K chunk the epilogue warps drain both into an exact integer count of
-// 2^-12 kept in a fourth TMEM region: all of ex (which the next chunk
-// restarts), and sm rounded to the 2^-12 grid, leaving in sm only its residual
-// (below 2^-13) for the next chunk to accumulate onto. sm thus never grows past
-// one chunk's worth, and nothing but the truncation of those small partial sums
-// and the dropped r1 r1' (< 2^-26) is lost.
+// exact picks up an error that grows with its magnitude and length. After each
+// 32-wide chunk the epilogue warps fold the integer parts of ex and sm into
+// main (exact: the bound above keeps main below 2^24) and leave the fractional
+// parts plus 2^-12 fn (all below 1) in sm as the start of the next chunk, so sm
+// never holds more than one chunk's worth; ex and fn are restarted by every
+// chunk. Dropped: products of two residual slices beyond r0 r1' (< 2^-25 u u').
 //
 // Cluster sharing of lambda. The FP64 recurrence is the costly part (FP64 runs
 // at ~1/64 of FP32 here), so the CTAs of a thread-block cluster, which work on
@@ -57,15 +58,14 @@ constexpr int TC_N = 128;                        // lambda rows per CTA (MMA N, 
 constexpr int KC = 32;                           // K per pipeline stage (2 MMA K-steps)
 constexpr int NST = 3;                           // pipeline stages
 constexpr int PR = 32;                           // rows per lambda piece
+constexpr int NPL = 4;                           // FP16 slices per operand (q, r0, r1, r2s)
 constexpr int A_PLANE = TC_M * KC * 2;           // 8 KB (data, one slice)
 constexpr int B_PLANE = TC_N * KC * 2;           // 8 KB (lambda, one slice)
 constexpr int PIECE_BYTES = PR * KC * 2;         // 2 KB of one B plane
-constexpr int STAGE_BYTES = 3 * A_PLANE + 3 * B_PLANE;   // 48 KB
-constexpr int STG_ROW = TC_M * 8;                // one K row of raw data (FP32 hi/lo per column): 1 KB
-constexpr int STG_BYTES = KC * STG_ROW;          // 32 KB: one K chunk of raw data for the CTA's columns
+constexpr int STAGE_BYTES = NPL * (A_PLANE + B_PLANE);   // 64 KB
 constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
 constexpr uint32_t ACC_SM = 256;                 //   small corrections (+ the residual of earlier chunks)
-constexpr uint32_t ACC_HX = 384;                 //   int32 count of 2^-12 drained so far
+constexpr uint32_t ACC_FN = 384;                 //   products with r2s (2^12 times their value)
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
 constexpr int MAX_CLUSTER = 8;
 
@@ -82,6 +82,12 @@ struct TcArgs {
     const float* rowmax;       // map2alm: max_p |mu_l(theta_p) 2^E| per packed (l, m)
     const float* pairmax;      // alm2map: max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
     const float* colmax;       // data: max |x| per [m][q][col]
+    // spin 2: normalised Wigner recurrences, per s = +2 / -2 and packed (l, m):
+    //   mu_l = (s2A x + s2B) mu_{l-1} - mu_{l-2},  s lambda_l = d_l mu_l (d_l the same for both s)
+    const double* s2A[2];
+    const double* s2B[2];
+    const float2* s2d2;        // d_l as an FP32 hi/lo pair (alm2map applies it to lambda)
+    const double* s2d64;       // d_l in FP64 (map2alm applies it per output row)
     int* err;
     int lmax, mmax, R;
     long long ncol, nalm;
@@ -104,55 +110,52 @@ __device__ __forceinline__ long long a_idx(int lmax, int l, int m)
     return (long long)m * (2 * lmax + 1 - m) / 2 + l;
 }
 
-// 8 consecutive k (16-byte chunk j) of row `row`, three slice planes
-__device__ __forceinline__ void put3x8(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
+// 8 consecutive k (16-byte chunk j) of row `row`, four slice planes
+__device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
                                        const float (&vl)[8])
 {
-    uint32_t qq[4], a[4], b[4];
+    uint32_t pk[NPL][4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        float q0, x0, y0, q1, x1, y1;
-        slice3d(v[2 * i], vl[2 * i], q0, x0, y0);
-        slice3d(v[2 * i + 1], vl[2 * i + 1], q1, x1, y1);
-        qq[i] = pack_h2(q0, q1);
-        a[i] = pack_h2(x0, x1);
-        b[i] = pack_h2(y0, y1);
+        float x0[NPL], x1[NPL];
+        slice4d(v[2 * i], vl[2 * i], x0[0], x0[1], x0[2], x0[3]);
+        slice4d(v[2 * i + 1], vl[2 * i + 1], x1[0], x1[1], x1[2], x1[3]);
+#pragma unroll
+        for (int b = 0; b < NPL; b++) pk[b][i] = pack_h2(x0[b], x1[b]);
     }
     const uint32_t off = sw64_chunk(row, j);
-    *reinterpret_cast<uint4*>(planes + off) = make_uint4(qq[0], qq[1], qq[2], qq[3]);
-    *reinterpret_cast<uint4*>(planes + plane_bytes + off) = make_uint4(a[0], a[1], a[2], a[3]);
-    *reinterpret_cast<uint4*>(planes + 2 * plane_bytes + off) = make_uint4(b[0], b[1], b[2], b[3]);
+#pragma unroll
+    for (int b = 0; b < NPL; b++)
+        *reinterpret_cast<uint4*>(planes + b * plane_bytes + off) = make_uint4(pk[b][0], pk[b][1], pk[b][2], pk[b][3]);
 }
 
-// one stage (two MMA K-steps), A = data, B = lambda: the main products into
-// TMEM column 0 (accumulated over the whole of K) ...
-__device__ __forceinline__ void issue_main(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
+// one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
+// whole of K, sm over the whole of K on top of the residual the epilogue warps
+// leave in it (only the first stage restarts them); ex and fn restart here.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
 {
-    const uint32_t A0 = st_addr, B0 = st_addr + 3 * A_PLANE;
+    uint32_t A[NPL], B[NPL];
 #pragma unroll
-    for (int kk = 0; kk < 2; kk++) {
-        const uint32_t o = kk * 32;
-        umma_f16(tmem, desc_sw64(A0 + o), desc_sw64(B0 + o), idesc, (first && kk == 0) ? 0u : 1u);   // q q'
+    for (int b = 0; b < NPL; b++) {
+        A[b] = st_addr + b * A_PLANE;
+        B[b] = st_addr + NPL * A_PLANE + b * B_PLANE;
     }
-}
-// ... and the seven correction products into the ex accumulator, which this
-// stage restarts, and the sm accumulator, which only the first stage restarts
-__device__ __forceinline__ void issue_corr(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
-{
-    const uint32_t A0 = st_addr, A1 = A0 + A_PLANE, A2 = A1 + A_PLANE;
-    const uint32_t B0 = st_addr + 3 * A_PLANE, B1 = B0 + B_PLANE, B2 = B1 + B_PLANE;
-    const uint32_t ex = tmem + ACC_EX, sm = tmem + ACC_SM;
+    const uint32_t ex = tmem + ACC_EX, sm = tmem + ACC_SM, fn = tmem + ACC_FN;
 #pragma unroll
     for (int kk = 0; kk < 2; kk++) {
         const uint32_t o = kk * 32;
-        const uint32_t acc = kk == 0 ? 0u : 1u;
-        umma_f16(ex, desc_sw64(A0 + o), desc_sw64(B1 + o), idesc, acc);                              // q r0'
-        umma_f16(ex, desc_sw64(A1 + o), desc_sw64(B0 + o), idesc, 1u);                               // r0 q'
-        umma_f16(sm, desc_sw64(A0 + o), desc_sw64(B2 + o), idesc, (first && kk == 0) ? 0u : 1u);     // q r1'
-        umma_f16(sm, desc_sw64(A2 + o), desc_sw64(B0 + o), idesc, 1u);                               // r1 q'
-        umma_f16(sm, desc_sw64(A1 + o), desc_sw64(B1 + o), idesc, 1u);                               // r0 r0'
-        umma_f16(sm, desc_sw64(A1 + o), desc_sw64(B2 + o), idesc, 1u);                               // r0 r1'
-        umma_f16(sm, desc_sw64(A2 + o), desc_sw64(B1 + o), idesc, 1u);                               // r1 r0'
+        const uint32_t fresh = kk == 0 ? 0u : 1u;
+        const uint32_t keep = (first && kk == 0) ? 0u : 1u;
+        umma_f16(tmem, desc_sw64(A[0] + o), desc_sw64(B[0] + o), idesc, keep);     // q q'
+        umma_f16(ex, desc_sw64(A[0] + o), desc_sw64(B[1] + o), idesc, fresh);      // q r0'
+        umma_f16(ex, desc_sw64(A[1] + o), desc_sw64(B[0] + o), idesc, 1u);         // r0 q'
+        umma_f16(sm, desc_sw64(A[0] + o), desc_sw64(B[2] + o), idesc, keep);       // q r1'
+        umma_f16(sm, desc_sw64(A[2] + o), desc_sw64(B[0] + o), idesc, 1u);         // r1 q'
+        umma_f16(sm, desc_sw64(A[1] + o), desc_sw64(B[1] + o), idesc, 1u);         // r0 r0'
+        umma_f16(sm, desc_sw64(A[1] + o), desc_sw64(B[2] + o), idesc, 1u);         // r0 r1'
+        umma_f16(sm, desc_sw64(A[2] + o), desc_sw64(B[1] + o), idesc, 1u);         // r1 r0'
+        umma_f16(fn, desc_sw64(A[0] + o), desc_sw64(B[3] + o), idesc, fresh);      // q r2s'
+        umma_f16(fn, desc_sw64(A[3] + o), desc_sw64(B[0] + o), idesc, 1u);         // r2s q'
     }
 }
 
@@ -162,7 +165,6 @@ struct TcShared {
     uint64_t accf;             // all MMAs of this CTA done
     uint64_t cdone;            // the correction accumulators hold a finished chunk
     uint64_t cfree;            // the correction accumulators drained (4 epilogue warps)
-    uint64_t sfull[2];         // raw-data staging buffer b filled (bulk copies)
     int released;              // highest chunk whose stage is free in every CTA of the cluster
     uint32_t tmem;
     int colexp[TC_M];
@@ -170,7 +172,7 @@ struct TcShared {
     double cA[TC_N], cB[TC_N]; // map2alm: recurrence coefficients of the tile's rows
     float2 rfac[TC_N];         // map2alm: c_l * factor as an FP32 hi/lo pair
 };
-constexpr int SMEM_TC = NST * STAGE_BYTES + 2 * STG_BYTES + (int)sizeof(TcShared) + 1024;
+constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
 
 // x * 2^-500 by exponent arithmetic (x is either 0 or has a biased exponent
 // above 500 here, or is flushed to 0 if it does not)
@@ -192,18 +194,37 @@ __device__ __forceinline__ void rescale(double& cur, double& prev, int& E)
     }
 }
 
+// column c of the spin-2 E/B (or Q/U) coupling perm(Xr, Xi, Yr, Yi) = (-Yi, Yr, Xi, -Xr):
+// source column within the group of four, and its sign
+__device__ __forceinline__ int perm_src(int c) { return (c & ~3) | (3 - (c & 3)); }
+__device__ __forceinline__ float perm_sign(int c) { return ((c & 3) == 0 || (c & 3) == 3) ? -1.0f : 1.0f; }
+
 // ===========================================================================
 // map2alm (M2A = true):  a[l, c] = f_l sum_p lambda_lm(theta_p) T[p, c]
 // alm2map (M2A = false): G[p, c] = s   sum_l lambda_lm(theta_p) a[l, c]
+//
+// Spin 2 (S2, Sec. 2.3 with F+- = -(2lambda +- -2lambda) / 2). Writing the two
+// spin-weighted functions as v+ = 2lambda, v- = -2lambda:
+//   map2alm, rows l of slot q:
+//     a_l = F+ T_q + F- P_{1-q} = -1/2 [ v+ (T_q + P_{1-q}) + v- (T_q - P_{1-q}) ]
+//   alm2map, slot q:
+//     G_q = sum_{l in q} F+ a_l + sum_{l not in q} F- P(a_l)
+//         = -1/2 sum_l [ v+ b_l + v- sigma_l b_l ],  b_l = a_l or P(a_l), sigma_l = +-1
+// with P the E/B coupling permutation (perm_src). So each contraction runs over
+// K' = 2 K: chunk 2u carries v+ and chunk 2u + 1 carries v- over the same 32
+// ring pairs (map2alm) or values of l (alm2map), and a lambda piece is one
+// recurrence (one s), like the spin-0 pieces. The data warps form the
+// combinations of the two slots (map2alm) or the parity-dependent permutation
+// and sign (alm2map) while slicing.
 // grid.x = work item (m, q, tile), grid.y = column tile; clusters along y
 // ===========================================================================
-template <bool M2A>
+template <bool M2A, bool S2>
 __global__ void __launch_bounds__(256, 1)
 k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES + 2 * STG_BYTES);
+    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES);
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, tile = w.z, ckb = w.w;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -213,15 +234,32 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
     const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;   // l rows of slot q
     const int n0 = tile * TC_N;                                         // first lambda row of the tile
     const int nrows = M2A ? min(TC_N, nl - n0) : min(TC_N, a.R - n0);
-    const int K = M2A ? a.R : nl;
-    const int nch = (K + KC - 1) / KC;
+    // contraction length: spin 0 over ring pairs (map2alm) or the l of slot q;
+    // spin 2 over ring pairs or all l >= m, each twice (v+ and v- chunks)
+    const int K = M2A ? a.R : (S2 ? a.lmax - m + 1 : nl);
+    const int nunit = (K + KC - 1) / KC;           // 32-wide units of raw data
+    const int nch = S2 ? 2 * nunit : nunit;        // MMA chunks (pipeline stages)
+    const int l0s = m > 2 ? m : 2;                 // first l of the spin-2 functions
     const int npieces = (nrows + PR - 1) / PR;
     const int nmma = (nrows + 15) & ~15;
     const uint32_t idesc = idesc_f16(TC_M, nmma);
     const long long qstride = (long long)a.R * a.ncol;
 
     for (int r = tid; r < TC_N; r += blockDim.x) {
-        if (M2A) {
+        if (M2A && S2) {
+            sh.cA[r] = 0.0; sh.cB[r] = 0.0;
+            if (r < nrows) {
+                const int l = l_first + 2 * (n0 + r);
+                const long long ci = a_idx(a.lmax, l, m);
+                sh.rowexp[r] = quantum_exp(a.rowmax[ci], a.Q);
+                // -d_l / 2 * factor; rows below l = 2 are zero
+                const double f = (l < 2) ? 0.0 : -0.5 * a.s2d64[ci] * (m == 0 ? a.fs0 : a.fs1);
+                const float fh = (float)f;
+                sh.rfac[r] = make_float2(fh, (float)(f - (double)fh));
+            } else {
+                sh.rowexp[r] = 0; sh.rfac[r] = make_float2(0.0f, 0.0f);
+            }
+        } else if (M2A) {
             if (r < nrows) {
                 const int l = l_first + 2 * (n0 + r);
                 const long long ci = a_idx(a.lmax, l, m);
@@ -242,7 +280,17 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
     }
     for (int c = tid; c < TC_M; c += blockDim.x) {
         const long long cg = c0 + c;
-        sh.colexp[c] = (cg < a.ncol) ? quantum_exp(a.colmax[((long long)m * 2 + q) * a.ncol + cg], a.Q) : 0;
+        float mx = 0.0f;
+        if (cg < a.ncol) {
+            mx = a.colmax[((long long)m * 2 + q) * a.ncol + cg];
+            if (S2) {
+                // the other slot, permuted: map2alm slices T_q +- P(T_{1-q}) (bounded by the
+                // sum), alm2map slices a_l or P(a_l) (bounded by the larger)
+                const float mo = a.colmax[((long long)m * 2 + (1 - q)) * a.ncol + (c0 + perm_src(c))];
+                mx = M2A ? mx + mo : fmaxf(mx, mo);
+            }
+        }
+        sh.colexp[c] = (cg < a.ncol) ? quantum_exp(mx, a.Q) : 0;
     }
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
@@ -252,7 +300,6 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         mbar_init(&sh.accf, 1);
         mbar_init(&sh.cdone, 1);
         mbar_init(&sh.cfree, 4);
-        for (int b = 0; b < 2; b++) mbar_init(&sh.sfull[b], 1);
         sh.released = NST - 1;
         mbar_fence_init();
     }
@@ -271,12 +318,11 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 const int s = kc % NST;
                 const uint32_t u = kc / NST;
                 if (!mbar_wait_cl(&sh.full[s], u & 1, a.err, 1)) break;
-                tc_fence_after();
-                issue_main(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
-                // the correction accumulators of chunk kc - 1 must have been drained
+                // the accumulators of chunk kc - 1 must have been drained (the
+                // drain rewrites main and sm)
                 if (kc >= 1 && !mbar_wait_cl(&sh.cfree, (kc - 1) & 1, a.err, 5)) break;
                 tc_fence_after();
-                issue_corr(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
+                issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
                 umma_commit_mc(&sh.empty[s], mask);
                 umma_commit(&sh.cdone);
             }
@@ -293,7 +339,59 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             const int s = kc % NST;
             float hb[PR], lb[PR];
             int prow;                                   // row of the B tile this lane writes (alm2map)
-            if (M2A) {
+            if constexpr (M2A && S2) {
+                // lane = ring pair (k) of unit kc / 2, walking the 64 l that hold the
+                // 32 rows (slot q) of piece j with the recurrence of s = (kc odd ? -2 : +2)
+                const int sg = kc & 1;
+                const int p = (kc >> 1) * KC + lane;
+                const int J = (n0 >> 5) + j;            // 32-row block of the slot's rows
+                const int L = m + 64 * J;               // first l of the walk (checkpoint block 2J)
+                const int lck = max(L, l0s);            // l of the checkpointed value
+                double cur = 0.0, prev = 0.0, x = 0.0;
+                int E = 0;
+                const bool live = p < a.R;
+                if (live) {
+                    const long long ci = ((long long)(ckb + 2 * J) * 2 + sg) * a.R + p;
+                    const double2 v = a.ck[ci];
+                    cur = v.x; prev = v.y;
+                    E = a.ck_exp[ci];
+                    x = a.pairs[p].x;
+                }
+                // coefficients of the walk: lane k holds l = L + k and L + 32 + k
+                double cA0 = 0.0, cB0 = 0.0, cA1 = 0.0, cB1 = 0.0;
+                if (L + lane <= a.lmax) {
+                    const long long ci = a_idx(a.lmax, L + lane, m);
+                    cA0 = a.s2A[sg][ci]; cB0 = a.s2B[sg][ci];
+                }
+                if (L + 32 + lane <= a.lmax) {
+                    const long long ci = a_idx(a.lmax, L + 32 + lane, m);
+                    cA1 = a.s2A[sg][ci]; cB1 = a.s2B[sg][ci];
+                }
+                const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
+                int lc = lck;                           // l of cur (warp-uniform)
+#pragma unroll
+                for (int i = 0; i < PR; i++) {
+                    hb[i] = 0.0f; lb[i] = 0.0f;
+                    if (i < rn) {
+                        const int lt = L + q + 2 * i;   // the row's l
+#pragma unroll
+                        for (int st = 0; st < 2; st++) {
+                            if (lc < lt) {
+                                const int k = lc + 1 - L;
+                                const double cA = __shfl_sync(0xffffffffu, k < 32 ? cA0 : cA1, k & 31);
+                                const double cB = __shfl_sync(0xffffffffu, k < 32 ? cB0 : cB1, k & 31);
+                                const double nxt = fma(fma(cA, x, cB), cur, -prev);
+                                prev = cur;
+                                cur = nxt;
+                                rescale(cur, prev, E);
+                                lc++;
+                            }
+                        }
+                        if (live && lt >= lck) f64_split_scaled(cur, E - sh.rowexp[j * PR + i], hb[i], lb[i]);
+                    }
+                }
+                prow = 0;
+            } else if constexpr (M2A) {
                 // lane = ring pair (k), walking the 32 l rows of piece j
                 const int p = kc * KC + lane;
                 double cur = 0.0, prev = 0.0, x2 = 0.0;
@@ -324,6 +422,55 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     }
                 }
                 prow = 0;
+            } else if constexpr (S2) {
+                // lane = ring pair (row), walking the 32 l of unit kc / 2 with the
+                // recurrence of s = (kc odd ? -2 : +2); d_l applied in double-float
+                const int sg = kc & 1;
+                const int u = kc >> 1;
+                const int r = j * PR + lane;
+                const int p = n0 + r;
+                const bool live = r < nrows;
+                const int L = m + KC * u;               // first l of the unit (checkpoint block u)
+                const int lck = max(L, l0s);
+                double cur = 0.0, prev = 0.0, x = 0.0;
+                int E = 0, pe = 0;
+                if (live) {
+                    const long long ci = ((long long)(ckb + u) * 2 + sg) * a.R + p;
+                    const double2 v = a.ck[ci];
+                    cur = v.x; prev = v.y;
+                    E = a.ck_exp[ci];
+                    x = a.pairs[p].x;
+                    pe = sh.rowexp[r];
+                }
+                double cAk = 0.0, cBk = 0.0;
+                float2 cdk = make_float2(0.0f, 0.0f);
+                if (L + lane <= a.lmax) {
+                    const long long ci = a_idx(a.lmax, L + lane, m);
+                    cAk = a.s2A[sg][ci]; cBk = a.s2B[sg][ci]; cdk = a.s2d2[ci];
+                }
+#pragma unroll
+                for (int i = 0; i < PR; i++) {
+                    hb[i] = 0.0f; lb[i] = 0.0f;
+                    const float d0 = __shfl_sync(0xffffffffu, cdk.x, i);
+                    const float d1 = __shfl_sync(0xffffffffu, cdk.y, i);
+                    const double cA = __shfl_sync(0xffffffffu, cAk, i);
+                    const double cB = __shfl_sync(0xffffffffu, cBk, i);
+                    const int l = L + i;
+                    if (l <= a.lmax && l >= lck) {
+                        if (l > lck) {
+                            const double nxt = fma(fma(cA, x, cB), cur, -prev);
+                            prev = cur;
+                            cur = nxt;
+                            rescale(cur, prev, E);
+                        }
+                        float h = 0.0f, lo = 0.0f;
+                        if (live) f64_split_scaled(cur, E - pe, h, lo);
+                        const float p1 = h * d0;                // lambda = d_l mu in double-float
+                        hb[i] = p1;
+                        lb[i] = fmaf(h, d0, -p1) + (h * d1 + lo * d0);
+                    }
+                }
+                prow = r;
             } else {
                 // lane = ring pair (row), walking the 32 l of stage kc; the
                 // coefficients of those 32 l are loaded once (lane k holds l_k)
@@ -380,16 +527,15 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             // of the stage barrier can tell apart, so it waits on the monotonic
             // count of released chunks that the data warps publish instead.
             if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
-            uint8_t* B = smem + s * STAGE_BYTES + 3 * A_PLANE;
-            if (M2A) {
+            uint8_t* B = smem + s * STAGE_BYTES + NPL * A_PLANE;
+            if constexpr (M2A) {
 #pragma unroll
                 for (int i = 0; i < PR; i++) {
-                    float q0, q1, q2;
-                    slice3d(hb[i], lb[i], q0, q1, q2);
+                    float x[NPL];
+                    slice4d(hb[i], lb[i], x[0], x[1], x[2], x[3]);
                     const uint32_t off = sw64_off(j * PR + i, lane);
-                    *reinterpret_cast<__half*>(B + off) = __float2half_rn(q0);
-                    *reinterpret_cast<__half*>(B + B_PLANE + off) = __float2half_rn(q1);
-                    *reinterpret_cast<__half*>(B + 2 * B_PLANE + off) = __float2half_rn(q2);
+#pragma unroll
+                    for (int b = 0; b < NPL; b++) *reinterpret_cast<__half*>(B + b * B_PLANE + off) = __float2half_rn(x[b]);
                 }
             } else {
 #pragma unroll
@@ -397,7 +543,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     float hv[8], lv[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) { hv[i] = hb[jj * 8 + i]; lv[i] = lb[jj * 8 + i]; }
-                    put3x8(B, B_PLANE, prow, jj, hv, lv);
+                    put4x8(B, B_PLANE, prow, jj, hv, lv);
                 }
             }
             fence_proxy_async_smem();
@@ -410,9 +556,9 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 } else {
                     const uint32_t src0 = smem_u32(B) + j * PIECE_BYTES;
                     const uint32_t fb = mapa_shared(smem_u32(&sh.full[s]), d);
-                    mbar_arrive_expect_tx_cl(fb, 3 * PIECE_BYTES);
+                    mbar_arrive_expect_tx_cl(fb, NPL * PIECE_BYTES);
 #pragma unroll
-                    for (int b = 0; b < 3; b++) {
+                    for (int b = 0; b < NPL; b++) {
                         const uint32_t sa = src0 + b * B_PLANE;
                         bulk_copy_s2cluster(mapa_shared(sa, d), sa, PIECE_BYTES, fb);
                     }
@@ -428,132 +574,162 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         bool dok = true;
-        // Move chunk c's corrections into the 2^-12 count and hand the
-        // accumulators back to the MMA. Per chunk |ex| <= 32 Q (1 + 2^-11) and
-        // |sm| < 10 + Q / 128, so the count stays below 2^12 (K Q (1 + 2^-11) +
-        // 11 nch) < 2^31 for K Q^2 <= 2^24 and K <= 8192.
-        // (A rolled loop: this runs once per chunk between other code, and a
-        // short body stays in the instruction cache.)
-        auto drain_cols = [&](uint32_t (&ve)[32], uint32_t (&vs)[32], uint32_t (&vh)[32], int n, bool first) {
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-                if (i < n) {
-                    // ex: a multiple of 2^-12 below 2^12, so ex 2^12 is an exact integer
-                    const int ne = __float2int_rn(__uint_as_float(ve[i]) * 4096.0f);
-                    // sm to the nearest multiple of 2^-12 (|sm| 2^12 < 2^22) and its exact residual
-                    const float v = __uint_as_float(vs[i]);
-                    const float y = fmaf(v, 4096.0f, 12582912.0f);
-                    const int ns = __float_as_int(y) - 0x4B400000;
-                    vs[i] = __float_as_uint(fmaf(y - 12582912.0f, -1.0f / 4096.0f, v));
-                    vh[i] = (uint32_t)((first ? 0 : (int)vh[i]) + ne + ns);
-                }
-            }
-        };
+        // Fold chunk c's corrections into main and sm and hand the accumulators
+        // back to the MMA: main += nearest integers of ex and sm (exact), sm =
+        // their fractional parts + 2^-12 fn (below 1). (A rolled loop: it runs
+        // once per chunk between other code, and a short body stays in the
+        // instruction cache.)
         auto drain = [&](int c) {
             dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, c & 1, a.err, 6));
             tc_fence_after();
-            uint32_t ve[32], vs[32], vh[32];
 #pragma unroll 1
-            for (int g = 0; g + 32 <= nmma; g += 32) {
-                tmem_ld32(tl + ACC_EX + g, ve);
-                tmem_ld32(tl + ACC_SM + g, vs);
-                tmem_ld32(tl + ACC_HX + g, vh);
-                tmem_wait_ld();
-                drain_cols(ve, vs, vh, 32, c == 0);
-                tmem_st32(tl + ACC_SM + g, vs);
-                tmem_st32(tl + ACC_HX + g, vh);
-            }
-            if (nmma & 16) {                          // a last group of 16 columns
-                const int g = nmma - 16;
-                uint32_t e16[16], s16[16], h16[16];
-                tmem_ld16(tl + ACC_EX + g, e16);
-                tmem_ld16(tl + ACC_SM + g, s16);
-                tmem_ld16(tl + ACC_HX + g, h16);
+            for (int g = 0; g < nmma; g += 16) {
+                uint32_t vm[16], ve[16], vs[16], vf[16];
+                tmem_ld16(tl + g, vm);
+                tmem_ld16(tl + ACC_EX + g, ve);
+                tmem_ld16(tl + ACC_SM + g, vs);
+                tmem_ld16(tl + ACC_FN + g, vf);
                 tmem_wait_ld();
 #pragma unroll
-                for (int i = 0; i < 16; i++) { ve[i] = e16[i]; vs[i] = s16[i]; vh[i] = h16[i]; }
-                drain_cols(ve, vs, vh, 16, c == 0);
-#pragma unroll
-                for (int i = 0; i < 16; i++) { s16[i] = vs[i]; h16[i] = vh[i]; }
-                tmem_st16(tl + ACC_SM + g, s16);
-                tmem_st16(tl + ACC_HX + g, h16);
+                for (int i = 0; i < 16; i++) {
+                    const float e = __uint_as_float(ve[i]), v = __uint_as_float(vs[i]);
+                    const float eh = rint_magic(e), vh = rint_magic(v);
+                    vm[i] = __float_as_uint(__fadd_rn(__fadd_rn(__uint_as_float(vm[i]), eh), vh));
+                    vs[i] = __float_as_uint(((e - eh) + (v - vh)) + __uint_as_float(vf[i]) * (1.0f / 4096.0f));
+                }
+                tmem_st16(tl + g, vm);
+                tmem_st16(tl + ACC_SM + g, vs);
             }
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.cfree);
         };
-        // Raw data: K row kc of the CTA's 128 columns is contiguous in global
-        // memory (T[m][q][p][c] for map2alm, the transposed a_lm A2[l,m][c] for
-        // alm2map, both FP32 hi/lo pairs), so one thread moves each chunk with
-        // 32 bulk copies (1 KB each) into staging buffer kc & 1.
-        const int ncv = (int)max(0ll, min((long long)TC_M, a.ncol - c0));   // valid columns of the tile
-        const float2* raw = (const float2*)src;
-        auto fetch = [&](int c) {
-            const int b = c & 1;
-            const int i1 = min(KC, K - c * KC);
-            const uint32_t rowb = (uint32_t)ncv * 8u;
-            mbar_arrive_expect_tx(&sh.sfull[b], rowb * (uint32_t)max(i1, 0));
-            if (rowb == 0) return;
-            const uint32_t dst = smem_u32(smem + NST * STAGE_BYTES + b * STG_BYTES);
-            for (int i = 0; i < i1; i++) {
-                const int k = c * KC + i;
-                const long long row = M2A ? ((long long)m * 2 + q) * a.R + k : a_idx(a.lmax, l_first + 2 * k, m);
-                bulk_copy_g2s(dst + i * STG_ROW, raw + row * a.ncol + c0, rowb, &sh.sfull[b]);
+        // release chunk c's stage to the lambda warps once every CTA of the
+        // cluster has consumed its previous use
+        auto release = [&](int c) {
+            if (dok && c < nch && c >= NST) {
+                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1, a.err, 3));
+                if (dok && lane == 0 && warp == 4) publish_counter(&sh.released, c);
             }
         };
-        const bool issuer = (warp == 4 && lane == 0);
-        if (issuer) {
-            if (nch > 0) fetch(0);
-            if (nch > 1) fetch(1);
-        }
+        // Raw data: each thread loads its own column (FP32 hi/lo pairs; a warp
+        // reads 256 contiguous bytes per K row) one block ahead into registers.
+        // A block is a unit of 32 K rows, or for spin-2 map2alm, which needs both
+        // slots, half a unit (16 rows) of each slot.
+        const float2* raw = (const float2*)src;
+        constexpr bool TWO = S2 && M2A;
+        constexpr int BR = TWO ? KC / 2 : KC;       // K rows per block and slot
+        const int nblk = TWO ? 2 * nunit : nunit;
+        float2 buf[KC];
+        auto load_block = [&](int blk) {
+            const int u = TWO ? blk >> 1 : blk;
+            const int rb = TWO ? (blk & 1) * BR : 0;
+#pragma unroll
+            for (int h = 0; h < (TWO ? 2 : 1); h++) {
+                const int slot = h ? 1 - q : q;
+#pragma unroll
+                for (int i = 0; i < BR; i++) {
+                    const int k = u * KC + rb + i;
+                    float2 x = make_float2(0.0f, 0.0f);
+                    if (cok && k < K) {
+                        long long row;
+                        if (M2A) row = ((long long)m * 2 + slot) * a.R + k;
+                        else row = S2 ? a_idx(a.lmax, m + k, m) : a_idx(a.lmax, l_first + 2 * k, m);
+                        x = __ldg(raw + row * a.ncol + cg);
+                    }
+                    buf[h * BR + i] = x;
+                }
+            }
+        };
         // the quantum 2^ce as an FP32 factor (exact scaling)
         const float csc = __int_as_float((127 - ce) << 23);
-        // (a wait that gives up turns dok off; the loop still runs to the end so
-        // that all four data warps keep meeting at the named barrier)
-        // (the stage of chunk kc is free: one of the first NST, or released at
-        // the end of iteration kc - 1)
-        for (int kc = 0; kc < nch; kc++) {
-            const int s = kc % NST;
-            if (dok) dok = __all_sync(0xffffffffu, mbar_wait(&sh.sfull[kc & 1], (kc >> 1) & 1, a.err, 8));
-            if (dok) {
-                const float2* stg =
-                    reinterpret_cast<const float2*>(smem + NST * STAGE_BYTES + (kc & 1) * STG_BYTES) + t;
-                const int kv = K - kc * KC;             // valid rows of this chunk
-                uint8_t* A = smem + s * STAGE_BYTES;
-#pragma unroll 1
-                for (int jj = 0; jj < KC / 8; jj++) {
+        const int psrc = (lane & ~3) | (3 - (lane & 3));     // spin 2: lane of the permuted column
+        const float sgp = perm_sign(t);
+        // slice block blk into the stage(s) of its unit's chunk(s)
+        auto slice_block = [&](int blk) {
+            const int u = TWO ? blk >> 1 : blk;
+            const int rb = TWO ? (blk & 1) * BR : 0;
+#pragma unroll
+            for (int sub = 0; sub < (S2 ? 2 : 1); sub++) {
+                uint8_t* A = smem + ((S2 ? 2 * u + sub : u) % NST) * STAGE_BYTES;
+#pragma unroll
+                for (int jj = 0; jj < BR / 8; jj++) {
                     float hv[8], lv[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
-                        const int r = jj * 8 + i;
-                        float2 x = make_float2(0.0f, 0.0f);
-                        if (cok && r < kv) x = stg[r * TC_M];
+                        const int r = jj * 8 + i;             // row within the block
+                        float2 x;
+                        if constexpr (!S2) {
+                            x = buf[r];
+                        } else if constexpr (M2A) {
+                            // T_q +- P(T_{1-q}) in double-float (TwoSum of the hi parts)
+                            const float2 x0 = buf[r];
+                            float2 x1;
+                            x1.x = __shfl_sync(0xffffffffu, buf[BR + r].x, psrc);
+                            x1.y = __shfl_sync(0xffffffffu, buf[BR + r].y, psrc);
+                            const float sb = sub ? -sgp : sgp;
+                            const float bh = sb * x1.x;
+                            const float s1 = x0.x + bh;
+                            const float bb = s1 - x0.x;
+                            const float lo = ((x0.x - (s1 - bb)) + (bh - bb)) + (x0.y + sb * x1.y);
+                            const float hi = s1 + lo;
+                            x = make_float2(hi, lo - (hi - s1));
+                        } else {
+                            // a_l (l - m = 32 u + r in slot q) or P(a_l); v- chunks negate the latter
+                            float2 xp;
+                            xp.x = __shfl_sync(0xffffffffu, buf[r].x, psrc);
+                            xp.y = __shfl_sync(0xffffffffu, buf[r].y, psrc);
+                            const bool same = (r & 1) == q;
+                            const float sg = same ? 1.0f : (sub ? -sgp : sgp);
+                            x = same ? buf[r] : xp;
+                            x.x *= sg;
+                            x.y *= sg;
+                        }
                         hv[i] = x.x * csc;
                         lv[i] = x.y * csc;
                     }
-                    put3x8(A, A_PLANE, t, jj, hv, lv);
+                    put4x8(A, A_PLANE, t, rb / 8 + jj, hv, lv);
                 }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh.full[s]);
             }
-            // all four data warps are done with staging buffer kc & 1: refill it
-            named_bar_sync(1, 128);
-            if (dok && issuer && kc + 2 < nch) fetch(kc + 2);
-            // once every CTA of the cluster has consumed the previous use of the
-            // stage of chunk kc + 1, release it to the lambda warps
-            const int kn = kc + 1;
-            if (dok && kn < nch && kn >= NST) {
-                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[kn % NST], (kn / NST - 1) & 1, a.err, 3));
-                if (dok && issuer) publish_counter(&sh.released, kn);
+        };
+        // (a wait that gives up turns dok off; the loop still runs to the end so
+        // that the barrier arrivals stay balanced)
+        if (nblk > 0) load_block(0);
+        for (int blk = 0; blk < nblk; blk++) {
+            const int u = TWO ? blk >> 1 : blk;
+            // the unit's stage(s) are free: among the first NST, or released at the
+            // end of the previous unit
+            if (dok) slice_block(blk);
+            if (blk + 1 < nblk) load_block(blk + 1);  // in flight during the waits below
+            if (TWO && (blk & 1) == 0) continue;
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                if (S2) {
+                    mbar_arrive(&sh.full[(2 * u) % NST]);
+                    mbar_arrive(&sh.full[(2 * u + 1) % NST]);
+                } else {
+                    mbar_arrive(&sh.full[u % NST]);
+                }
             }
-            if (kc >= 1 && dok) drain(kc - 1);
+            // release the next unit's stages and drain the chunks whose MMAs the
+            // next ones wait for (in this order: release c needs MMA(c - NST), which
+            // must not wait for a drain that comes after it)
+            if (S2) {
+                release(2 * u + 2);
+                if (u >= 1 && dok) drain(2 * u - 1);
+                release(2 * u + 3);
+                if (dok) drain(2 * u);
+            } else {
+                release(u + 1);
+                if (u >= 1 && dok) drain(u - 1);
+            }
         }
         // Tail: wait until every CTA of the cluster has consumed the last use of
         // each stage. All their MMA commits then have arrived on this CTA's
         // barriers, so none can land after it exits. (These waits continue the
-        // sequential phase walk of the loop above.)
+        // sequential phase walk of the releases above.)
         for (int kc = nch; kc < nch + NST && dok; kc++) {
             const int s = kc % NST;
             const uint32_t u = kc / NST;
@@ -562,16 +738,15 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         }
         if (dok && nch >= 1) drain(nch - 1);
 
-        // ---------------- epilogue: out = (main + ex + sm) * scales ----------------
+        // ---------------- epilogue: out = (main + sm) * scales ----------------
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
         tc_fence_after();
 #pragma unroll
         for (int g = 0; g < TC_N / 32; g++) {
             if (g * 32 >= nmma) continue;
-            uint32_t v0[32], vh[32], vr[32];
+            uint32_t v0[32], vr[32];
             if (nch > 0) {
                 tmem_ld32(tl + g * 32, v0);
-                tmem_ld32(tl + ACC_HX + g * 32, vh);
                 tmem_ld32(tl + ACC_SM + g * 32, vr);
                 tmem_wait_ld();
             }
@@ -584,19 +759,11 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 for (int i = 0; i < 32; i++) {
                     const int r = g * 32 + i;
                     if (r < nrows) {
-                        // main + the count (integer and 2^-12 parts) + the residual as
-                        // an FP32 pair (two TwoSums), times c_l f (hi/lo)
-                        const float x0 = __uint_as_float(v0[i]);
-                        const int hc = (int)vh[i];
-                        const float eh = (float)(hc >> 12);                        // exact, < 2^19
-                        const float el = (float)(hc & 4095) * (1.0f / 4096.0f);    // exact
-                        const float s1 = x0 + eh;
-                        const float b1 = s1 - x0;
-                        const float e1 = (x0 - (s1 - b1)) + (eh - b1);             // exact (an integer)
-                        const float t1 = (el + e1) + __uint_as_float(vr[i]);
-                        const float sm = s1 + t1;
-                        const float bb = sm - s1;
-                        const float er = (s1 - (sm - bb)) + (t1 - bb);
+                        // main (exact integer) + the residual as an FP32 pair, times c_l f (hi/lo)
+                        const float x0 = __uint_as_float(v0[i]), x1 = __uint_as_float(vr[i]);
+                        const float sm = x0 + x1;
+                        const float bb = sm - x0;
+                        const float er = (x0 - (sm - bb)) + (x1 - bb);
                         const float2 F = sh.rfac[r];
                         const float p1 = __fmul_rn(sm, F.x);
                         const float lo = fmaf(sm, F.x, -p1) + er * F.x + sm * F.y;
@@ -609,18 +776,14 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 }
             } else {
                 float* Gq = (float*)dst + ((long long)m * 2 + q) * qstride + cg;
-                const float sc = (m == 0) ? a.s0 : a.s1;
+                const float sc = ((m == 0) ? a.s0 : a.s1) * (S2 ? -0.5f : 1.0f);
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
                     const int r = g * 32 + i;
                     if (r < nrows) {
                         float gv = 0.0f;
-                        if (nch > 0) {
-                            const int hc = (int)vh[i];
-                            const float x = (__uint_as_float(v0[i]) + (float)(hc >> 12)) +
-                                            ((float)(hc & 4095) * (1.0f / 4096.0f) + __uint_as_float(vr[i]));
-                            gv = sc * ldexpf_fast(x, sh.rowexp[r] + ce);
-                        }
+                        if (nch > 0)
+                            gv = sc * ldexpf_fast(__uint_as_float(v0[i]) + __uint_as_float(vr[i]), sh.rowexp[r] + ce);
                         Gq[(long long)(n0 + r) * a.ncol] = gv;
                     }
                 }
@@ -692,6 +855,70 @@ k_split_tables(TcArgs a, const int* __restrict__ ck_base, double2* __restrict__ 
 }
 
 // ===========================================================================
+// spin-2 plan-time walk (one block per m, threads over ring pairs): both
+// normalised Wigner recurrences over every l >= l0 = max(m, 2), checkpoints
+// at l = max(m + 32 b, l0) for every 32-wide block b of l - m, the per-row
+// maxima over ring pairs and both s of |mu 2^E| (map2alm quanta) and the
+// per-pair maxima over l and s of |d_l mu 2^E| (alm2map quanta; the same for
+// both slots).
+// ===========================================================================
+__global__ void __launch_bounds__(256)
+k_split_tables_s2(TcArgs a, const int* __restrict__ ck_base, double2* __restrict__ ck, int* __restrict__ ck_exp,
+                  const double* __restrict__ seed_mant, const int* __restrict__ seed_exp,
+                  unsigned int* __restrict__ rowmax_bits, float* __restrict__ pairmax)
+{
+    const int m = blockIdx.x;
+    const int l0 = m > 2 ? m : 2;
+    const int base = ck_base[m];
+    for (int p0 = 0; p0 < a.R; p0 += blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        const bool valid = p < a.R;
+        double cur[2] = {0.0, 0.0}, prev[2] = {0.0, 0.0}, x = 0.0;
+        int E[2] = {0, 0};
+        if (valid) {
+            for (int si = 0; si < 2; si++) {
+                const long long i0 = ((long long)m * 2 + si) * a.R + p;
+                cur[si] = seed_mant[i0];
+                E[si] = seed_exp[i0];
+            }
+            x = a.pairs[p].x;
+        }
+        float pm = 0.0f;
+        for (int l = l0; l <= a.lmax; l++) {
+            const long long ci = a_idx(a.lmax, l, m);
+            if (valid && l > l0) {
+                for (int si = 0; si < 2; si++) {
+                    const double nxt = fma(fma(a.s2A[si][ci], x, a.s2B[si][ci]), cur[si], -prev[si]);
+                    prev[si] = cur[si];
+                    cur[si] = nxt;
+                    rescale(cur[si], prev[si], E[si]);
+                }
+            }
+            if (valid && (l == l0 || (l - m) % CK_ROWS == 0)) {
+                const int b = (l - m) / CK_ROWS;      // l0 < m + 32: block 0 starts at l0
+                for (int si = 0; si < 2; si++) {
+                    const long long i1 = ((long long)(base + b) * 2 + si) * a.R + p;
+                    ck[i1] = make_double2(cur[si], prev[si]);
+                    ck_exp[i1] = E[si];
+                }
+            }
+            float vmu = 0.0f;
+            if (valid)
+                for (int si = 0; si < 2; si++) vmu = fmaxf(vmu, fabsf(f64_to_f32_scaled(cur[si], E[si])));
+            pm = fmaxf(pm, vmu * fabsf(a.s2d2[ci].x) * 1.0000003f);
+            float wv = vmu * 1.0000003f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wv = fmaxf(wv, __shfl_xor_sync(0xffffffffu, wv, o));
+            if ((threadIdx.x & 31) == 0 && wv > 0.0f) atomicMax(rowmax_bits + ci, __float_as_uint(wv));
+        }
+        if (valid) {
+            pairmax[((long long)m * 2 + 0) * a.R + p] = pm;
+            pairmax[((long long)m * 2 + 1) * a.R + p] = pm;
+        }
+    }
+}
+
+// ===========================================================================
 // alm2map input preparation: the a_lm of the batch, transposed to
 // A2[idx(l, m)][col] (col = (map, component, Re/Im)) as FP32 hi/lo pairs, so
 // each K row of the contraction is contiguous, plus the column maxima per
@@ -755,6 +982,8 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.pairs = p->t.pairs;
     a.nA = p->s.nA; a.nB = p->s.nB; a.nc = p->s.nc; a.nc64 = p->s.nc64; a.nc2 = p->s.nc2;
     a.ck = p->s.ck; a.ck_exp = p->s.ck_exp;
+    for (int si = 0; si < 2; si++) { a.s2A[si] = p->s.s2A[si]; a.s2B[si] = p->s.s2B[si]; }
+    a.s2d2 = p->s.s2d2; a.s2d64 = p->s.s2d64;
     a.rowmax = (const float*)p->s.rowmax_bits;
     a.pairmax = p->s.pairmax;
     a.colmax = colmax;
@@ -795,12 +1024,12 @@ static int pick_cluster(long long ntiles)
     return best;
 }
 
-template <bool M2A>
+template <bool M2A, bool S2>
 static cudaError_t launch_tc(const sht_plan* p, int nwork, const void* src, void* dst,
                              const TcArgs& a, const char* name, cudaStream_t st)
 {
     (void)p;
-    auto kern = k_leg_tc<M2A>;
+    auto kern = k_leg_tc<M2A, S2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
     if (e != cudaSuccess) return e;
     const long long ntiles = (a.ncol + TC_M - 1) / TC_M;
@@ -837,7 +1066,8 @@ cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const flo
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_m2a);
     a.fs0 = fs0; a.fs1 = fs1;
     a.work = p->s.work_m2a;
-    return launch_tc<true>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc", st);
+    if (p->spin) return launch_tc<true, true>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc_s2", st);
+    return launch_tc<true, false>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc", st);
 }
 
 cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, float* G,
@@ -847,7 +1077,8 @@ cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const fl
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_a2m);
     a.s0 = s0; a.s1 = s1;
     a.work = p->s.work_a2m;
-    return launch_tc<false>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc", st);
+    if (p->spin) return launch_tc<false, true>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc_s2", st);
+    return launch_tc<false, false>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc", st);
 }
 
 cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,
@@ -868,9 +1099,14 @@ cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, un
 cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base)
 {
     TcArgs a = make_tc(p, 1, nullptr, p->s.Q_m2a);
-    dim3 grid((unsigned)(p->mmax + 1), 2);
-    k_split_tables<<<grid, 256>>>(a, d_ck_base, p->s.ck, p->s.ck_exp, p->t.seed_mant, p->t.seed_exp,
-                                  p->s.rowmax_bits, p->s.pairmax);
+    if (p->spin) {
+        k_split_tables_s2<<<(unsigned)(p->mmax + 1), 256>>>(a, d_ck_base, p->s.ck, p->s.ck_exp, p->t.seed_mant,
+                                                             p->t.seed_exp, p->s.rowmax_bits, p->s.pairmax);
+    } else {
+        dim3 grid((unsigned)(p->mmax + 1), 2);
+        k_split_tables<<<grid, 256>>>(a, d_ck_base, p->s.ck, p->s.ck_exp, p->t.seed_mant, p->t.seed_exp,
+                                      p->s.rowmax_bits, p->s.pairmax);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;

@@ -387,12 +387,128 @@ static cudaError_t build_tables(sht_plan* p)
     return cudaSuccess;
 }
 
+// integer range Q of the slices for a contraction of length K: main (the sum
+// of q q' plus the integer parts folded in after every 32-wide chunk, at most
+// Q (Q + 1) K + 12 K / 32) must stay below 2^24, where FP32 holds integers
+// exactly, and Q <= 127 keeps a chunk of q r0' + r0 q' (multiples of 2^-12, at
+// most 32 Q (1 + 2^-11)) below 2^12
+static float slice_range(double K)
+{
+    K = std::max(K, 1.0);
+    double Q = std::min(std::floor(std::sqrt(16777216.0 / K)), 127.0);
+    while (Q > 1 && Q * (Q + 1) * K + 12.0 * std::ceil(K / 32.0) > 16777216.0) Q -= 1;
+    return (float)Q;
+}
+
+// ---------------------------------------------------------------------------
+// spin-2 split-form tables. The Wigner recurrence of build_tables,
+//   s lambda_l = A_l (x + B_l) s lambda_{l-1} - C_l s lambda_{l-2},
+// with s lambda_l = d_l mu_l and d_l = C_l d_{l-2} (d_{l0} = d_{l0+1} = 1)
+// becomes mu_l = (A'_l x + B'_l) mu_{l-1} - mu_{l-2},
+//   A'_l = A_l d_{l-1} / d_l,  B'_l = A_l B_l d_{l-1} / d_l
+// (2 FP64 operations per step). C_l depends on s only through s^2, so d_l is
+// the same for s = +2 and -2.
+// ---------------------------------------------------------------------------
+static cudaError_t build_split_tables_s2(sht_plan* p)
+{
+    const int lmax = p->lmax, mmax = p->mmax, R = p->R;
+    const long long nalm = p->nalm;
+    size_t acc = 0;
+    cudaError_t e;
+    std::vector<double> cA[2] = {std::vector<double>(nalm, 0.0), std::vector<double>(nalm, 0.0)};
+    std::vector<double> cB[2] = {std::vector<double>(nalm, 0.0), std::vector<double>(nalm, 0.0)};
+    std::vector<double> d64(nalm, 0.0);
+    std::vector<float2> d2(nalm, make_float2(0.0f, 0.0f));
+    for (int m = 0; m <= mmax; m++) {
+        const int l0 = m > 2 ? m : 2;
+        if (l0 > lmax) continue;
+        const ld M = m, S2 = 4;
+        std::vector<ld> d(lmax + 1, 0);
+        d[l0] = 1;
+        if (l0 + 1 <= lmax) d[l0 + 1] = 1;
+        for (int l = l0 + 2; l <= lmax; l++) {
+            const ld L = l;
+            const ld den = (L * L - M * M) * (L * L - S2);
+            const ld num = ((L - 1) * (L - 1) - M * M) * ((L - 1) * (L - 1) - S2);
+            const ld Cl = (L / (L - 1)) * sqrtl((2 * L + 1) / (2 * L - 3)) * sqrtl(num / den);
+            d[l] = Cl * d[l - 2];
+        }
+        for (int l = l0; l <= lmax; l++) {
+            const long long ci = alm_index(lmax, l, m);
+            d64[ci] = (double)d[l];
+            const float dh = (float)d[l];
+            d2[ci] = make_float2(dh, (float)(d[l] - (ld)dh));
+        }
+        for (int si = 0; si < 2; si++) {
+            const ld s = si == 0 ? 2 : -2;
+            for (int l = l0 + 1; l <= lmax; l++) {
+                const long long ci = alm_index(lmax, l, m);
+                const ld L = l;
+                const ld Al = L * sqrtl((2 * L + 1) * (2 * L - 1)) / sqrtl((L * L - M * M) * (L * L - s * s));
+                const ld Bl = M * s / (L * (L - 1));
+                cA[si][ci] = (double)(Al * d[l - 1] / d[l]);
+                cB[si][ci] = (double)(Al * Bl * d[l - 1] / d[l]);
+            }
+        }
+    }
+    for (int si = 0; si < 2; si++) {
+        if ((e = upload(&p->s.s2A[si], cA[si], &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->s.s2B[si], cB[si], &acc)) != cudaSuccess) return e;
+    }
+    if ((e = upload(&p->s.s2d64, d64, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.s2d2, d2, &acc)) != cudaSuccess) return e;
+    // work lists; checkpoint blocks: every 32 l from m, per m
+    const int TM = split_row_tile(), CKL = split_ck_rows();
+    std::vector<int4> w1, w2;
+    std::vector<int> base((size_t)(mmax + 1));
+    int nblk = 0;
+    for (int m = 0; m <= mmax; m++) {
+        base[m] = nblk;
+        for (int q = 0; q < 2; q++) {
+            const int lf = m + q;
+            const int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
+            for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk));
+            if (lmax >= m)
+                for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, nblk));
+        }
+        nblk += (lmax >= m) ? (lmax - m + 1 + CKL - 1) / CKL : 0;
+    }
+    p->s.nwork_m2a = (int)w1.size();
+    p->s.nwork_a2m = (int)w2.size();
+    if ((e = upload(&p->s.work_m2a, w1, &acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.work_a2m, w2, &acc)) != cudaSuccess) return e;
+    int* d_base = nullptr;
+    if ((e = upload(&d_base, base, &acc)) != cudaSuccess) return e;
+    const size_t nck = (size_t)std::max(nblk, 1) * 2 * R;
+    const size_t npm = (size_t)(mmax + 1) * 2 * R;
+    if ((e = cudaMalloc(&p->s.ck, nck * sizeof(double2))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.ck_exp, nck * sizeof(int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.rowmax_bits, (size_t)nalm * sizeof(unsigned int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.pairmax, npm * sizeof(float))) != cudaSuccess) { cudaFree(d_base); return e; }
+    if ((e = cudaMalloc(&p->s.err, sizeof(int))) != cudaSuccess) { cudaFree(d_base); return e; }
+    acc += nck * (sizeof(double2) + sizeof(int)) + (size_t)nalm * 4 + npm * 4 + 4;
+    cudaMemset(p->s.ck, 0, nck * sizeof(double2));
+    cudaMemset(p->s.ck_exp, 0, nck * sizeof(int));
+    cudaMemset(p->s.rowmax_bits, 0, (size_t)nalm * sizeof(unsigned int));
+    cudaMemset(p->s.pairmax, 0, npm * sizeof(float));
+    cudaMemset(p->s.err, 0, sizeof(int));
+    e = run_split_tables(p, d_base);
+    cudaFree(d_base);
+    if (e != cudaSuccess) return e;
+    // each contraction runs twice over its range (v+ and v- chunks)
+    p->s.Q_m2a = slice_range(2.0 * R);
+    p->s.Q_a2m = slice_range(2.0 * (lmax + 1));
+    p->table_bytes += acc;
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // split-form tables: normalised two-step recurrence (2 FP64 ops per lambda),
 // plan-time checkpoints of the map2alm row tiles and lambda maxima
 // ---------------------------------------------------------------------------
 static cudaError_t build_split_tables(sht_plan* p)
 {
+    if (p->spin) return build_split_tables_s2(p);
     const int lmax = p->lmax, mmax = p->mmax, R = p->R;
     const long long nalm = p->nalm;
     size_t acc = 0;
@@ -469,12 +585,8 @@ static cudaError_t build_split_tables(sht_plan* p)
     e = run_split_tables(p, d_base);
     cudaFree(d_base);
     if (e != cudaSuccess) return e;
-    // integer ranges of the slices: Q^2 K <= 2^24 keeps the main sums exact, and
-    // Q <= 127 keeps a 32-wide chunk of q r0' + r0 q' (multiples of 2^-12, at most
-    // 32 Q (1 + 2^-11)) below 2^12, where FP32 holds it exactly
-    auto qfor = [](double K) { double Q = std::floor(std::sqrt(16777216.0 / std::max(K, 1.0))); return (float)std::min(Q, 127.0); };
-    p->s.Q_m2a = qfor((double)R);
-    p->s.Q_a2m = qfor((double)(lmax / 2 + 1));
+    p->s.Q_m2a = slice_range((double)R);
+    p->s.Q_a2m = slice_range((double)(lmax / 2 + 1));
     p->table_bytes += acc;
     return cudaSuccess;
 }
@@ -489,7 +601,8 @@ static void free_tables(sht_plan* p)
     void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
-                  p->s.work_m2a, p->s.work_a2m};
+                  p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,
+                  p->s.s2d64};
     for (void* q : sp) if (q) cudaFree(q);
     if (p->pin_in) cudaFreeHost(p->pin_in);
     if (p->pin_out) cudaFreeHost(p->pin_out);
@@ -635,12 +748,11 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     }
     // the contraction lengths (ring pairs, l of one parity) bound the exact
     // integer sums of the tensor-core form
-    if (precision == SHT_SPLIT_BF16 && (2 * nside > 8192 || lmax / 2 + 1 > 8192)) {
-        set_error("SHT_SPLIT_BF16 supports nside <= 4096 and lmax <= 16383");
-        return SHT_EUNSUPPORTED;
-    }
-    if (precision == SHT_SPLIT_BF16 && spin != 0) {
-        set_error("SHT_SPLIT_BF16 supports spin 0 in this build");
+    // (spin 2 contracts twice over each range)
+    const int kmul = spin ? 2 : 1;
+    if (precision == SHT_SPLIT_BF16 && (kmul * 2 * nside > 8192 || (spin ? lmax + 1 : lmax / 2 + 1) * kmul > 8192)) {
+        set_error(spin ? "SHT_SPLIT_BF16 spin 2 supports nside <= 2048 and lmax <= 4095"
+                       : "SHT_SPLIT_BF16 supports nside <= 4096 and lmax <= 16383");
         return SHT_EUNSUPPORTED;
     }
     int ndev = 0;

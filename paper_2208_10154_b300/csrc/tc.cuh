@@ -351,19 +351,28 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
     return __int_as_float((u & ~0x7F800000) | (en << 23));
 }
 
-// Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into
-//     q  = nearest integer                          (exact in FP16 for Q <= 2048)
-//     r0 = v + vl - q rounded to the grid 2^-12     (|r0| <= 1/2 + 2^-12: exact in FP16)
-//     r1 = the rest                                 (|r1| <= 2^-13; FP16 keeps it to 2^-25)
-// so v + vl = q + r0 + r1 to ~2^-25 of the quantum. The fixed grid of r0 makes
-// every product q r0' a multiple of 2^-12, so sums of them are exact in FP32
-// while they stay below 2^12.
-__device__ __forceinline__ void slice3d(float v, float vl, float& q, float& r0, float& r1)
+// Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into four
+// FP16 pieces:
+//     q   = nearest integer                           (exact in FP16 for Q <= 2048)
+//     r0  = v - q rounded to the grid 2^-12           (|r0| <= 1/2: exact in FP16)
+//     r1  = rem = (v - q - r0) + vl rounded to FP16   (|rem| < 2^-12)
+//     r2s = (rem - r1) 2^12 rounded to FP16           (the next 11 bits, scaled up)
+// v - q and v - q - r0 are exact, so v + vl = q + r0 + r1 + 2^-12 r2s to ~2^-36
+// of the quantum. The fixed grid of r0 makes every product q r0' a multiple of
+// 2^-12, so sums of them are exact in FP32 while they stay below 2^12.
+__device__ __forceinline__ void slice4d(float v, float vl, float& q, float& r0, float& r1, float& r2s)
 {
     q = __fadd_rn(__fadd_rn(v, 12582912.0f), -12582912.0f);   // 1.5 * 2^23: nearest integer
-    const float r = __fadd_rn(v - q, vl);
+    const float r = __fadd_rn(v, -q);
     r0 = __fadd_rn(__fadd_rn(r, 3072.0f), -3072.0f);          // 1.5 * 2^11: ulp 2^-12
-    r1 = r - r0;
+    const float rem = __fadd_rn(__fadd_rn(r, -r0), vl);
+    r1 = __half2float(__float2half_rn(rem));
+    r2s = __fmul_rn(__fadd_rn(rem, -r1), 4096.0f);
+}
+// nearest integer of |x| < 2^22 (exact)
+__device__ __forceinline__ float rint_magic(float x)
+{
+    return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
 }
 __device__ __forceinline__ uint32_t pack_h2(float lo, float hi)
 {

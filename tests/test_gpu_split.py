@@ -98,3 +98,72 @@ def test_split_clusters_many_chunks(orc, sht, nside, lmax, nmaps):
     T = got + 0.01 * np.sqrt(np.mean(got ** 2, axis=-1, keepdims=True)) * rng.standard_normal(got.shape)
     ga = plan.map2alm(torch.from_numpy(T).cuda()).cpu().numpy()
     assert colerr(ga[pick], orc.map2alm(T[pick], nside, lmax)) < TOL
+
+
+# ---------------------------------------------------------------- spin 2
+S2_CASES = [
+    (16, 47, 47, 3, 1.0),       # aliasing, lmax = 3 nside - 1
+    (32, 64, 64, 4, 0.01),      # E/B spectra of the polarization workload (C_BB = 0.01 C_EE)
+    (8, 20, 20, 1, 1.0),
+    (1, 3, 3, 2, 1.0),          # smallest grid: only l = 2, 3
+    (16, 40, 20, 5, 1.0),       # mmax < lmax
+    (64, 127, 127, 70, 0.01),   # 280 columns: three column tiles, ragged
+    (128, 300, 300, 5, 0.01),   # several row / pair tiles, K' = 2 x 256 ring pairs
+    (8, 23, 23, 130, 1.0),      # 520 columns: clusters of column tiles
+]
+
+
+def _s2_alm(seed, nmaps, lmax, mmax, bb):
+    cl = inputs.cl_inv_llp1(lmax)
+    a = inputs.gaussian_alm(seed, nmaps, 2, lmax, mmax, cls=np.stack([cl, bb * cl]))
+    ls, _ = inputs.lm_arrays(lmax, mmax)
+    a[..., ls < 2] = 0
+    return a
+
+
+@pytest.mark.parametrize("nside,lmax,mmax,nmaps,bb", S2_CASES)
+def test_alm2map_split_spin2(orc, sht, nside, lmax, mmax, nmaps, bb):
+    a = _s2_alm(nside + 11, nmaps, lmax, mmax, bb)
+    want = orc.alm2map(a, nside, lmax, mmax, spin=2)
+    plan = sht.Plan(nside, lmax, mmax, 2, "split")
+    got = plan.alm2map(torch.from_numpy(a).cuda()).cpu().numpy()
+    assert colerr(got, want) < TOL
+
+
+@pytest.mark.parametrize("nside,lmax,mmax,nmaps,bb", S2_CASES)
+def test_map2alm_split_spin2(orc, sht, nside, lmax, mmax, nmaps, bb):
+    a = _s2_alm(nside + 12, nmaps, lmax, mmax, bb)
+    T = orc.alm2map(a, nside, lmax, mmax, spin=2)
+    rng = np.random.default_rng(nside + 1)
+    T += 0.01 * np.sqrt(np.mean(T ** 2, axis=-1, keepdims=True)) * rng.standard_normal(T.shape)
+    want = orc.map2alm(T, nside, lmax, mmax, spin=2)
+    plan = sht.Plan(nside, lmax, mmax, 2, "split")
+    got = plan.map2alm(torch.from_numpy(T).cuda()).cpu().numpy()
+    assert colerr(got, want) < TOL
+
+
+def test_split_spin2_adjoints(orc, sht):
+    nside, lmax, nmaps = 16, 32, 2
+    plan = sht.Plan(nside, lmax, None, 2, "split")
+    rng = np.random.default_rng(7)
+    h = rng.standard_normal((nmaps, 2, 12 * nside * nside))
+    assert colerr(plan.alm2map_adjoint(torch.from_numpy(h).cuda()).cpu().numpy(),
+                  orc.alm2map_adjoint(h, nside, lmax, spin=2)) < TOL
+    g = _s2_alm(8, nmaps, lmax, lmax, 1.0)
+    assert colerr(plan.map2alm_adjoint(torch.from_numpy(g).cuda()).cpu().numpy(),
+                  orc.map2alm_adjoint(g, nside, lmax, spin=2)) < TOL
+
+
+def test_split_spin2_many_chunks(orc, sht):
+    """Spin 2 with 1100 Q/U pairs (4400 columns, clusters of column tiles) and
+    many K chunks; the oracle checks maps spread over the column tiles."""
+    nside, lmax, nmaps = 64, 160, 1100
+    a = _s2_alm(21, nmaps, lmax, lmax, 0.01)
+    plan = sht.Plan(nside, lmax, None, 2, "split")
+    pick = [0, nmaps // 2 + 1, nmaps - 1]
+    got = plan.alm2map(torch.from_numpy(a).cuda()).cpu().numpy()
+    assert colerr(got[pick], orc.alm2map(a[pick], nside, lmax, spin=2)) < TOL
+    rng = np.random.default_rng(9)
+    T = got + 0.01 * np.sqrt(np.mean(got ** 2, axis=-1, keepdims=True)) * rng.standard_normal(got.shape)
+    ga = plan.map2alm(torch.from_numpy(T).cuda()).cpu().numpy()
+    assert colerr(ga[pick], orc.map2alm(T[pick], nside, lmax, spin=2)) < TOL
