@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "maps/s batched vs per-map on one B300 at <=1e-6 rel err; served p50/p99 latency"
 WORKLOAD = "t_nside512"
 FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (recipe table); probe measured 1.13 at 2032 MHz
-SPLIT_PRODUCTS = 8           # tensor-core products per output term in the split form
+SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split form (4 FP16 slices)
 
 
 def parse():
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--per-map-samples", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qu-maps", type=int, default=500,
+                    help="Q/U map pairs of the spin-2 (polarization) measurement at the same nside; 0 skips it")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -204,8 +206,77 @@ def ref_config(a):
 # {0.3, 0.3, 0.2, 0.15} (renormalised), spin 2 for 30% of the nside <= 128
 # requests, maps per request uniform in 1..64, seed 3. Spin-0 requests run in
 # the split form, spin-2 in the FP64 form (the split form is spin 0 only).
-SERVE_NSIDES = [64, 128, 256, 512]
-SERVE_W = [0.3, 0.3, 0.2, 0.15]
+SERVE_NSIDES = [64, 128, 256, 512, 1024]
+SERVE_W = [0.3, 0.3, 0.2, 0.15, 0.05]
+
+
+def run_qu(nside, lmax, npairs, steps, warmup, precision):
+    """Spin-2 (Q/U <-> E/B) alm2map + map2alm of `npairs` Q/U map pairs per step,
+    E/B a_lm Gaussian with C_EE = 1/(l(l+1)), C_BB = 0.01 C_EE, beside the
+    per-pair FP64 form; kernel times from libsht's own profiler."""
+    import torch
+    from paper_2208_10154_b300 import sht
+    plan = sht.Plan(nside, lmax, None, 2, precision)
+    ls = torch.arange(lmax + 1, dtype=torch.float64)
+    cl = torch.zeros(lmax + 1, dtype=torch.float64)
+    cl[2:] = 1.0 / (ls[2:] * (ls[2:] + 1.0))
+    from paper_2208_10154_b300 import inputs
+    lsa, msa = inputs.lm_arrays(lmax)
+    sd = torch.sqrt(cl[torch.from_numpy(lsa)] / torch.where(torch.from_numpy(msa) == 0, 1.0, 2.0)).cuda()
+    sd = torch.stack([sd, 0.1 * sd])[None, :, :]
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    re = torch.randn((npairs, 2, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
+    im = torch.randn((npairs, 2, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
+    im[..., torch.from_numpy(msa == 0).cuda()] = 0.0
+    alm = torch.complex(re, im).contiguous()
+    del re, im
+    ws = torch.empty(plan.workspace_bytes(npairs) + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    maps = plan.alm2map(alm, workspace=ws)
+    alm_out = torch.empty_like(alm)
+
+    def step():
+        plan.alm2map(alm, out=maps, workspace=ws)
+        plan.map2alm(maps, out=alm_out, workspace=ws)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sht.sht_profile_begin()
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    prof = sht.sht_profile_end()
+    ms = e0.elapsed_time(e1) / steps
+    # per-pair FP64 form
+    p64 = sht.Plan(nside, lmax, None, 2, "fp64")
+    a1 = alm[:1].contiguous()
+    m1 = p64.alm2map(a1)
+    p64.map2alm(m1)
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(2):
+        m1 = p64.alm2map(a1)
+        p64.map2alm(m1)
+    s1.record()
+    torch.cuda.synchronize()
+    per = 2 / (s0.elapsed_time(s1) / 1e3)
+    out = {"value": npairs / (ms / 1e3), "unit": "Q/U map pairs/s", "ms_per_step": ms, "steps": steps,
+           "config": {"workload": "qu", "nside": nside, "lmax": lmax, "npairs": npairs, "spin": 2,
+                      "precision": precision, "cl": "EE 1/(l(l+1)), BB 0.01 EE", "seed": 2},
+           "per_map": {"value": per, "unit": "Q/U map pairs/s", "form": "fp64, one pair"},
+           "batched_over_per_map": npairs / (ms / 1e3) / per,
+           "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / steps} for k, v in prof.items()}}
+    del plan, p64, ws, maps, alm, alm_out
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_serving(n_req, load, device):
@@ -217,7 +288,7 @@ def run_serving(n_req, load, device):
     spec = []
     for _ in range(n_req):
         nside = int(rng.choice(SERVE_NSIDES, p=w))
-        spin = 2 if (nside <= 128 and rng.random() < 0.3) else 0
+        spin = 2 if rng.random() < 0.3 else 0
         op = "alm2map" if rng.random() < 0.5 else "map2alm"
         spec.append((op, nside, spin, int(rng.integers(1, 65))))
     # one input pool per (op, nside, spin) of 64 maps; a request takes its first n
@@ -271,8 +342,9 @@ def run_serving(n_req, load, device):
             "maps_per_s": opened["maps_per_s"], "batches": opened["batches"],
             "saturation_maps_per_s": closed["maps_per_s"], "errors": opened["errors"] + closed["errors"],
             "peak_admitted_gb": srv.peak_used / 1e9,
-            "workload": "Poisson stream; alm2map/map2alm 50/50; nside 64/128/256/512 (0.3/0.3/0.2/0.15); "
-                        "spin 2 in 30% of nside<=128; 1-64 maps per request; split form for spin 0, FP64 for spin 2"}
+            "workload": "Poisson stream; alm2map/map2alm 50/50; nside 64/128/256/512/1024 "
+                        "(0.3/0.3/0.2/0.15/0.05); spin 2 in 30%; 1-64 maps per request (inputs from pools "
+                        "of 64 maps); split form"}
 
 
 # ----------------------------------------------------------------------------
@@ -458,10 +530,14 @@ def main():
         cpu = {"value": 1.0 / dt, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"1 map (alm2map + map2alm, nside {nside}, lmax {lmax}), separable tier"}
 
+    del alm, maps_in
+    torch.cuda.empty_cache()
+    qu = None
+    if rank == 0 and a.qu_maps > 0:
+        qu = run_qu(nside, lmax, a.qu_maps, max(1, min(a.steps, 3)), max(1, min(a.warmup, 2)), precision)
+
     serving = None
     if rank == 0 and a.serve_requests > 0:
-        del alm, maps_in
-        torch.cuda.empty_cache()
         serving = run_serving(a.serve_requests, a.serve_load, dev)
 
     if rank == 0:
@@ -476,7 +552,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
             "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
-            "kernels": prof, "plan_create_s": plan_s, "serving": serving,
+            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -28,7 +28,7 @@ import time
 from dataclasses import dataclass, field
 
 
-@dataclass
+@dataclass(eq=False)          # compared by identity (the payloads are arrays)
 class Request:
     op: str                      # "alm2map" or "map2alm"
     nside: int
@@ -48,7 +48,7 @@ class Request:
         return (self.op, self.nside, lmax, self.spin, precision)
 
 
-@dataclass
+@dataclass(eq=False)
 class _Batch:
     key: tuple
     reqs: list
@@ -220,7 +220,9 @@ class GpuExecutor:
         op, nside, lmax, spin, prec = key
         if prec != "auto":
             return prec
-        return "split" if spin == 0 and lmax <= 2047 else "fp64"
+        # the split form's limits (libsht returns SHT_EUNSUPPORTED beyond them)
+        ok = lmax <= 2047 and nside <= (4096 if spin == 0 else 2048)
+        return "split" if ok else "fp64"
 
     def prepare(self, key):
         pk = key[1:4] + (self._precision(key),)

@@ -92,6 +92,25 @@ def test_failed_batch_fails_only_its_requests():
     assert a.error and b.error is None and b.result is not None
 
 
+def test_batches_finishing_out_of_order():
+    """A later batch can finish first; retiring it must not compare the
+    array payloads of the others."""
+    class Lifo(FakeExecutor):
+        def launch(self, key, inputs):
+            h = super().launch(key, inputs)
+            h["left"] = 10 - len(self.launched)      # later launches finish sooner
+            return h
+    rng = np.random.default_rng(4)
+    ex = Lifo()
+    srv = Server(ex, hbm_budget=1e9, max_batch_maps=3, slots=4)
+    reqs = [srv.submit(_req("alm2map", 8, 3, rng)) for i in range(4)]    # one key, one batch each
+    srv.run_until_idle()
+    for r in reqs:
+        assert r.error is None
+        np.testing.assert_array_equal(r.result, 2 * r.data)
+    assert srv.completed != reqs                      # retired out of order
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("graphs", [False, True])
 def test_gpu_results_same_alone_and_in_the_mix(graphs):
