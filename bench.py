@@ -30,6 +30,11 @@ METRIC = "maps/s batched vs per-map on one B300 at <=1e-6 rel err; served p50/p9
 WORKLOAD = "t_nside512"
 FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (recipe table); probe measured 1.13 at 2032 MHz
 SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split form (4 FP16 slices)
+# DRAM traffic (read + write) of one launch from an ncu capture of the same
+# kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
+# and lmax it grows in proportion to the map columns (profiles/k_leg_tc_nside512.md)
+TRAFFIC_NCU = {"k_leg_a2m_tc": 3.545e9, "k_leg_m2a_tc": 5.783e9}
+TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
 
 def parse():
@@ -478,8 +483,12 @@ def main():
             ach_alg = flops / (avg_ms / 1e3) / 1e12
             ach = SPLIT_PRODUCTS * ach_alg
             pk = peaks.get("bf16_tflops_sustained", 1400.0)
+            traffic = None
+            if name in TRAFFIC_NCU and (nside, lmax) == (TRAFFIC_NCU_AT["nside"], TRAFFIC_NCU_AT["lmax"]):
+                traffic = TRAFFIC_NCU[name] * (2 * nmaps) / TRAFFIC_NCU_AT["ncol"]
             roofline = {"kernel": name, "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                        "frac": ach / pk, "traffic": None,
+                        "frac": ach / pk, "traffic": traffic,
+                        "traffic_source": "ncu capture at 128 maps, scaled by map columns" if traffic else None,
                         "peak_source": f"bf16 dense sustained ({peak_src}); the kernel runs inside a long step",
                         "executed_flops_per_launch": SPLIT_PRODUCTS * flops, "algorithmic_tflops": ach_alg,
                         "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
