@@ -258,6 +258,7 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
     torch.cuda.synchronize()
     prof = sht.sht_profile_end()
     ms = e0.elapsed_time(e1) / steps
+    status = plan.device_status()
     # per-pair FP64 form
     p64 = sht.Plan(nside, lmax, None, 2, "fp64")
     a1 = alm[:1].contiguous()
@@ -277,7 +278,7 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
            "config": {"workload": "qu", "nside": nside, "lmax": lmax, "npairs": npairs, "spin": 2,
                       "precision": precision, "cl": "EE 1/(l(l+1)), BB 0.01 EE", "seed": 2},
            "per_map": {"value": per, "unit": "Q/U map pairs/s", "form": "fp64, one pair"},
-           "batched_over_per_map": npairs / (ms / 1e3) / per,
+           "batched_over_per_map": npairs / (ms / 1e3) / per, "device_status": status,
            "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / steps} for k, v in prof.items()}}
     del plan, p64, ws, maps, alm, alm_out
     torch.cuda.empty_cache()
@@ -435,6 +436,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
     prof = sht.sht_profile_end()
+    plan.device_status()                 # raises if a bounded device wait gave up
     if world > 1:
         dist.barrier()
     ms_step = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, "cuda")

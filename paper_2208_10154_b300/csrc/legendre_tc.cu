@@ -110,23 +110,34 @@ __device__ __forceinline__ long long a_idx(int lmax, int l, int m)
     return (long long)m * (2 * lmax + 1 - m) / 2 + l;
 }
 
-// 8 consecutive k (16-byte chunk j) of row `row`, four slice planes
-__device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
-                                       const float (&vl)[8])
+// the four slice planes of 8 consecutive k, packed as FP16 pairs
+__device__ __forceinline__ void pack4x8(const float (&v)[8], const float (&vl)[8], uint4 (&pk)[NPL])
 {
-    uint32_t pk[NPL][4];
+    uint32_t w[NPL][4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         float x0[NPL], x1[NPL];
         slice4d(v[2 * i], vl[2 * i], x0[0], x0[1], x0[2], x0[3]);
         slice4d(v[2 * i + 1], vl[2 * i + 1], x1[0], x1[1], x1[2], x1[3]);
 #pragma unroll
-        for (int b = 0; b < NPL; b++) pk[b][i] = pack_h2(x0[b], x1[b]);
+        for (int b = 0; b < NPL; b++) w[b][i] = pack_h2(x0[b], x1[b]);
     }
+#pragma unroll
+    for (int b = 0; b < NPL; b++) pk[b] = make_uint4(w[b][0], w[b][1], w[b][2], w[b][3]);
+}
+// ... stored as the 16-byte chunk j of row `row` of each plane
+__device__ __forceinline__ void store4x8(uint8_t* planes, int plane_bytes, int row, int j, const uint4 (&pk)[NPL])
+{
     const uint32_t off = sw64_chunk(row, j);
 #pragma unroll
-    for (int b = 0; b < NPL; b++)
-        *reinterpret_cast<uint4*>(planes + b * plane_bytes + off) = make_uint4(pk[b][0], pk[b][1], pk[b][2], pk[b][3]);
+    for (int b = 0; b < NPL; b++) *reinterpret_cast<uint4*>(planes + b * plane_bytes + off) = pk[b];
+}
+__device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
+                                       const float (&vl)[8])
+{
+    uint4 pk[NPL];
+    pack4x8(v, vl, pk);
+    store4x8(planes, plane_bytes, row, j, pk);
 }
 
 // one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
@@ -166,11 +177,13 @@ struct TcShared {
     uint64_t cdone;            // the correction accumulators hold a finished chunk
     uint64_t cfree;            // the correction accumulators drained (4 epilogue warps)
     int released;              // highest chunk whose stage is free in every CTA of the cluster
+    int eok;                   // the data warps' waits all succeeded (read by the epilogue)
     uint32_t tmem;
     int colexp[TC_M];
     int rowexp[TC_N];          // quantum exponent per lambda row (l or ring pair)
     double cA[TC_N], cB[TC_N]; // map2alm: recurrence coefficients of the tile's rows
     float2 rfac[TC_N];         // map2alm: c_l * factor as an FP32 hi/lo pair
+    int rowidx[TC_N];          // map2alm: packed index of the row's (l, m)
 };
 constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
 
@@ -246,6 +259,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
     const long long qstride = (long long)a.R * a.ncol;
 
     for (int r = tid; r < TC_N; r += blockDim.x) {
+        if (M2A) sh.rowidx[r] = (r < nrows) ? (int)a_idx(a.lmax, l_first + 2 * (n0 + r), m) : 0;
         if (M2A && S2) {
             sh.cA[r] = 0.0; sh.cB[r] = 0.0;
             if (r < nrows) {
@@ -301,6 +315,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         mbar_init(&sh.cdone, 1);
         mbar_init(&sh.cfree, 4);
         sh.released = NST - 1;
+        sh.eok = 1;
         mbar_fence_init();
     }
     if (warp == 0) tmem_alloc(&sh.tmem, 512);
@@ -526,16 +541,18 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             // A warp's pieces can be several chunks apart, more than the parity
             // of the stage barrier can tell apart, so it waits on the monotonic
             // count of released chunks that the data warps publish instead.
-            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
-            uint8_t* B = smem + s * STAGE_BYTES + NPL * A_PLANE;
+            // slice and pack the piece while the stage may still be in use
+            // (map2alm: per row, planes (q, r0) and (r1, r2s) as FP16 pairs;
+            // alm2map: 16-byte chunks of 8 consecutive k per plane)
+            uint32_t pk2[M2A ? 2 * PR : 1];
+            uint4 pk4[M2A ? 1 : (KC / 8) * NPL];
             if constexpr (M2A) {
 #pragma unroll
                 for (int i = 0; i < PR; i++) {
                     float x[NPL];
                     slice4d(hb[i], lb[i], x[0], x[1], x[2], x[3]);
-                    const uint32_t off = sw64_off(j * PR + i, lane);
-#pragma unroll
-                    for (int b = 0; b < NPL; b++) *reinterpret_cast<__half*>(B + b * B_PLANE + off) = __float2half_rn(x[b]);
+                    pk2[2 * i] = pack_h2(x[0], x[1]);
+                    pk2[2 * i + 1] = pack_h2(x[2], x[3]);
                 }
             } else {
 #pragma unroll
@@ -543,7 +560,31 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     float hv[8], lv[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) { hv[i] = hb[jj * 8 + i]; lv[i] = lb[jj * 8 + i]; }
-                    put4x8(B, B_PLANE, prow, jj, hv, lv);
+                    uint4 t4[NPL];
+                    pack4x8(hv, lv, t4);
+#pragma unroll
+                    for (int b = 0; b < NPL; b++) pk4[jj * NPL + b] = t4[b];
+                }
+            }
+            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
+            uint8_t* B = smem + s * STAGE_BYTES + NPL * A_PLANE;
+            if constexpr (M2A) {
+#pragma unroll
+                for (int i = 0; i < PR; i++) {
+                    const uint32_t off = sw64_off(j * PR + i, lane);
+                    const uint32_t w01 = pk2[2 * i], w23 = pk2[2 * i + 1];
+                    *reinterpret_cast<uint16_t*>(B + off) = (uint16_t)(w01 & 0xFFFFu);
+                    *reinterpret_cast<uint16_t*>(B + B_PLANE + off) = (uint16_t)(w01 >> 16);
+                    *reinterpret_cast<uint16_t*>(B + 2 * B_PLANE + off) = (uint16_t)(w23 & 0xFFFFu);
+                    *reinterpret_cast<uint16_t*>(B + 3 * B_PLANE + off) = (uint16_t)(w23 >> 16);
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < KC / 8; jj++) {
+                    uint4 t4[NPL];
+#pragma unroll
+                    for (int b = 0; b < NPL; b++) t4[b] = pk4[jj * NPL + b];
+                    store4x8(B, B_PLANE, prow, jj, t4);
                 }
             }
             fence_proxy_async_smem();
@@ -738,11 +779,29 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         }
         if (dok && nch >= 1) drain(nch - 1);
 
-        // ---------------- epilogue: out = (main + sm) * scales ----------------
+        // the last MMAs are complete once every wait above succeeded
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
-        tc_fence_after();
+        if (lane == 0 && !ok) sh.eok = 0;
+        tmem_wait_st();
+    }
+
+    // ---------------- epilogue: out = (main + sm) * scales, all eight warps ----------------
+    // (warps w and w + 4 reach the same TMEM lanes, i.e. the same map column;
+    // warps 4-7 take rows 0-63, warps 0-3 rows 64-127)
+    __syncwarp();
+    tc_fence_before();
+    named_bar_sync(2, 256);
+    tc_fence_after();
+    {
+        const int t = tid & (TC_M - 1);
+        const long long cg = c0 + t;
+        const bool cok = cg < a.ncol;
+        const int ce = sh.colexp[t];
+        const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const bool ok = sh.eok != 0;
+        const int g0 = (warp >= 4) ? 0 : 2;
 #pragma unroll
-        for (int g = 0; g < TC_N / 32; g++) {
+        for (int g = g0; g < g0 + 2; g++) {
             if (g * 32 >= nmma) continue;
             uint32_t v0[32], vr[32];
             if (nch > 0) {
@@ -752,9 +811,8 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             }
             if (!ok || !cok) continue;
             if (M2A) {
-                double* alm = (double*)dst;
-                const long long mp = cg >> 1;
-                const int reim = (int)(cg & 1);
+                double* alm = (double*)dst + ((cg >> 1) * a.nalm) * 2 + (cg & 1);
+                const bool zero_im = (m == 0) && (cg & 1);
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
                     const int r = g * 32 + i;
@@ -769,9 +827,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                         const float lo = fmaf(sm, F.x, -p1) + er * F.x + sm * F.y;
                         double v = f32_to_f64(p1) + f32_to_f64(lo);            // final FP64 accumulation
                         v = ldexp_fast(v, sh.rowexp[r] + ce);
-                        if (m == 0 && reim) v = 0.0;
-                        const int l = l_first + 2 * (n0 + r);
-                        alm[(mp * a.nalm + a_idx(a.lmax, l, m)) * 2 + reim] = v;
+                        alm[(long long)sh.rowidx[r] * 2] = zero_im ? 0.0 : v;
                     }
                 }
             } else {
