@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--qu-maps", type=int, default=500,
                     help="Q/U map pairs of the spin-2 (polarization) measurement at the same nside; 0 skips it")
+    ap.add_argument("--no-context", action="store_true",
+                    help="skip the context run (nside 256, lmax 767, 1000 maps, Legendre only)")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -281,6 +283,58 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
            "batched_over_per_map": npairs / (ms / 1e3) / per, "device_status": status,
            "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / steps} for k, v in prof.items()}}
     del plan, p64, ws, maps, alm, alm_out
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_context(precision, steps=3):
+    """Context run beside the paper's Appendix B timing model: spin 0, nside 256,
+    lmax 767, 1000 maps; the Legendre contractions alone (one alm2map and one
+    map2alm per step, their kernel times from libsht's profiler) against the
+    paper's t1 = 0.222 s for one Legendre-only transform of 1000 maps on an
+    A100 in FP64. Also map2alm with 3 iteration rounds (Algorithm 2) against
+    the same without: the paper's round costs 2 t1 = 0.444 s."""
+    import torch
+    from paper_2208_10154_b300 import sht
+    nside, lmax, nmaps = 256, 767, 1000
+    plan = sht.Plan(nside, lmax, None, 0, precision)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    alm = torch.view_as_complex(torch.randn((nmaps, 1, plan.nalm, 2), generator=g, dtype=torch.float64,
+                                            device="cuda")).contiguous()
+    ws = torch.empty(plan.workspace_bytes(nmaps, 3) + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    maps = plan.alm2map(alm, workspace=ws)
+    alm_out = torch.empty_like(alm)
+    plan.map2alm(maps, out=alm_out, workspace=ws)
+    torch.cuda.synchronize()
+    sht.sht_profile_begin()
+    for _ in range(steps):
+        plan.alm2map(alm, out=maps, workspace=ws)
+        plan.map2alm(maps, out=alm_out, workspace=ws)
+    torch.cuda.synchronize()
+    prof = sht.sht_profile_end()
+    plan.device_status()
+    leg = {k: v["ms"] / steps for k, v in prof.items() if "leg" in k}
+    per_transform = sum(leg.values()) / 2.0
+    iter_ms = {}
+    for niter in (0, 3):
+        plan.map2alm(maps, out=alm_out, niter=niter, workspace=ws)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.map2alm(maps, out=alm_out, niter=niter, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        iter_ms[niter] = e0.elapsed_time(e1)
+    plan.device_status()
+    out = {"config": {"nside": nside, "lmax": lmax, "nmaps": nmaps, "spin": 0, "precision": precision},
+           "legendre_ms_per_transform": per_transform, "legendre_kernels_ms": leg,
+           "paper_t1_ms": 222.0, "paper_hw": "one A100, FP64 (App. B)",
+           "ratio_paper_over_ours": 222.0 / per_transform,
+           "map2alm_ms": {"niter0": iter_ms[0], "niter3": iter_ms[3]},
+           "iteration_round_ms": (iter_ms[3] - iter_ms[0]) / 3.0, "paper_round_ms": 444.0}
+    del plan, ws, maps, alm, alm_out
     torch.cuda.empty_cache()
     return out
 
@@ -543,6 +597,9 @@ def main():
 
     del alm, maps_in
     torch.cuda.empty_cache()
+    context = None
+    if rank == 0 and not a.no_context:
+        context = run_context(precision)
     qu = None
     if rank == 0 and a.qu_maps > 0:
         qu = run_qu(nside, lmax, a.qu_maps, max(1, min(a.steps, 3)), max(1, min(a.warmup, 2)), precision)
@@ -563,7 +620,7 @@ def main():
             "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
             "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
-            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "serving": serving,
+            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

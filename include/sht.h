@@ -84,8 +84,9 @@ void sht_plan_destroy(sht_plan* plan);
 size_t sht_workspace_bytes(const sht_plan* plan, int nmaps);
 
 /* Workspace for sht_map2alm with `niter` > 0 refinement steps of
- * Algorithm 2 (adds a residual map buffer and a coefficient increment
- * buffer). Equal to sht_workspace_bytes for niter = 0. */
+ * Algorithm 2 (adds a second ring-spectrum buffer for the residual, in the
+ * split form also its column maxima, and a coefficient increment buffer).
+ * Equal to sht_workspace_bytes for niter = 0. */
 size_t sht_workspace_bytes_iter(const sht_plan* plan, int nmaps, int niter);
 
 /* Plan properties. */
@@ -109,6 +110,9 @@ sht_status sht_alm2map(sht_plan* plan, const void* alm, void* map, int nmaps,
  * equ:alm-eb, equ:aeab mat form). map -> alm, layouts as above, with
  * `niter` >= 0 refinement steps of Algorithm 2 (0 = plain quadrature):
  *   a^0 = map2alm(T), a^{n+1} = a^n + map2alm(T - alm2map(a^n)).
+ * The steps run on the ring spectra (the residual's backward and forward
+ * FFTs are replaced by their exact action on the Fourier coefficients), so
+ * a step costs two Legendre contractions and no FFT.
  * niter > 0 needs sht_workspace_bytes_iter(plan, nmaps, niter) bytes. */
 sht_status sht_map2alm(sht_plan* plan, const void* map, void* alm, int nmaps, int niter,
                        void* workspace, size_t workspace_bytes, void* stream);

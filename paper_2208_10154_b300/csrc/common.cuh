@@ -183,6 +183,11 @@ cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const fl
                                    int nmaps, float s0, float s1, cudaStream_t st);
 cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,
                             cudaStream_t st);
+// Fourier-domain residual of the iteration, D = T - F(G) (fft.cu), and the
+// split form's column maxima of a T-layout buffer
+cudaError_t launch_alias_residual(const sht_plan* p, const void* T, const void* G, void* D, int nmaps,
+                                  cudaStream_t st);
+cudaError_t launch_colmax_T(const sht_plan* p, const float2* T, unsigned int* colmax, int nmaps, cudaStream_t st);
 // split form, alm2map: offset of the transposed a_lm (A2) inside the T / G buffer
 size_t split_a2_offset(const sht_plan* p, int nmaps);
 cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base);

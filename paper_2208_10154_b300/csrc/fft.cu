@@ -8,6 +8,8 @@
 // afterwards. Power-of-two N uses an in-place radix-2 FFT in shared memory;
 // any other N (the 4i-pixel cap rings) uses Bluestein's chirp-z algorithm on
 // the next power of two >= 2N-1 with resident chirp tables.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace sht {
@@ -273,6 +275,202 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
     k_fft_backward<double><<<grid, 256, sm, st>>>(G, map, p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp,
                                                    p->t.bhat, p->fft_max, p->R, p->mmax, p->npix,
                                                    ncols(p, nmaps));
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fourier-domain residual of the iteration (Algorithm 2 restricted to the
+// ring spectra): D = T - F(G), where F is what a backward FFT followed by a
+// forward FFT does to the coefficients G[m][q][p][c] of a ring pair. Per ring
+// of N pixels and phase offset phi0 (0 or pi/N), both steps fold m onto the
+// FFT circle (Appendix A.1); with k0 = m div N, j = m mod N, j' = (N - j) mod N
+// and sigma = -1 if phi0 != 0 else 1 (the phases e^{+-i m phi0} of two
+// aliases differ by e^{i k N phi0} = sigma^k), for a ring's own coefficients
+//     F(c)_m = (N / 2) sigma^{k0} [B(j) + sigma_j conj(B(j'))],
+//     B(j) = sum_k sigma^k w_{j+kN} c_{j+kN}   (w_0 = 1, w_{m>0} = 2)
+// with sigma_j = sigma for j > 0 and 1 for j = 0. For a pair of rings (north
+// = E + O, south = E - O, the same N and phi0) it acts on the E and O slots
+// separately with N in place of N / 2; the equator ring has no mirror (its
+// forward FFT sees only the north ring), so there E' = O' = F(E + O).
+// No trigonometry. One thread per complex column (coalesced over the
+// columns); it walks the bin pairs (j, N - j), folding their aliases and
+// writing D for every m on them. FP64, or for the split form FP32 G and
+// double-float sums with FP32 hi/lo T and D. D may be G itself (FP64): each
+// thread reads its G before it writes D on the same m.
+// grid = (ring pair, column blocks of 128)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v)
+{
+    const float s = hi + v, bb = s - hi;
+    lo += (hi - (s - bb)) + (v - bb);
+    hi = s;
+}
+__device__ __forceinline__ float2 df_norm(float hi, float lo)
+{
+    const float s = hi + lo;
+    return make_float2(s, lo - (s - hi));
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(128)
+k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const PairGeom* __restrict__ pairs,
+                 int R_, int mmax, long long ncol, int nmc)
+{
+    const int p = blockIdx.x;
+    const int mc = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mc >= nmc) return;
+    const PairGeom g = pairs[p];
+    const int N = g.n;
+    const bool neg = g.phi0 != 0.0;               // sigma = -1
+    const bool eq = g.start_s < 0;                // the equator ring: no mirror
+    const long long qs = (long long)R_ * ncol;
+    auto idx = [&](int m, int slot) -> long long {
+        return ((long long)m * 2 + slot) * qs + (long long)p * ncol + (long long)mc * 2;
+    };
+    const int jmax = min(N / 2, mmax);
+    if constexpr (SPLIT) {
+        const float2* G = (const float2*)Gv;      // (re, im) of one complex column, FP32
+        const float4* T = (const float4*)Tv;      // (re hi, re lo, im hi, im lo)
+        float4* D = (float4*)Dv;
+        auto fold = [&](int j, int slot) -> float4 {
+            float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
+            bool odd = false;
+            for (int m = j; m <= mmax; m += N) {
+                // w = w_m sigma^k: the products w G are exact in FP32
+                const float w = (m ? 2.0f : 1.0f) * ((neg && odd) ? -1.0f : 1.0f);
+                const float2 v = G[idx(m, slot) >> 1];
+                df_add(rh, rl, w * v.x);
+                df_add(ih, il, w * v.y);
+                if (eq) {                          // the ring's coefficient E + O
+                    const float2 o = G[idx(m, 1) >> 1];
+                    df_add(rh, rl, w * o.x);
+                    df_add(ih, il, w * o.y);
+                }
+                odd = !odd;
+            }
+            return make_float4(rh, rl, ih, il);
+        };
+        // D = T - f sigma^k0 (B + s conj(Bc)) on every m = j + k N
+        auto unfold = [&](int j, int slot, float4 B, float4 Bc, bool sneg) {
+            float xr = B.x, xrl = B.y, xi = B.z, xil = B.w;
+            const float sj = sneg ? -1.0f : 1.0f;
+            df_add(xr, xrl, sj * Bc.x);
+            xrl += sj * Bc.y;
+            df_add(xi, xil, -sj * Bc.z);
+            xil -= sj * Bc.w;
+            bool odd = false;
+            for (int m = j; m <= mmax; m += N) {
+                // f = (N or N / 2) sigma^k0, exact in FP32
+                const float f = (eq ? 0.5f : 1.0f) * (float)N * ((neg && odd) ? -1.0f : 1.0f);
+                const float fr = xr * f, fi = xi * f;
+                const float frl = fmaf(xr, f, -fr) + xrl * f, fil = fmaf(xi, f, -fi) + xil * f;
+                for (int s2 = 0; s2 < (eq ? 2 : 1); s2++) {
+                    const long long i = idx(m, eq ? s2 : slot) >> 1;
+                    const float4 t = T[i];
+                    float dr = t.x, drl = t.y, di = t.z, dil = t.w;
+                    df_add(dr, drl, -fr);
+                    drl -= frl;
+                    df_add(di, dil, -fi);
+                    dil -= fil;
+                    const float2 a = df_norm(dr, drl), b = df_norm(di, dil);
+                    D[i] = make_float4(a.x, a.y, b.x, b.y);
+                }
+                odd = !odd;
+            }
+        };
+        for (int slot = 0; slot < (eq ? 1 : 2); slot++) {
+            for (int j = 0; j <= jmax; j++) {
+                const int jp = (N - j) % N;
+                const float4 Bj = fold(j, slot);
+                const float4 Bjp = (jp == j) ? Bj : (jp <= mmax ? fold(jp, slot) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                unfold(j, slot, Bj, Bjp, neg && j);
+                if (jp != j && jp <= mmax) unfold(jp, slot, Bjp, Bj, neg && jp);
+            }
+        }
+    } else {
+        const double2* G = (const double2*)Gv;
+        const double2* T = (const double2*)Tv;
+        double2* D = (double2*)Dv;
+        auto fold = [&](int j, int slot) -> double2 {
+            double2 b = make_double2(0.0, 0.0);
+            double sk = 1.0;
+            for (int m = j; m <= mmax; m += N) {
+                double2 v = G[idx(m, slot) >> 1];
+                if (eq) {                          // the ring's coefficient E + O
+                    const double2 o = G[idx(m, 1) >> 1];
+                    v.x += o.x;
+                    v.y += o.y;
+                }
+                const double w = (m ? 2.0 : 1.0) * sk;
+                b.x += w * v.x;
+                b.y += w * v.y;
+                if (neg) sk = -sk;
+            }
+            return b;
+        };
+        auto unfold = [&](int j, int slot, double2 B, double2 Bc, bool sneg) {
+            const double sj = sneg ? -1.0 : 1.0;
+            const double xr = B.x + sj * Bc.x, xi = B.y - sj * Bc.y;
+            double fk = (eq ? 0.5 : 1.0) * (double)N;
+            for (int m = j; m <= mmax; m += N) {
+                for (int s2 = 0; s2 < (eq ? 2 : 1); s2++) {
+                    const long long i = idx(m, eq ? s2 : slot) >> 1;
+                    const double2 t = T[i];
+                    D[i] = make_double2(t.x - fk * xr, t.y - fk * xi);
+                }
+                if (neg) fk = -fk;
+            }
+        };
+        for (int slot = 0; slot < (eq ? 1 : 2); slot++) {
+            for (int j = 0; j <= jmax; j++) {
+                const int jp = (N - j) % N;
+                const double2 Bj = fold(j, slot);
+                const double2 Bjp = (jp == j) ? Bj : (jp <= mmax ? fold(jp, slot) : make_double2(0.0, 0.0));
+                unfold(j, slot, Bj, Bjp, neg && j);
+                if (jp != j && jp <= mmax) unfold(jp, slot, Bjp, Bj, neg && jp);
+            }
+        }
+    }
+}
+
+// column maxima of T[m][q][p][c] (FP32 hi/lo) over the ring pairs, as float
+// bits: the quanta of the split map2alm. grid = ((mmax + 1) * 2, column
+// blocks of 256)
+__global__ void __launch_bounds__(256)
+k_colmax_T(const float2* __restrict__ T, unsigned int* __restrict__ colmax, int R_, long long ncol)
+{
+    const long long c = (long long)blockIdx.y * blockDim.x + threadIdx.x;
+    if (c >= ncol) return;
+    const float2* t = T + (long long)blockIdx.x * R_ * ncol + c;
+    float mx = 0.0f;
+    for (int p = 0; p < R_; p++) mx = fmaxf(mx, fabsf(t[(long long)p * ncol].x));
+    colmax[(long long)blockIdx.x * ncol + c] = __float_as_uint(mx);
+}
+
+cudaError_t launch_alias_residual(const sht_plan* p, const void* T, const void* G, void* D, int nmaps,
+                                  cudaStream_t st)
+{
+    const bool split = p->precision != SHT_FP64;
+    const int nmc = nmaps * p->ncomp;
+    dim3 grid(p->R, (nmc + 127) / 128);
+    prof_start("k_alias_residual", st);
+    if (split)
+        k_alias_residual<true><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc);
+    else
+        k_alias_residual<false><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmax_T(const sht_plan* p, const float2* T, unsigned int* colmax, int nmaps, cudaStream_t st)
+{
+    const long long nc = ncols(p, nmaps);
+    dim3 grid((unsigned)((p->mmax + 1) * 2), (unsigned)((nc + 255) / 256));
+    prof_start("k_colmax_T", st);
+    k_colmax_T<<<grid, 256, 0, st>>>(T, colmax, p->R, nc);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

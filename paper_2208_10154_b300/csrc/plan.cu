@@ -625,30 +625,44 @@ size_t tbuf_bytes(const sht_plan* p, int nmaps)
     return std::max(n * sizeof(float2), split_a2_offset(p, nmaps) + a2);
 }
 
-// workspace layout: [T/G buffer][residual map][delta alm] (the last two only
-// for map2alm with niter > 0)
 static size_t colmax_bytes(const sht_plan* p, int nmaps)
 {
     return p->precision == SHT_FP64 ? 0 : (size_t)(p->mmax + 1) * 2 * (size_t)ncols(p, nmaps) * sizeof(float);
 }
 
+// Workspace layout: [T / G buffer][column maxima] for one transform. map2alm
+// with niter > 0 keeps the ring spectra T of the first pass and adds, for the
+// Fourier-domain iteration: [G buffer of alm2map (FP64: also the residual D)]
+// [split form: residual D (FP32 hi/lo)][split: column maxima][delta a_lm].
+struct IterWs {
+    size_t g, d, cm, da, end;
+};
+static IterWs iter_ws(const sht_plan* p, int nmaps)
+{
+    IterWs w;
+    const size_t tb = round_up(tbuf_bytes(p, nmaps), 256), cb = round_up(colmax_bytes(p, nmaps), 256);
+    const size_t n = (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps);
+    w.g = tb + cb;
+    if (p->precision == SHT_FP64) {
+        w.d = w.g;
+        w.cm = w.g + tb;
+        w.da = w.cm;
+    } else {
+        w.d = w.g + tb;
+        w.cm = w.d + round_up(n * sizeof(float2), 256);
+        w.da = w.cm + cb;
+    }
+    w.end = w.da + round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
+    return w;
+}
+
 static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
 {
-    size_t b = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
-    if (niter > 0) {
-        b += round_up((size_t)nmaps * p->ncomp * (size_t)p->npix * sizeof(double), 256);
-        b += round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
-    }
-    return b;
+    if (niter > 0) return iter_ws(p, nmaps).end;
+    return round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
 }
 
 // elementwise helpers for the iteration (Algorithm 2)
-__global__ void k_sub(double* __restrict__ r, const double* __restrict__ a, long long n)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    long long st = (long long)gridDim.x * blockDim.x;
-    for (; i < n; i += st) r[i] = a[i] - r[i];
-}
 __global__ void k_add(double* __restrict__ a, const double* __restrict__ d, long long n)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -886,29 +900,40 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     const double dsig = 4.0 * PI_D / (double)p->npix;
     s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
     if (s != SHT_OK || niter == 0) return s;
-    // Algorithm 2: a += map2alm(T - alm2map(a)), niter times
-    size_t off = round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
-    double* res = (double*)((char*)ws + off);
-    long long nm = (long long)nmaps * p->ncomp * p->npix;
-    off += round_up((size_t)nm * sizeof(double), 256);
-    double* da = (double*)((char*)ws + off);
-    long long na = (long long)nmaps * p->ncomp * p->nalm * 2;
-    for (int it = 0; it < niter; it++) {
-        s = do_alm2map(p, (const double*)alm, res, nmaps, ws, 1.0, 1.0, st);
-        if (s != SHT_OK) return s;
-        prof_start("k_sub", st);
-        k_sub<<<ew_grid(nm), 256, 0, st>>>(res, (const double*)map, nm);
-        prof_stop(st);
-        count_launch();
-        s = do_map2alm(p, res, da, nmaps, ws, dsig, dsig, st);
-        if (s != SHT_OK) return s;
+    // Algorithm 2, a += map2alm(T - alm2map(a)) niter times, restricted to the
+    // ring spectra: T (kept from the first pass) - F(G) with G the Legendre
+    // alm2map of a and F what the backward + forward FFTs do to it (the
+    // Fourier-domain residual, fft.cu), so the iteration runs no FFT.
+    const IterWs w = iter_ws(p, nmaps);
+    char* base = (char*)ws;
+    double* da = (double*)(base + w.da);
+    const long long na = (long long)nmaps * p->ncomp * p->nalm * 2;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < niter && e == cudaSuccess; it++) {
+        if (p->precision == SHT_FP64) {
+            double* G = (double*)(base + w.g);
+            e = launch_legendre_a2m_f64(p, (const double*)alm, G, nmaps, 1.0, 1.0, st);
+            if (e == cudaSuccess) e = launch_alias_residual(p, ws, G, G, nmaps, st);
+            if (e == cudaSuccess) e = launch_legendre_m2a_f64(p, G, da, nmaps, dsig, dsig, st);
+        } else {
+            float* G = (float*)(base + w.g);
+            float2* A2 = (float2*)(base + w.g + split_a2_offset(p, nmaps));
+            float2* D = (float2*)(base + w.d);
+            unsigned int* cm = (unsigned int*)(base + w.cm);
+            e = launch_alm_prep(p, (const double*)alm, A2, cm, nmaps, st);
+            if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, A2, (const float*)cm, G, nmaps, 1.0f, 1.0f, st);
+            if (e == cudaSuccess) e = launch_alias_residual(p, ws, G, D, nmaps, st);
+            if (e == cudaSuccess) e = launch_colmax_T(p, D, cm, nmaps, st);
+            if (e == cudaSuccess) e = launch_legendre_m2a_tc(p, D, (const float*)cm, da, nmaps, dsig, dsig, st);
+        }
+        if (e != cudaSuccess) break;
         prof_start("k_add", st);
         k_add<<<ew_grid(na), 256, 0, st>>>((double*)alm, da, na);
         prof_stop(st);
         count_launch();
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return SHT_ECUDA; }
+        e = cudaGetLastError();
     }
+    if (e != cudaSuccess) { set_error(std::string("map2alm iteration: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
 }
 

@@ -90,15 +90,22 @@ def test_adjoints_fp64(orc, sht, spin):
     assert colerr(got, want) < TOL
 
 
-@pytest.mark.parametrize("spin", [0, 2])
-def test_iteration_fp64(orc, sht, spin):
-    nside, lmax, nmaps = 16, 32, 2
+@pytest.mark.parametrize("nside,lmax,mmax,spin,niter", [
+    (16, 32, 32, 0, 3), (16, 32, 32, 2, 3),
+    (8, 23, 23, 0, 2),        # lmax = 3 nside - 1: every cap ring folds several m onto a bin
+    (16, 47, 47, 2, 2),
+    (16, 40, 20, 0, 2),       # mmax < lmax
+    (32, 64, 64, 0, 1),
+])
+def test_iteration_fp64(orc, sht, nside, lmax, mmax, spin, niter):
+    """The iteration runs on the ring spectra (no FFT); it must equal the
+    oracle's pixel-domain Algorithm 2 on white-noise maps (not band-limited)."""
     ncomp = 2 if spin else 1
-    rng = np.random.default_rng(17)
-    T = rng.standard_normal((nmaps, ncomp, 12 * nside * nside))
-    want = orc.map2alm(T, nside, lmax, spin=spin, niter=3)
-    plan = sht.Plan(nside, lmax, None, spin, "fp64")
-    got = plan.map2alm(torch.from_numpy(T).cuda(), niter=3).cpu().numpy()
+    rng = np.random.default_rng(17 + nside + lmax)
+    T = rng.standard_normal((2, ncomp, 12 * nside * nside))
+    want = orc.map2alm(T, nside, lmax, mmax, spin=spin, niter=niter)
+    plan = sht.Plan(nside, lmax, mmax, spin, "fp64")
+    got = plan.map2alm(torch.from_numpy(T).cuda(), niter=niter).cpu().numpy()
     assert colerr(got, want) < TOL
 
 

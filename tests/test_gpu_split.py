@@ -167,3 +167,15 @@ def test_split_spin2_many_chunks(orc, sht):
     T = got + 0.01 * np.sqrt(np.mean(got ** 2, axis=-1, keepdims=True)) * rng.standard_normal(got.shape)
     ga = plan.map2alm(torch.from_numpy(T).cuda()).cpu().numpy()
     assert colerr(ga[pick], orc.map2alm(T[pick], nside, lmax, spin=2)) < TOL
+
+
+@pytest.mark.parametrize("nside,lmax,spin,niter", [(16, 47, 0, 3), (16, 47, 2, 2), (64, 127, 0, 2), (32, 63, 2, 1)])
+def test_split_iteration(orc, sht, nside, lmax, spin, niter):
+    """Fourier-domain iteration in the split form against the oracle's
+    pixel-domain Algorithm 2."""
+    ncomp = 2 if spin else 1
+    rng = np.random.default_rng(31 + nside)
+    h = rng.standard_normal((3, ncomp, 12 * nside * nside))
+    plan = sht.Plan(nside, lmax, None, spin, "split")
+    got = plan.map2alm(torch.from_numpy(h).cuda(), niter=niter).cpu().numpy()
+    assert colerr(got, orc.map2alm(h, nside, lmax, spin=spin, niter=niter)) < TOL
