@@ -131,9 +131,12 @@ sht_status sht_map2alm_adjoint(sht_plan* plan, const void* alm, void* map, int n
                                void* workspace, size_t workspace_bytes, void* stream);
 
 /* End-to-end variants on HOST buffers (pageable or pinned): the library
- * stages the batch through its own pinned buffers in chunks and returns
- * after the result is back in host memory (synchronous on `stream`).
- * Same layouts as above. The staging buffers are owned by the plan. */
+ * moves the batch in chunks through two device buffer pairs, overlapping
+ * chunk k's transform (on `stream`) with chunk k+1's host->device copy and
+ * chunk k-1's device->host copy (two plan-owned copy streams); pageable
+ * buffers are staged through plan-owned pinned buffers. Returns after the
+ * result is back in host memory. Same layouts as above. Not for concurrent
+ * calls on one plan. */
 sht_status sht_alm2map_host(sht_plan* plan, const void* alm_host, void* map_host, int nmaps,
                             void* stream);
 sht_status sht_map2alm_host(sht_plan* plan, const void* map_host, void* alm_host, int nmaps,

@@ -138,6 +138,9 @@ struct sht_plan {
     void* host_dev_in = nullptr;
     void* host_dev_out = nullptr;
     size_t host_dev_in_bytes = 0, host_dev_out_bytes = 0;
+    // the host entry points' copy streams and their events (created lazily)
+    cudaStream_t hp_h2d = nullptr, hp_d2h = nullptr;
+    cudaEvent_t hp_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace sht {

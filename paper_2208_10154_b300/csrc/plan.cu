@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <map>
 
+#include <cstdlib>
 #include "common.cuh"
 
 namespace sht {
@@ -604,6 +605,9 @@ static void free_tables(sht_plan* p)
                   p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,
                   p->s.s2d64};
     for (void* q : sp) if (q) cudaFree(q);
+    for (cudaEvent_t ev : p->hp_ev) if (ev) cudaEventDestroy(ev);
+    if (p->hp_h2d) cudaStreamDestroy(p->hp_h2d);
+    if (p->hp_d2h) cudaStreamDestroy(p->hp_d2h);
     if (p->pin_in) cudaFreeHost(p->pin_in);
     if (p->pin_out) cudaFreeHost(p->pin_out);
 }
@@ -959,7 +963,14 @@ sht_status sht_map2alm_adjoint(sht_plan* p, const void* alm, void* map, int nmap
                       (cudaStream_t)stream);
 }
 
-// ---- host-buffer entry points: chunked through pinned staging ----
+// ---- host-buffer entry points: a three-stage pipeline over map chunks ----
+// Chunk k's host->device copy (copy stream), transform (the caller's stream)
+// and device->host copy (second copy stream) overlap with chunk k+1's copy in
+// and chunk k-1's copy out; two device buffers per direction alternate.
+// Events order the stages: in_ready[b] (copy in done), comp_done[b]
+// (transform done: buffer b's input may be overwritten, its output copied
+// out) and out_done[b] (copy out done: buffer b's output may be overwritten).
+// Pageable caller buffers go through pinned staging, one buffer per parity.
 static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, int nmaps, int niter,
                             bool to_map, cudaStream_t st)
 {
@@ -970,10 +981,13 @@ static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, in
     const size_t alm_b = (size_t)p->ncomp * p->nalm * 2 * sizeof(double);
     const size_t in_b = to_map ? alm_b : map_b, out_b = to_map ? map_b : alm_b;
     int chunk = nmaps;
-    const size_t cap = (size_t)8 << 30;
-    while (chunk > 1 && (size_t)chunk * (in_b + out_b) + ws_bytes(p, chunk, niter) > cap) chunk = (chunk + 1) / 2;
-    size_t need_in = (size_t)chunk * in_b, need_out = (size_t)chunk * out_b;
-    size_t need_ws = ws_bytes(p, chunk, niter);
+    const size_t cap = (size_t)24 << 30;
+    while (chunk > 1 && 2 * (size_t)chunk * (in_b + out_b) + ws_bytes(p, chunk, niter) > cap) chunk = (chunk + 1) / 2;
+    if (const char* env = std::getenv("SHT_HOST_CHUNK_MAPS")) {      // smaller chunks (tests)
+        const int c = std::atoi(env);
+        if (c >= 1) chunk = std::min(chunk, c);
+    }
+    const size_t cin = round_up((size_t)chunk * in_b, 256), cout = round_up((size_t)chunk * out_b, 256);
     auto grow_dev = [&](void** ptr, size_t* have, size_t need) -> cudaError_t {
         if (*have >= need) return cudaSuccess;
         if (*ptr) cudaFree(*ptr);
@@ -990,11 +1004,6 @@ static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, in
         if (e == cudaSuccess) *have = need;
         return e;
     };
-    SHT_CUDA_TRY(grow_dev(&p->host_dev_in, &p->host_dev_in_bytes, need_in));
-    SHT_CUDA_TRY(grow_dev(&p->host_dev_out, &p->host_dev_out_bytes, need_out));
-    SHT_CUDA_TRY(grow_dev(&p->host_ws, &p->host_ws_bytes, need_ws));
-    SHT_CUDA_TRY(grow_pin(&p->pin_in, &p->pin_in_bytes, need_in));
-    SHT_CUDA_TRY(grow_pin(&p->pin_out, &p->pin_out_bytes, need_out));
     // pinned (page-locked) caller buffers are copied directly; pageable ones
     // are staged through the plan's pinned buffers
     auto is_pinned = [](const void* ptr) {
@@ -1003,23 +1012,66 @@ static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, in
         return at.type == cudaMemoryTypeHost;
     };
     const bool in_pinned = is_pinned(in_host), out_pinned = is_pinned(out_host);
-    int launches = 0;
-    for (int b0 = 0; b0 < nmaps; b0 += chunk) {
-        int nb = std::min(chunk, nmaps - b0);
-        const char* src = (const char*)in_host + (size_t)b0 * in_b;
-        if (!in_pinned) { memcpy(p->pin_in, src, (size_t)nb * in_b); src = (const char*)p->pin_in; }
-        SHT_CUDA_TRY(cudaMemcpyAsync(p->host_dev_in, src, (size_t)nb * in_b, cudaMemcpyHostToDevice, st));
-        sht_status s = to_map
-            ? sht_alm2map(p, p->host_dev_in, p->host_dev_out, nb, p->host_ws, p->host_ws_bytes, st)
-            : sht_map2alm(p, p->host_dev_in, p->host_dev_out, nb, niter, p->host_ws, p->host_ws_bytes, st);
-        if (s != SHT_OK) return s;
-        launches += t_launches;
-        char* dst = (char*)out_host + (size_t)b0 * out_b;
-        SHT_CUDA_TRY(cudaMemcpyAsync(out_pinned ? dst : (char*)p->pin_out, p->host_dev_out, (size_t)nb * out_b,
-                                     cudaMemcpyDeviceToHost, st));
-        SHT_CUDA_TRY(cudaStreamSynchronize(st));
-        if (!out_pinned) memcpy(dst, p->pin_out, (size_t)nb * out_b);
+    SHT_CUDA_TRY(grow_dev(&p->host_dev_in, &p->host_dev_in_bytes, 2 * cin));
+    SHT_CUDA_TRY(grow_dev(&p->host_dev_out, &p->host_dev_out_bytes, 2 * cout));
+    SHT_CUDA_TRY(grow_dev(&p->host_ws, &p->host_ws_bytes, ws_bytes(p, chunk, niter)));
+    if (!in_pinned) SHT_CUDA_TRY(grow_pin(&p->pin_in, &p->pin_in_bytes, 2 * cin));
+    if (!out_pinned) SHT_CUDA_TRY(grow_pin(&p->pin_out, &p->pin_out_bytes, 2 * cout));
+    if (!p->hp_h2d) {
+        SHT_CUDA_TRY(cudaStreamCreateWithFlags(&p->hp_h2d, cudaStreamNonBlocking));
+        SHT_CUDA_TRY(cudaStreamCreateWithFlags(&p->hp_d2h, cudaStreamNonBlocking));
+        for (cudaEvent_t& ev : p->hp_ev) SHT_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
+    cudaEvent_t* in_ready = p->hp_ev;
+    cudaEvent_t* comp_done = p->hp_ev + 2;
+    cudaEvent_t* out_done = p->hp_ev + 4;
+    char* dev_in = (char*)p->host_dev_in;
+    char* dev_out = (char*)p->host_dev_out;
+    const int nch = (nmaps + chunk - 1) / chunk;
+    int launches = 0;
+    // finish the pageable copy-out of chunk k (its device->host copy is queued)
+    auto finish_out = [&](int k) -> cudaError_t {
+        if (out_pinned || k < 0) return cudaSuccess;
+        const int b = k & 1, b0 = k * chunk, nb = std::min(chunk, nmaps - b0);
+        cudaError_t e = cudaEventSynchronize(out_done[b]);
+        if (e == cudaSuccess) memcpy((char*)out_host + (size_t)b0 * out_b, (char*)p->pin_out + b * cout, (size_t)nb * out_b);
+        return e;
+    };
+    for (int k = 0; k < nch; k++) {
+        const int b = k & 1, b0 = k * chunk, nb = std::min(chunk, nmaps - b0);
+        // copy in: the transform of chunk k - 2 must be done with buffer b
+        const char* src = (const char*)in_host + (size_t)b0 * in_b;
+        if (k >= 2) SHT_CUDA_TRY(cudaStreamWaitEvent(p->hp_h2d, comp_done[b], 0));
+        if (!in_pinned) {
+            if (k >= 2) SHT_CUDA_TRY(cudaEventSynchronize(in_ready[b]));    // staging b copied in
+            memcpy((char*)p->pin_in + b * cin, src, (size_t)nb * in_b);
+            src = (const char*)p->pin_in + b * cin;
+        }
+        SHT_CUDA_TRY(cudaMemcpyAsync(dev_in + b * cin, src, (size_t)nb * in_b, cudaMemcpyHostToDevice, p->hp_h2d));
+        SHT_CUDA_TRY(cudaEventRecord(in_ready[b], p->hp_h2d));
+        // transform: its input is in, and output buffer b has been copied out
+        SHT_CUDA_TRY(cudaStreamWaitEvent(st, in_ready[b], 0));
+        if (k >= 2) SHT_CUDA_TRY(cudaStreamWaitEvent(st, out_done[b], 0));
+        sht_status s = to_map
+            ? sht_alm2map(p, dev_in + b * cin, dev_out + b * cout, nb, p->host_ws, p->host_ws_bytes, st)
+            : sht_map2alm(p, dev_in + b * cin, dev_out + b * cout, nb, niter, p->host_ws, p->host_ws_bytes, st);
+        if (s != SHT_OK) {
+            cudaStreamSynchronize(p->hp_h2d);
+            cudaStreamSynchronize(p->hp_d2h);
+            return s;
+        }
+        launches += t_launches;
+        SHT_CUDA_TRY(cudaEventRecord(comp_done[b], st));
+        // copy out
+        char* dst = out_pinned ? (char*)out_host + (size_t)b0 * out_b : (char*)p->pin_out + b * cout;
+        SHT_CUDA_TRY(cudaStreamWaitEvent(p->hp_d2h, comp_done[b], 0));
+        SHT_CUDA_TRY(cudaMemcpyAsync(dst, dev_out + b * cout, (size_t)nb * out_b, cudaMemcpyDeviceToHost, p->hp_d2h));
+        SHT_CUDA_TRY(cudaEventRecord(out_done[b], p->hp_d2h));
+        SHT_CUDA_TRY(finish_out(k - 1));
+    }
+    SHT_CUDA_TRY(finish_out(nch - 1));
+    SHT_CUDA_TRY(cudaStreamSynchronize(p->hp_d2h));
+    SHT_CUDA_TRY(cudaStreamSynchronize(st));
     t_launches = launches;
     return SHT_OK;
 }

@@ -138,3 +138,25 @@ def test_invalid_calls_report_status(sht):
     rc = lib.sht_alm2map(plan.handle, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), 0,
                          None, 0, st)
     assert rc == sht.SHT_EINVAL
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_entry_points_pipelined_chunks(sht, monkeypatch, pinned):
+    """Several chunks through the copy / transform / copy pipeline (chunk size
+    forced to 2 maps), pageable and pinned host buffers: bit-identical to the
+    device entry points."""
+    monkeypatch.setenv("SHT_HOST_CHUNK_MAPS", "2")
+    nside, lmax, nmaps = 16, 32, 7
+    plan = sht.Plan(nside, lmax, None, 2, "fp64")
+    a = make_alm(nside, lmax, lmax, 2, nmaps, seed=19)
+    dev = plan.alm2map(torch.from_numpy(a).cuda()).cpu().numpy()
+    if pinned:
+        a_h = torch.from_numpy(a).pin_memory()
+        out = torch.empty(dev.shape, dtype=torch.float64).pin_memory()
+        plan.alm2map_host(a_h.numpy(), out_host=out.numpy())
+        host = out.numpy()
+    else:
+        host = plan.alm2map_host(a)
+    np.testing.assert_array_equal(host, dev)
+    back_dev = plan.map2alm(torch.from_numpy(dev).cuda(), niter=1).cpu().numpy()
+    np.testing.assert_array_equal(plan.map2alm_host(dev, niter=1), back_dev)
