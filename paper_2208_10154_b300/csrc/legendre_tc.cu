@@ -15,20 +15,21 @@
 // Accuracy. Every operand x is written, per row or column, in units of a
 // power-of-two quantum u with |x/u| <= Q (Q (Q + 1) K + 12 K / 32 <= 2^24,
 // Q <= 127) as four FP16 slices q + r0 + r1 + 2^-12 r2s (tc::slice4d: integer,
-// a multiple of 2^-12, the next 11 bits and the 11 after, ~2^-36 of u). Ten
+// a multiple of 2^-11, the next 11 bits and the 11 after, ~2^-35 of u). Ten
 // products per K step, in four TMEM accumulators:
 //     main = sum q q'                              integers: exact
-//     ex   = q r0' + r0 q'                         multiples of 2^-12 below 2^12
-//                                                  per 32-wide K chunk: exact
-//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'        below ~10 per chunk
+//     ex   = q r0' + r0 q'                         multiples of 2^-11 below 2^13
+//                                                  per 64-wide K span: exact
+//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'        below ~20 per span
 //     fn   = q r2s' + r2s q'                       (2^12 times their value)
 // The TMEM accumulator truncates toward zero on every MMA, so a sum that is not
 // exact picks up an error that grows with its magnitude and length. After each
-// 32-wide chunk the epilogue warps fold the integer parts of ex and sm into
-// main (exact: the bound above keeps main below 2^24) and leave the fractional
-// parts plus 2^-12 fn (all below 1) in sm as the start of the next chunk, so sm
-// never holds more than one chunk's worth; ex and fn are restarted by every
-// chunk. Dropped: products of two residual slices beyond r0 r1' (< 2^-25 u u').
+// span of two chunks (64 of K) the epilogue warps fold the integer parts of ex
+// and sm into main (exact: the bound above keeps main below 2^24) and leave
+// the fractional parts plus 2^-12 fn (all below 1) in sm as the start of the
+// next span, so sm never holds more than one span's worth; ex and fn restart
+// with every span. Dropped: products of two residual slices beyond r0 r1'
+// (< 2^-23 u u').
 //
 // Cluster sharing of lambda. The FP64 recurrence is the costly part (FP64 runs
 // at ~1/64 of FP32 here), so the CTAs of a thread-block cluster, which work on
@@ -142,8 +143,10 @@ __device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row
 
 // one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
 // whole of K, sm over the whole of K on top of the residual the epilogue warps
-// leave in it (only the first stage restarts them); ex and fn restart here.
-__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first)
+// leave in it (only the first stage restarts them); ex and fn restart at the
+// first stage of each two-chunk span.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first,
+                                            bool span_start)
 {
     uint32_t A[NPL], B[NPL];
 #pragma unroll
@@ -155,7 +158,7 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uin
 #pragma unroll
     for (int kk = 0; kk < 2; kk++) {
         const uint32_t o = kk * 32;
-        const uint32_t fresh = kk == 0 ? 0u : 1u;
+        const uint32_t fresh = (span_start && kk == 0) ? 0u : 1u;
         const uint32_t keep = (first && kk == 0) ? 0u : 1u;
         umma_f16(tmem, desc_sw64(A[0] + o), desc_sw64(B[0] + o), idesc, keep);     // q q'
         umma_f16(ex, desc_sw64(A[0] + o), desc_sw64(B[1] + o), idesc, fresh);      // q r0'
@@ -333,13 +336,13 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                 const int s = kc % NST;
                 const uint32_t u = kc / NST;
                 if (!mbar_wait_cl(&sh.full[s], u & 1, a.err, 1)) break;
-                // the accumulators of chunk kc - 1 must have been drained (the
-                // drain rewrites main and sm)
-                if (kc >= 1 && !mbar_wait_cl(&sh.cfree, (kc - 1) & 1, a.err, 5)) break;
+                // a span (chunks 2j, 2j + 1) starts once the previous span has
+                // been drained (the drain rewrites main and sm)
+                if (kc >= 2 && (kc & 1) == 0 && !mbar_wait_cl(&sh.cfree, ((kc >> 1) - 1) & 1, a.err, 5)) break;
                 tc_fence_after();
-                issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0);
+                issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0, (kc & 1) == 0);
                 umma_commit_mc(&sh.empty[s], mask);
-                umma_commit(&sh.cdone);
+                if ((kc & 1) || kc == nch - 1) umma_commit(&sh.cdone);
             }
             umma_commit(&sh.accf);
         }
@@ -615,11 +618,11 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
         const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         bool dok = true;
-        // Fold chunk c's corrections into main and sm and hand the accumulators
-        // back to the MMA: main += nearest integers of ex and sm (exact), sm =
-        // their fractional parts + 2^-12 fn (below 1). (A rolled loop: it runs
-        // once per chunk between other code, and a short body stays in the
-        // instruction cache.)
+        // Fold span c's corrections (chunks 2c, 2c + 1) into main and sm and
+        // hand the accumulators back to the MMA: main += nearest integers of ex
+        // and sm (exact), sm = their fractional parts + 2^-12 fn (below 1). (A
+        // rolled loop: it runs once per span between other code, and a short
+        // body stays in the instruction cache.)
         auto drain = [&](int c) {
             dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, c & 1, a.err, 6));
             tc_fence_after();
@@ -754,17 +757,16 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                     mbar_arrive(&sh.full[u % NST]);
                 }
             }
-            // release the next unit's stages and drain the chunks whose MMAs the
+            // release the next unit's stages and drain the span whose MMAs the
             // next ones wait for (in this order: release c needs MMA(c - NST), which
             // must not wait for a drain that comes after it)
-            if (S2) {
+            if (S2) {                                  // unit u = span u
                 release(2 * u + 2);
-                if (u >= 1 && dok) drain(2 * u - 1);
+                if (u >= 1 && dok) drain(u - 1);
                 release(2 * u + 3);
-                if (dok) drain(2 * u);
             } else {
                 release(u + 1);
-                if (u >= 1 && dok) drain(u - 1);
+                if (u >= 2 && (u & 1) == 0 && dok) drain((u >> 1) - 1);
             }
         }
         // Tail: wait until every CTA of the cluster has consumed the last use of
@@ -777,7 +779,7 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             if (u >= 1)
                 dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 7));
         }
-        if (dok && nch >= 1) drain(nch - 1);
+        if (dok && nch >= 1) drain((nch - 1) >> 1);
 
         // the last MMAs are complete once every wait above succeeded
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));

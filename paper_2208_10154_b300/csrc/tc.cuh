@@ -354,17 +354,17 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
 // Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into four
 // FP16 pieces:
 //     q   = nearest integer                           (exact in FP16 for Q <= 2048)
-//     r0  = v - q rounded to the grid 2^-12           (|r0| <= 1/2: exact in FP16)
-//     r1  = rem = (v - q - r0) + vl rounded to FP16   (|rem| < 2^-12)
+//     r0  = v - q rounded to the grid 2^-11           (|r0| <= 1/2: exact in FP16)
+//     r1  = rem = (v - q - r0) + vl rounded to FP16   (|rem| < 2^-11)
 //     r2s = (rem - r1) 2^12 rounded to FP16           (the next 11 bits, scaled up)
-// v - q and v - q - r0 are exact, so v + vl = q + r0 + r1 + 2^-12 r2s to ~2^-36
+// v - q and v - q - r0 are exact, so v + vl = q + r0 + r1 + 2^-12 r2s to ~2^-35
 // of the quantum. The fixed grid of r0 makes every product q r0' a multiple of
-// 2^-12, so sums of them are exact in FP32 while they stay below 2^12.
+// 2^-11, so sums of them are exact in FP32 while they stay below 2^13.
 __device__ __forceinline__ void slice4d(float v, float vl, float& q, float& r0, float& r1, float& r2s)
 {
     q = __fadd_rn(__fadd_rn(v, 12582912.0f), -12582912.0f);   // 1.5 * 2^23: nearest integer
     const float r = __fadd_rn(v, -q);
-    r0 = __fadd_rn(__fadd_rn(r, 3072.0f), -3072.0f);          // 1.5 * 2^11: ulp 2^-12
+    r0 = __fadd_rn(__fadd_rn(r, 6144.0f), -6144.0f);          // 1.5 * 2^12: ulp 2^-11
     const float rem = __fadd_rn(__fadd_rn(r, -r0), vl);
     r1 = __half2float(__float2half_rn(rem));
     r2s = __fmul_rn(__fadd_rn(rem, -r1), 4096.0f);
