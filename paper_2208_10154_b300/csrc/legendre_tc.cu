@@ -148,28 +148,32 @@ __device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first,
                                             bool span_start)
 {
-    uint32_t A[NPL], B[NPL];
+    // descriptors as one base plus constant offsets (the start-address field
+    // counts 16 bytes and shared memory stays below 2^18 bytes, so adding to
+    // the 64-bit descriptor cannot carry out of that field)
+    const uint64_t d0 = desc_sw64(st_addr);
+    uint64_t A[NPL], B[NPL];
 #pragma unroll
     for (int b = 0; b < NPL; b++) {
-        A[b] = st_addr + b * A_PLANE;
-        B[b] = st_addr + NPL * A_PLANE + b * B_PLANE;
+        A[b] = d0 + (uint64_t)((b * A_PLANE) >> 4);
+        B[b] = d0 + (uint64_t)((NPL * A_PLANE + b * B_PLANE) >> 4);
     }
     const uint32_t ex = tmem + ACC_EX, sm = tmem + ACC_SM, fn = tmem + ACC_FN;
 #pragma unroll
     for (int kk = 0; kk < 2; kk++) {
-        const uint32_t o = kk * 32;
+        const uint64_t o = (uint64_t)(kk * 32 >> 4);
         const uint32_t fresh = (span_start && kk == 0) ? 0u : 1u;
         const uint32_t keep = (first && kk == 0) ? 0u : 1u;
-        umma_f16(tmem, desc_sw64(A[0] + o), desc_sw64(B[0] + o), idesc, keep);     // q q'
-        umma_f16(ex, desc_sw64(A[0] + o), desc_sw64(B[1] + o), idesc, fresh);      // q r0'
-        umma_f16(ex, desc_sw64(A[1] + o), desc_sw64(B[0] + o), idesc, 1u);         // r0 q'
-        umma_f16(sm, desc_sw64(A[0] + o), desc_sw64(B[2] + o), idesc, keep);       // q r1'
-        umma_f16(sm, desc_sw64(A[2] + o), desc_sw64(B[0] + o), idesc, 1u);         // r1 q'
-        umma_f16(sm, desc_sw64(A[1] + o), desc_sw64(B[1] + o), idesc, 1u);         // r0 r0'
-        umma_f16(sm, desc_sw64(A[1] + o), desc_sw64(B[2] + o), idesc, 1u);         // r0 r1'
-        umma_f16(sm, desc_sw64(A[2] + o), desc_sw64(B[1] + o), idesc, 1u);         // r1 r0'
-        umma_f16(fn, desc_sw64(A[0] + o), desc_sw64(B[3] + o), idesc, fresh);      // q r2s'
-        umma_f16(fn, desc_sw64(A[3] + o), desc_sw64(B[0] + o), idesc, 1u);         // r2s q'
+        umma_f16(tmem, A[0] + o, B[0] + o, idesc, keep);     // q q'
+        umma_f16(ex, A[0] + o, B[1] + o, idesc, fresh);      // q r0'
+        umma_f16(ex, A[1] + o, B[0] + o, idesc, 1u);         // r0 q'
+        umma_f16(sm, A[0] + o, B[2] + o, idesc, keep);       // q r1'
+        umma_f16(sm, A[2] + o, B[0] + o, idesc, 1u);         // r1 q'
+        umma_f16(sm, A[1] + o, B[1] + o, idesc, 1u);         // r0 r0'
+        umma_f16(sm, A[1] + o, B[2] + o, idesc, 1u);         // r0 r1'
+        umma_f16(sm, A[2] + o, B[1] + o, idesc, 1u);         // r1 r0'
+        umma_f16(fn, A[0] + o, B[3] + o, idesc, fresh);      // q r2s'
+        umma_f16(fn, A[3] + o, B[0] + o, idesc, 1u);         // r2s q'
     }
 }
 
