@@ -108,6 +108,14 @@ struct SplitTables {
     int4* work_m2a = nullptr; int nwork_m2a = 0;
     int4* work_a2m = nullptr; int nwork_a2m = 0;
     float Q_m2a = 0.0f, Q_a2m = 0.0f;   // integer range of the main slices (K Q^2 <= 2^24)
+    // pre-sliced data images (32 KB per 32-wide chunk of K and 128-column tile):
+    // first image chunk per [m][q], slicing units (m, q, unit, image chunk) and
+    // the image chunks of one contraction, per direction
+    int* img_base_m2a = nullptr;
+    int* img_base_a2m = nullptr;
+    int4* sunits_m2a = nullptr; int nsunits_m2a = 0;
+    int4* sunits_a2m = nullptr; int nsunits_a2m = 0;
+    long long img_chunks_m2a = 0, img_chunks_a2m = 0;
 };
 
 }  // namespace sht
@@ -180,10 +188,12 @@ int legendre_f64_pair_tile();
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st);
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
-cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, double* alm,
-                                   int nmaps, double fs0, double fs1, cudaStream_t st);
-cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, float* G,
-                                   int nmaps, float s0, float s1, cudaStream_t st);
+// (each runs the slicing pass into `img`, split_img_bytes long, then the contraction)
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, uint8_t* img,
+                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st);
+cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, uint8_t* img,
+                                   float* G, int nmaps, float s0, float s1, cudaStream_t st);
+size_t split_img_bytes(const sht_plan* p, int nmaps);
 cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,
                             cudaStream_t st);
 // Fourier-domain residual of the iteration, D = T - F(G) (fft.cu), and the

@@ -40,10 +40,16 @@
 // on the destination's mbarrier. Each CTA's MMA completion is multicast to the
 // "stage free" barriers of all CTAs of the cluster.
 //
+// Data operand. A separate pass (k_slice) writes, per 32-wide chunk of K and
+// column tile, the four slice planes of the data as the exact 32 KB image of
+// the stage's A operand; the contraction fetches it with one bulk copy per
+// chunk, so no thread of the contraction touches the data.
+//
 // CTA: 256 threads, one per SM (192 KB of pipeline stages, 512 TMEM columns).
 //   warp 0       TMEM allocation; lane 0 issues the MMAs
 //   warps 1-3    lambda pieces (32 ring pairs x 32 rows / steps each)
-//   warps 4-7    slice the data (one map column per thread), then the epilogue
+//   warps 4-7    data copies (one lane), stage releases, the drains of the
+//                correction accumulators, then the epilogue with warps 0-3
 #include <algorithm>
 #include <cstdlib>
 
@@ -63,6 +69,7 @@ constexpr int NPL = 4;                           // FP16 slices per operand (q, 
 constexpr int A_PLANE = TC_M * KC * 2;           // 8 KB (data, one slice)
 constexpr int B_PLANE = TC_N * KC * 2;           // 8 KB (lambda, one slice)
 constexpr int PIECE_BYTES = PR * KC * 2;         // 2 KB of one B plane
+constexpr int A_BYTES = NPL * A_PLANE;           // 32 KB: one chunk of the data operand
 constexpr int STAGE_BYTES = NPL * (A_PLANE + B_PLANE);   // 64 KB
 constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
 constexpr uint32_t ACC_SM = 256;                 //   small corrections (+ the residual of earlier chunks)
@@ -89,8 +96,14 @@ struct TcArgs {
     const double* s2B[2];
     const float2* s2d2;        // d_l as an FP32 hi/lo pair (alm2map applies it to lambda)
     const double* s2d64;       // d_l in FP64 (map2alm applies it per output row)
+    // data operand: per chunk and column tile, the 32 KB shared-memory image of the
+    // four FP16 slice planes (written by k_slice), at image chunk img_base[m][q] + chunk
+    const uint8_t* img;
+    const int* img_base;
+    const int4* sunits;        // k_slice: (m, q, unit, image chunk of the unit)
     int* err;
     int lmax, mmax, R;
+    int ntile;                 // column tiles of 128
     long long ncol, nalm;
     float Q;                   // integer range of the main slices
     double fs0, fs1;           // map2alm: output factor (dsigma times any adjoint weight), m = 0 / m > 0
@@ -219,6 +232,22 @@ __device__ __forceinline__ void rescale(double& cur, double& prev, int& E)
 __device__ __forceinline__ int perm_src(int c) { return (c & ~3) | (3 - (c & 3)); }
 __device__ __forceinline__ float perm_sign(int c) { return ((c & 3) == 0 || (c & 3) == 3) ? -1.0f : 1.0f; }
 
+// quantum exponent of data column c0 + c of (m, q). Spin 2 also bounds the
+// other slot, permuted: map2alm slices T_q +- P(T_{1-q}) (bounded by the sum),
+// alm2map slices a_l or P(a_l) (bounded by the larger).
+template <bool M2A, bool S2>
+__device__ __forceinline__ int col_quantum(const TcArgs& a, int m, int q, long long c0, int c)
+{
+    const long long cg = c0 + c;
+    if (cg >= a.ncol) return 0;
+    float mx = a.colmax[((long long)m * 2 + q) * a.ncol + cg];
+    if (S2) {
+        const float mo = a.colmax[((long long)m * 2 + (1 - q)) * a.ncol + (c0 + perm_src(c))];
+        mx = M2A ? mx + mo : fmaxf(mx, mo);
+    }
+    return quantum_exp(mx, a.Q);
+}
+
 // ===========================================================================
 // map2alm (M2A = true):  a[l, c] = f_l sum_p lambda_lm(theta_p) T[p, c]
 // alm2map (M2A = false): G[p, c] = s   sum_l lambda_lm(theta_p) a[l, c]
@@ -240,7 +269,7 @@ __device__ __forceinline__ float perm_sign(int c) { return ((c & 3) == 0 || (c &
 // ===========================================================================
 template <bool M2A, bool S2>
 __global__ void __launch_bounds__(256, 1)
-k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
+k_leg_tc(void* __restrict__ dst, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -299,23 +328,10 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             sh.rowexp[r] = (r < nrows) ? quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + n0 + r], a.Q) : 0;
         }
     }
-    for (int c = tid; c < TC_M; c += blockDim.x) {
-        const long long cg = c0 + c;
-        float mx = 0.0f;
-        if (cg < a.ncol) {
-            mx = a.colmax[((long long)m * 2 + q) * a.ncol + cg];
-            if (S2) {
-                // the other slot, permuted: map2alm slices T_q +- P(T_{1-q}) (bounded by the
-                // sum), alm2map slices a_l or P(a_l) (bounded by the larger)
-                const float mo = a.colmax[((long long)m * 2 + (1 - q)) * a.ncol + (c0 + perm_src(c))];
-                mx = M2A ? mx + mo : fmaxf(mx, mo);
-            }
-        }
-        sh.colexp[c] = (cg < a.ncol) ? quantum_exp(mx, a.Q) : 0;
-    }
+    for (int c = tid; c < TC_M; c += blockDim.x) sh.colexp[c] = col_quantum<M2A, S2>(a, m, q, c0, c);
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
-            mbar_init(&sh.full[s], 4 + npieces);
+            mbar_init(&sh.full[s], 1 + npieces);
             mbar_init(&sh.empty[s], csize);
         }
         mbar_init(&sh.accf, 1);
@@ -488,8 +504,10 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
                         float h = 0.0f, lo = 0.0f;
                         if (live) f64_split_scaled(cur, E - pe, h, lo);
                         const float p1 = h * d0;                // lambda = d_l mu in double-float
-                        hb[i] = p1;
-                        lb[i] = fmaf(h, d0, -p1) + (h * d1 + lo * d0);
+                        // v- chunks carry sigma_l = -1 for the rows of the other parity
+                        const float sgn = (sg && (i & 1) != q) ? -1.0f : 1.0f;
+                        hb[i] = sgn * p1;
+                        lb[i] = sgn * (fmaf(h, d0, -p1) + (h * d1 + lo * d0));
                     }
                 }
                 prow = r;
@@ -614,19 +632,27 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             }
         }
     } else {
-        // ---------------- data slices: one map column per thread ----------------
-        const int t = tid - 128;
-        const long long cg = c0 + t;
-        const bool cok = cg < a.ncol;
-        const int ce = sh.colexp[t];
+        // ---------------- data copies, stage releases, span drains ----------------
         const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         bool dok = true;
+        // chunk c's data: one 32 KB bulk copy of its pre-sliced image (spin-2
+        // alm2map: both chunks of a unit read the unit's image). Column tiles
+        // that only pad the cluster read the last real tile and write nothing.
+        const int ytile = min((int)blockIdx.y, a.ntile - 1);
+        const uint8_t* img0 = a.img + ((long long)a.img_base[m * 2 + q] * a.ntile + ytile) * A_BYTES;
+        auto copy = [&](int c) {
+            if (warp == 4 && lane == 0) {
+                const int s = c % NST;
+                const long long ci = (S2 && !M2A) ? (c >> 1) : c;
+                mbar_arrive_expect_tx(&sh.full[s], A_BYTES);
+                bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
+            }
+        };
         // Fold span c's corrections (chunks 2c, 2c + 1) into main and sm and
         // hand the accumulators back to the MMA: main += nearest integers of ex
         // and sm (exact), sm = their fractional parts + 2^-12 fn (below 1). (A
-        // rolled loop: it runs once per span between other code, and a short
-        // body stays in the instruction cache.)
+        // rolled loop: a short body stays in the instruction cache.)
         auto drain = [&](int c) {
             dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, c & 1, a.err, 6));
             tc_fence_after();
@@ -653,137 +679,29 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.cfree);
         };
-        // release chunk c's stage to the lambda warps once every CTA of the
-        // cluster has consumed its previous use
-        auto release = [&](int c) {
-            if (dok && c < nch && c >= NST) {
+        // The first NST chunks have free stages. Chunk c >= NST waits until
+        // every CTA of the cluster has consumed the stage's previous use
+        // (chunk c - NST), then starts its data copy and releases the stage to
+        // the lambda warps. Span j is drained after chunk 2j + 4 is released:
+        // that wait implies span j's MMAs are done, and the MMAs of chunk
+        // 2j + 2 (which chunk 2j + 5 waits for) wait for the drain. The walk
+        // continues NST chunks past the end, so that every MMA commit of the
+        // cluster has arrived on this CTA's barriers before it exits. (A wait
+        // that gives up turns dok off; the walk still runs to the end.)
+        const int nspan = (nch + 1) >> 1;
+        int nd = 0;                                   // spans drained
+        for (int c = 0; c < min(nch, NST); c++) copy(c);
+        for (int c = NST; c < nch + NST; c++) {
+            if (dok) {
                 dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1, a.err, 3));
-                if (dok && lane == 0 && warp == 4) publish_counter(&sh.released, c);
-            }
-        };
-        // Raw data: each thread loads its own column (FP32 hi/lo pairs; a warp
-        // reads 256 contiguous bytes per K row) one block ahead into registers.
-        // A block is a unit of 32 K rows, or for spin-2 map2alm, which needs both
-        // slots, half a unit (16 rows) of each slot.
-        const float2* raw = (const float2*)src;
-        constexpr bool TWO = S2 && M2A;
-        constexpr int BR = TWO ? KC / 2 : KC;       // K rows per block and slot
-        const int nblk = TWO ? 2 * nunit : nunit;
-        float2 buf[KC];
-        auto load_block = [&](int blk) {
-            const int u = TWO ? blk >> 1 : blk;
-            const int rb = TWO ? (blk & 1) * BR : 0;
-#pragma unroll
-            for (int h = 0; h < (TWO ? 2 : 1); h++) {
-                const int slot = h ? 1 - q : q;
-#pragma unroll
-                for (int i = 0; i < BR; i++) {
-                    const int k = u * KC + rb + i;
-                    float2 x = make_float2(0.0f, 0.0f);
-                    if (cok && k < K) {
-                        long long row;
-                        if (M2A) row = ((long long)m * 2 + slot) * a.R + k;
-                        else row = S2 ? a_idx(a.lmax, m + k, m) : a_idx(a.lmax, l_first + 2 * k, m);
-                        x = __ldg(raw + row * a.ncol + cg);
-                    }
-                    buf[h * BR + i] = x;
+                if (dok && c < nch) {
+                    copy(c);
+                    if (warp == 4 && lane == 0) publish_counter(&sh.released, c);
                 }
             }
-        };
-        // the quantum 2^ce as an FP32 factor (exact scaling)
-        const float csc = __int_as_float((127 - ce) << 23);
-        const int psrc = (lane & ~3) | (3 - (lane & 3));     // spin 2: lane of the permuted column
-        const float sgp = perm_sign(t);
-        // slice block blk into the stage(s) of its unit's chunk(s)
-        auto slice_block = [&](int blk) {
-            const int u = TWO ? blk >> 1 : blk;
-            const int rb = TWO ? (blk & 1) * BR : 0;
-#pragma unroll
-            for (int sub = 0; sub < (S2 ? 2 : 1); sub++) {
-                uint8_t* A = smem + ((S2 ? 2 * u + sub : u) % NST) * STAGE_BYTES;
-#pragma unroll
-                for (int jj = 0; jj < BR / 8; jj++) {
-                    float hv[8], lv[8];
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int r = jj * 8 + i;             // row within the block
-                        float2 x;
-                        if constexpr (!S2) {
-                            x = buf[r];
-                        } else if constexpr (M2A) {
-                            // T_q +- P(T_{1-q}) in double-float (TwoSum of the hi parts)
-                            const float2 x0 = buf[r];
-                            float2 x1;
-                            x1.x = __shfl_sync(0xffffffffu, buf[BR + r].x, psrc);
-                            x1.y = __shfl_sync(0xffffffffu, buf[BR + r].y, psrc);
-                            const float sb = sub ? -sgp : sgp;
-                            const float bh = sb * x1.x;
-                            const float s1 = x0.x + bh;
-                            const float bb = s1 - x0.x;
-                            const float lo = ((x0.x - (s1 - bb)) + (bh - bb)) + (x0.y + sb * x1.y);
-                            const float hi = s1 + lo;
-                            x = make_float2(hi, lo - (hi - s1));
-                        } else {
-                            // a_l (l - m = 32 u + r in slot q) or P(a_l); v- chunks negate the latter
-                            float2 xp;
-                            xp.x = __shfl_sync(0xffffffffu, buf[r].x, psrc);
-                            xp.y = __shfl_sync(0xffffffffu, buf[r].y, psrc);
-                            const bool same = (r & 1) == q;
-                            const float sg = same ? 1.0f : (sub ? -sgp : sgp);
-                            x = same ? buf[r] : xp;
-                            x.x *= sg;
-                            x.y *= sg;
-                        }
-                        hv[i] = x.x * csc;
-                        lv[i] = x.y * csc;
-                    }
-                    put4x8(A, A_PLANE, t, rb / 8 + jj, hv, lv);
-                }
-            }
-        };
-        // (a wait that gives up turns dok off; the loop still runs to the end so
-        // that the barrier arrivals stay balanced)
-        if (nblk > 0) load_block(0);
-        for (int blk = 0; blk < nblk; blk++) {
-            const int u = TWO ? blk >> 1 : blk;
-            // the unit's stage(s) are free: among the first NST, or released at the
-            // end of the previous unit
-            if (dok) slice_block(blk);
-            if (blk + 1 < nblk) load_block(blk + 1);  // in flight during the waits below
-            if (TWO && (blk & 1) == 0) continue;
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-                if (S2) {
-                    mbar_arrive(&sh.full[(2 * u) % NST]);
-                    mbar_arrive(&sh.full[(2 * u + 1) % NST]);
-                } else {
-                    mbar_arrive(&sh.full[u % NST]);
-                }
-            }
-            // release the next unit's stages and drain the span whose MMAs the
-            // next ones wait for (in this order: release c needs MMA(c - NST), which
-            // must not wait for a drain that comes after it)
-            if (S2) {                                  // unit u = span u
-                release(2 * u + 2);
-                if (u >= 1 && dok) drain(u - 1);
-                release(2 * u + 3);
-            } else {
-                release(u + 1);
-                if (u >= 2 && (u & 1) == 0 && dok) drain((u >> 1) - 1);
-            }
+            if ((c & 1) == 0 && c >= 4 && nd < nspan && dok) drain(nd++);
         }
-        // Tail: wait until every CTA of the cluster has consumed the last use of
-        // each stage. All their MMA commits then have arrived on this CTA's
-        // barriers, so none can land after it exits. (These waits continue the
-        // sequential phase walk of the releases above.)
-        for (int kc = nch; kc < nch + NST && dok; kc++) {
-            const int s = kc % NST;
-            const uint32_t u = kc / NST;
-            if (u >= 1)
-                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[s], (u - 1) & 1, a.err, 7));
-        }
-        if (dok && nch >= 1) drain((nch - 1) >> 1);
+        while (nd < nspan && dok) drain(nd++);
 
         // the last MMAs are complete once every wait above succeeded
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
@@ -857,6 +775,97 @@ k_leg_tc(const void* __restrict__ src, void* __restrict__ dst, TcArgs a)
     cluster_sync();            // no CTA leaves while others may still copy into it
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ===========================================================================
+// data operand of the contraction, pre-sliced: for each 32-wide unit of K of
+// (m, q) and each column tile, the four FP16 slice planes (tc::slice4d in the
+// column's quantum) of the 128 columns x 32 K values, written as the exact
+// shared-memory image the MMAs read (K-major, 64-byte swizzle), 32 KB per
+// chunk, so that k_leg_tc fetches a chunk with one bulk copy. Rows past K and
+// columns past ncol are written as zeros.
+//   map2alm: rows = ring pairs of T[m][q]; spin 2: chunk 2u holds
+//            T_q + P(T_{1-q}) and chunk 2u + 1 holds T_q - P(T_{1-q}) (the two
+//            combinations of Sec. 2.3 that meet v+ and v-).
+//   alm2map: rows = the l of slot q (spin 0: l = m + q + 2k) or all l >= m
+//            (spin 2: a_l for l - m of parity q, P(a_l) otherwise; the sign
+//            sigma_l of the v- chunks is carried by lambda).
+// grid.x = unit (m, q, u, image chunk), grid.y = column tile; one column per thread
+// ===========================================================================
+template <bool M2A, bool S2>
+__global__ void __launch_bounds__(TC_M)
+k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
+{
+    const int4 w = a.sunits[blockIdx.x];
+    const int m = w.x, q = w.y, u = w.z;
+    const int t = threadIdx.x, lane = t & 31;
+    const long long c0 = (long long)blockIdx.y * TC_M;
+    const long long cg = c0 + t;
+    const bool cok = cg < a.ncol;
+    const int l_first = m + q;
+    const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
+    const int K = M2A ? a.R : (S2 ? a.lmax - m + 1 : nl);
+    constexpr bool TWO = S2 && M2A;                 // map2alm spin 2 reads both slots
+    float2 buf[TWO ? 2 * KC : KC];
+#pragma unroll
+    for (int h = 0; h < (TWO ? 2 : 1); h++) {
+        const int slot = h ? 1 - q : q;
+#pragma unroll
+        for (int i = 0; i < KC; i++) {
+            const int k = u * KC + i;
+            float2 x = make_float2(0.0f, 0.0f);
+            if (cok && k < K) {
+                long long row;
+                if (M2A) row = ((long long)m * 2 + slot) * a.R + k;
+                else row = S2 ? a_idx(a.lmax, m + k, m) : a_idx(a.lmax, l_first + 2 * k, m);
+                x = __ldg(raw + row * a.ncol + cg);
+            }
+            buf[h * KC + i] = x;
+        }
+    }
+    const int ce = col_quantum<M2A, S2>(a, m, q, c0, t);
+    const float csc = __int_as_float((127 - ce) << 23);   // 2^-ce (exact scaling)
+    const int psrc = (lane & ~3) | (3 - (lane & 3));     // spin 2: lane of the permuted column
+    const float sgp = perm_sign(t);
+#pragma unroll
+    for (int sub = 0; sub < (TWO ? 2 : 1); sub++) {
+        uint8_t* A = img + ((long long)(w.w + sub) * a.ntile + blockIdx.y) * A_BYTES;
+#pragma unroll
+        for (int jj = 0; jj < KC / 8; jj++) {
+            float hv[8], lv[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int r = jj * 8 + i;
+                float2 x;
+                if constexpr (!S2) {
+                    x = buf[r];
+                } else if constexpr (M2A) {
+                    // T_q +- P(T_{1-q}) in double-float (TwoSum of the hi parts)
+                    const float2 x0 = buf[r];
+                    float2 x1;
+                    x1.x = __shfl_sync(0xffffffffu, buf[KC + r].x, psrc);
+                    x1.y = __shfl_sync(0xffffffffu, buf[KC + r].y, psrc);
+                    const float sb = sub ? -sgp : sgp;
+                    const float bh = sb * x1.x;
+                    const float s1 = x0.x + bh;
+                    const float bb = s1 - x0.x;
+                    const float lo = ((x0.x - (s1 - bb)) + (bh - bb)) + (x0.y + sb * x1.y);
+                    const float hi = s1 + lo;
+                    x = make_float2(hi, lo - (hi - s1));
+                } else {
+                    // a_l (l - m = 32 u + r of parity q) or P(a_l)
+                    float2 xp;
+                    xp.x = __shfl_sync(0xffffffffu, buf[r].x, psrc);
+                    xp.y = __shfl_sync(0xffffffffu, buf[r].y, psrc);
+                    const bool same = (r & 1) == q;
+                    x = same ? buf[r] : make_float2(sgp * xp.x, sgp * xp.y);
+                }
+                hv[i] = x.x * csc;
+                lv[i] = x.y * csc;
+            }
+            put4x8(A, A_PLANE, t, jj, hv, lv);
+        }
+    }
 }
 
 // ===========================================================================
@@ -1052,6 +1061,8 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.err = p->s.err;
     a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;
     a.ncol = ncols(p, nmaps); a.nalm = p->nalm;
+    a.ntile = (int)((a.ncol + TC_M - 1) / TC_M);
+    a.img = nullptr; a.img_base = nullptr; a.sunits = nullptr;
     a.Q = Q;
     a.fs0 = a.fs1 = 1.0;
     a.s0 = a.s1 = 1.0f;
@@ -1087,7 +1098,19 @@ static int pick_cluster(long long ntiles)
 }
 
 template <bool M2A, bool S2>
-static cudaError_t launch_tc(const sht_plan* p, int nwork, const void* src, void* dst,
+static cudaError_t launch_slice(int nunits, const void* src, uint8_t* img, const TcArgs& a, const char* name,
+                                cudaStream_t st)
+{
+    if (nunits == 0) return cudaSuccess;
+    prof_start(name, st);
+    k_slice<M2A, S2><<<dim3((unsigned)nunits, (unsigned)a.ntile), TC_M, 0, st>>>((const float2*)src, img, a);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <bool M2A, bool S2>
+static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
                              const TcArgs& a, const char* name, cudaStream_t st)
 {
     (void)p;
@@ -1111,7 +1134,7 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, const void* src, void
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, kern, src, dst, a);
+        e = cudaLaunchKernelEx(&cfg, kern, dst, a);
         if (e == cudaSuccess || C == 1) break;
         (void)cudaGetLastError();      // clear a failed cluster launch, retry smaller
         C = std::max(1, C / 2);
@@ -1121,26 +1144,51 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, const void* src, void
     return e;
 }
 
-cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, double* alm,
-                                   int nmaps, double fs0, double fs1, cudaStream_t st)
+// (the slicing pass writes the image that the contraction then reads, in stream order)
+cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, uint8_t* img,
+                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st)
 {
     if (p->s.nwork_m2a == 0) return cudaSuccess;
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_m2a);
     a.fs0 = fs0; a.fs1 = fs1;
     a.work = p->s.work_m2a;
-    if (p->spin) return launch_tc<true, true>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc_s2", st);
-    return launch_tc<true, false>(p, p->s.nwork_m2a, T, alm, a, "k_leg_m2a_tc", st);
+    a.img = img; a.img_base = p->s.img_base_m2a; a.sunits = p->s.sunits_m2a;
+    cudaError_t e;
+    if (p->spin) {
+        e = launch_slice<true, true>(p->s.nsunits_m2a, T, img, a, "k_slice_m2a_s2", st);
+        if (e == cudaSuccess) e = launch_tc<true, true>(p, p->s.nwork_m2a, alm, a, "k_leg_m2a_tc_s2", st);
+    } else {
+        e = launch_slice<true, false>(p->s.nsunits_m2a, T, img, a, "k_slice_m2a", st);
+        if (e == cudaSuccess) e = launch_tc<true, false>(p, p->s.nwork_m2a, alm, a, "k_leg_m2a_tc", st);
+    }
+    return e;
 }
 
-cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, float* G,
-                                   int nmaps, float s0, float s1, cudaStream_t st)
+cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, uint8_t* img,
+                                   float* G, int nmaps, float s0, float s1, cudaStream_t st)
 {
     if (p->s.nwork_a2m == 0) return cudaSuccess;
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_a2m);
     a.s0 = s0; a.s1 = s1;
     a.work = p->s.work_a2m;
-    if (p->spin) return launch_tc<false, true>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc_s2", st);
-    return launch_tc<false, false>(p, p->s.nwork_a2m, A2, G, a, "k_leg_a2m_tc", st);
+    a.img = img; a.img_base = p->s.img_base_a2m; a.sunits = p->s.sunits_a2m;
+    cudaError_t e;
+    if (p->spin) {
+        e = launch_slice<false, true>(p->s.nsunits_a2m, A2, img, a, "k_slice_a2m_s2", st);
+        if (e == cudaSuccess) e = launch_tc<false, true>(p, p->s.nwork_a2m, G, a, "k_leg_a2m_tc_s2", st);
+    } else {
+        e = launch_slice<false, false>(p->s.nsunits_a2m, A2, img, a, "k_slice_a2m", st);
+        if (e == cudaSuccess) e = launch_tc<false, false>(p, p->s.nwork_a2m, G, a, "k_leg_a2m_tc", st);
+    }
+    return e;
+}
+
+// bytes of the pre-sliced data image of one contraction (the larger direction)
+size_t split_img_bytes(const sht_plan* p, int nmaps)
+{
+    const long long ntile = (ncols(p, nmaps) + TC_M - 1) / TC_M;
+    const long long nch = std::max(p->s.img_chunks_m2a, p->s.img_chunks_a2m);
+    return (size_t)(nch * ntile) * (size_t)A_BYTES;
 }
 
 cudaError_t launch_alm_prep(const sht_plan* p, const double* alm, float2* A2, unsigned int* colmax, int nmaps,

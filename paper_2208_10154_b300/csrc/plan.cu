@@ -9,6 +9,7 @@
 #include <map>
 
 #include <cstdlib>
+#include <climits>
 #include "common.cuh"
 
 namespace sht {
@@ -401,6 +402,46 @@ static float slice_range(double K)
     return (float)Q;
 }
 
+// Slicing units and image chunks of the pre-sliced data (32-wide units of K
+// per (m, q)). map2alm: K = the ring pairs, for every (m, q) that has l rows;
+// spin 2 stores two chunks per unit (T_q + P(T_{1-q}) and T_q - P(T_{1-q})).
+// alm2map: K = the l of slot q (spin 0) or all l >= m (spin 2, one chunk per
+// unit shared by the v+ and v- chunks of the contraction).
+static cudaError_t build_slice_lists(sht_plan* p, size_t* acc)
+{
+    const int lmax = p->lmax, mmax = p->mmax, KCH = 32;
+    const int nuR = (p->R + KCH - 1) / KCH;
+    std::vector<int> bm((size_t)(mmax + 1) * 2, 0), ba((size_t)(mmax + 1) * 2, 0);
+    std::vector<int4> um, ua;
+    long long cm = 0, ca = 0;
+    for (int m = 0; m <= mmax; m++)
+        for (int q = 0; q < 2; q++) {
+            const int mq = m * 2 + q;
+            const int nl = (lmax >= m + q) ? (lmax - m - q) / 2 + 1 : 0;
+            bm[mq] = (int)cm;
+            if (nl > 0) {
+                for (int u = 0; u < nuR; u++) um.push_back(make_int4(m, q, u, (int)(cm + (p->spin ? 2 * u : u))));
+                cm += p->spin ? 2 * nuR : nuR;
+            }
+            const int Ka = p->spin ? (lmax >= m ? lmax - m + 1 : 0) : nl;
+            const int nua = (Ka + KCH - 1) / KCH;
+            ba[mq] = (int)ca;
+            for (int u = 0; u < nua; u++) ua.push_back(make_int4(m, q, u, (int)(ca + u)));
+            ca += nua;
+        }
+    if (cm > INT_MAX || ca > INT_MAX) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if ((e = upload(&p->s.img_base_m2a, bm, acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.img_base_a2m, ba, acc)) != cudaSuccess) return e;
+    if (!um.empty() && (e = upload(&p->s.sunits_m2a, um, acc)) != cudaSuccess) return e;
+    if (!ua.empty() && (e = upload(&p->s.sunits_a2m, ua, acc)) != cudaSuccess) return e;
+    p->s.nsunits_m2a = (int)um.size();
+    p->s.nsunits_a2m = (int)ua.size();
+    p->s.img_chunks_m2a = cm;
+    p->s.img_chunks_a2m = ca;
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // spin-2 split-form tables. The Wigner recurrence of build_tables,
 //   s lambda_l = A_l (x + B_l) s lambda_{l-1} - C_l s lambda_{l-2},
@@ -499,6 +540,7 @@ static cudaError_t build_split_tables_s2(sht_plan* p)
     // each contraction runs twice over its range (v+ and v- chunks)
     p->s.Q_m2a = slice_range(2.0 * R);
     p->s.Q_a2m = slice_range(2.0 * (lmax + 1));
+    if ((e = build_slice_lists(p, &acc)) != cudaSuccess) return e;
     p->table_bytes += acc;
     return cudaSuccess;
 }
@@ -588,6 +630,7 @@ static cudaError_t build_split_tables(sht_plan* p)
     if (e != cudaSuccess) return e;
     p->s.Q_m2a = slice_range((double)R);
     p->s.Q_a2m = slice_range((double)(lmax / 2 + 1));
+    if ((e = build_slice_lists(p, &acc)) != cudaSuccess) return e;
     p->table_bytes += acc;
     return cudaSuccess;
 }
@@ -603,7 +646,7 @@ static void free_tables(sht_plan* p)
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,
-                  p->s.s2d64};
+                  p->s.s2d64, p->s.img_base_m2a, p->s.img_base_a2m, p->s.sunits_m2a, p->s.sunits_a2m};
     for (void* q : sp) if (q) cudaFree(q);
     for (cudaEvent_t ev : p->hp_ev) if (ev) cudaEventDestroy(ev);
     if (p->hp_h2d) cudaStreamDestroy(p->hp_h2d);
@@ -634,12 +677,19 @@ static size_t colmax_bytes(const sht_plan* p, int nmaps)
     return p->precision == SHT_FP64 ? 0 : (size_t)(p->mmax + 1) * 2 * (size_t)ncols(p, nmaps) * sizeof(float);
 }
 
+static size_t img_bytes(const sht_plan* p, int nmaps)
+{
+    return p->precision == SHT_FP64 ? 0 : split_img_bytes(p, nmaps);
+}
+
 // Workspace layout: [T / G buffer][column maxima] for one transform. map2alm
 // with niter > 0 keeps the ring spectra T of the first pass and adds, for the
 // Fourier-domain iteration: [G buffer of alm2map (FP64: also the residual D)]
 // [split form: residual D (FP32 hi/lo)][split: column maxima][delta a_lm].
+// The split form ends with the pre-sliced data image of the contractions
+// (one at a time, in stream order).
 struct IterWs {
-    size_t g, d, cm, da, end;
+    size_t g, d, cm, da, img, end;
 };
 static IterWs iter_ws(const sht_plan* p, int nmaps)
 {
@@ -656,14 +706,21 @@ static IterWs iter_ws(const sht_plan* p, int nmaps)
         w.cm = w.d + round_up(n * sizeof(float2), 256);
         w.da = w.cm + cb;
     }
-    w.end = w.da + round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
+    w.img = w.da + round_up((size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double), 256);
+    w.end = w.img + round_up(img_bytes(p, nmaps), 256);
     return w;
+}
+
+// offset of the data image in the workspace of a transform without iteration
+static size_t img_offset(const sht_plan* p, int nmaps)
+{
+    return round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
 }
 
 static size_t ws_bytes(const sht_plan* p, int nmaps, int niter)
 {
     if (niter > 0) return iter_ws(p, nmaps).end;
-    return round_up(tbuf_bytes(p, nmaps), 256) + round_up(colmax_bytes(p, nmaps), 256);
+    return img_offset(p, nmaps) + round_up(img_bytes(p, nmaps), 256);
 }
 
 // elementwise helpers for the iteration (Algorithm 2)
@@ -857,8 +914,10 @@ static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nm
         float* G = (float*)ws;
         float2* A2 = (float2*)((char*)ws + split_a2_offset(p, nmaps));
         unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
+        uint8_t* img = (uint8_t*)ws + img_offset(p, nmaps);
         e = launch_alm_prep(p, alm, A2, cm, nmaps, st);
-        if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, A2, (const float*)cm, G, nmaps, (float)s0, (float)s1, st);
+        if (e == cudaSuccess)
+            e = launch_legendre_a2m_tc(p, A2, (const float*)cm, img, G, nmaps, (float)s0, (float)s1, st);
         if (e == cudaSuccess) e = launch_fft_backward_f32(p, G, map, nmaps, st);
     }
     if (e != cudaSuccess) { set_error(std::string("alm2map launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
@@ -866,7 +925,7 @@ static sht_status do_alm2map(sht_plan* p, const double* alm, double* map, int nm
 }
 
 static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nmaps, void* ws,
-                             double s0, double s1, cudaStream_t st)
+                             double s0, double s1, cudaStream_t st, uint8_t* img)
 {
     cudaError_t e;
     if (p->precision == SHT_FP64) {
@@ -879,7 +938,7 @@ static sht_status do_map2alm(sht_plan* p, const double* map, double* alm, int nm
         unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
         e = launch_fft_forward_split(p, map, T, cm, nmaps, st);
         if (e == cudaSuccess)
-            e = launch_legendre_m2a_tc(p, T, (const float*)cm, alm, nmaps, s0, s1, st);
+            e = launch_legendre_m2a_tc(p, T, (const float*)cm, img, alm, nmaps, s0, s1, st);
     }
     if (e != cudaSuccess) { set_error(std::string("map2alm launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
@@ -902,7 +961,8 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     cudaSetDevice(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const double dsig = 4.0 * PI_D / (double)p->npix;
-    s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st);
+    uint8_t* img = (uint8_t*)ws + (niter > 0 ? iter_ws(p, nmaps).img : img_offset(p, nmaps));
+    s = do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, dsig, dsig, st, img);
     if (s != SHT_OK || niter == 0) return s;
     // Algorithm 2, a += map2alm(T - alm2map(a)) niter times, restricted to the
     // ring spectra: T (kept from the first pass) - F(G) with G the Legendre
@@ -925,10 +985,11 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
             float2* D = (float2*)(base + w.d);
             unsigned int* cm = (unsigned int*)(base + w.cm);
             e = launch_alm_prep(p, (const double*)alm, A2, cm, nmaps, st);
-            if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, A2, (const float*)cm, G, nmaps, 1.0f, 1.0f, st);
+            uint8_t* img = (uint8_t*)(base + w.img);
+            if (e == cudaSuccess) e = launch_legendre_a2m_tc(p, A2, (const float*)cm, img, G, nmaps, 1.0f, 1.0f, st);
             if (e == cudaSuccess) e = launch_alias_residual(p, ws, G, D, nmaps, st);
             if (e == cudaSuccess) e = launch_colmax_T(p, D, cm, nmaps, st);
-            if (e == cudaSuccess) e = launch_legendre_m2a_tc(p, D, (const float*)cm, da, nmaps, dsig, dsig, st);
+            if (e == cudaSuccess) e = launch_legendre_m2a_tc(p, D, (const float*)cm, img, da, nmaps, dsig, dsig, st);
         }
         if (e != cudaSuccess) break;
         prof_start("k_add", st);
@@ -948,7 +1009,8 @@ sht_status sht_alm2map_adjoint(sht_plan* p, const void* map, void* alm, int nmap
     sht_status s = check_call(p, map, alm, nmaps, ws, wsb, 0);
     if (s != SHT_OK) return s;
     cudaSetDevice(p->device);
-    return do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, 1.0, 2.0, (cudaStream_t)stream);
+    return do_map2alm(p, (const double*)map, (double*)alm, nmaps, ws, 1.0, 2.0, (cudaStream_t)stream,
+                      (uint8_t*)ws + img_offset(p, nmaps));
 }
 
 sht_status sht_map2alm_adjoint(sht_plan* p, const void* alm, void* map, int nmaps, void* ws,
