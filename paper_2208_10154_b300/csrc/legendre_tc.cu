@@ -3,8 +3,9 @@
 //
 // The paper's per-m GEMMs (Sec. 2.2 equ:matrix form: A_m = P_m T_m and
 // T_m = P_m^t A_m) are evaluated per (m, slot q) with lambda generated on the
-// fly by the FP64 recurrence with scaled exponents (normalised same-parity
-// two-step form), so the Legendre matrix never lands in HBM.
+// fly by the normalised recurrence (same-parity two-step form for spin 0), run
+// in double-float (FP32 pair) arithmetic with scaled exponents from FP64
+// checkpoints every 32 rows, so the Legendre matrix never lands in HBM.
 //
 // Orientation. The MMA's M dimension (TMEM lanes) is 128 map columns
 // (map, component, Re/Im); its N dimension is the lambda side: l rows for
@@ -31,8 +32,8 @@
 // with every span. Dropped: products of two residual slices beyond r0 r1'
 // (< 2^-23 u u').
 //
-// Cluster sharing of lambda. The FP64 recurrence is the costly part (FP64 runs
-// at ~1/64 of FP32 here), so the CTAs of a thread-block cluster, which work on
+// Cluster sharing of lambda. The recurrence is a serial chain per ring pair,
+// so the CTAs of a thread-block cluster, which work on
 // the same (m, q, tile) for different column tiles, split the lambda work:
 // lambda for one stage is cut into 32-row pieces, each produced by one warp of
 // one CTA, written to its own shared memory and copied to every other CTA of
@@ -47,7 +48,8 @@
 //
 // CTA: 256 threads, one per SM (192 KB of pipeline stages, 512 TMEM columns).
 //   warp 0       TMEM allocation; lane 0 issues the MMAs
-//   warps 1-3    lambda pieces (32 ring pairs x 32 rows / steps each)
+//   warps 1-3    lambda pieces (32 ring pairs x 32 rows / steps each; 8 KB
+//                of shared scratch per warp)
 //   warps 4-7    data copies (one lane), stage releases, the drains of the
 //                correction accumulators, then the epilogue with warps 0-3
 #include <algorithm>
@@ -69,6 +71,9 @@ constexpr int NPL = 4;                           // FP16 slices per operand (q, 
 constexpr int A_PLANE = TC_M * KC * 2;           // 8 KB (data, one slice)
 constexpr int B_PLANE = TC_N * KC * 2;           // 8 KB (lambda, one slice)
 constexpr int PIECE_BYTES = PR * KC * 2;         // 2 KB of one B plane
+constexpr int SCR_BYTES = NPL * PIECE_BYTES;      // 8 KB: one lambda piece (scratch per lambda warp)
+constexpr int LAM_SM = 256;                      // SM ids covered by the L2 slots of the lambda pieces
+constexpr int LAM_SLOTS = 4;                     // L2 slots per lambda warp (used round-robin)
 constexpr int A_BYTES = NPL * A_PLANE;           // 32 KB: one chunk of the data operand
 constexpr int STAGE_BYTES = NPL * (A_PLANE + B_PLANE);   // 64 KB
 constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
@@ -154,6 +159,29 @@ __device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row
     store4x8(planes, plane_bytes, row, j, pk);
 }
 
+// lambda piece scratch (4 planes of 32 rows x 64 B, the swizzle of rows
+// 32 j .. 32 j + 31 of a stage plane). map2alm: rows i0 .. i0 + 7 of K column
+// `lane` (one FP16 per plane and row); alm2map: the 16-byte chunk jj (k = 8 jj
+// .. 8 jj + 7) of row `lane`.
+__device__ __forceinline__ void put_rows8(uint8_t* scr, int i0, int lane, const float (&hv)[8], const float (&lv)[8])
+{
+#pragma unroll
+    for (int ii = 0; ii < 8; ii++) {
+        float x[NPL];
+        slice4d(hv[ii], lv[ii], x[0], x[1], x[2], x[3]);
+        const uint32_t w01 = pack_h2(x[0], x[1]), w23 = pack_h2(x[2], x[3]);
+        const uint32_t off = sw64_off(i0 + ii, lane);
+        *reinterpret_cast<uint16_t*>(scr + off) = (uint16_t)(w01 & 0xFFFFu);
+        *reinterpret_cast<uint16_t*>(scr + PIECE_BYTES + off) = (uint16_t)(w01 >> 16);
+        *reinterpret_cast<uint16_t*>(scr + 2 * PIECE_BYTES + off) = (uint16_t)(w23 & 0xFFFFu);
+        *reinterpret_cast<uint16_t*>(scr + 3 * PIECE_BYTES + off) = (uint16_t)(w23 >> 16);
+    }
+}
+__device__ __forceinline__ void put_chunk8(uint8_t* scr, int row, int jj, const float (&hv)[8], const float (&lv)[8])
+{
+    put4x8(scr, PIECE_BYTES, row, jj, hv, lv);
+}
+
 // one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
 // whole of K, sm over the whole of K on top of the residual the epilogue warps
 // leave in it (only the first stage restarts them); ex and fn restart at the
@@ -190,6 +218,15 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uin
     }
 }
 
+// Lambda pieces travel through L2: a lambda warp writes its piece to its own
+// slot (per SM id, warp and round-robin index) and multicasts it from there
+// into the stage of every CTA of the cluster. Only one CTA of the contraction
+// runs on an SM at a time (its shared memory), and a CTA exits only after
+// every piece it sent has landed, so the slots of an SM are never shared.
+__device__ __align__(128) uint8_t g_lam_slots[(size_t)LAM_SM * 3 * LAM_SLOTS * SCR_BYTES];
+
+struct df { float h, l; };   // double-float value hi + lo
+
 struct TcShared {
     uint64_t full[NST];        // stage filled: 4 data warps + one arrival per lambda piece
     uint64_t empty[NST];       // stage consumed by the MMAs of every CTA of the cluster
@@ -201,11 +238,98 @@ struct TcShared {
     uint32_t tmem;
     int colexp[TC_M];
     int rowexp[TC_N];          // quantum exponent per lambda row (l or ring pair)
-    double cA[TC_N], cB[TC_N]; // map2alm: recurrence coefficients of the tile's rows
+    df cA2[TC_N], cB2[TC_N];   // map2alm: recurrence coefficients of the tile's rows
     float2 rfac[TC_N];         // map2alm: c_l * factor as an FP32 hi/lo pair
     int rowidx[TC_N];          // map2alm: packed index of the row's (l, m)
 };
-constexpr int SMEM_TC = NST * STAGE_BYTES + (int)sizeof(TcShared) + 1024;
+constexpr int SMEM_TC = NST * STAGE_BYTES + 3 * SCR_BYTES + (int)sizeof(TcShared) + 1024;
+static_assert(SMEM_TC <= 227 * 1024, "shared memory of k_leg_tc");
+
+// ---------------------------------------------------------------------------
+// double-float ("hi + lo" FP32 pair) arithmetic for the lambda recurrences.
+// An FP64 operation costs hundreds of cycles of latency on this GPU (a
+// dependent FP64 recurrence step measured ~510 cycles), a double-float step
+// ~70; the pair carries ~48 bits, far below what the FP16 slices keep
+// (~2^-35 of the quantum). Error-free transformations: TwoSum (Knuth) and the
+// FMA-based TwoProduct, written with non-contracting intrinsics.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df df_norm(float s, float e)
+{
+    const float h = __fadd_rn(s, e);
+    return df{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// an FP64 value as a pair (|v| < 2^127; parts below the FP32 normal range flush to 0)
+__device__ __forceinline__ df df_of(double v)
+{
+    df r;
+    f64_split_scaled(v, 0, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df_norm(p, e);
+}
+// A x + B
+__device__ __forceinline__ df df_axb(df A, df x, df B)
+{
+    const float p = __fmul_rn(A.h, x.h);
+    float pe = __fmaf_rn(A.h, x.h, -p);
+    pe = __fmaf_rn(A.h, x.l, pe);
+    pe = __fmaf_rn(A.l, x.h, pe);
+    const float s = __fadd_rn(p, B.h);
+    const float bb = __fsub_rn(s, p);
+    float e = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(B.h, bb));
+    e = __fadd_rn(e, __fadd_rn(pe, B.l));
+    return df_norm(s, e);
+}
+// one step of a three-term recurrence: (cur, prev) <- (t cur + sgn prev, cur), sgn = +-1
+__device__ __forceinline__ void df_rec(df t, df& cur, df& prev, float sgn)
+{
+    const float m = __fmul_rn(t.h, cur.h);
+    float me = __fmaf_rn(t.h, cur.h, -m);
+    me = __fmaf_rn(t.h, cur.l, me);
+    me = __fmaf_rn(t.l, cur.h, me);
+    const float ph = sgn * prev.h, pl = sgn * prev.l;
+    const float s = __fadd_rn(m, ph);
+    const float bb = __fsub_rn(s, m);
+    float e = __fadd_rn(__fsub_rn(m, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+    e = __fadd_rn(e, __fadd_rn(me, pl));
+    prev = cur;
+    cur = df_norm(s, e);
+}
+// keep the pair in range: above 2^64 scale both values down by 2^64 (exact)
+__device__ __forceinline__ void rescale_df(df& cur, df& prev, int& E)
+{
+    if (((__float_as_uint(cur.h) >> 23) & 0xFF) > 127 + 64) {
+        cur.h *= 0x1p-64f; cur.l *= 0x1p-64f;
+        prev.h *= 0x1p-64f; prev.l *= 0x1p-64f;
+        E += 64;
+    }
+}
+// a checkpoint (mu_l, mu_{l-1 or l-2}) 2^E as pairs scaled near 1 (E absorbs the scale)
+__device__ __forceinline__ void ck_to_df(double2 v, df& cur, df& prev, int& E)
+{
+    const int ec = (__double2hiint(v.x) >> 20) & 0x7FF, ep = (__double2hiint(v.y) >> 20) & 0x7FF;
+    const int eb = max(ec, ep);
+    const int sc = (eb == 0) ? 0 : eb - 1023;
+    f64_split_scaled(v.x, -sc, cur.h, cur.l);
+    f64_split_scaled(v.y, -sc, prev.h, prev.l);
+    E += sc;
+}
+// the pair times 2^k as (hi, lo) (flushes below the FP32 normal range)
+__device__ __forceinline__ void df_scaled(df c, int k, float& h, float& l)
+{
+    h = ldexpf_fast(c.h, k);
+    l = ldexpf_fast(c.l, k);
+}
+__device__ __forceinline__ df shfl_df(df v, int src)
+{
+    return df{__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
 
 // x * 2^-500 by exponent arithmetic (x is either 0 or has a biased exponent
 // above 500 here, or is flushed to 0 if it does not)
@@ -273,7 +397,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES);
+    TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES + 3 * SCR_BYTES);
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, tile = w.z, ckb = w.w;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -297,7 +421,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     for (int r = tid; r < TC_N; r += blockDim.x) {
         if (M2A) sh.rowidx[r] = (r < nrows) ? (int)a_idx(a.lmax, l_first + 2 * (n0 + r), m) : 0;
         if (M2A && S2) {
-            sh.cA[r] = 0.0; sh.cB[r] = 0.0;
+            sh.cA2[r] = df{0.0f, 0.0f}; sh.cB2[r] = df{0.0f, 0.0f};
             if (r < nrows) {
                 const int l = l_first + 2 * (n0 + r);
                 const long long ci = a_idx(a.lmax, l, m);
@@ -313,8 +437,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             if (r < nrows) {
                 const int l = l_first + 2 * (n0 + r);
                 const long long ci = a_idx(a.lmax, l, m);
-                sh.cA[r] = a.nA[ci];
-                sh.cB[r] = a.nB[ci];
+                sh.cA2[r] = df_of(a.nA[ci]);
+                sh.cB2[r] = df_of(a.nB[ci]);
                 sh.rowexp[r] = quantum_exp(a.rowmax[ci], a.Q);
                 // c_l * dsigma applied once per output in double-float, so its
                 // rounding is not a coherent error along the row
@@ -322,7 +446,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const float fh = (float)f;
                 sh.rfac[r] = make_float2(fh, (float)(f - (double)fh));
             } else {
-                sh.cA[r] = 0.0; sh.cB[r] = 0.0; sh.rowexp[r] = 0; sh.rfac[r] = make_float2(0.0f, 0.0f);
+                sh.cA2[r] = df{0.0f, 0.0f}; sh.cB2[r] = df{0.0f, 0.0f};
+                sh.rowexp[r] = 0; sh.rfac[r] = make_float2(0.0f, 0.0f);
             }
         } else {
             sh.rowexp[r] = (r < nrows) ? quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + n0 + r], a.Q) : 0;
@@ -331,7 +456,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     for (int c = tid; c < TC_M; c += blockDim.x) sh.colexp[c] = col_quantum<M2A, S2>(a, m, q, c0, c);
     if (tid == 0) {
         for (int s = 0; s < NST; s++) {
-            mbar_init(&sh.full[s], 1 + npieces);
+            mbar_init(&sh.full[s], 1);     // the data warp's arrival; every byte completes as tx
             mbar_init(&sh.empty[s], csize);
         }
         mbar_init(&sh.accf, 1);
@@ -368,15 +493,24 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         }
     } else if (warp < 4) {
         // ---------------- lambda pieces ----------------
-        // A piece is computed into registers first (32 recurrence steps, ~one
-        // FP64 FMA latency each) and only then does the warp wait for its stage
-        // to be released, so the recurrence overlaps the MMAs of earlier chunks.
-        const int total = nch * npieces;
-        for (int g = (int)crank + (int)csize * (warp - 1); g < total; g += (int)csize * 3) {
+        // A piece is computed first, in groups of 8 rows / steps, into this
+        // warp's scratch (the piece's exact shared-memory image), and only then
+        // does the warp wait for its stage to be released, so the recurrence
+        // overlaps the MMAs of earlier chunks. A warp's pieces can be several
+        // chunks apart, more than the parity of the stage barrier can tell
+        // apart, so it waits on the monotonic count of released chunks that the
+        // data warps publish instead.
+        uint8_t* scr = smem + NST * STAGE_BYTES + (warp - 1) * SCR_BYTES;
+        const uint32_t smid = sm_id();
+        if (smid >= (uint32_t)LAM_SM && lane == 0) atomicCAS(a.err, 0, 9);
+        uint8_t* gslots = g_lam_slots + ((size_t)(smid % LAM_SM) * 3 + (warp - 1)) * LAM_SLOTS * SCR_BYTES;
+        const uint16_t mask = (uint16_t)((1u << csize) - 1u);
+        const int total = (smid < (uint32_t)LAM_SM) ? nch * npieces : 0;
+        const int gstep = (int)csize * 3;
+        int npc = 0;                                    // pieces of this warp so far
+        for (int g = (int)crank + (int)csize * (warp - 1); g < total; g += gstep, npc++) {
             const int kc = g / npieces, j = g - kc * npieces;
             const int s = kc % NST;
-            float hb[PR], lb[PR];
-            int prow;                                   // row of the B tile this lane writes (alm2map)
             if constexpr (M2A && S2) {
                 // lane = ring pair (k) of unit kc / 2, walking the 64 l that hold the
                 // 32 rows (slot q) of piece j with the recurrence of s = (kc odd ? -2 : +2)
@@ -385,81 +519,85 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const int J = (n0 >> 5) + j;            // 32-row block of the slot's rows
                 const int L = m + 64 * J;               // first l of the walk (checkpoint block 2J)
                 const int lck = max(L, l0s);            // l of the checkpointed value
-                double cur = 0.0, prev = 0.0, x = 0.0;
+                df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x = {0.0f, 0.0f};
                 int E = 0;
                 const bool live = p < a.R;
                 if (live) {
                     const long long ci = ((long long)(ckb + 2 * J) * 2 + sg) * a.R + p;
-                    const double2 v = a.ck[ci];
-                    cur = v.x; prev = v.y;
                     E = a.ck_exp[ci];
-                    x = a.pairs[p].x;
+                    ck_to_df(a.ck[ci], cur, prev, E);
+                    x = df_of(a.pairs[p].x);
                 }
                 // coefficients of the walk: lane k holds l = L + k and L + 32 + k
-                double cA0 = 0.0, cB0 = 0.0, cA1 = 0.0, cB1 = 0.0;
+                df cA0 = {0.0f, 0.0f}, cB0 = {0.0f, 0.0f}, cA1 = {0.0f, 0.0f}, cB1 = {0.0f, 0.0f};
                 if (L + lane <= a.lmax) {
                     const long long ci = a_idx(a.lmax, L + lane, m);
-                    cA0 = a.s2A[sg][ci]; cB0 = a.s2B[sg][ci];
+                    cA0 = df_of(a.s2A[sg][ci]); cB0 = df_of(a.s2B[sg][ci]);
                 }
                 if (L + 32 + lane <= a.lmax) {
                     const long long ci = a_idx(a.lmax, L + 32 + lane, m);
-                    cA1 = a.s2A[sg][ci]; cB1 = a.s2B[sg][ci];
+                    cA1 = df_of(a.s2A[sg][ci]); cB1 = df_of(a.s2B[sg][ci]);
                 }
                 const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
                 int lc = lck;                           // l of cur (warp-uniform)
+#pragma unroll 1
+                for (int i0 = 0; i0 < PR; i0 += 8) {
+                    float hv[8], lv[8];
 #pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    hb[i] = 0.0f; lb[i] = 0.0f;
-                    if (i < rn) {
-                        const int lt = L + q + 2 * i;   // the row's l
+                    for (int ii = 0; ii < 8; ii++) {
+                        const int i = i0 + ii;
+                        hv[ii] = 0.0f; lv[ii] = 0.0f;
+                        if (i < rn) {
+                            const int lt = L + q + 2 * i;   // the row's l
 #pragma unroll
-                        for (int st = 0; st < 2; st++) {
-                            if (lc < lt) {
-                                const int k = lc + 1 - L;
-                                const double cA = __shfl_sync(0xffffffffu, k < 32 ? cA0 : cA1, k & 31);
-                                const double cB = __shfl_sync(0xffffffffu, k < 32 ? cB0 : cB1, k & 31);
-                                const double nxt = fma(fma(cA, x, cB), cur, -prev);
-                                prev = cur;
-                                cur = nxt;
-                                rescale(cur, prev, E);
-                                lc++;
+                            for (int st = 0; st < 2; st++) {
+                                if (lc < lt) {
+                                    const int k = lc + 1 - L;
+                                    const df cA = shfl_df(k < 32 ? cA0 : cA1, k & 31);
+                                    const df cB = shfl_df(k < 32 ? cB0 : cB1, k & 31);
+                                    df_rec(df_axb(cA, x, cB), cur, prev, -1.0f);
+                                    rescale_df(cur, prev, E);
+                                    lc++;
+                                }
                             }
+                            if (live && lt >= lck) df_scaled(cur, E - sh.rowexp[j * PR + i], hv[ii], lv[ii]);
                         }
-                        if (live && lt >= lck) f64_split_scaled(cur, E - sh.rowexp[j * PR + i], hb[i], lb[i]);
                     }
+                    put_rows8(scr, i0, lane, hv, lv);
                 }
-                prow = 0;
             } else if constexpr (M2A) {
                 // lane = ring pair (k), walking the 32 l rows of piece j
                 const int p = kc * KC + lane;
-                double cur = 0.0, prev = 0.0, x2 = 0.0;
+                df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x2 = {0.0f, 0.0f};
                 int E = 0;
                 const bool live = p < a.R;
                 if (live) {
                     const long long ci = (long long)(ckb + (n0 + j * PR) / CK_ROWS) * a.R + p;
-                    const double2 v = a.ck[ci];
-                    cur = v.x; prev = v.y;
                     E = a.ck_exp[ci];
-                    const double x = a.pairs[p].x;
-                    x2 = x * x;
+                    ck_to_df(a.ck[ci], cur, prev, E);
+                    const df x = df_of(a.pairs[p].x);
+                    x2 = df_mul(x, x);
                 }
                 const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
-                double tn = fma(sh.cA[j * PR], x2, sh.cB[j * PR]);
+                df tn = df_axb(sh.cA2[j * PR], x2, sh.cB2[j * PR]);
+#pragma unroll 1
+                for (int i0 = 0; i0 < PR; i0 += 8) {
+                    float hv[8], lv[8];
 #pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    hb[i] = 0.0f; lb[i] = 0.0f;
-                    if (i < rn) {
-                        const int r = j * PR + i;
-                        if (live) f64_split_scaled(cur, E - sh.rowexp[r], hb[i], lb[i]);
-                        const double t = tn;            // coefficient FMA one step ahead
-                        if (i + 1 < rn) tn = fma(sh.cA[r + 1], x2, sh.cB[r + 1]);
-                        const double nxt = fma(t, cur, prev);
-                        prev = cur;
-                        cur = nxt;
-                        rescale(cur, prev, E);
+                    for (int ii = 0; ii < 8; ii++) {
+                        const int i = i0 + ii;
+                        hv[ii] = 0.0f; lv[ii] = 0.0f;
+                        if (i < rn) {
+                            const int r = j * PR + i;
+                            if (live) df_scaled(cur, E - sh.rowexp[r], hv[ii], lv[ii]);
+                            const df t = tn;            // coefficient one step ahead
+                            if (i + 1 < rn) tn = df_axb(sh.cA2[r + 1], x2, sh.cB2[r + 1]);
+                            df_rec(t, cur, prev, 1.0f);
+                            rescale_df(cur, prev, E);
+                        }
                     }
+                    put_rows8(scr, i0, lane, hv, lv);
                 }
-                prow = 0;
             } else if constexpr (S2) {
                 // lane = ring pair (row), walking the 32 l of unit kc / 2 with the
                 // recurrence of s = (kc odd ? -2 : +2); d_l applied in double-float
@@ -470,47 +608,49 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const bool live = r < nrows;
                 const int L = m + KC * u;               // first l of the unit (checkpoint block u)
                 const int lck = max(L, l0s);
-                double cur = 0.0, prev = 0.0, x = 0.0;
+                df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x = {0.0f, 0.0f};
                 int E = 0, pe = 0;
                 if (live) {
                     const long long ci = ((long long)(ckb + u) * 2 + sg) * a.R + p;
-                    const double2 v = a.ck[ci];
-                    cur = v.x; prev = v.y;
                     E = a.ck_exp[ci];
-                    x = a.pairs[p].x;
+                    ck_to_df(a.ck[ci], cur, prev, E);
+                    x = df_of(a.pairs[p].x);
                     pe = sh.rowexp[r];
                 }
-                double cAk = 0.0, cBk = 0.0;
+                df cAk = {0.0f, 0.0f}, cBk = {0.0f, 0.0f};
                 float2 cdk = make_float2(0.0f, 0.0f);
                 if (L + lane <= a.lmax) {
                     const long long ci = a_idx(a.lmax, L + lane, m);
-                    cAk = a.s2A[sg][ci]; cBk = a.s2B[sg][ci]; cdk = a.s2d2[ci];
+                    cAk = df_of(a.s2A[sg][ci]); cBk = df_of(a.s2B[sg][ci]); cdk = a.s2d2[ci];
                 }
+#pragma unroll 1
+                for (int i0 = 0; i0 < PR; i0 += 8) {
+                    float hv[8], lv[8];
 #pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    hb[i] = 0.0f; lb[i] = 0.0f;
-                    const float d0 = __shfl_sync(0xffffffffu, cdk.x, i);
-                    const float d1 = __shfl_sync(0xffffffffu, cdk.y, i);
-                    const double cA = __shfl_sync(0xffffffffu, cAk, i);
-                    const double cB = __shfl_sync(0xffffffffu, cBk, i);
-                    const int l = L + i;
-                    if (l <= a.lmax && l >= lck) {
-                        if (l > lck) {
-                            const double nxt = fma(fma(cA, x, cB), cur, -prev);
-                            prev = cur;
-                            cur = nxt;
-                            rescale(cur, prev, E);
+                    for (int ii = 0; ii < 8; ii++) {
+                        const int i = i0 + ii;
+                        hv[ii] = 0.0f; lv[ii] = 0.0f;
+                        const float d0 = __shfl_sync(0xffffffffu, cdk.x, i);
+                        const float d1 = __shfl_sync(0xffffffffu, cdk.y, i);
+                        const df cA = shfl_df(cAk, i);
+                        const df cB = shfl_df(cBk, i);
+                        const int l = L + i;
+                        if (l <= a.lmax && l >= lck) {
+                            if (l > lck) {
+                                df_rec(df_axb(cA, x, cB), cur, prev, -1.0f);
+                                rescale_df(cur, prev, E);
+                            }
+                            float h = 0.0f, lo = 0.0f;
+                            if (live) df_scaled(cur, E - pe, h, lo);
+                            const float p1 = __fmul_rn(h, d0);      // lambda = d_l mu in double-float
+                            // v- chunks carry sigma_l = -1 for the rows of the other parity
+                            const float sgn = (sg && (i & 1) != q) ? -1.0f : 1.0f;
+                            hv[ii] = sgn * p1;
+                            lv[ii] = sgn * (fmaf(h, d0, -p1) + (h * d1 + lo * d0));
                         }
-                        float h = 0.0f, lo = 0.0f;
-                        if (live) f64_split_scaled(cur, E - pe, h, lo);
-                        const float p1 = h * d0;                // lambda = d_l mu in double-float
-                        // v- chunks carry sigma_l = -1 for the rows of the other parity
-                        const float sgn = (sg && (i & 1) != q) ? -1.0f : 1.0f;
-                        hb[i] = sgn * p1;
-                        lb[i] = sgn * (fmaf(h, d0, -p1) + (h * d1 + lo * d0));
                     }
+                    put_chunk8(scr, lane, i0 >> 3, hv, lv);
                 }
-                prow = r;
             } else {
                 // lane = ring pair (row), walking the 32 l of stage kc; the
                 // coefficients of those 32 l are loaded once (lane k holds l_k)
@@ -518,118 +658,78 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const int r = j * PR + lane;
                 const int p = n0 + r;
                 const bool live = r < nrows;
-                double cur = 0.0, prev = 0.0, x2 = 0.0;
+                df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x2 = {0.0f, 0.0f};
                 int E = 0, pe = 0;
                 if (live) {
                     const long long ci = (long long)(ckb + kc * KC / CK_ROWS) * a.R + p;
-                    const double2 v = a.ck[ci];
-                    cur = v.x; prev = v.y;
                     E = a.ck_exp[ci];
-                    const double x = a.pairs[p].x;
-                    x2 = x * x;
+                    ck_to_df(a.ck[ci], cur, prev, E);
+                    const df x = df_of(a.pairs[p].x);
+                    x2 = df_mul(x, x);
                     pe = sh.rowexp[r];
                 }
-                double cAk = 0.0, cBk = 0.0;
+                df cAk = {0.0f, 0.0f}, cBk = {0.0f, 0.0f};
                 float2 cck = make_float2(0.0f, 0.0f);
                 {
                     const int k = kc * KC + lane;
                     if (k < K) {
                         const long long ci = a_idx(a.lmax, l_first + 2 * k, m);
-                        cAk = a.nA[ci]; cBk = a.nB[ci]; cck = a.nc2[ci];
+                        cAk = df_of(a.nA[ci]); cBk = df_of(a.nB[ci]); cck = a.nc2[ci];
                     }
                 }
                 const int kn = min(KC, K - kc * KC);    // valid l of this chunk (warp-uniform)
-                double tn = fma(__shfl_sync(0xffffffffu, cAk, 0), x2, __shfl_sync(0xffffffffu, cBk, 0));
-#pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    hb[i] = 0.0f; lb[i] = 0.0f;
-                    const float c0_ = __shfl_sync(0xffffffffu, cck.x, i);
-                    const float c1_ = __shfl_sync(0xffffffffu, cck.y, i);
-                    const double cAn = __shfl_sync(0xffffffffu, cAk, (i + 1) & (PR - 1));
-                    const double cBn = __shfl_sync(0xffffffffu, cBk, (i + 1) & (PR - 1));
-                    if (i < kn) {
-                        float h = 0.0f, lo = 0.0f;
-                        if (live) f64_split_scaled(cur, E - pe, h, lo);
-                        const float p1 = h * c0_;               // lambda = c_l mu in double-float
-                        hb[i] = p1;
-                        lb[i] = fmaf(h, c0_, -p1) + (h * c1_ + lo * c0_);
-                        const double t = tn;
-                        if (i + 1 < kn) tn = fma(cAn, x2, cBn);
-                        const double nxt = fma(t, cur, prev);
-                        prev = cur;
-                        cur = nxt;
-                        rescale(cur, prev, E);
-                    }
-                }
-                prow = r;
-            }
-            // A warp's pieces can be several chunks apart, more than the parity
-            // of the stage barrier can tell apart, so it waits on the monotonic
-            // count of released chunks that the data warps publish instead.
-            // slice and pack the piece while the stage may still be in use
-            // (map2alm: per row, planes (q, r0) and (r1, r2s) as FP16 pairs;
-            // alm2map: 16-byte chunks of 8 consecutive k per plane)
-            uint32_t pk2[M2A ? 2 * PR : 1];
-            uint4 pk4[M2A ? 1 : (KC / 8) * NPL];
-            if constexpr (M2A) {
-#pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    float x[NPL];
-                    slice4d(hb[i], lb[i], x[0], x[1], x[2], x[3]);
-                    pk2[2 * i] = pack_h2(x[0], x[1]);
-                    pk2[2 * i + 1] = pack_h2(x[2], x[3]);
-                }
-            } else {
-#pragma unroll
-                for (int jj = 0; jj < KC / 8; jj++) {
+                df tn = df_axb(shfl_df(cAk, 0), x2, shfl_df(cBk, 0));
+#pragma unroll 1
+                for (int i0 = 0; i0 < PR; i0 += 8) {
                     float hv[8], lv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; i++) { hv[i] = hb[jj * 8 + i]; lv[i] = lb[jj * 8 + i]; }
-                    uint4 t4[NPL];
-                    pack4x8(hv, lv, t4);
-#pragma unroll
-                    for (int b = 0; b < NPL; b++) pk4[jj * NPL + b] = t4[b];
-                }
-            }
-            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
-            uint8_t* B = smem + s * STAGE_BYTES + NPL * A_PLANE;
-            if constexpr (M2A) {
-#pragma unroll
-                for (int i = 0; i < PR; i++) {
-                    const uint32_t off = sw64_off(j * PR + i, lane);
-                    const uint32_t w01 = pk2[2 * i], w23 = pk2[2 * i + 1];
-                    *reinterpret_cast<uint16_t*>(B + off) = (uint16_t)(w01 & 0xFFFFu);
-                    *reinterpret_cast<uint16_t*>(B + B_PLANE + off) = (uint16_t)(w01 >> 16);
-                    *reinterpret_cast<uint16_t*>(B + 2 * B_PLANE + off) = (uint16_t)(w23 & 0xFFFFu);
-                    *reinterpret_cast<uint16_t*>(B + 3 * B_PLANE + off) = (uint16_t)(w23 >> 16);
-                }
-            } else {
-#pragma unroll
-                for (int jj = 0; jj < KC / 8; jj++) {
-                    uint4 t4[NPL];
-#pragma unroll
-                    for (int b = 0; b < NPL; b++) t4[b] = pk4[jj * NPL + b];
-                    store4x8(B, B_PLANE, prow, jj, t4);
-                }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            // lane d sends the piece to CTA d of the cluster (its own CTA: a plain arrival)
-            if (lane < (int)csize) {
-                const uint32_t d = (uint32_t)lane;
-                if (d == crank) {
-                    mbar_arrive(&sh.full[s]);
-                } else {
-                    const uint32_t src0 = smem_u32(B) + j * PIECE_BYTES;
-                    const uint32_t fb = mapa_shared(smem_u32(&sh.full[s]), d);
-                    mbar_arrive_expect_tx_cl(fb, NPL * PIECE_BYTES);
-#pragma unroll
-                    for (int b = 0; b < NPL; b++) {
-                        const uint32_t sa = src0 + b * B_PLANE;
-                        bulk_copy_s2cluster(mapa_shared(sa, d), sa, PIECE_BYTES, fb);
+                    for (int ii = 0; ii < 8; ii++) {
+                        const int i = i0 + ii;
+                        hv[ii] = 0.0f; lv[ii] = 0.0f;
+                        const float c0_ = __shfl_sync(0xffffffffu, cck.x, i);
+                        const float c1_ = __shfl_sync(0xffffffffu, cck.y, i);
+                        const df cAn = shfl_df(cAk, (i + 1) & (PR - 1));
+                        const df cBn = shfl_df(cBk, (i + 1) & (PR - 1));
+                        if (i < kn) {
+                            float h = 0.0f, lo = 0.0f;
+                            if (live) df_scaled(cur, E - pe, h, lo);
+                            const float p1 = __fmul_rn(h, c0_);     // lambda = c_l mu in double-float
+                            hv[ii] = p1;
+                            lv[ii] = fmaf(h, c0_, -p1) + (h * c1_ + lo * c0_);
+                            const df t = tn;
+                            if (i + 1 < kn) tn = df_axb(cAn, x2, cBn);
+                            df_rec(t, cur, prev, 1.0f);
+                            rescale_df(cur, prev, E);
+                        }
                     }
+                    put_chunk8(scr, lane, i0 >> 3, hv, lv);
                 }
             }
+            __syncwarp();
+            // The piece into its L2 slot, once the slot's previous piece (LAM_SLOTS
+            // pieces ago, chunk kp) has landed in every CTA: true once chunk kp + NST
+            // is released, which needs the MMAs of chunk kp in every CTA.
+            const int gp = g - LAM_SLOTS * gstep;
+            if (gp >= 0 && !__all_sync(0xffffffffu, wait_counter(&sh.released, gp / npieces + NST, a.err, 8))) break;
+            uint8_t* gs = gslots + (npc & (LAM_SLOTS - 1)) * SCR_BYTES;
+#pragma unroll
+            for (int v = 0; v < SCR_BYTES / 512; v++) {
+                const int off = (v * 32 + lane) * 16;
+                *reinterpret_cast<uint4*>(gs + off) = *reinterpret_cast<const uint4*>(scr + off);
+            }
+            fence_proxy_async_global();
+            __syncwarp();
+            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
+            // stage free in every CTA: one multicast copy per plane into rows
+            // 32 j .. 32 j + 31 (one contiguous 2 KB block: the swizzle repeats
+            // every 8 rows); each CTA's data warp announced these bytes
+            if (lane == 0) {
+                const uint32_t dst = smem_u32(smem + s * STAGE_BYTES + NPL * A_PLANE) + j * PIECE_BYTES;
+#pragma unroll
+                for (int b = 0; b < NPL; b++)
+                    bulk_copy_g2s_mc(dst + b * B_PLANE, gs + b * PIECE_BYTES, PIECE_BYTES, &sh.full[s], mask);
+            }
+            __syncwarp();                               // scratch reads done before the next piece
         }
     } else {
         // ---------------- data copies, stage releases, span drains ----------------
@@ -645,7 +745,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             if (warp == 4 && lane == 0) {
                 const int s = c % NST;
                 const long long ci = (S2 && !M2A) ? (c >> 1) : c;
-                mbar_arrive_expect_tx(&sh.full[s], A_BYTES);
+                mbar_arrive_expect_tx(&sh.full[s], A_BYTES + npieces * SCR_BYTES);
                 bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
             }
         };
@@ -694,10 +794,9 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         for (int c = NST; c < nch + NST; c++) {
             if (dok) {
                 dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1, a.err, 3));
-                if (dok && c < nch) {
-                    copy(c);
-                    if (warp == 4 && lane == 0) publish_counter(&sh.released, c);
-                }
+                if (dok && c < nch) copy(c);
+                // (published past nch too: the lambda warps' L2 slots wait on it)
+                if (dok && warp == 4 && lane == 0) publish_counter(&sh.released, c);
             }
             if ((c & 1) == 0 && c >= 4 && nd < nspan && dok) drain(nd++);
         }

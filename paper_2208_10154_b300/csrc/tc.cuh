@@ -132,6 +132,27 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  :: "r"(dst), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
 }
+// 1-D bulk copy global -> the shared memory at the same offset in every CTA of
+// `mask` (cluster multicast; source in this GPU's own memory), completing on the
+// mbarrier at the same offset in each destination CTA
+__device__ __forceinline__ void bulk_copy_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* mbar,
+                                                 uint16_t mask)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+                 " [%0], [%1], %2, [%3], %4;"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(smem_u32(mbar)), "h"(mask) : "memory");
+}
+// generic-proxy writes to global memory made visible to later async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t sm_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
 // named barrier over `n` threads (id 1..15; id 0 is __syncthreads)
 __device__ __forceinline__ void named_bar_sync(int id, int n)
 {
