@@ -16,21 +16,23 @@
 // Accuracy. Every operand x is written, per row or column, in units of a
 // power-of-two quantum u with |x/u| <= Q (Q (Q + 1) K + 12 K / 32 <= 2^24,
 // Q <= 127) as four FP16 slices q + r0 + r1 + 2^-12 r2s (tc::slice4d: integer,
-// a multiple of 2^-11, the next 11 bits and the 11 after, ~2^-35 of u). Ten
+// a multiple of 2^-G, the next 11 bits and the 11 after, ~2^-(G+24) of u). Ten
 // products per K step, in four TMEM accumulators:
 //     main = sum q q'                              integers: exact
-//     ex   = q r0' + r0 q'                         multiples of 2^-11 below 2^13
-//                                                  per 64-wide K span: exact
-//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'        below ~20 per span
+//     ex   = q r0' + r0 q'                         multiples of 2^-G below 2^(24-G)
+//                                                  per span of K: exact
+//     sm   = q r1' + r1 q' + r0 r0' + r0 r1' + r1 r0'        small per span
 //     fn   = q r2s' + r2s q'                       (2^12 times their value)
 // The TMEM accumulator truncates toward zero on every MMA, so a sum that is not
 // exact picks up an error that grows with its magnitude and length. After each
-// span of two chunks (64 of K) the epilogue warps fold the integer parts of ex
-// and sm into main (exact: the bound above keeps main below 2^24) and leave
-// the fractional parts plus 2^-12 fn (all below 1) in sm as the start of the
-// next span, so sm never holds more than one span's worth; ex and fn restart
-// with every span. Dropped: products of two residual slices beyond r0 r1'
-// (< 2^-23 u u').
+// span the drain warps fold the integer parts of ex and sm into main (exact:
+// the bound above keeps main below 2^24) and leave the fractional parts plus
+// 2^-12 fn (all below 1) in sm as the start of the next span, so sm never
+// holds more than one span's worth; ex and fn restart with every span.
+// Dropped: products of two residual slices beyond r0 r1' (< 2^-2G u u').
+// Spans: map2alm 64 of K (G = 11: the truncation of the sm sums is its largest
+// error term); alm2map 128 of K (G = 10: half the drains; its error is set by
+// the FP32 ring spectra instead).
 //
 // Cluster sharing of lambda. The recurrence is a serial chain per ring pair,
 // so the CTAs of a thread-block cluster, which work on
@@ -47,11 +49,12 @@
 // chunk, so no thread of the contraction touches the data.
 //
 // CTA: 256 threads, one per SM (192 KB of pipeline stages, 512 TMEM columns).
-//   warp 0       TMEM allocation; lane 0 issues the MMAs
+//   warp 0       TMEM allocation; lane 0 issues the MMAs, the stage
+//                releases and the data copies, in one non-blocking event loop
 //   warps 1-3    lambda pieces (32 ring pairs x 32 rows / steps each; 8 KB
 //                of shared scratch per warp)
-//   warps 4-7    data copies (one lane), stage releases, the drains of the
-//                correction accumulators, then the epilogue with warps 0-3
+//   warps 4-7    the drains of the correction accumulators, then the
+//                epilogue with warps 0-3
 #include <algorithm>
 #include <cstdlib>
 
@@ -79,8 +82,12 @@ constexpr int STAGE_BYTES = NPL * (A_PLANE + B_PLANE);   // 64 KB
 constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
 constexpr uint32_t ACC_SM = 256;                 //   small corrections (+ the residual of earlier chunks)
 constexpr uint32_t ACC_FN = 384;                 //   products with r2s (2^12 times their value)
+// chunks per drained span and the grid exponent of the r0 slices, per direction
+template <bool M2A> __host__ __device__ constexpr int span_chunks() { return M2A ? 2 : 4; }
+template <bool M2A> __host__ __device__ constexpr int r0_grid() { return M2A ? 11 : 10; }
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
 constexpr int MAX_CLUSTER = 8;
+constexpr int TC_THREADS = 256;                  // 8 warps (roles below)
 
 struct TcArgs {
     const int4* work;          // (m, q, tile, first checkpoint block of (m, q))
@@ -130,14 +137,15 @@ __device__ __forceinline__ long long a_idx(int lmax, int l, int m)
 }
 
 // the four slice planes of 8 consecutive k, packed as FP16 pairs
+template <int G>
 __device__ __forceinline__ void pack4x8(const float (&v)[8], const float (&vl)[8], uint4 (&pk)[NPL])
 {
     uint32_t w[NPL][4];
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         float x0[NPL], x1[NPL];
-        slice4d(v[2 * i], vl[2 * i], x0[0], x0[1], x0[2], x0[3]);
-        slice4d(v[2 * i + 1], vl[2 * i + 1], x1[0], x1[1], x1[2], x1[3]);
+        slice4d<G>(v[2 * i], vl[2 * i], x0[0], x0[1], x0[2], x0[3]);
+        slice4d<G>(v[2 * i + 1], vl[2 * i + 1], x1[0], x1[1], x1[2], x1[3]);
 #pragma unroll
         for (int b = 0; b < NPL; b++) w[b][i] = pack_h2(x0[b], x1[b]);
     }
@@ -151,11 +159,12 @@ __device__ __forceinline__ void store4x8(uint8_t* planes, int plane_bytes, int r
 #pragma unroll
     for (int b = 0; b < NPL; b++) *reinterpret_cast<uint4*>(planes + b * plane_bytes + off) = pk[b];
 }
+template <int G>
 __device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row, int j, const float (&v)[8],
                                        const float (&vl)[8])
 {
     uint4 pk[NPL];
-    pack4x8(v, vl, pk);
+    pack4x8<G>(v, vl, pk);
     store4x8(planes, plane_bytes, row, j, pk);
 }
 
@@ -168,7 +177,7 @@ __device__ __forceinline__ void put_rows8(uint8_t* scr, int i0, int lane, const 
 #pragma unroll
     for (int ii = 0; ii < 8; ii++) {
         float x[NPL];
-        slice4d(hv[ii], lv[ii], x[0], x[1], x[2], x[3]);
+        slice4d<r0_grid<true>()>(hv[ii], lv[ii], x[0], x[1], x[2], x[3]);
         const uint32_t w01 = pack_h2(x[0], x[1]), w23 = pack_h2(x[2], x[3]);
         const uint32_t off = sw64_off(i0 + ii, lane);
         *reinterpret_cast<uint16_t*>(scr + off) = (uint16_t)(w01 & 0xFFFFu);
@@ -179,13 +188,13 @@ __device__ __forceinline__ void put_rows8(uint8_t* scr, int i0, int lane, const 
 }
 __device__ __forceinline__ void put_chunk8(uint8_t* scr, int row, int jj, const float (&hv)[8], const float (&lv)[8])
 {
-    put4x8(scr, PIECE_BYTES, row, jj, hv, lv);
+    put4x8<r0_grid<false>()>(scr, PIECE_BYTES, row, jj, hv, lv);
 }
 
 // one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
-// whole of K, sm over the whole of K on top of the residual the epilogue warps
-// leave in it (only the first stage restarts them); ex and fn restart at the
-// first stage of each two-chunk span.
+// whole of K, sm over the whole of K on top of the residual the drain leaves in
+// it (only the first stage restarts them); ex and fn restart at the first
+// stage of each span.
 __device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t st_addr, uint32_t idesc, bool first,
                                             bool span_start)
 {
@@ -231,8 +240,8 @@ struct TcShared {
     uint64_t full[NST];        // stage filled: 4 data warps + one arrival per lambda piece
     uint64_t empty[NST];       // stage consumed by the MMAs of every CTA of the cluster
     uint64_t accf;             // all MMAs of this CTA done
-    uint64_t cdone;            // the correction accumulators hold a finished chunk
-    uint64_t cfree;            // the correction accumulators drained (4 epilogue warps)
+    uint64_t cdone;            // the correction accumulators hold a finished span
+    uint64_t cfree;            // the span drained (4 drain warps)
     int released;              // highest chunk whose stage is free in every CTA of the cluster
     int eok;                   // the data warps' waits all succeeded (read by the epilogue)
     uint32_t tmem;
@@ -392,7 +401,7 @@ __device__ __forceinline__ int col_quantum(const TcArgs& a, int m, int q, long l
 // grid.x = work item (m, q, tile), grid.y = column tile; clusters along y
 // ===========================================================================
 template <bool M2A, bool S2>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 k_leg_tc(void* __restrict__ dst, TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -416,6 +425,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const int npieces = (nrows + PR - 1) / PR;
     const int nmma = (nrows + 15) & ~15;
     const uint32_t idesc = idesc_f16(TC_M, nmma);
+    constexpr int SPAN = span_chunks<M2A>();
     const long long qstride = (long long)a.R * a.ncol;
 
     for (int r = tid; r < TC_N; r += blockDim.x) {
@@ -474,22 +484,66 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const uint32_t smem_base = smem_u32(smem);
 
     if (warp == 0) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0 && nch > 0) {
+        // ---------------- MMA issue and stages (one lane) ----------------
+        // A non-blocking event loop over two ordered streams:
+        //  - stages: chunk c >= NST waits until every CTA of the cluster has
+        //    consumed the stage's previous use (chunk c - NST), then starts its
+        //    data copy and releases the stage to the lambda warps. The walk
+        //    continues NST chunks past the end (publishing those too: the lambda
+        //    warps' L2 slots wait on them), so that every MMA commit of the
+        //    cluster has arrived on this CTA's barriers before it exits;
+        //  - MMAs: chunk kc, once the stage is full and (first chunk of a span)
+        //    the previous span has been drained (the drain rewrites main and sm).
+        // Polls without progress are bounded.
+        if (lane == 0) {
             const uint16_t mask = (uint16_t)((1u << csize) - 1u);
-            for (int kc = 0; kc < nch; kc++) {
-                const int s = kc % NST;
-                const uint32_t u = kc / NST;
-                if (!mbar_wait_cl(&sh.full[s], u & 1, a.err, 1)) break;
-                // a span (chunks 2j, 2j + 1) starts once the previous span has
-                // been drained (the drain rewrites main and sm)
-                if (kc >= 2 && (kc & 1) == 0 && !mbar_wait_cl(&sh.cfree, ((kc >> 1) - 1) & 1, a.err, 5)) break;
-                tc_fence_after();
-                issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0, (kc & 1) == 0);
-                umma_commit_mc(&sh.empty[s], mask);
-                if ((kc & 1) || kc == nch - 1) umma_commit(&sh.cdone);
+            // chunk c's data: one 32 KB bulk copy of its pre-sliced image (spin-2
+            // alm2map: both chunks of a unit read the unit's image); the same
+            // arrival announces the lambda pieces that the cluster multicasts in.
+            // Column tiles that only pad the cluster read the last real tile.
+            const int ytile = min((int)blockIdx.y, a.ntile - 1);
+            const uint8_t* img0 = a.img + ((long long)a.img_base[m * 2 + q] * a.ntile + ytile) * A_BYTES;
+            auto copy = [&](int c) {
+                const int s = c % NST;
+                const long long ci = (S2 && !M2A) ? (c >> 1) : c;
+                mbar_arrive_expect_tx(&sh.full[s], A_BYTES + npieces * SCR_BYTES);
+                bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
+            };
+            for (int c = 0; c < min(nch, NST); c++) copy(c);
+            int c = NST;                                // next stage event
+            int kc = 0;                                 // next MMA chunk
+            bool full_ok = false;
+            int idle = 0;
+            while (kc < nch || c < nch + NST) {
+                bool did = false;
+                if (c < nch + NST && mbar_test_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1)) {
+                    if (c < nch) copy(c);
+                    publish_counter(&sh.released, c);
+                    c++;
+                    did = true;
+                }
+                if (kc < nch) {
+                    const int s = kc % NST;
+                    if (!full_ok) full_ok = mbar_test_wait_cl(&sh.full[s], (kc / NST) & 1);
+                    const int kq = kc % SPAN;
+                    if (full_ok && (kc < SPAN || kq != 0 || mbar_test_wait_cl(&sh.cfree, (kc / SPAN - 1) & 1))) {
+                        tc_fence_after();
+                        issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0, kq == 0);
+                        umma_commit_mc(&sh.empty[s], mask);
+                        if (kq == SPAN - 1 || kc == nch - 1) umma_commit(&sh.cdone);
+                        kc++;
+                        full_ok = false;
+                        if (kc == nch) umma_commit(&sh.accf);
+                        did = true;
+                    }
+                }
+                if (did) {
+                    idle = 0;
+                } else if (++idle > (1 << 24)) {
+                    atomicCAS(a.err, 0, 1);
+                    break;
+                }
             }
-            umma_commit(&sh.accf);
         }
     } else if (warp < 4) {
         // ---------------- lambda pieces ----------------
@@ -732,75 +786,65 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             __syncwarp();                               // scratch reads done before the next piece
         }
     } else {
-        // ---------------- data copies, stage releases, span drains ----------------
+        // ---------------- span drains (warps 4-7) ----------------
         const int quarter = warp & 3;                 // TMEM lanes 32 quarter .. + 31
         const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
         bool dok = true;
-        // chunk c's data: one 32 KB bulk copy of its pre-sliced image (spin-2
-        // alm2map: both chunks of a unit read the unit's image). Column tiles
-        // that only pad the cluster read the last real tile and write nothing.
-        const int ytile = min((int)blockIdx.y, a.ntile - 1);
-        const uint8_t* img0 = a.img + ((long long)a.img_base[m * 2 + q] * a.ntile + ytile) * A_BYTES;
-        auto copy = [&](int c) {
-            if (warp == 4 && lane == 0) {
-                const int s = c % NST;
-                const long long ci = (S2 && !M2A) ? (c >> 1) : c;
-                mbar_arrive_expect_tx(&sh.full[s], A_BYTES + npieces * SCR_BYTES);
-                bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
-            }
+        // Fold span j's corrections (chunks SPAN j .. SPAN j + SPAN - 1) into
+        // main and sm and hand the accumulators back to the MMA: main +=
+        // nearest integers of ex and sm (exact), sm = their fractional parts +
+        // 2^-12 fn (below 1). Groups of 16 columns, the next
+        // group's TMEM loads in flight while the current one is folded; packed
+        // FP32 pairs. (A rolled loop: a short body stays in the instruction cache.)
+        const unsigned long long MAG2 = f2_pack(0x4B400000u, 0x4B400000u);   // 1.5 * 2^23: nearest integer
+        const unsigned long long SC2 = f2_pack(0x39800000u, 0x39800000u);    // 2^-12
+        auto drain_load = [&](int g, uint32_t (&v)[4][16]) {
+            tmem_ld16(tl + g, v[0]);
+            tmem_ld16(tl + ACC_EX + g, v[1]);
+            tmem_ld16(tl + ACC_SM + g, v[2]);
+            tmem_ld16(tl + ACC_FN + g, v[3]);
         };
-        // Fold span c's corrections (chunks 2c, 2c + 1) into main and sm and
-        // hand the accumulators back to the MMA: main += nearest integers of ex
-        // and sm (exact), sm = their fractional parts + 2^-12 fn (below 1). (A
-        // rolled loop: a short body stays in the instruction cache.)
-        auto drain = [&](int c) {
-            dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, c & 1, a.err, 6));
-            tc_fence_after();
-#pragma unroll 1
-            for (int g = 0; g < nmma; g += 16) {
-                uint32_t vm[16], ve[16], vs[16], vf[16];
-                tmem_ld16(tl + g, vm);
-                tmem_ld16(tl + ACC_EX + g, ve);
-                tmem_ld16(tl + ACC_SM + g, vs);
-                tmem_ld16(tl + ACC_FN + g, vf);
-                tmem_wait_ld();
+        auto drain_fold = [&](int g, uint32_t (&v)[4][16]) {
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    const float e = __uint_as_float(ve[i]), v = __uint_as_float(vs[i]);
-                    const float eh = rint_magic(e), vh = rint_magic(v);
-                    vm[i] = __float_as_uint(__fadd_rn(__fadd_rn(__uint_as_float(vm[i]), eh), vh));
-                    vs[i] = __float_as_uint(((e - eh) + (v - vh)) + __uint_as_float(vf[i]) * (1.0f / 4096.0f));
+            for (int i = 0; i < 16; i += 2) {
+                const unsigned long long M = f2_pack(v[0][i], v[0][i + 1]), E = f2_pack(v[1][i], v[1][i + 1]);
+                const unsigned long long V = f2_pack(v[2][i], v[2][i + 1]), F = f2_pack(v[3][i], v[3][i + 1]);
+                const unsigned long long EH = f2_sub(f2_add(E, MAG2), MAG2);
+                const unsigned long long VH = f2_sub(f2_add(V, MAG2), MAG2);
+                f2_unpack(f2_add(f2_add(M, EH), VH), v[0][i], v[0][i + 1]);
+                f2_unpack(f2_fma(F, SC2, f2_add(f2_sub(E, EH), f2_sub(V, VH))), v[2][i], v[2][i + 1]);
+            }
+            tmem_st16(tl + g, v[0]);
+            tmem_st16(tl + ACC_SM + g, v[2]);
+        };
+        auto drain = [&](int j) {
+            dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, j & 1, a.err, 6));
+            if (!dok) return;
+            tc_fence_after();
+            const int gb = 0, ge = nmma;
+            uint32_t va[4][16], vb[4][16];
+            drain_load(gb, va);
+            tmem_wait_ld();
+#pragma unroll 1
+            for (int g = gb; g < ge; g += 32) {
+                if (g + 16 < ge) drain_load(g + 16, vb);
+                drain_fold(g, va);
+                tmem_wait_ld();
+                if (g + 16 < ge) {
+                    if (g + 32 < ge) drain_load(g + 32, va);
+                    drain_fold(g + 16, vb);
+                    tmem_wait_ld();
                 }
-                tmem_st16(tl + g, vm);
-                tmem_st16(tl + ACC_SM + g, vs);
             }
             tmem_wait_st();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh.cfree);
         };
-        // The first NST chunks have free stages. Chunk c >= NST waits until
-        // every CTA of the cluster has consumed the stage's previous use
-        // (chunk c - NST), then starts its data copy and releases the stage to
-        // the lambda warps. Span j is drained after chunk 2j + 4 is released:
-        // that wait implies span j's MMAs are done, and the MMAs of chunk
-        // 2j + 2 (which chunk 2j + 5 waits for) wait for the drain. The walk
-        // continues NST chunks past the end, so that every MMA commit of the
-        // cluster has arrived on this CTA's barriers before it exits. (A wait
-        // that gives up turns dok off; the walk still runs to the end.)
-        const int nspan = (nch + 1) >> 1;
-        int nd = 0;                                   // spans drained
-        for (int c = 0; c < min(nch, NST); c++) copy(c);
-        for (int c = NST; c < nch + NST; c++) {
-            if (dok) {
-                dok = __all_sync(0xffffffffu, mbar_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1, a.err, 3));
-                if (dok && c < nch) copy(c);
-                // (published past nch too: the lambda warps' L2 slots wait on it)
-                if (dok && warp == 4 && lane == 0) publish_counter(&sh.released, c);
-            }
-            if ((c & 1) == 0 && c >= 4 && nd < nspan && dok) drain(nd++);
-        }
-        while (nd < nspan && dok) drain(nd++);
+        // (the MMAs of the next span wait for each drain; a wait that gives up
+        // turns dok off and ends the drains)
+        const int nspan = (nch + SPAN - 1) / SPAN;
+        for (int j = 0; j < nspan && dok; j++) drain(j);
 
         // the last MMAs are complete once every wait above succeeded
         const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
@@ -808,7 +852,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         tmem_wait_st();
     }
 
-    // ---------------- epilogue: out = (main + sm) * scales, all eight warps ----------------
+    // ---------------- epilogue: out = (main + sm) * scales, warps 0-7 ----------------
     // (warps w and w + 4 reach the same TMEM lanes, i.e. the same map column;
     // warps 4-7 take rows 0-63, warps 0-3 rows 64-127)
     __syncwarp();
@@ -962,7 +1006,7 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
                 hv[i] = x.x * csc;
                 lv[i] = x.y * csc;
             }
-            put4x8(A, A_PLANE, t, jj, hv, lv);
+            put4x8<r0_grid<M2A>()>(A, A_PLANE, t, jj, hv, lv);
         }
     }
 }
@@ -1223,7 +1267,7 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
         const long long gy = (ntiles + C - 1) / C * C;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)nwork, (unsigned)gy, 1);
-        cfg.blockDim = dim3(256, 1, 1);
+        cfg.blockDim = dim3(TC_THREADS, 1, 1);
         cfg.dynamicSmemBytes = SMEM_TC;
         cfg.stream = st;
         cudaLaunchAttribute at[1];

@@ -62,6 +62,15 @@ __device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity, int* 
     return false;
 }
 
+// one non-blocking test of a barrier phase (cluster-scope acquire)
+__device__ __forceinline__ bool mbar_test_wait_cl(uint64_t* b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
 // Bounded wait until a monotonic shared-memory counter reaches `target`
 // (acquire); records `code` in *err and returns false after ~2^22 polls.
 __device__ __forceinline__ bool wait_counter(const int* ctr, int target, int* err, int code)
@@ -373,22 +382,56 @@ __device__ __forceinline__ float ldexpf_fast(float x, int k)
 }
 
 // Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into four
-// FP16 pieces:
+// FP16 pieces, with r0 on the grid 2^-G (G = 10 or 11):
 //     q   = nearest integer                           (exact in FP16 for Q <= 2048)
-//     r0  = v - q rounded to the grid 2^-11           (|r0| <= 1/2: exact in FP16)
-//     r1  = rem = (v - q - r0) + vl rounded to FP16   (|rem| < 2^-11)
+//     r0  = v - q rounded to the grid 2^-G            (|r0| <= 1/2: exact in FP16)
+//     r1  = rem = (v - q - r0) + vl rounded to FP16   (|rem| <= 2^-G-1)
 //     r2s = (rem - r1) 2^12 rounded to FP16           (the next 11 bits, scaled up)
-// v - q and v - q - r0 are exact, so v + vl = q + r0 + r1 + 2^-12 r2s to ~2^-35
-// of the quantum. The fixed grid of r0 makes every product q r0' a multiple of
-// 2^-11, so sums of them are exact in FP32 while they stay below 2^13.
+// v - q and v - q - r0 are exact, so v + vl = q + r0 + r1 + 2^-12 r2s to
+// ~2^-(G+24) of the quantum. The fixed grid of r0 makes every product q r0' a
+// multiple of 2^-G, so sums of them are exact in FP32 while they stay below
+// 2^(24-G).
+template <int G>
 __device__ __forceinline__ void slice4d(float v, float vl, float& q, float& r0, float& r1, float& r2s)
 {
+    static_assert(G == 10 || G == 11, "r0 grid");
+    constexpr float magic = (G == 10) ? 12288.0f : 6144.0f;  // 1.5 * 2^(23-G): ulp 2^-G
     q = __fadd_rn(__fadd_rn(v, 12582912.0f), -12582912.0f);   // 1.5 * 2^23: nearest integer
     const float r = __fadd_rn(v, -q);
-    r0 = __fadd_rn(__fadd_rn(r, 6144.0f), -6144.0f);          // 1.5 * 2^12: ulp 2^-11
+    r0 = __fadd_rn(__fadd_rn(r, magic), -magic);
     const float rem = __fadd_rn(__fadd_rn(r, -r0), vl);
     r1 = __half2float(__float2half_rn(rem));
     r2s = __fmul_rn(__fadd_rn(rem, -r1), 4096.0f);
+}
+// packed FP32 pairs (two lanes per instruction, each rounded to nearest)
+__device__ __forceinline__ unsigned long long f2_pack(uint32_t lo, uint32_t hi)
+{
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, uint32_t& lo, uint32_t& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
 }
 // nearest integer of |x| < 2^22 (exact)
 __device__ __forceinline__ float rint_magic(float x)
