@@ -33,7 +33,7 @@ SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split
 # DRAM traffic (read + write) of one launch from an ncu capture of the same
 # kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
 # and lmax it grows in proportion to the map columns (profiles/k_leg_tc_nside512.md)
-TRAFFIC_NCU = {"k_leg_a2m_tc": 3.545e9, "k_leg_m2a_tc": 5.783e9}
+TRAFFIC_NCU = {"k_leg_a2m_tc": 3.625e9, "k_leg_m2a_tc": 6.087e9}
 TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
 
@@ -521,7 +521,9 @@ def main():
 
     # ---- roofline of the dominant kernel ----
     peaks, peak_src = measured_peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    # the contraction is the roofline kernel (the largest Legendre kernel of the step)
+    legs = {k: v for k, v in prof.items() if "leg" in k} if prof else {}
+    dom = max((legs or prof).items(), key=lambda kv: kv[1]["ms"]) if prof else None
     roofline = None
     if dom:
         name, rec = dom
@@ -554,6 +556,20 @@ def main():
             roofline = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
                         "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
                         "peak_source": peak_src, "avg_launch_ms": avg_ms}
+
+    # ---- ring FFTs against HBM: algorithmic bytes of both directions per step
+    # (maps read and written in FP64; T written as FP32 hi/lo pairs, G read in FP32)
+    # over the summed device time of the FFT kernels ----
+    fft_roofline = None
+    fft_ms = sum(v["ms"] for k, v in prof.items() if "fft" in k) / max(a.steps, 1) if prof else 0.0
+    if fft_ms > 0:
+        nring = 4 * nside - 1
+        fft_bytes_map = 16.0 * plan.npix * plan.ncomp + (plan.mmax + 1) * nring * plan.ncomp * (16.0 + 8.0)
+        ach = fft_bytes_map * nmaps / (fft_ms / 1e3) / 1e9
+        fft_roofline = {"kernels": "ring FFTs (all size classes, both directions)", "bound": "hbm",
+                        "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
+                        "ms_per_step": fft_ms, "algorithmic_bytes_per_step": fft_bytes_map * nmaps,
+                        "note": "compensated FP32 (double-float) arithmetic: issue-bound, not HBM-bound"}
 
     # ---- end to end through the host-buffer C-ABI entry points ----
     e2e = None
@@ -618,6 +634,7 @@ def main():
                            l2="inputs larger than L2 (maps 25.2 GB per GPU), no flush",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
             "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
+            "roofline_fft": fft_roofline,
             "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
             "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
             "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "serving": serving,

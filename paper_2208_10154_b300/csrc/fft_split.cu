@@ -23,7 +23,7 @@
 
 namespace sht {
 
-struct cx { float hr, hi, lr, li; };     // (hr + lr) + i (hi + li)
+struct __align__(16) cx { float hr, hi, lr, li; };   // (hr + lr) + i (hi + li); 16-byte aligned: one 128-bit access
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
@@ -87,16 +87,28 @@ struct FftTabsF {
     const long long* phoff;       // offset of each ring length's phase table
 };
 
-__device__ __forceinline__ void twid(const FftTabsF& t, int idx, bool inv, float2& wh, float2& wl)
+// twiddles of one FFT size M, staged in shared memory: tw[u] = exp(-2 pi i u / M),
+// u < M / 2, as (hi re, hi im, lo re, lo im)
+__device__ __forceinline__ void twid(const float4* tw, int idx, bool inv, float2& wh, float2& wl)
 {
-    wh = t.twh[idx]; wl = t.twl[idx];
-    if (inv) { wh.y = -wh.y; wl.y = -wl.y; }
+    const float4 v = tw[idx];
+    wh = make_float2(v.x, inv ? -v.y : v.y);
+    wl = make_float2(v.z, inv ? -v.w : v.w);
+}
+// copy the size-M twiddles out of the global table (exp(-2 pi i t / fftmax), t < fftmax / 2)
+__device__ __forceinline__ void stage_twiddles(float4* tw, int M, int fftmax, const FftTabsF& t)
+{
+    const int st = fftmax / M;
+    for (int u = threadIdx.x; u < M / 2; u += blockDim.x) {
+        const float2 h = t.twh[u * st], l = t.twl[u * st];
+        tw[u] = make_float4(h.x, h.y, l.x, l.y);
+    }
 }
 
 // In-place decimation-in-time FFTs of nb sequences of M = 2^L points stored
 // back to back in buf, input in bit-reversed order, output natural. Two
 // radix-2 stages (spans h and 2h) per pass; W = exp(-+2 pi i / M).
-__device__ void fft_dit(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, bool inv)
+__device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
 {
     const int M = 1 << L;
     int lh = 0;
@@ -112,7 +124,7 @@ __device__ void fft_dit(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, b
     }
     for (; lh + 2 <= L; lh += 2) {
         const int h = 1 << lh;
-        const int s1 = fftmax >> (lh + 1), s2 = fftmax >> (lh + 2);
+        const int s1 = M >> (lh + 1), s2 = M >> (lh + 2);
         const int ng = M >> 2;                       // groups per sequence
         for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
             const int f = b >> (L - 2), g = b & (ng - 1);
@@ -121,8 +133,8 @@ __device__ void fft_dit(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, b
             cx x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
             if (k != 0) {
                 float2 w1h, w1l, w2h, w2l;
-                twid(t, k * s1, inv, w1h, w1l);
-                twid(t, k * s2, inv, w2h, w2l);
+                twid(tw, k * s1, inv, w1h, w1l);
+                twid(tw, k * s2, inv, w2h, w2l);
                 x1 = cmulc(x1, w1h, w1l);
                 x3 = cmulc(x3, w1h, w1l);
                 const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
@@ -143,13 +155,13 @@ __device__ void fft_dit(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, b
 
 // In-place decimation-in-frequency FFTs (natural input, bit-reversed output),
 // two radix-2 stages (spans h and h/2) per pass.
-__device__ void fft_dif(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, bool inv)
+__device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
 {
     const int M = 1 << L;
     int lh = L - 1;
     for (; lh >= 1; lh -= 2) {
         const int h = 1 << lh, hq = h >> 1;
-        const int s1 = fftmax >> (lh + 1), s2 = fftmax >> lh;
+        const int s1 = M >> (lh + 1), s2 = M >> lh;
         const int ng = M >> 2;
         for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
             const int f = b >> (L - 2), g = b & (ng - 1);
@@ -160,8 +172,8 @@ __device__ void fft_dif(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, b
             c3 = inv ? cmul_pi(c3) : cmul_mi(c3);
             if (k != 0) {
                 float2 v1h, v1l, v2h, v2l;
-                twid(t, k * s1, inv, v1h, v1l);
-                twid(t, k * s2, inv, v2h, v2l);
+                twid(tw, k * s1, inv, v1h, v1l);
+                twid(tw, k * s2, inv, v2h, v2l);
                 c2 = cmulc(c2, v1h, v1l);
                 c3 = cmulc(c3, v1h, v1l);
                 y[0] = caddc(c0, c1); y[hq] = cmulc(csubc(c0, c1), v2h, v2l);
@@ -185,20 +197,20 @@ __device__ void fft_dif(cx* buf, int nb, int L, int fftmax, const FftTabsF& t, b
 }
 
 // forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of nb sequences placed by placec()
-__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, int fftmax, const FftTabsF& t)
+__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const FftTabsF& t)
 {
     const int M = f.m, L = 31 - __clz(M);
     if (!f.bluestein) {
-        fft_dit(buf, nb, L, fftmax, t, false);
+        fft_dit(buf, nb, L, tw, false);
         return;
     }
-    fft_dif(buf, nb, L, fftmax, t, false);
+    fft_dif(buf, nb, L, tw, false);
     for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
         const int ii = i & (M - 1);
         buf[i] = cmulc(buf[i], t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
     }
     __syncthreads();
-    fft_dit(buf, nb, L, fftmax, t, true);
+    fft_dit(buf, nb, L, tw, true);
     const float inv = 1.0f / (float)M;
     for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
         const int s = i / f.n, k = i - s * f.n;
@@ -228,8 +240,9 @@ __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m,
 // ---------------------------------------------------------------------------
 // forward: maps -> T[m][q][p][c] (FP32 hi/lo pairs) and the per (m, slot,
 // column) maxima used for the tensor-core column quanta. One launch per FFT
-// size class; grid.x = block of FWD_PB ring pairs of the class, grid.y = pair
-// of map columns (map * ncomp + comp).
+// size class; grid.x = pair of map columns (map * ncomp + comp), grid.y = block
+// of FWD_PB ring pairs of the class (neighbouring column pairs, which share
+// the cache lines of T, run together).
 // ---------------------------------------------------------------------------
 constexpr int FWD_PB = 64;
 
@@ -243,7 +256,9 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    const int mc0 = blockIdx.y * mpc;
+    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * M * sizeof(cx));
+    stage_twiddles(tw, M, fftmax, tb);              // (the first __syncthreads below publishes it)
+    const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
     constexpr int FWD_MJ = 4;
@@ -252,8 +267,8 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
     for (int j = 0; j < FWD_MJ; j++)
 #pragma unroll
         for (int s = 0; s < 2; s++) mx[j][s][0] = mx[j][s][1] = mx[j][s][2] = mx[j][s][3] = 0.0f;
-    const int iend = min(ncls, (int)(blockIdx.x + 1) * FWD_PB);
-    for (int ip = blockIdx.x * FWD_PB; ip < iend; ip++) {
+    const int iend = min(ncls, (int)(blockIdx.y + 1) * FWD_PB);
+    for (int ip = blockIdx.y * FWD_PB; ip < iend; ip++) {
         const int p = cls[ip];
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
@@ -272,7 +287,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                 buf[s * M + N + i] = czero();
             }
         __syncthreads();
-        dftc_forward(buf, nb, f, fftmax, tb);
+        dftc_forward(buf, nb, f, tw, tb);
 #pragma unroll
         for (int jj = 0; jj < FWD_MJ; jj++) {
             const int m = threadIdx.x + jj * NT;
@@ -331,94 +346,102 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 // ---------------------------------------------------------------------------
 // backward: G[m][q][p][c] (FP32) -> maps. Every m is folded onto bin m mod N
 // with weight w_0 = 1, w_{m>0} = 2 and phase e^{+i m phi0}; the real ring is
-// the IDFT of the Hermitian part. One launch per FFT size class; grid.x = ring
-// pair of the class, grid.y = pair of map columns.
+// the IDFT of the Hermitian part. One launch per FFT size class; grid.x = pair
+// of map columns, grid.y = block of BWD_PB ring pairs of the class.
 // ---------------------------------------------------------------------------
+constexpr int BWD_PB = 16;
+
 template <int NT>
 __global__ void __launch_bounds__(NT)
-k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls,
+k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls, int ncls,
                 const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax,
                 int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    const int p = cls[blockIdx.x];
-    const int mc0 = blockIdx.y * mpc;
+    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * M * sizeof(cx));
+    stage_twiddles(tw, M, fftmax, tb);              // (published by the __syncthreads before the FFT)
+    const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
-    const PairGeom g = pairs[p];
-    const FftLen f = ffts[g.fft];
-    const int N = g.n;
     const long long qstride = (long long)R_ * ncol;
-    const float* g0 = G + (long long)p * ncol + mc0 * 2;
-    for (int j = threadIdx.x; j <= N / 2; j += NT) {
-        const int jj[2] = {j, (N - j) % N};
-        cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][map]
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-            cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
-            for (int m = jj[t]; m <= mmax; m += N) {
-                const float* e = g0 + (long long)m * 2 * qstride;
-                float4 E4, O4;
-                if (nb == 2 && (ncol & 3) == 0) {          // 16-byte aligned: ncol a multiple of 4
-                    E4 = *reinterpret_cast<const float4*>(e);
-                    O4 = *reinterpret_cast<const float4*>(e + qstride);
-                } else if (nb == 2) {
-                    const float2 a0 = *reinterpret_cast<const float2*>(e), a1 = *reinterpret_cast<const float2*>(e + 2);
-                    const float2 b0 = *reinterpret_cast<const float2*>(e + qstride);
-                    const float2 b1 = *reinterpret_cast<const float2*>(e + qstride + 2);
-                    E4 = make_float4(a0.x, a0.y, a1.x, a1.y);
-                    O4 = make_float4(b0.x, b0.y, b1.x, b1.y);
-                } else {
-                    const float2 E2 = *reinterpret_cast<const float2*>(e), O2 = *reinterpret_cast<const float2*>(e + qstride);
-                    E4 = make_float4(E2.x, E2.y, 0.0f, 0.0f);
-                    O4 = make_float4(O2.x, O2.y, 0.0f, 0.0f);
+    const int iend = min(ncls, (int)(blockIdx.y + 1) * BWD_PB);
+    for (int ip = blockIdx.y * BWD_PB; ip < iend; ip++) {
+        const int p = cls[ip];
+        const PairGeom g = pairs[p];
+        const FftLen f = ffts[g.fft];
+        const int N = g.n;
+        const float* g0 = G + (long long)p * ncol + mc0 * 2;
+        for (int j = threadIdx.x; j <= N / 2; j += NT) {
+            const int jj[2] = {j, (N - j) % N};
+            cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][map]
+    #pragma unroll
+            for (int t = 0; t < 2; t++) {
+                cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
+                for (int m = jj[t]; m <= mmax; m += N) {
+                    const float* e = g0 + (long long)m * 2 * qstride;
+                    float4 E4, O4;
+                    if (nb == 2 && (ncol & 3) == 0) {          // 16-byte aligned: ncol a multiple of 4
+                        E4 = *reinterpret_cast<const float4*>(e);
+                        O4 = *reinterpret_cast<const float4*>(e + qstride);
+                    } else if (nb == 2) {
+                        const float2 a0 = *reinterpret_cast<const float2*>(e), a1 = *reinterpret_cast<const float2*>(e + 2);
+                        const float2 b0 = *reinterpret_cast<const float2*>(e + qstride);
+                        const float2 b1 = *reinterpret_cast<const float2*>(e + qstride + 2);
+                        E4 = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        O4 = make_float4(b0.x, b0.y, b1.x, b1.y);
+                    } else {
+                        const float2 E2 = *reinterpret_cast<const float2*>(e), O2 = *reinterpret_cast<const float2*>(e + qstride);
+                        E4 = make_float4(E2.x, E2.y, 0.0f, 0.0f);
+                        O4 = make_float4(O2.x, O2.y, 0.0f, 0.0f);
+                    }
+                    const float w = m ? 2.0f : 1.0f;
+                    float2 ph, pl;
+                    if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, ph, pl);
+    #pragma unroll
+                    for (int s = 0; s < 2; s++) {
+                        const float er = s ? E4.z : E4.x, ei = s ? E4.w : E4.y;
+                        const float orr = s ? O4.z : O4.x, oi = s ? O4.w : O4.y;
+                        cx tn, ts;
+                        two_sum(er, orr, tn.hr, tn.lr); two_sum(ei, oi, tn.hi, tn.li);
+                        two_sum(er, -orr, ts.hr, ts.lr); two_sum(ei, -oi, ts.hi, ts.li);
+                        tn = cscale(tn, w); ts = cscale(ts, w);
+                        if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
+                        sn[s] = caddc(sn[s], tn);
+                        ss[s] = caddc(ss[s], ts);
+                    }
                 }
-                const float w = m ? 2.0f : 1.0f;
-                float2 ph, pl;
-                if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, ph, pl);
-#pragma unroll
+                Bn[t][0] = sn[0]; Bn[t][1] = sn[1]; Bs[t][0] = ss[0]; Bs[t][1] = ss[1];
+            }
+    #pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int jt = jj[t];
+                if (t == 1 && jt == jj[0]) break;
+    #pragma unroll
                 for (int s = 0; s < 2; s++) {
-                    const float er = s ? E4.z : E4.x, ei = s ? E4.w : E4.y;
-                    const float orr = s ? O4.z : O4.x, oi = s ? O4.w : O4.y;
-                    cx tn, ts;
-                    two_sum(er, orr, tn.hr, tn.lr); two_sum(ei, oi, tn.hi, tn.li);
-                    two_sum(er, -orr, ts.hr, ts.lr); two_sum(ei, -oi, ts.hi, ts.li);
-                    tn = cscale(tn, w); ts = cscale(ts, w);
-                    if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
-                    sn[s] = caddc(sn[s], tn);
-                    ss[s] = caddc(ss[s], ts);
+                    if (s >= nb) break;
+                    // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
+                    const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
+                    const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
+                    const cx z = cconjc(caddc(hn, cmul_pi(hs)));
+                    buf[s * M + placec(f, jt)] = chirp_in(f, tb, z, jt);
                 }
             }
-            Bn[t][0] = sn[0]; Bn[t][1] = sn[1]; Bs[t][0] = ss[0]; Bs[t][1] = ss[1];
         }
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-            const int jt = jj[t];
-            if (t == 1 && jt == jj[0]) break;
-#pragma unroll
-            for (int s = 0; s < 2; s++) {
-                if (s >= nb) break;
-                // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
-                const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
-                const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
-                const cx z = cconjc(caddc(hn, cmul_pi(hs)));
-                buf[s * M + placec(f, jt)] = chirp_in(f, tb, z, jt);
+        if (f.bluestein)
+            for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
+                const int s = e / (M - N), i = e - s * (M - N);
+                buf[s * M + N + i] = czero();
             }
+        __syncthreads();
+        dftc_forward(buf, nb, f, tw, tb);
+        for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
+            const int s = e / N, n = e - s * N;
+            const cx z = buf[s * M + n];               // conj of the inverse transform
+            double* mp = map + (long long)(mc0 + s) * npix;
+            mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
+            if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi) + tc::f32_to_f64(z.li));
         }
-    }
-    if (f.bluestein)
-        for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
-            const int s = e / (M - N), i = e - s * (M - N);
-            buf[s * M + N + i] = czero();
-        }
-    __syncthreads();
-    dftc_forward(buf, nb, f, fftmax, tb);
-    for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
-        const int s = e / N, n = e - s * N;
-        const cx z = buf[s * M + n];               // conj of the inverse transform
-        double* mp = map + (long long)(mc0 + s) * npix;
-        mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
-        if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi) + tc::f32_to_f64(z.li));
+        __syncthreads();                               // buf is rewritten by the next ring pair
     }
 }
 
@@ -434,12 +457,13 @@ static FftTabsF tabs(const sht_plan* p)
 }
 
 // FFT size classes of the plan: launch configuration per class (two map
-// columns per CTA while their buffers fit in 128 KB of shared memory)
+// columns per CTA while their buffers fit in 128 KB of shared memory), plus
+// the class's twiddles (M / 2 x 16 bytes)
 static void class_cfg(int M, int mmax, int& nt, int& mpc, size_t& sm)
 {
     nt = (M >= 4096 || mmax >= 1024) ? 512 : 256;
     mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
-    sm = (size_t)mpc * M * sizeof(cx);
+    sm = (size_t)mpc * M * sizeof(cx) + (size_t)(M / 2) * sizeof(float4);
 }
 
 static cudaError_t set_smem(const void* fn, const sht_plan* p)
@@ -466,7 +490,7 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
     for (const FftClass& c : p->h_fcls) {
         int nt, mpc; size_t sm;
         class_cfg(c.m, p->mmax, nt, mpc, sm);
-        dim3 grid((c.cnt + FWD_PB - 1) / FWD_PB, (nmc + mpc - 1) / mpc);
+        dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + FWD_PB - 1) / FWD_PB);
         prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
             k_fftc_forward<512><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
@@ -491,16 +515,16 @@ cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* m
     for (const FftClass& c : p->h_fcls) {
         int nt, mpc; size_t sm;
         class_cfg(c.m, p->mmax, nt, mpc, sm);
-        dim3 grid(c.cnt, (nmc + mpc - 1) / mpc);
+        dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
         prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
-            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, p->t.pairs, p->t.fft, tabs(p),
-                                                       p->fft_max, c.m, p->R, p->mmax, p->npix, ncols(p, nmaps),
-                                                       nmc, mpc);
+            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->t.fft,
+                                                       tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix,
+                                                       ncols(p, nmaps), nmc, mpc);
         else
-            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, p->t.pairs, p->t.fft, tabs(p),
-                                                       p->fft_max, c.m, p->R, p->mmax, p->npix, ncols(p, nmaps),
-                                                       nmc, mpc);
+            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->t.fft,
+                                                       tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix,
+                                                       ncols(p, nmaps), nmc, mpc);
         prof_stop(st);
         count_launch();
     }
