@@ -205,6 +205,7 @@ cudaError_t launch_colmax_T(const sht_plan* p, const float2* T, unsigned int* co
 size_t split_a2_offset(const sht_plan* p, int nmaps);
 cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base);
 int split_row_tile();
+int split_a2m_tiles();
 int split_ck_rows();
 int split_col_tile();
 

@@ -242,6 +242,7 @@ struct TcShared {
     uint64_t accf;             // all MMAs of this CTA done
     uint64_t cdone;            // the correction accumulators hold a finished span
     uint64_t cfree;            // the span drained (4 drain warps)
+    uint64_t tfree;            // alm2map: a tile's epilogue has read the accumulators (4 drain warps)
     int released;              // highest chunk whose stage is free in every CTA of the cluster
     int eok;                   // the data warps' waits all succeeded (read by the epilogue)
     uint32_t tmem;
@@ -408,24 +409,32 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     TcShared& sh = *reinterpret_cast<TcShared*>(smem + NST * STAGE_BYTES + 3 * SCR_BYTES);
     const int4 w = a.work[blockIdx.x];
-    const int m = w.x, q = w.y, tile = w.z, ckb = w.w;
+    // work item: (m, q, first tile | tiles << 16, first checkpoint block of (m, q));
+    // an alm2map CTA walks several ring-pair tiles of (m, q) in one pipeline
+    const int m = w.x, q = w.y, tile0 = w.z & 0xFFFF, ckb = w.w;
+    const int ntl = M2A ? 1 : max(1, w.z >> 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t crank = cluster_ctarank(), csize = cluster_nctarank();
     const long long c0 = (long long)blockIdx.y * TC_M;
     const int l_first = m + q;
     const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;   // l rows of slot q
-    const int n0 = tile * TC_N;                                         // first lambda row of the tile
-    const int nrows = M2A ? min(TC_N, nl - n0) : min(TC_N, a.R - n0);
+    const int nrow_all = M2A ? nl : a.R;           // lambda rows of (m, q)
+    // tile t of the CTA: first lambda row, rows, 32-row pieces, MMA N
+    auto t_n0 = [&](int t) { return (tile0 + t) * TC_N; };
+    auto t_nrows = [&](int t) { return min(TC_N, nrow_all - t_n0(t)); };
+    auto t_npieces = [&](int t) { return (t_nrows(t) + PR - 1) / PR; };
+    auto t_nmma = [&](int t) { return (t_nrows(t) + 15) & ~15; };
+    const int n0 = t_n0(0), nrows = t_nrows(0);    // map2alm: its only tile
     // contraction length: spin 0 over ring pairs (map2alm) or the l of slot q;
     // spin 2 over ring pairs or all l >= m, each twice (v+ and v- chunks)
     const int K = M2A ? a.R : (S2 ? a.lmax - m + 1 : nl);
     const int nunit = (K + KC - 1) / KC;           // 32-wide units of raw data
-    const int nch = S2 ? 2 * nunit : nunit;        // MMA chunks (pipeline stages)
+    const int nch = S2 ? 2 * nunit : nunit;        // MMA chunks (pipeline stages) per tile
+    const int nchunk = ntl * nch;                  // chunks of the CTA: chunk g = tile g / nch, kc = g % nch
     const int l0s = m > 2 ? m : 2;                 // first l of the spin-2 functions
-    const int npieces = (nrows + PR - 1) / PR;
-    const int nmma = (nrows + 15) & ~15;
-    const uint32_t idesc = idesc_f16(TC_M, nmma);
+    const int nmma = t_nmma(0);
     constexpr int SPAN = span_chunks<M2A>();
+    const int nspan = (nch + SPAN - 1) / SPAN;     // drained spans per tile
     const long long qstride = (long long)a.R * a.ncol;
 
     for (int r = tid; r < TC_N; r += blockDim.x) {
@@ -459,8 +468,6 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 sh.cA2[r] = df{0.0f, 0.0f}; sh.cB2[r] = df{0.0f, 0.0f};
                 sh.rowexp[r] = 0; sh.rfac[r] = make_float2(0.0f, 0.0f);
             }
-        } else {
-            sh.rowexp[r] = (r < nrows) ? quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + n0 + r], a.Q) : 0;
         }
     }
     for (int c = tid; c < TC_M; c += blockDim.x) sh.colexp[c] = col_quantum<M2A, S2>(a, m, q, c0, c);
@@ -472,6 +479,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         mbar_init(&sh.accf, 1);
         mbar_init(&sh.cdone, 1);
         mbar_init(&sh.cfree, 4);
+        mbar_init(&sh.tfree, 4);
         sh.released = NST - 1;
         sh.eok = 1;
         mbar_fence_init();
@@ -503,37 +511,50 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             // Column tiles that only pad the cluster read the last real tile.
             const int ytile = min((int)blockIdx.y, a.ntile - 1);
             const uint8_t* img0 = a.img + ((long long)a.img_base[m * 2 + q] * a.ntile + ytile) * A_BYTES;
-            auto copy = [&](int c) {
+            auto copy = [&](int c) {                    // c: chunk of the CTA
                 const int s = c % NST;
-                const long long ci = (S2 && !M2A) ? (c >> 1) : c;
-                mbar_arrive_expect_tx(&sh.full[s], A_BYTES + npieces * SCR_BYTES);
+                const int t = c / nch, kc = c - t * nch;
+                const long long ci = (S2 && !M2A) ? (kc >> 1) : kc;
+                mbar_arrive_expect_tx(&sh.full[s], A_BYTES + t_npieces(t) * SCR_BYTES);
                 bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
             };
-            for (int c = 0; c < min(nch, NST); c++) copy(c);
+            for (int c = 0; c < min(nchunk, NST); c++) copy(c);
             int c = NST;                                // next stage event
-            int kc = 0;                                 // next MMA chunk
+            int g = 0, t = 0, kc = 0;                   // next MMA chunk g = t nch + kc
+            uint32_t idesc = idesc_f16(TC_M, t_nmma(0));
             bool full_ok = false;
             int idle = 0;
-            while (kc < nch || c < nch + NST) {
+            while (g < nchunk || c < nchunk + NST) {
                 bool did = false;
-                if (c < nch + NST && mbar_test_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1)) {
-                    if (c < nch) copy(c);
+                if (c < nchunk + NST && mbar_test_wait_cl(&sh.empty[c % NST], (c / NST - 1) & 1)) {
+                    if (c < nchunk) copy(c);
                     publish_counter(&sh.released, c);
                     c++;
                     did = true;
                 }
-                if (kc < nch) {
-                    const int s = kc % NST;
-                    if (!full_ok) full_ok = mbar_test_wait_cl(&sh.full[s], (kc / NST) & 1);
+                if (g < nchunk) {
+                    const int s = g % NST;
+                    if (!full_ok) full_ok = mbar_test_wait_cl(&sh.full[s], (g / NST) & 1);
                     const int kq = kc % SPAN;
-                    if (full_ok && (kc < SPAN || kq != 0 || mbar_test_wait_cl(&sh.cfree, (kc / SPAN - 1) & 1))) {
+                    bool ready = full_ok;
+                    if (ready && kq == 0) {
+                        // a tile's first span waits until the previous tile's epilogue has
+                        // read the accumulators; a later span until the previous one is drained
+                        if (kc == 0) ready = (t == 0) || mbar_test_wait_cl(&sh.tfree, (t - 1) & 1);
+                        else ready = mbar_test_wait_cl(&sh.cfree, (t * nspan + kc / SPAN - 1) & 1);
+                    }
+                    if (ready) {
                         tc_fence_after();
                         issue_stage(tmem, smem_base + s * STAGE_BYTES, idesc, kc == 0, kq == 0);
                         umma_commit_mc(&sh.empty[s], mask);
                         if (kq == SPAN - 1 || kc == nch - 1) umma_commit(&sh.cdone);
-                        kc++;
+                        if (kc == nch - 1) umma_commit(&sh.accf);
+                        g++;
                         full_ok = false;
-                        if (kc == nch) umma_commit(&sh.accf);
+                        if (++kc == nch) {
+                            kc = 0;
+                            if (++t < ntl) idesc = idesc_f16(TC_M, t_nmma(t));
+                        }
                         did = true;
                     }
                 }
@@ -559,18 +580,39 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         if (smid >= (uint32_t)LAM_SM && lane == 0) atomicCAS(a.err, 0, 9);
         uint8_t* gslots = g_lam_slots + ((size_t)(smid % LAM_SM) * 3 + (warp - 1)) * LAM_SLOTS * SCR_BYTES;
         const uint16_t mask = (uint16_t)((1u << csize) - 1u);
-        const int total = (smid < (uint32_t)LAM_SM) ? nch * npieces : 0;
+        // the CTA's pieces in order (tile, chunk, piece); every tile but the last
+        // has full 128-row tiles, TC_N / PR pieces per chunk
+        constexpr int NPF = TC_N / PR;
+        const int np_last = t_npieces(ntl - 1);
+        const int pfull = (ntl - 1) * nch * NPF;
+        const int total = (smid < (uint32_t)LAM_SM) ? pfull + nch * np_last : 0;
+        auto piece_at = [&](int gi, int& t, int& kc, int& j) {
+            if (gi < pfull) {
+                t = gi / (nch * NPF);
+                const int r = gi - t * nch * NPF;
+                kc = r / NPF;
+                j = r - kc * NPF;
+            } else {
+                const int r = gi - pfull;
+                t = ntl - 1;
+                kc = r / np_last;
+                j = r - kc * np_last;
+            }
+        };
         const int gstep = (int)csize * 3;
         int npc = 0;                                    // pieces of this warp so far
         for (int g = (int)crank + (int)csize * (warp - 1); g < total; g += gstep, npc++) {
-            const int kc = g / npieces, j = g - kc * npieces;
-            const int s = kc % NST;
+            int t, kc, j;
+            piece_at(g, t, kc, j);
+            const int gch = t * nch + kc;               // chunk of the CTA
+            const int s = gch % NST;
+            const int n0t = t_n0(t), nrt = t_nrows(t);  // the tile's rows
             if constexpr (M2A && S2) {
                 // lane = ring pair (k) of unit kc / 2, walking the 64 l that hold the
                 // 32 rows (slot q) of piece j with the recurrence of s = (kc odd ? -2 : +2)
                 const int sg = kc & 1;
                 const int p = (kc >> 1) * KC + lane;
-                const int J = (n0 >> 5) + j;            // 32-row block of the slot's rows
+                const int J = (n0t >> 5) + j;            // 32-row block of the slot's rows
                 const int L = m + 64 * J;               // first l of the walk (checkpoint block 2J)
                 const int lck = max(L, l0s);            // l of the checkpointed value
                 df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x = {0.0f, 0.0f};
@@ -592,7 +634,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                     const long long ci = a_idx(a.lmax, L + 32 + lane, m);
                     cA1 = df_of(a.s2A[sg][ci]); cB1 = df_of(a.s2B[sg][ci]);
                 }
-                const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
+                const int rn = min(PR, nrt - j * PR);  // rows of this piece (warp-uniform)
                 int lc = lck;                           // l of cur (warp-uniform)
 #pragma unroll 1
                 for (int i0 = 0; i0 < PR; i0 += 8) {
@@ -626,13 +668,13 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 int E = 0;
                 const bool live = p < a.R;
                 if (live) {
-                    const long long ci = (long long)(ckb + (n0 + j * PR) / CK_ROWS) * a.R + p;
+                    const long long ci = (long long)(ckb + (n0t + j * PR) / CK_ROWS) * a.R + p;
                     E = a.ck_exp[ci];
                     ck_to_df(a.ck[ci], cur, prev, E);
                     const df x = df_of(a.pairs[p].x);
                     x2 = df_mul(x, x);
                 }
-                const int rn = min(PR, nrows - j * PR);  // rows of this piece (warp-uniform)
+                const int rn = min(PR, nrt - j * PR);  // rows of this piece (warp-uniform)
                 df tn = df_axb(sh.cA2[j * PR], x2, sh.cB2[j * PR]);
 #pragma unroll 1
                 for (int i0 = 0; i0 < PR; i0 += 8) {
@@ -658,8 +700,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const int sg = kc & 1;
                 const int u = kc >> 1;
                 const int r = j * PR + lane;
-                const int p = n0 + r;
-                const bool live = r < nrows;
+                const int p = n0t + r;
+                const bool live = r < nrt;
                 const int L = m + KC * u;               // first l of the unit (checkpoint block u)
                 const int lck = max(L, l0s);
                 df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x = {0.0f, 0.0f};
@@ -669,7 +711,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                     E = a.ck_exp[ci];
                     ck_to_df(a.ck[ci], cur, prev, E);
                     x = df_of(a.pairs[p].x);
-                    pe = sh.rowexp[r];
+                    pe = quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + p], a.Q);
                 }
                 df cAk = {0.0f, 0.0f}, cBk = {0.0f, 0.0f};
                 float2 cdk = make_float2(0.0f, 0.0f);
@@ -710,8 +752,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 // coefficients of those 32 l are loaded once (lane k holds l_k)
                 // and broadcast with shuffles
                 const int r = j * PR + lane;
-                const int p = n0 + r;
-                const bool live = r < nrows;
+                const int p = n0t + r;
+                const bool live = r < nrt;
                 df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x2 = {0.0f, 0.0f};
                 int E = 0, pe = 0;
                 if (live) {
@@ -720,7 +762,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                     ck_to_df(a.ck[ci], cur, prev, E);
                     const df x = df_of(a.pairs[p].x);
                     x2 = df_mul(x, x);
-                    pe = sh.rowexp[r];
+                    pe = quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + p], a.Q);
                 }
                 df cAk = {0.0f, 0.0f}, cBk = {0.0f, 0.0f};
                 float2 cck = make_float2(0.0f, 0.0f);
@@ -764,7 +806,9 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             // pieces ago, chunk kp) has landed in every CTA: true once chunk kp + NST
             // is released, which needs the MMAs of chunk kp in every CTA.
             const int gp = g - LAM_SLOTS * gstep;
-            if (gp >= 0 && !__all_sync(0xffffffffu, wait_counter(&sh.released, gp / npieces + NST, a.err, 8))) break;
+            int tp = 0, kcp = 0, jp = 0;
+            if (gp >= 0) piece_at(gp, tp, kcp, jp);
+            if (gp >= 0 && !__all_sync(0xffffffffu, wait_counter(&sh.released, tp * nch + kcp + NST, a.err, 8))) break;
             uint8_t* gs = gslots + (npc & (LAM_SLOTS - 1)) * SCR_BYTES;
 #pragma unroll
             for (int v = 0; v < SCR_BYTES / 512; v++) {
@@ -773,7 +817,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             }
             fence_proxy_async_global();
             __syncwarp();
-            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, kc, a.err, 2))) break;
+            if (!__all_sync(0xffffffffu, wait_counter(&sh.released, gch, a.err, 2))) break;
             // stage free in every CTA: one multicast copy per plane into rows
             // 32 j .. 32 j + 31 (one contiguous 2 KB block: the swizzle repeats
             // every 8 rows); each CTA's data warp announced these bytes
@@ -817,11 +861,11 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             tmem_st16(tl + g, v[0]);
             tmem_st16(tl + ACC_SM + g, v[2]);
         };
-        auto drain = [&](int j) {
+        auto drain = [&](int j, int nm) {          // j: span of the CTA; nm: its tile's MMA N
             dok = dok && __all_sync(0xffffffffu, mbar_wait_cl(&sh.cdone, j & 1, a.err, 6));
             if (!dok) return;
             tc_fence_after();
-            const int gb = 0, ge = nmma;
+            const int gb = 0, ge = nm;
             uint32_t va[4][16], vb[4][16];
             drain_load(gb, va);
             tmem_wait_ld();
@@ -843,23 +887,73 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         };
         // (the MMAs of the next span wait for each drain; a wait that gives up
         // turns dok off and ends the drains)
-        const int nspan = (nch + SPAN - 1) / SPAN;
-        for (int j = 0; j < nspan && dok; j++) drain(j);
-
-        // the last MMAs are complete once every wait above succeeded
-        const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
-        if (lane == 0 && !ok) sh.eok = 0;
-        tmem_wait_st();
+        if constexpr (M2A) {
+            for (int j = 0; j < nspan && dok; j++) drain(j, nmma);
+            // the last MMAs are complete once every wait above succeeded
+            const bool ok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, 0, a.err, 4)));
+            if (lane == 0 && !ok) sh.eok = 0;
+            tmem_wait_st();
+        } else {
+            // alm2map, per tile: its spans, then its epilogue for this thread's
+            // column: G = (main + sm) * scales. The accumulators are read into
+            // registers and handed back (tfree) before the stores, which then
+            // overlap the next tile's MMAs.
+            const int tcol = tid - 128;
+            const long long cg = c0 + tcol;
+            const bool cok = cg < a.ncol;
+            const int ce = sh.colexp[tcol];
+            const float sc = ((m == 0) ? a.s0 : a.s1) * (S2 ? -0.5f : 1.0f);
+            float* Gq = (float*)dst + ((long long)m * 2 + q) * qstride + cg;
+            for (int t = 0; t < ntl; t++) {
+                const int nmt = t_nmma(t), nrt = t_nrows(t), n0t = t_n0(t);
+                for (int j = 0; j < nspan && dok; j++) drain(t * nspan + j, nmt);
+                dok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, t & 1, a.err, 4)));
+                tc_fence_after();
+                float gv[TC_N];
+#pragma unroll
+                for (int gq = 0; gq < TC_N / 16; gq++) {
+                    uint32_t v0[16], vr[16];
+                    if (dok && nch > 0 && gq * 16 < nmt) {
+                        tmem_ld16(tl + gq * 16, v0);
+                        tmem_ld16(tl + ACC_SM + gq * 16, vr);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int i = 0; i < 16; i++) gv[gq * 16 + i] = __uint_as_float(v0[i]) + __uint_as_float(vr[i]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) gv[gq * 16 + i] = 0.0f;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh.tfree);
+                // row quanta: lane i holds the one of row 32 gq + i
+#pragma unroll
+                for (int gq = 0; gq < TC_N / 32; gq++) {
+                    if (gq * 32 >= nrt) continue;
+                    const int rl = gq * 32 + lane;
+                    const int pe = (rl < nrt) ? quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + n0t + rl], a.Q) : 0;
+#pragma unroll
+                    for (int i = 0; i < 32; i++) {
+                        const int e = __shfl_sync(0xffffffffu, pe, i);
+                        const int r = gq * 32 + i;
+                        if (r < nrt && cok && dok)
+                            Gq[(long long)(n0t + r) * a.ncol] = (nch > 0) ? sc * ldexpf_fast(gv[r], e + ce) : 0.0f;
+                    }
+                }
+            }
+            tmem_wait_st();
+        }
     }
 
-    // ---------------- epilogue: out = (main + sm) * scales, warps 0-7 ----------------
+    // ---------------- map2alm epilogue: out = (main + sm) * scales, warps 0-7 ----------------
     // (warps w and w + 4 reach the same TMEM lanes, i.e. the same map column;
     // warps 4-7 take rows 0-63, warps 0-3 rows 64-127)
-    __syncwarp();
-    tc_fence_before();
-    named_bar_sync(2, 256);
-    tc_fence_after();
-    {
+    if constexpr (M2A) {
+        __syncwarp();
+        tc_fence_before();
+        named_bar_sync(2, 256);
+        tc_fence_after();
         const int t = tid & (TC_M - 1);
         const long long cg = c0 + t;
         const bool cok = cg < a.ncol;
@@ -877,7 +971,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 tmem_wait_ld();
             }
             if (!ok || !cok) continue;
-            if (M2A) {
+            {
                 double* alm = (double*)dst + ((cg >> 1) * a.nalm) * 2 + (cg & 1);
                 const bool zero_im = (m == 0) && (cg & 1);
 #pragma unroll
@@ -895,19 +989,6 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                         double v = f32_to_f64(p1) + f32_to_f64(lo);            // final FP64 accumulation
                         v = ldexp_fast(v, sh.rowexp[r] + ce);
                         alm[(long long)sh.rowidx[r] * 2] = zero_im ? 0.0 : v;
-                    }
-                }
-            } else {
-                float* Gq = (float*)dst + ((long long)m * 2 + q) * qstride + cg;
-                const float sc = ((m == 0) ? a.s0 : a.s1) * (S2 ? -0.5f : 1.0f);
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int r = g * 32 + i;
-                    if (r < nrows) {
-                        float gv = 0.0f;
-                        if (nch > 0)
-                            gv = sc * ldexpf_fast(__uint_as_float(v0[i]) + __uint_as_float(vr[i]), sh.rowexp[r] + ce);
-                        Gq[(long long)(n0 + r) * a.ncol] = gv;
                     }
                 }
             }
@@ -1366,6 +1447,8 @@ cudaError_t run_split_tables(sht_plan* p, const int* d_ck_base)
 }
 
 int split_row_tile() { return TC_N; }
+// ring-pair tiles one alm2map CTA walks in one pipeline
+int split_a2m_tiles() { return 8; }
 int split_ck_rows() { return CK_ROWS; }
 int split_col_tile() { return TC_M; }
 

@@ -501,6 +501,8 @@ static cudaError_t build_split_tables_s2(sht_plan* p)
     if ((e = upload(&p->s.s2d2, d2, &acc)) != cudaSuccess) return e;
     // work lists; checkpoint blocks: every 32 l from m, per m
     const int TM = split_row_tile(), CKL = split_ck_rows();
+    // alm2map work items cover GA ring-pair tiles each (first tile | count << 16)
+    const int GA = split_a2m_tiles(), ntR = (R + TM - 1) / TM;
     std::vector<int4> w1, w2;
     std::vector<int> base((size_t)(mmax + 1));
     int nblk = 0;
@@ -511,7 +513,7 @@ static cudaError_t build_split_tables_s2(sht_plan* p)
             const int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
             for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk));
             if (lmax >= m)
-                for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, nblk));
+                for (int t = 0; t * TM < R; t += GA) w2.push_back(make_int4(m, q, t | (std::min(GA, ntR - t) << 16), nblk));
         }
         nblk += (lmax >= m) ? (lmax - m + 1 + CKL - 1) / CKL : 0;
     }
@@ -597,6 +599,8 @@ static cudaError_t build_split_tables(sht_plan* p)
     if ((e = upload(&p->s.nc2, nc2, &acc)) != cudaSuccess) return e;
     // work lists and checkpoint blocks (one block every CKR rows of a chain)
     const int TM = split_row_tile(), CKR = split_ck_rows();
+    // alm2map work items cover GA ring-pair tiles each (first tile | count << 16)
+    const int GA = split_a2m_tiles(), ntR = (R + TM - 1) / TM;
     std::vector<int4> w1, w2;
     std::vector<int> base((size_t)(mmax + 1) * 2);
     int nblk = 0;
@@ -606,7 +610,7 @@ static cudaError_t build_split_tables(sht_plan* p)
             int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
             base[m * 2 + q] = nblk;
             for (int t = 0; t * TM < nrows; t++) w1.push_back(make_int4(m, q, t, nblk));
-            for (int t = 0; t * TM < R; t++) w2.push_back(make_int4(m, q, t, nblk));
+            for (int t = 0; t * TM < R; t += GA) w2.push_back(make_int4(m, q, t | (std::min(GA, ntR - t) << 16), nblk));
             nblk += (nrows + CKR - 1) / CKR;
         }
     p->s.nwork_m2a = (int)w1.size();
