@@ -54,6 +54,8 @@ def parse():
                     help="Q/U map pairs of the spin-2 (polarization) measurement at the same nside; 0 skips it")
     ap.add_argument("--no-context", action="store_true",
                     help="skip the context run (nside 256, lmax 767, 1000 maps, Legendre only)")
+    ap.add_argument("--no-next-rows", action="store_true",
+                    help="skip the compact-storage and E-projection measurements")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving measurement (0: skip)")
     ap.add_argument("--serve-load", type=float, default=0.8,
@@ -285,6 +287,54 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
     del plan, p64, ws, maps, alm, alm_out
     torch.cuda.empty_cache()
     return out
+
+
+def run_next_rows(nside, lmax, nmaps, npairs, precision):
+    """The widening rows: the compact square a_lm storage (Sec. 5) converted
+    both ways for the benchmark's batch (bytes moved / time against HBM), and
+    the pixel-domain E projection (Sec. 2.3) of npairs Q/U pairs."""
+    import torch
+    from paper_2208_10154_b300 import sht
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    p0 = sht.Plan(nside, lmax, None, 0, "fp64")
+    alm = torch.view_as_complex(torch.randn((nmaps, 1, p0.nalm, 2), generator=g, dtype=torch.float64,
+                                            device="cuda")).contiguous()
+    sq = p0.alm_to_square(alm)
+    back = p0.square_to_alm(sq)
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record()
+    p0.alm_to_square(alm, out=sq)
+    e1.record()
+    p0.square_to_alm(sq, out=back)
+    e2.record()
+    torch.cuda.synchronize()
+    t_sq, t_back = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    ref = alm.clone()
+    ref[..., :lmax + 1] = ref[..., :lmax + 1].real.to(torch.complex128)     # Im a_l0 is not stored
+    exact = bool(torch.equal(back, ref))
+    del ref
+    nbytes = alm.numel() * 16 + sq.numel() * 8
+    peaks, _ = measured_peaks()
+    layout = {"maps": nmaps, "lmax": lmax, "to_square_ms": t_sq, "to_alm_ms": t_back,
+              "to_square_gbs": nbytes / (t_sq / 1e3) / 1e9, "to_alm_gbs": nbytes / (t_back / 1e3) / 1e9,
+              "hbm_peak_gbs": peaks["hbm_gbs"], "round_trip_exact": exact}
+    del alm, sq, back
+    torch.cuda.empty_cache()
+    p2 = sht.Plan(nside, lmax, None, 2, precision)
+    qu = torch.randn((npairs, 2, p2.npix), generator=g, dtype=torch.float64, device="cuda")
+    out = p2.eb_project(qu, "E", 0)
+    torch.cuda.synchronize()
+    e0.record()
+    p2.eb_project(qu, "E", 0, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = p2.device_status()
+    proj = {"pairs": npairs, "which": "E", "niter": 0, "precision": precision, "ms": ms,
+            "pairs_per_s": npairs / (ms / 1e3), "device_status": status}
+    return {"square_storage": layout, "eb_projection": proj}
 
 
 def run_context(precision, steps=3):
@@ -620,6 +670,10 @@ def main():
     if rank == 0 and a.qu_maps > 0:
         qu = run_qu(nside, lmax, a.qu_maps, max(1, min(a.steps, 3)), max(1, min(a.warmup, 2)), precision)
 
+    next_rows = None
+    if rank == 0 and not a.no_next_rows:
+        next_rows = run_next_rows(nside, lmax, nmaps, 100, precision)
+
     serving = None
     if rank == 0 and a.serve_requests > 0:
         serving = run_serving(a.serve_requests, a.serve_load, dev)
@@ -637,7 +691,8 @@ def main():
             "roofline_fft": fft_roofline,
             "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
             "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
-            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "serving": serving,
+            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "next_rows": next_rows,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

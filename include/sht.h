@@ -161,6 +161,28 @@ sht_status sht_alm2map_noalloc(sht_plan* plan, const void* alm, void* map, int n
                                void* stream);
 size_t     sht_noalloc_scratch_bytes(void);
 
+/* The paper's compact square storage of a_lm (Sec. 5, equ:new alm save scheme):
+ * per map and component one real (lmax+1) x (lmax+1) row-major matrix, every
+ * element used:
+ *     Re a_lm at (row l,     column m)              for 0 <= m <= l <= lmax
+ *     Im a_lm at (row l - m, column lmax - m + 1)   for 1 <= m <= l <= lmax
+ * sq: double [nmaps][ncomp][lmax+1][lmax+1] (device); alm as above. Entries
+ * with m > mmax are written as 0 (to_square) or ignored (to_alm); to_alm
+ * writes Im a_l0 = 0. Exact (element copies). Asynchronous on `stream`. */
+sht_status sht_alm_to_square(const sht_plan* plan, const void* alm, void* sq, int nmaps, void* stream);
+sht_status sht_square_to_alm(const sht_plan* plan, const void* sq, void* alm, int nmaps, void* stream);
+
+/* Pixel-domain E or B projection of Q/U maps (Sec. 2.3, equ:aeab mat form
+ * pixel): out = alm2map(keep(map2alm(map, niter))), keep = the E (which = 0)
+ * or B (which = 1) component of every a_lm, the other set to zero. Spin-2
+ * plans only (SHT_EINVAL otherwise). map, out: double [nmaps][2][npix]
+ * (device, distinct); the result is the band-limited E- (B-) part of the
+ * input, within the accuracy of the plan's precision and niter. Needs
+ * sht_workspace_bytes_project(plan, nmaps, niter) bytes of workspace. */
+sht_status sht_eb_project(sht_plan* plan, const void* map, void* out, int nmaps, int which, int niter,
+                          void* workspace, size_t workspace_bytes, void* stream);
+size_t     sht_workspace_bytes_project(const sht_plan* plan, int nmaps, int niter);
+
 /* Device-side status of a plan's tensor-core kernels (no counterpart in the
  * paper). Every wait inside those kernels is bounded; one that gives up
  * records a nonzero code (which wait) in a per-plan device word, skips the

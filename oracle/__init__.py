@@ -15,7 +15,9 @@ with ncomp = 1 for spin 0 and 2 (Q,U resp. E,B) for spin 2.
 Pins that tie each function to something other than itself live in
 ``tests/test_oracle_*.py`` (closed forms, mpmath, addition theorem,
 orthonormality, brute force vs separable, quadrature identities, adjoint
-identity, iteration convergence, E/B rotation).
+identity, iteration convergence, E/B rotation, the compact square storage
+against a worked example, the E/B projection's complementarity and
+idempotence).
 """
 from __future__ import annotations
 
@@ -208,3 +210,51 @@ def _mweights(lmax, mmax):
         i0 = alm_index(lmax, m, m)
         w[i0:i0 + lmax - m + 1] = 1.0 if m == 0 else 2.0
     return w
+
+
+# ---------------------------------------------------------------------------
+# Compact square a_lm storage (Sec. 5, equ:new alm save scheme): a real
+# (lmax+1) x (lmax+1) matrix per map and component, every element used:
+#   Re a_lm -> (l, m)                 for 0 <= m <= l <= lmax
+#   Im a_lm -> (l - m, lmax - m + 1)  for 1 <= m <= l <= lmax
+# Entries with m > mmax stay zero. Plain loops over (l, m).
+# ---------------------------------------------------------------------------
+def alm_to_square(alm, lmax: int, mmax: int | None = None) -> np.ndarray:
+    mmax = lmax if mmax is None else mmax
+    a = np.asarray(alm, dtype=np.complex128)
+    lead = a.shape[:-1]
+    flat = a.reshape(-1, a.shape[-1])
+    sq = np.zeros((flat.shape[0], lmax + 1, lmax + 1))
+    for m in range(mmax + 1):
+        for l in range(m, lmax + 1):
+            v = flat[:, alm_index(lmax, l, m)]
+            sq[:, l, m] = v.real
+            if m >= 1:
+                sq[:, l - m, lmax - m + 1] = v.imag
+    return sq.reshape(lead + (lmax + 1, lmax + 1))
+
+
+def square_to_alm(sq, lmax: int, mmax: int | None = None) -> np.ndarray:
+    """Inverse of alm_to_square (Im a_l0 = 0)."""
+    mmax = lmax if mmax is None else mmax
+    q = np.asarray(sq, dtype=np.float64)
+    lead = q.shape[:-2]
+    flat = q.reshape(-1, lmax + 1, lmax + 1)
+    out = np.zeros((flat.shape[0], nalm(lmax, mmax)), dtype=np.complex128)
+    for m in range(mmax + 1):
+        for l in range(m, lmax + 1):
+            im = flat[:, l - m, lmax - m + 1] if m >= 1 else 0.0
+            out[:, alm_index(lmax, l, m)] = flat[:, l, m] + 1j * im
+    return out.reshape(lead + (out.shape[-1],))
+
+
+# ---------------------------------------------------------------------------
+# Pixel-domain E / B projection (Sec. 2.3, equ:aeab mat form pixel): the Q/U
+# maps of the E (or B) part, i.e. alm2map of map2alm with the other
+# component of every a_lm set to zero (lambda^{E,B} keeps one diagonal block).
+# ---------------------------------------------------------------------------
+def eb_project(maps, nside: int, lmax: int, which: str = "E", niter: int = 0,
+               mmax: int | None = None) -> np.ndarray:
+    a = map2alm(maps, nside, lmax, mmax, spin=2, niter=niter)
+    a[:, 1 if which == "E" else 0, :] = 0.0
+    return alm2map(a, nside, lmax, mmax, spin=2)

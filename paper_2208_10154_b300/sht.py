@@ -67,8 +67,14 @@ def load() -> ctypes.CDLL:
         lib.sht_map2alm_adjoint.argtypes = [P, P, P, I, P, S, P]
         lib.sht_alm2map_host.argtypes = [P, P, P, I, P]
         lib.sht_map2alm_host.argtypes = [P, P, P, I, I, P]
+        lib.sht_alm_to_square.argtypes = [P, P, P, I, P]
+        lib.sht_square_to_alm.argtypes = [P, P, P, I, P]
+        lib.sht_eb_project.argtypes = [P, P, P, I, I, I, P, S, P]
+        lib.sht_workspace_bytes_project.argtypes = [P, I, I]
+        lib.sht_workspace_bytes_project.restype = S
         for f in (lib.sht_alm2map, lib.sht_map2alm, lib.sht_alm2map_adjoint,
-                  lib.sht_map2alm_adjoint, lib.sht_alm2map_host, lib.sht_map2alm_host):
+                  lib.sht_map2alm_adjoint, lib.sht_alm2map_host, lib.sht_map2alm_host,
+                  lib.sht_alm_to_square, lib.sht_square_to_alm, lib.sht_eb_project):
             f.restype = I
         lib.sht_last_error.restype = ctypes.c_char_p
         lib.sht_last_launch_count.restype = I
@@ -280,4 +286,43 @@ class Plan:
         out = np.empty((nmaps, self.ncomp, self.nalm), dtype=np.complex128) if out_host is None else out_host
         sht_map2alm_host(self.handle, ctypes.c_void_p(x.ctypes.data), ctypes.c_void_p(out.ctypes.data),
                          nmaps, int(niter), _stream())
+        return out
+
+    # ---- the paper's compact square a_lm storage and E / B projection ----
+    def alm_to_square(self, alm: torch.Tensor, out=None) -> torch.Tensor:
+        """a_lm [..., ncomp, nalm] -> compact square [nmaps, ncomp, lmax+1, lmax+1] (float64)."""
+        alm = self._in(alm, torch.complex128, self.nalm)
+        nmaps = alm.numel() // (self.ncomp * self.nalm)
+        L = self.lmax + 1
+        if out is None:
+            out = torch.empty((nmaps, self.ncomp, L, L), dtype=torch.float64, device=alm.device)
+        _check(load().sht_alm_to_square(self.handle, ctypes.c_void_p(alm.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), nmaps, _stream()))
+        return out
+
+    def square_to_alm(self, sq: torch.Tensor, out=None) -> torch.Tensor:
+        """compact square [..., ncomp, lmax+1, lmax+1] (float64) -> a_lm [nmaps, ncomp, nalm]."""
+        L = self.lmax + 1
+        if not (sq.is_cuda and sq.dtype == torch.float64 and sq.is_contiguous()) or sq.shape[-2:] != (L, L):
+            raise ValueError(f"expected a contiguous float64 CUDA tensor [..., {L}, {L}]")
+        nmaps = sq.numel() // (self.ncomp * L * L)
+        if out is None:
+            out = torch.empty((nmaps, self.ncomp, self.nalm), dtype=torch.complex128, device=sq.device)
+        _check(load().sht_square_to_alm(self.handle, ctypes.c_void_p(sq.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), nmaps, _stream()))
+        return out
+
+    def eb_project(self, maps: torch.Tensor, which: str = "E", niter: int = 0, out=None) -> torch.Tensor:
+        """Pixel-domain E (which="E") or B ("B") part of Q/U maps [nmaps, 2, npix] (spin-2 plans)."""
+        maps = self._in(maps, torch.float64, self.npix)
+        nmaps = maps.numel() // (self.ncomp * self.npix)
+        if out is None:
+            out = torch.empty((nmaps, self.ncomp, self.npix), dtype=torch.float64, device=maps.device)
+        lib = load()
+        need = lib.sht_workspace_bytes_project(self.handle, nmaps, int(niter))
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=maps.device)
+        off = (-ws.data_ptr()) % 256
+        _check(lib.sht_eb_project(self.handle, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  nmaps, {"E": 0, "B": 1}[which], int(niter), ctypes.c_void_p(ws.data_ptr() + off),
+                                  need, _stream()))
         return out
