@@ -40,6 +40,8 @@ CASES = [
     (128, 300, 300, 7, "inv_llp1"),     # several row / pair tiles
     (16, 40, 40, 300, "inv_llp1"),      # 5 column tiles: one cluster of 5 CTAs
     (8, 23, 23, 520, "flat"),           # 9 column tiles: clusters of 5, one padded tile
+    (96, 200, 200, 6, "inv_llp1"),      # 192 ring pairs: an alm2map CTA walks a full and a 64-row tile
+    (560, 100, 100, 3, "flat"),         # 1120 ring pairs: two alm2map groups (8 tiles, then a 96-row tile)
 ]
 
 
@@ -110,6 +112,7 @@ S2_CASES = [
     (64, 127, 127, 70, 0.01),   # 280 columns: three column tiles, ragged
     (128, 300, 300, 5, 0.01),   # several row / pair tiles, K' = 2 x 256 ring pairs
     (8, 23, 23, 130, 1.0),      # 520 columns: clusters of column tiles
+    (96, 150, 150, 2, 0.01),    # 192 ring pairs: a full and a 64-row tile in one alm2map CTA
 ]
 
 
