@@ -248,7 +248,10 @@ struct TcShared {
     uint32_t tmem;
     int colexp[TC_M];
     int rowexp[TC_N];          // quantum exponent per lambda row (l or ring pair)
-    df cA2[TC_N], cB2[TC_N];   // map2alm: recurrence coefficients of the tile's rows
+    // map2alm: recurrence coefficients of the tile's rows. alm2map leaves them
+    // unused and keeps the row scale factors of two tiles in their place
+    // (float [2][TC_N], by tile parity).
+    alignas(16) df cA2[TC_N], cB2[TC_N];
     float2 rfac[TC_N];         // map2alm: c_l * factor as an FP32 hi/lo pair
     int rowidx[TC_N];          // map2alm: packed index of the row's (l, m)
 };
@@ -901,12 +904,21 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             const int tcol = tid - 128;
             const long long cg = c0 + tcol;
             const bool cok = cg < a.ncol;
-            const int ce = sh.colexp[tcol];
-            const float sc = ((m == 0) ? a.s0 : a.s1) * (S2 ? -0.5f : 1.0f);
+            // G = sc 2^(ce + pe) (main + sm): the column factor sc 2^ce per
+            // thread, the row factor 2^pe per row (powers of two: exact down to
+            // 2^-149), so each output costs two multiplies and a store
+            const float csc = ldexpf(((m == 0) ? a.s0 : a.s1) * (S2 ? -0.5f : 1.0f), sh.colexp[tcol]);
             float* Gq = (float*)dst + ((long long)m * 2 + q) * qstride + cg;
+            float* rsc = reinterpret_cast<float*>(sh.cA2);
             for (int t = 0; t < ntl; t++) {
                 const int nmt = t_nmma(t), nrt = t_nrows(t), n0t = t_n0(t);
-                for (int j = 0; j < nspan && dok; j++) drain(t * nspan + j, nmt);
+                {   // the tile's row factors; the load overlaps the span drains
+                    const int rl = quarter * 32 + lane;
+                    const float pm = (rl < nrt) ? a.pairmax[((long long)m * 2 + q) * a.R + n0t + rl] : 0.0f;
+                    for (int j = 0; j < nspan && dok; j++) drain(t * nspan + j, nmt);
+                    rsc[(t & 1) * TC_N + rl] = (pm > 0.0f) ? ldexpf(1.0f, quantum_exp(pm, a.Q)) : 0.0f;
+                    named_bar_sync(3, 128);    // drain warps only
+                }
                 dok = dok && ((nch == 0) || __all_sync(0xffffffffu, mbar_wait_cl(&sh.accf, t & 1, a.err, 4)));
                 tc_fence_after();
                 float gv[TC_N];
@@ -927,18 +939,20 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh.tfree);
-                // row quanta: lane i holds the one of row 32 gq + i
+                // (row factors of tile t were written before the barrier above; the
+                // next write to this half is two barriers later)
+                if (cok && dok) {
+                    const float4* rs4 = reinterpret_cast<const float4*>(rsc + (t & 1) * TC_N);
+                    float* gp = Gq + (long long)n0t * a.ncol;
 #pragma unroll
-                for (int gq = 0; gq < TC_N / 32; gq++) {
-                    if (gq * 32 >= nrt) continue;
-                    const int rl = gq * 32 + lane;
-                    const int pe = (rl < nrt) ? quantum_exp(a.pairmax[((long long)m * 2 + q) * a.R + n0t + rl], a.Q) : 0;
+                    for (int r4 = 0; r4 < TC_N / 4; r4++) {
+                        const float4 f = rs4[r4];
+                        const float fr[4] = {f.x, f.y, f.z, f.w};
 #pragma unroll
-                    for (int i = 0; i < 32; i++) {
-                        const int e = __shfl_sync(0xffffffffu, pe, i);
-                        const int r = gq * 32 + i;
-                        if (r < nrt && cok && dok)
-                            Gq[(long long)(n0t + r) * a.ncol] = (nch > 0) ? sc * ldexpf_fast(gv[r], e + ce) : 0.0f;
+                        for (int i = 0; i < 4; i++) {
+                            const int r = 4 * r4 + i;
+                            if (r < nrt) gp[(long long)r * a.ncol] = (nch > 0) ? (gv[r] * csc) * fr[i] : 0.0f;
+                        }
                     }
                 }
             }
