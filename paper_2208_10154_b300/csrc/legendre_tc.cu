@@ -30,9 +30,11 @@
 // 2^-12 fn (all below 1) in sm as the start of the next span, so sm never
 // holds more than one span's worth; ex and fn restart with every span.
 // Dropped: products of two residual slices beyond r0 r1' (< 2^-2G u u').
-// Spans: map2alm 64 of K (G = 11: the truncation of the sm sums is its largest
-// error term); alm2map 128 of K (G = 10: half the drains; its error is set by
-// the FP32 ring spectra instead).
+// Spans: spin-2 map2alm 64 of K (G = 11: the truncation of the sm sums is its
+// largest error term, and its B component is a difference of E-sized terms);
+// spin-0 map2alm and alm2map 128 of K (G = 10: half the drains; spin-0
+// map2alm stays near 1e-8 of the RMS, alm2map's error is set by the FP32 ring
+// spectra).
 //
 // Cluster sharing of lambda. The recurrence is a serial chain per ring pair,
 // so the CTAs of a thread-block cluster, which work on
@@ -82,9 +84,11 @@ constexpr int STAGE_BYTES = NPL * (A_PLANE + B_PLANE);   // 64 KB
 constexpr uint32_t ACC_EX = 128;                 // TMEM columns: exact corrections of one chunk
 constexpr uint32_t ACC_SM = 256;                 //   small corrections (+ the residual of earlier chunks)
 constexpr uint32_t ACC_FN = 384;                 //   products with r2s (2^12 times their value)
-// chunks per drained span and the grid exponent of the r0 slices, per direction
-template <bool M2A> __host__ __device__ constexpr int span_chunks() { return M2A ? 2 : 4; }
-template <bool M2A> __host__ __device__ constexpr int r0_grid() { return M2A ? 11 : 10; }
+// chunks per drained span and the grid exponent G of the r0 slices: spin-2
+// map2alm 64 of K with G = 11 (its error budget is the tightest), the others
+// 128 of K with G = 10
+template <bool M2A, bool S2> __host__ __device__ constexpr int span_chunks() { return (M2A && S2) ? 2 : 4; }
+template <bool M2A, bool S2> __host__ __device__ constexpr int r0_grid() { return (M2A && S2) ? 11 : 10; }
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
 constexpr int MAX_CLUSTER = 8;
 constexpr int TC_THREADS = 256;                  // 8 warps (roles below)
@@ -172,12 +176,13 @@ __device__ __forceinline__ void put4x8(uint8_t* planes, int plane_bytes, int row
 // 32 j .. 32 j + 31 of a stage plane). map2alm: rows i0 .. i0 + 7 of K column
 // `lane` (one FP16 per plane and row); alm2map: the 16-byte chunk jj (k = 8 jj
 // .. 8 jj + 7) of row `lane`.
+template <int G>
 __device__ __forceinline__ void put_rows8(uint8_t* scr, int i0, int lane, const float (&hv)[8], const float (&lv)[8])
 {
 #pragma unroll
     for (int ii = 0; ii < 8; ii++) {
         float x[NPL];
-        slice4d<r0_grid<true>()>(hv[ii], lv[ii], x[0], x[1], x[2], x[3]);
+        slice4d<G>(hv[ii], lv[ii], x[0], x[1], x[2], x[3]);
         const uint32_t w01 = pack_h2(x[0], x[1]), w23 = pack_h2(x[2], x[3]);
         const uint32_t off = sw64_off(i0 + ii, lane);
         *reinterpret_cast<uint16_t*>(scr + off) = (uint16_t)(w01 & 0xFFFFu);
@@ -188,7 +193,7 @@ __device__ __forceinline__ void put_rows8(uint8_t* scr, int i0, int lane, const 
 }
 __device__ __forceinline__ void put_chunk8(uint8_t* scr, int row, int jj, const float (&hv)[8], const float (&lv)[8])
 {
-    put4x8<r0_grid<false>()>(scr, PIECE_BYTES, row, jj, hv, lv);
+    put4x8<r0_grid<false, false>()>(scr, PIECE_BYTES, row, jj, hv, lv);
 }
 
 // one stage (two MMA K-steps), A = data, B = lambda: main accumulates over the
@@ -436,7 +441,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const int nchunk = ntl * nch;                  // chunks of the CTA: chunk g = tile g / nch, kc = g % nch
     const int l0s = m > 2 ? m : 2;                 // first l of the spin-2 functions
     const int nmma = t_nmma(0);
-    constexpr int SPAN = span_chunks<M2A>();
+    constexpr int SPAN = span_chunks<M2A, S2>();
     const int nspan = (nch + SPAN - 1) / SPAN;     // drained spans per tile
     const long long qstride = (long long)a.R * a.ncol;
 
@@ -662,7 +667,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                             if (live && lt >= lck) df_scaled(cur, E - sh.rowexp[j * PR + i], hv[ii], lv[ii]);
                         }
                     }
-                    put_rows8(scr, i0, lane, hv, lv);
+                    put_rows8<r0_grid<M2A, S2>()>(scr, i0, lane, hv, lv);
                 }
             } else if constexpr (M2A) {
                 // lane = ring pair (k), walking the 32 l rows of piece j
@@ -695,7 +700,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                             rescale_df(cur, prev, E);
                         }
                     }
-                    put_rows8(scr, i0, lane, hv, lv);
+                    put_rows8<r0_grid<M2A, S2>()>(scr, i0, lane, hv, lv);
                 }
             } else if constexpr (S2) {
                 // lane = ring pair (row), walking the 32 l of unit kc / 2 with the
@@ -1101,7 +1106,7 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
                 hv[i] = x.x * csc;
                 lv[i] = x.y * csc;
             }
-            put4x8<r0_grid<M2A>()>(A, A_PLANE, t, jj, hv, lv);
+            put4x8<r0_grid<M2A, S2>()>(A, A_PLANE, t, jj, hv, lv);
         }
     }
 }

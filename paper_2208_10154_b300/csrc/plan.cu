@@ -390,10 +390,11 @@ static cudaError_t build_tables(sht_plan* p)
 }
 
 // integer range Q of the slices for a contraction of length K: main (the sum
-// of q q' plus the integer parts folded in after every 64-wide span, at most
+// of q q' plus the integer parts folded in after every span, at most
 // Q (Q + 1) K + 12 K / 32) must stay below 2^24, where FP32 holds integers
-// exactly, and Q <= 127 keeps a span of q r0' + r0 q' (multiples of 2^-11, at
-// most 64 Q (1 + 2^-10)) below 2^13
+// exactly, and Q <= 127 keeps a span of q r0' + r0 q' (multiples of 2^-G: 64
+// wide with G = 11, at most 64 Q (1 + 2^-10) < 2^13, or 128 wide with G = 10,
+// at most 128 Q (1 + 2^-9) < 2^14) below 2^(24 - G)
 static float slice_range(double K)
 {
     K = std::max(K, 1.0);

@@ -324,15 +324,6 @@ __device__ __forceinline__ float f64_to_f32_scaled(double v, int sh)
     unsigned int f = (hi & 0x80000000u) | ((unsigned int)ef << 23) | m23;
     return __uint_as_float(f);
 }
-__device__ __forceinline__ float ldexpf_fast_i(float x, int k)
-{
-    int u = __float_as_int(x);
-    int e = (u >> 23) & 0xFF;
-    if (e == 0) return 0.0f;
-    int en = e + k;
-    if (en <= 0) return 0.0f;
-    return __int_as_float((u & ~0x7F800000) | (en << 23));
-}
 // v * 2^sh as an FP32 pair hi + lo (|v 2^sh| < 2^127; parts below the FP32
 // normal range flush to 0). Integer and FP32 operations only: the 29 mantissa
 // bits below hi become lo through the 1.5 * 2^23 magic constant (their lowest
@@ -366,19 +357,18 @@ __device__ __forceinline__ double f32_to_f64(float x)
 // x * 2^k for an FP64 x (exact; 0 stays 0)
 __device__ __forceinline__ double ldexp_fast(double x, int k)
 {
-    long long b = __double_as_longlong(x);
-    if ((b & 0x7FF0000000000000ll) == 0) return 0.0;
-    return __longlong_as_double(b + ((long long)k << 52));
+    const long long b = __double_as_longlong(x);
+    return ((b & 0x7FF0000000000000ll) == 0) ? 0.0 : __longlong_as_double(b + ((long long)k << 52));
 }
 // x * 2^k for an FP32 x (exact when the result stays normal; flushes below)
+// (selects, no early exits: the callers' unrolled loops stay one basic block)
 __device__ __forceinline__ float ldexpf_fast(float x, int k)
 {
-    int u = __float_as_int(x);
-    int e = (u >> 23) & 0xFF;
-    if (e == 0) return 0.0f;
-    int en = e + k;
-    if (en <= 0) return 0.0f;
-    return __int_as_float((u & ~0x7F800000) | (en << 23));
+    const int u = __float_as_int(x);
+    const int e = (u >> 23) & 0xFF;
+    const int en = e + k;
+    const int r = (u & ~0x7F800000) | (en << 23);
+    return (e != 0 && en > 0) ? __int_as_float(r) : 0.0f;
 }
 
 // Slice v + vl (|v| <= Q, |vl| <= 2^-23 |v|; units of the quantum) into four
