@@ -131,7 +131,10 @@ __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
             const int k = g & (h - 1);
             cx* y = buf + f * M + ((g - k) << 2) + k;
             cx x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
-            if (k != 0) {
+            // (the branch is per pass, not per lane: for k = 0 the twiddled
+            // path multiplies by exactly 1, and a warp whose lanes took both
+            // paths would execute both)
+            if (h > 1) {
                 float2 w1h, w1l, w2h, w2l;
                 twid(tw, k * s1, inv, w1h, w1l);
                 twid(tw, k * s2, inv, w2h, w2l);
@@ -170,7 +173,7 @@ __device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
             const cx x0 = y[0], x1 = y[hq], x2 = y[h], x3 = y[h + hq];
             cx c0 = caddc(x0, x2), c2 = csubc(x0, x2), c1 = caddc(x1, x3), c3 = csubc(x1, x3);
             c3 = inv ? cmul_pi(c3) : cmul_mi(c3);
-            if (k != 0) {
+            if (hq > 1) {                            // per pass (see fft_dit)
                 float2 v1h, v1l, v2h, v2l;
                 twid(tw, k * s1, inv, v1h, v1l);
                 twid(tw, k * s2, inv, v2h, v2l);

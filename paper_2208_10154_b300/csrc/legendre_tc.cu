@@ -90,7 +90,8 @@ constexpr uint32_t ACC_FN = 384;                 //   products with r2s (2^12 ti
 template <bool M2A, bool S2> __host__ __device__ constexpr int span_chunks() { return (M2A && S2) ? 2 : 4; }
 template <bool M2A, bool S2> __host__ __device__ constexpr int r0_grid() { return (M2A && S2) ? 11 : 10; }
 constexpr int CK_ROWS = 32;                      // rows between recurrence checkpoints
-constexpr int MAX_CLUSTER = 8;
+constexpr int MAX_CLUSTER = 16;                 // non-portable above 8
+constexpr int DEF_CLUSTER = 8;
 constexpr int TC_THREADS = 256;                  // 8 warps (roles below)
 
 struct TcArgs {
@@ -1313,12 +1314,12 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     return a;
 }
 
-// largest cluster: 8 (portable limit), or SHT_MAX_CLUSTER from the environment
+// largest cluster: 8 (portable limit), or SHT_MAX_CLUSTER from the environment (up to 16)
 static int max_cluster()
 {
     static int mc = [] {
         const char* e = std::getenv("SHT_MAX_CLUSTER");
-        int v = e ? std::atoi(e) : MAX_CLUSTER;
+        int v = e ? std::atoi(e) : DEF_CLUSTER;
         return std::max(1, std::min(v, MAX_CLUSTER));
     }();
     return mc;
@@ -1362,6 +1363,10 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
     if (e != cudaSuccess) return e;
     const long long ntiles = (a.ncol + TC_M - 1) / TC_M;
     int C = pick_cluster(ntiles);
+    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        C = 8;
+    }
     prof_start(name, st);
     for (;;) {
         const long long gy = (ntiles + C - 1) / C * C;
