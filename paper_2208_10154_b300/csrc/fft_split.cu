@@ -276,13 +276,36 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
         const int N = g.n;
-        for (int e = threadIdx.x; e < nb * N; e += NT) {
-            const int s = e / N, n = e - s * N;
-            const double* mp = map + (long long)(mc0 + s) * npix;
-            cx z = czero();
-            tc::f64_split_scaled(mp[g.start_n + n], 0, z.hr, z.lr);
-            if (g.start_s >= 0) tc::f64_split_scaled(mp[g.start_s + n], 0, z.hi, z.li);
-            buf[s * M + placec(f, n)] = chirp_in(f, tb, z, n);
+        // the ring's samples (and Bluestein chirps) in batches of FWD_UB per
+        // thread: every load of a batch is in flight before the first is used
+        constexpr int FWD_UB = 4;
+        for (int e0 = threadIdx.x; e0 < nb * N; e0 += FWD_UB * NT) {
+            double vn[FWD_UB], vs[FWD_UB];
+            float2 cwh[FWD_UB], cwl[FWD_UB];
+#pragma unroll
+            for (int u = 0; u < FWD_UB; u++) {
+                const int e = e0 + u * NT;
+                vn[u] = 0.0; vs[u] = 0.0;
+                cwh[u] = make_float2(1.0f, 0.0f); cwl[u] = make_float2(0.0f, 0.0f);
+                if (e < nb * N) {
+                    const int s = e / N, n = e - s * N;
+                    const double* mp = map + (long long)(mc0 + s) * npix;
+                    vn[u] = mp[g.start_n + n];
+                    if (g.start_s >= 0) vs[u] = mp[g.start_s + n];
+                    if (f.bluestein) { cwh[u] = tb.chh[f.chirp + n]; cwl[u] = tb.chl[f.chirp + n]; }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < FWD_UB; u++) {
+                const int e = e0 + u * NT;
+                if (e < nb * N) {
+                    const int s = e / N, n = e - s * N;
+                    cx z = czero();
+                    tc::f64_split_scaled(vn[u], 0, z.hr, z.lr);
+                    if (g.start_s >= 0) tc::f64_split_scaled(vs[u], 0, z.hi, z.li);
+                    buf[s * M + placec(f, n)] = f.bluestein ? cmulc(z, cwh[u], cwl[u]) : z;
+                }
+            }
         }
         if (f.bluestein)
             for (int e = threadIdx.x; e < nb * (M - N); e += NT) {
@@ -374,52 +397,42 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         const FftLen f = ffts[g.fft];
         const int N = g.n;
         const float* g0 = G + (long long)p * ncol + mc0 * 2;
-        for (int j = threadIdx.x; j <= N / 2; j += NT) {
-            const int jj[2] = {j, (N - j) % N};
-            cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][map]
-    #pragma unroll
-            for (int t = 0; t < 2; t++) {
-                cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
-                for (int m = jj[t]; m <= mmax; m += N) {
-                    const float* e = g0 + (long long)m * 2 * qstride;
-                    float4 E4, O4;
-                    if (nb == 2 && (ncol & 3) == 0) {          // 16-byte aligned: ncol a multiple of 4
-                        E4 = *reinterpret_cast<const float4*>(e);
-                        O4 = *reinterpret_cast<const float4*>(e + qstride);
-                    } else if (nb == 2) {
-                        const float2 a0 = *reinterpret_cast<const float2*>(e), a1 = *reinterpret_cast<const float2*>(e + 2);
-                        const float2 b0 = *reinterpret_cast<const float2*>(e + qstride);
-                        const float2 b1 = *reinterpret_cast<const float2*>(e + qstride + 2);
-                        E4 = make_float4(a0.x, a0.y, a1.x, a1.y);
-                        O4 = make_float4(b0.x, b0.y, b1.x, b1.y);
-                    } else {
-                        const float2 E2 = *reinterpret_cast<const float2*>(e), O2 = *reinterpret_cast<const float2*>(e + qstride);
-                        E4 = make_float4(E2.x, E2.y, 0.0f, 0.0f);
-                        O4 = make_float4(O2.x, O2.y, 0.0f, 0.0f);
-                    }
-                    const float w = m ? 2.0f : 1.0f;
-                    float2 ph, pl;
-                    if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, ph, pl);
-    #pragma unroll
-                    for (int s = 0; s < 2; s++) {
-                        const float er = s ? E4.z : E4.x, ei = s ? E4.w : E4.y;
-                        const float orr = s ? O4.z : O4.x, oi = s ? O4.w : O4.y;
-                        cx tn, ts;
-                        two_sum(er, orr, tn.hr, tn.lr); two_sum(ei, oi, tn.hi, tn.li);
-                        two_sum(er, -orr, ts.hr, ts.lr); two_sum(ei, -oi, ts.hi, ts.li);
-                        tn = cscale(tn, w); ts = cscale(ts, w);
-                        if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
-                        sn[s] = caddc(sn[s], tn);
-                        ss[s] = caddc(ss[s], ts);
-                    }
-                }
-                Bn[t][0] = sn[0]; Bn[t][1] = sn[1]; Bs[t][0] = ss[0]; Bs[t][1] = ss[1];
+        // E and O of the two columns at order m (16-byte loads when aligned)
+        auto load_eo = [&](int m, float4& E4, float4& O4) {
+            const float* e = g0 + (long long)m * 2 * qstride;
+            if (nb == 2 && (ncol & 3) == 0) {          // 16-byte aligned: ncol a multiple of 4
+                E4 = *reinterpret_cast<const float4*>(e);
+                O4 = *reinterpret_cast<const float4*>(e + qstride);
+            } else if (nb == 2) {
+                const float2 a0 = *reinterpret_cast<const float2*>(e), a1 = *reinterpret_cast<const float2*>(e + 2);
+                const float2 b0 = *reinterpret_cast<const float2*>(e + qstride);
+                const float2 b1 = *reinterpret_cast<const float2*>(e + qstride + 2);
+                E4 = make_float4(a0.x, a0.y, a1.x, a1.y);
+                O4 = make_float4(b0.x, b0.y, b1.x, b1.y);
+            } else {
+                const float2 E2 = *reinterpret_cast<const float2*>(e), O2 = *reinterpret_cast<const float2*>(e + qstride);
+                E4 = make_float4(E2.x, E2.y, 0.0f, 0.0f);
+                O4 = make_float4(O2.x, O2.y, 0.0f, 0.0f);
             }
-    #pragma unroll
+        };
+        // column s's north / south terms of order m: w_m (E +- O) e^{+i m phi0}
+        auto term = [&](int m, const float4& E4, const float4& O4, float2 ph, float2 pl, int s, cx& tn, cx& ts) {
+            const float er = s ? E4.z : E4.x, ei = s ? E4.w : E4.y;
+            const float orr = s ? O4.z : O4.x, oi = s ? O4.w : O4.y;
+            two_sum(er, orr, tn.hr, tn.lr); two_sum(ei, oi, tn.hi, tn.li);
+            two_sum(er, -orr, ts.hr, ts.lr); two_sum(ei, -oi, ts.hi, ts.li);
+            const float w = m ? 2.0f : 1.0f;
+            tn = cscale(tn, w); ts = cscale(ts, w);
+            if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
+        };
+        // bins j and N - j of both columns into the transform buffer
+        auto emit = [&](int j, const cx (&Bn)[2][2], const cx (&Bs)[2][2]) {
+            const int jj[2] = {j, (N - j) % N};
+#pragma unroll
             for (int t = 0; t < 2; t++) {
                 const int jt = jj[t];
                 if (t == 1 && jt == jj[0]) break;
-    #pragma unroll
+#pragma unroll
                 for (int s = 0; s < 2; s++) {
                     if (s >= nb) break;
                     // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
@@ -428,6 +441,69 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                     const cx z = cconjc(caddc(hn, cmul_pi(hs)));
                     buf[s * M + placec(f, jt)] = chirp_in(f, tb, z, jt);
                 }
+            }
+        };
+        if (N > mmax) {
+            // every bin receives at most one order (m = j or m = N - j): the
+            // loads of BWD_JB bins per thread are all in flight before any is used
+            constexpr int BWD_JB = 2;
+            for (int j0 = threadIdx.x; j0 <= N / 2; j0 += BWD_JB * NT) {
+                float4 E[BWD_JB][2], O[BWD_JB][2];
+                float2 PH[BWD_JB][2], PL[BWD_JB][2];
+#pragma unroll
+                for (int u = 0; u < BWD_JB; u++) {
+                    const int j = j0 + u * NT;
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const int m = t ? (N - j) % N : j;
+                        E[u][t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); O[u][t] = E[u][t];
+                        PH[u][t] = make_float2(1.0f, 0.0f); PL[u][t] = make_float2(0.0f, 0.0f);
+                        if (j <= N / 2 && m <= mmax) {
+                            load_eo(m, E[u][t], O[u][t]);
+                            if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, PH[u][t], PL[u][t]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < BWD_JB; u++) {
+                    const int j = j0 + u * NT;
+                    if (j > N / 2) break;
+                    cx Bn[2][2], Bs[2][2];                 // [bin j / N - j][column]
+#pragma unroll
+                    for (int t = 0; t < 2; t++) {
+                        const int m = t ? (N - j) % N : j;
+#pragma unroll
+                        for (int s = 0; s < 2; s++) {
+                            Bn[t][s] = czero(); Bs[t][s] = czero();
+                            if (m <= mmax) term(m, E[u][t], O[u][t], PH[u][t], PL[u][t], s, Bn[t][s], Bs[t][s]);
+                        }
+                    }
+                    emit(j, Bn, Bs);
+                }
+            }
+        } else {
+            for (int j = threadIdx.x; j <= N / 2; j += NT) {
+                const int jj[2] = {j, (N - j) % N};
+                cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][column]
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+                    cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
+                    for (int m = jj[t]; m <= mmax; m += N) {
+                        float4 E4, O4;
+                        load_eo(m, E4, O4);
+                        float2 ph = make_float2(1.0f, 0.0f), pl = make_float2(0.0f, 0.0f);
+                        if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, ph, pl);
+#pragma unroll
+                        for (int s = 0; s < 2; s++) {
+                            cx tn, ts;
+                            term(m, E4, O4, ph, pl, s, tn, ts);
+                            sn[s] = caddc(sn[s], tn);
+                            ss[s] = caddc(ss[s], ts);
+                        }
+                    }
+                    Bn[t][0] = sn[0]; Bn[t][1] = sn[1]; Bs[t][0] = ss[0]; Bs[t][1] = ss[1];
+                }
+                emit(j, Bn, Bs);
             }
         }
         if (f.bluestein)
