@@ -31,41 +31,64 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
-// x * w with w = wh + wl (hi/lo twiddle); the products of the hi parts are
-// error-free (FMA residuals) and their sum a TwoSum, so only the lo terms round
-__device__ __forceinline__ cx cmulc(const cx& x, float2 wh, float2 wl)
+// additions on the (re, im) pairs as packed FP32x2 operations (both lanes at
+// once; every lane rounds exactly as the scalar TwoSum would)
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
 {
-    cx t;
-    float s, e;
-    {
-        const float p1 = __fmul_rn(x.hr, wh.x), p2 = __fmul_rn(x.hi, wh.y);
-        const float e1 = fmaf(x.hr, wh.x, -p1), e2 = fmaf(x.hi, wh.y, -p2);
-        two_sum(p1, -p2, s, e);
-        t.hr = s;
-        t.lr = (e + (e1 - e2)) + (x.lr * wh.x - x.li * wh.y) + (x.hr * wl.x - x.hi * wl.y);
-    }
-    {
-        const float p1 = __fmul_rn(x.hr, wh.y), p2 = __fmul_rn(x.hi, wh.x);
-        const float e1 = fmaf(x.hr, wh.y, -p1), e2 = fmaf(x.hi, wh.x, -p2);
-        two_sum(p1, p2, s, e);
-        t.hi = s;
-        t.li = (e + (e1 + e2)) + (x.lr * wh.y + x.li * wh.x) + (x.hr * wl.y + x.hi * wl.x);
-    }
-    return t;
+    return tc::f2_pack(__float_as_uint(a), __float_as_uint(b));
+}
+__device__ __forceinline__ void up2(unsigned long long v, float& a, float& b)
+{
+    uint32_t x, y;
+    tc::f2_unpack(v, x, y);
+    a = __uint_as_float(x);
+    b = __uint_as_float(y);
 }
 __device__ __forceinline__ cx caddc(const cx& a, const cx& b)
 {
-    cx s; float e;
-    two_sum(a.hr, b.hr, s.hr, e); s.lr = a.lr + b.lr + e;
-    two_sum(a.hi, b.hi, s.hi, e); s.li = a.li + b.li + e;
+    using namespace tc;
+    const unsigned long long A = pk2(a.hr, a.hi), B = pk2(b.hr, b.hi);
+    const unsigned long long S = f2_add(A, B), BB = f2_sub(S, A);
+    const unsigned long long E = f2_add(f2_sub(A, f2_sub(S, BB)), f2_sub(B, BB));
+    const unsigned long long L = f2_add(f2_add(pk2(a.lr, a.li), pk2(b.lr, b.li)), E);
+    cx s;
+    up2(S, s.hr, s.hi);
+    up2(L, s.lr, s.li);
     return s;
 }
+// a - b: TwoSum of a and -b, written with subtractions ((-b) - bb = -(b + bb) exactly)
 __device__ __forceinline__ cx csubc(const cx& a, const cx& b)
 {
-    cx s; float e;
-    two_sum(a.hr, -b.hr, s.hr, e); s.lr = a.lr - b.lr + e;
-    two_sum(a.hi, -b.hi, s.hi, e); s.li = a.li - b.li + e;
+    using namespace tc;
+    const unsigned long long A = pk2(a.hr, a.hi), B = pk2(b.hr, b.hi);
+    const unsigned long long S = f2_sub(A, B), BB = f2_sub(S, A);
+    const unsigned long long E = f2_sub(f2_sub(A, f2_sub(S, BB)), f2_add(B, BB));
+    const unsigned long long L = f2_add(f2_sub(pk2(a.lr, a.li), pk2(b.lr, b.li)), E);
+    cx s;
+    up2(S, s.hr, s.hi);
+    up2(L, s.lr, s.li);
     return s;
+}
+// x * w with w = wh + wl (hi/lo twiddle); the products of the hi parts are
+// error-free (FMA residuals) and their sum a TwoSum, so only the lo terms
+// round. Packed: lane 0 the real part, lane 1 the imaginary part.
+__device__ __forceinline__ cx cmulc(const cx& x, float2 wh, float2 wl)
+{
+    using namespace tc;
+    const unsigned long long WH = pk2(wh.x, wh.y), WS = pk2(-wh.y, wh.x);
+    const unsigned long long XR = pk2(x.hr, x.hr), XI = pk2(x.hi, x.hi);
+    const unsigned long long P1 = f2_mul(XR, WH), P2 = f2_mul(XI, WS);      // (hr wx, hr wy), (-hi wy, hi wx)
+    // minus the rounding errors of P1 and P2 (exact)
+    const unsigned long long N1 = f2_fma(pk2(-x.hr, -x.hr), WH, P1), N2 = f2_fma(pk2(-x.hi, -x.hi), WS, P2);
+    const unsigned long long S = f2_add(P1, P2), BB = f2_sub(S, P1);
+    const unsigned long long E = f2_add(f2_sub(P1, f2_sub(S, BB)), f2_sub(P2, BB));
+    const unsigned long long Q1 = f2_fma(pk2(x.li, x.li), WS, f2_mul(pk2(x.lr, x.lr), WH));
+    const unsigned long long Q2 = f2_fma(XI, pk2(-wl.y, wl.x), f2_mul(XR, pk2(wl.x, wl.y)));
+    const unsigned long long L = f2_add(f2_add(f2_sub(E, f2_add(N1, N2)), Q1), Q2);
+    cx t;
+    up2(S, t.hr, t.hi);
+    up2(L, t.lr, t.li);
+    return t;
 }
 __device__ __forceinline__ cx cscale(cx a, float s) { a.hr *= s; a.hi *= s; a.lr *= s; a.li *= s; return a; }
 __device__ __forceinline__ cx cconjc(cx a) { a.hi = -a.hi; a.li = -a.li; return a; }
