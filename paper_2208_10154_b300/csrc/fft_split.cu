@@ -110,11 +110,20 @@ struct FftTabsF {
     const long long* phoff;       // offset of each ring length's phase table
 };
 
-// twiddles of one FFT size M, staged in shared memory: tw[u] = exp(-2 pi i u / M),
-// u < M / 2, as (hi re, hi im, lo re, lo im)
+// twiddles of one FFT size M, staged in shared memory: exp(-2 pi i u / M),
+// u < M / 2, as (hi re, hi im, lo re, lo im), at slot tw_slot(u). A pass reads
+// u = k s for a power-of-two stride s, which in a plain table puts every lane
+// of a warp on the same banks; XOR-ing the low three bits of u (the 16-byte
+// slot within 128 bytes) with a fold of the higher bits spreads them (a
+// bijection within each aligned block of eight).
+__device__ __forceinline__ int tw_slot(int u)
+{
+    const int v = u >> 3;
+    return u ^ ((v ^ (v >> 3) ^ (v >> 6) ^ (v >> 9)) & 7);
+}
 __device__ __forceinline__ void twid(const float4* tw, int idx, bool inv, float2& wh, float2& wl)
 {
-    const float4 v = tw[idx];
+    const float4 v = tw[tw_slot(idx)];
     wh = make_float2(v.x, inv ? -v.y : v.y);
     wl = make_float2(v.z, inv ? -v.w : v.w);
 }
@@ -124,7 +133,7 @@ __device__ __forceinline__ void stage_twiddles(float4* tw, int M, int fftmax, co
     const int st = fftmax / M;
     for (int u = threadIdx.x; u < M / 2; u += blockDim.x) {
         const float2 h = t.twh[u * st], l = t.twl[u * st];
-        tw[u] = make_float4(h.x, h.y, l.x, l.y);
+        tw[tw_slot(u)] = make_float4(h.x, h.y, l.x, l.y);
     }
 }
 
