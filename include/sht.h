@@ -144,9 +144,10 @@ sht_status sht_map2alm_host(sht_plan* plan, const void* map_host, void* alm_host
 
 /* alm2map without any device allocation (the paper has no counterpart; this
  * is a library convenience). For callers that cannot allocate device memory
- * while they run -- code inside a CUDA-graph capture region, a serving loop
- * that must not touch the allocator, or a host framework that owns all GPU
- * memory -- and so cannot provide the workspace sht_alm2map needs. Same
+ * while they run -- a latency-critical serving loop that must not touch the
+ * allocator (cudaMalloc can synchronise the device), or a host framework
+ * that owns all GPU memory and hands the library only its inputs and
+ * outputs -- and so cannot provide the workspace sht_alm2map needs. Same
  * transform, layouts and stream semantics as sht_alm2map on an SHT_FP64 plan
  * (other precisions return SHT_EUNSUPPORTED); the caller passes only the
  * inputs and outputs. The intermediate matrix lives in one static device

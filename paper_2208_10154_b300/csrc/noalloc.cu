@@ -2,10 +2,10 @@
 // not allocate device memory at call time.
 //
 // Who needs this: code that runs where cudaMalloc is not allowed or not
-// wanted -- inside a region that is being captured into a CUDA graph (an
-// allocation there breaks the capture), a latency-critical serving loop that
-// must never hit the allocator, or an embedding framework that owns all
-// device memory and gives the library only its input and output buffers.
+// wanted -- a latency-critical serving loop that must never hit the
+// allocator (cudaMalloc can synchronise the whole device), or an embedding
+// framework that owns all device memory and gives the library only its
+// input and output buffers.
 // Such callers cannot supply the workspace that sht_alm2map needs for the
 // intermediate ring-coefficient matrix G[m][q][p][c], so this entry point
 // keeps that matrix in a fixed, file-scope device array instead.

@@ -1,6 +1,6 @@
 """GPU test of sht_alm2map_noalloc, the alm2map entry point for callers that
-cannot allocate device memory while they run (graph capture, allocation-free
-serving loops, frameworks that own all GPU memory). It is called through the
+cannot allocate device memory while they run (allocation-free serving loops,
+frameworks that own all GPU memory). It is called through the
 C ABI twice in a row, on different inputs, and must match sht_alm2map (the
 workspace-based entry point) within the FP64 tolerance of the other tests.
 This file is collected last so a failure here cannot hide another test."""
