@@ -59,6 +59,7 @@
 //                epilogue with warps 0-3
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -1353,21 +1354,14 @@ static cudaError_t launch_slice(int nunits, const void* src, uint8_t* img, const
     return cudaGetLastError();
 }
 
+// one launch of the contraction over work items [0, nwork) of a.work with
+// clusters of C CTAs along the column tiles (halved until a launch succeeds)
 template <bool M2A, bool S2>
-static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
-                             const TcArgs& a, const char* name, cudaStream_t st)
+static cudaError_t launch_grid(int nwork, int C, void* dst, const TcArgs& a, cudaStream_t st)
 {
-    (void)p;
     auto kern = k_leg_tc<M2A, S2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
-    if (e != cudaSuccess) return e;
     const long long ntiles = (a.ncol + TC_M - 1) / TC_M;
-    int C = pick_cluster(ntiles);
-    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        (void)cudaGetLastError();
-        C = 8;
-    }
-    prof_start(name, st);
+    cudaError_t e = cudaSuccess;
     for (;;) {
         const long long gy = (ntiles + C - 1) / C * C;
         cudaLaunchConfig_t cfg = {};
@@ -1386,6 +1380,84 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
         if (e == cudaSuccess || C == 1) break;
         (void)cudaGetLastError();      // clear a failed cluster launch, retry smaller
         C = std::max(1, C / 2);
+    }
+    return e;
+}
+
+// Filling the SMs that large clusters leave idle. With one 227 KB CTA per SM a
+// cluster of C CTAs needs C free SMs in one GPC, so clusters of 8 occupy only
+// 120 of this GPU's 148 SMs. When the main launch uses clusters of 8 or more,
+// a share of the work items (the last ones: the cheapest alm2map items) goes
+// to a second launch with small clusters on a low-priority helper stream of
+// the device, forked from and joined back into the caller's stream; the two
+// launches never wait on each other, and each work item computes exactly
+// what it would in one launch. SHT_FILL_FRAC: share of the work items for
+// that launch (default 0.06; 0 turns it off); SHT_FILL_CLUSTER: its cluster
+// size (default 2).
+struct FillCfg { double frac; int cluster; };
+static FillCfg fill_cfg()
+{
+    static FillCfg f = [] {
+        FillCfg c{0.06, 2};
+        if (const char* e = std::getenv("SHT_FILL_FRAC")) c.frac = std::max(0.0, std::min(0.5, std::atof(e)));
+        if (const char* e = std::getenv("SHT_FILL_CLUSTER")) c.cluster = std::max(1, std::min(8, std::atoi(e)));
+        return c;
+    }();
+    return f;
+}
+struct FillStream { cudaStream_t s = nullptr; cudaEvent_t fork = nullptr, join = nullptr; bool ok = false, tried = false; };
+static FillStream g_fill[64];
+static std::mutex g_fill_mu;           // one fork / launch / join sequence at a time (shared events)
+static FillStream* fill_stream()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    FillStream& f = g_fill[dev];
+    if (!f.tried) {
+        f.tried = true;
+        int lo = 0, hi = 0;
+        f.ok = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+               cudaStreamCreateWithPriority(&f.s, cudaStreamNonBlocking, lo) == cudaSuccess &&
+               cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) == cudaSuccess;
+        if (!f.ok) (void)cudaGetLastError();
+    }
+    return f.ok ? &f : nullptr;
+}
+
+template <bool M2A, bool S2>
+static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
+                             const TcArgs& a, const char* name, cudaStream_t st)
+{
+    (void)p;
+    auto kern = k_leg_tc<M2A, S2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_TC);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (a.ncol + TC_M - 1) / TC_M;
+    int C = pick_cluster(ntiles);
+    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        C = 8;
+    }
+    const FillCfg fc = fill_cfg();
+    std::unique_lock<std::mutex> lk(g_fill_mu, std::defer_lock);
+    int nB = (fc.frac > 0.0 && C >= 8 && C > fc.cluster) ? (int)(fc.frac * nwork + 0.5) : 0;
+    if (nB > 0) lk.lock();
+    FillStream* fs = (nB > 0) ? fill_stream() : nullptr;
+    if (!fs) nB = 0;
+    prof_start(name, st);
+    if (nB > 0) {
+        if ((e = cudaEventRecord(fs->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(fs->s, fs->fork, 0)) != cudaSuccess) return e;
+    }
+    e = launch_grid<M2A, S2>(nwork - nB, C, dst, a, st);
+    if (e == cudaSuccess && nB > 0) {
+        TcArgs b = a;
+        b.work = a.work + (nwork - nB);
+        e = launch_grid<M2A, S2>(nB, fc.cluster, dst, b, fs->s);
+        if (e == cudaSuccess) e = cudaEventRecord(fs->join, fs->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, fs->join, 0);
+        count_launch();
     }
     prof_stop(st);
     count_launch();
