@@ -137,19 +137,28 @@ __device__ __forceinline__ void stage_twiddles(float4* tw, int M, int fftmax, co
     }
 }
 
-// In-place decimation-in-time FFTs of nb sequences of M = 2^L points stored
-// back to back in buf, input in bit-reversed order, output natural. Two
-// radix-2 stages (spans h and 2h) per pass; W = exp(-+2 pi i / M).
+// Transform buffers in shared memory: sequence s of a size-M class starts at
+// s * fft_pad_len(M), and its point i sits at fft_pad(i). One 16-byte slot of
+// padding per 8 points and one more per 64 keep the 16-byte accesses of a
+// warp on distinct banks for the bit-reversed input scatter, the first
+// small-span passes and the consecutive runs of the other phases.
+__host__ __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 3) + (i >> 6); }
+__host__ __device__ __forceinline__ int fft_pad_len(int M) { return M + (M >> 3) + (M >> 6); }
+
+// In-place decimation-in-time FFTs of nb sequences of M = 2^L points (padded
+// layout above), input in bit-reversed order, output natural. Two radix-2
+// stages (spans h and 2h) per pass; W = exp(-+2 pi i / M).
 __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
 {
-    const int M = 1 << L;
+    const int M = 1 << L, P = fft_pad_len(M);
     int lh = 0;
     if (L & 1) {                                     // one radix-2 stage of span 1 (twiddle 1)
         for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
-            cx* x = buf + 2 * b;
-            const cx a = x[0], c = x[1];
-            x[0] = caddc(a, c);
-            x[1] = csubc(a, c);
+            cx* x = buf + (b >> (L - 1)) * P;
+            const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
+            const cx a = x[i0], c = x[i1];
+            x[i0] = caddc(a, c);
+            x[i1] = csubc(a, c);
         }
         __syncthreads();
         lh = 1;
@@ -161,8 +170,10 @@ __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
         for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
             const int f = b >> (L - 2), g = b & (ng - 1);
             const int k = g & (h - 1);
-            cx* y = buf + f * M + ((g - k) << 2) + k;
-            cx x0 = y[0], x1 = y[h], x2 = y[2 * h], x3 = y[3 * h];
+            cx* y = buf + f * P;
+            const int y0 = ((g - k) << 2) + k;
+            const int i0 = fft_pad(y0), i1 = fft_pad(y0 + h), i2 = fft_pad(y0 + 2 * h), i3 = fft_pad(y0 + 3 * h);
+            cx x0 = y[i0], x1 = y[i1], x2 = y[i2], x3 = y[i3];
             // (the branch is per pass, not per lane: for k = 0 the twiddled
             // path multiplies by exactly 1, and a warp whose lanes took both
             // paths would execute both)
@@ -175,13 +186,13 @@ __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
                 const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
                 const cx u2 = cmulc(b2, w2h, w2l);
                 const cx u3 = inv ? cmul_pi(cmulc(b3, w2h, w2l)) : cmul_mi(cmulc(b3, w2h, w2l));
-                y[0] = caddc(b0, u2); y[2 * h] = csubc(b0, u2);
-                y[h] = caddc(b1, u3); y[3 * h] = csubc(b1, u3);
+                y[i0] = caddc(b0, u2); y[i2] = csubc(b0, u2);
+                y[i1] = caddc(b1, u3); y[i3] = csubc(b1, u3);
             } else {
                 const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
                 const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
-                y[0] = caddc(b0, b2); y[2 * h] = csubc(b0, b2);
-                y[h] = caddc(b1, u3); y[3 * h] = csubc(b1, u3);
+                y[i0] = caddc(b0, b2); y[i2] = csubc(b0, b2);
+                y[i1] = caddc(b1, u3); y[i3] = csubc(b1, u3);
             }
         }
         __syncthreads();
@@ -192,7 +203,7 @@ __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
 // two radix-2 stages (spans h and h/2) per pass.
 __device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
 {
-    const int M = 1 << L;
+    const int M = 1 << L, P = fft_pad_len(M);
     int lh = L - 1;
     for (; lh >= 1; lh -= 2) {
         const int h = 1 << lh, hq = h >> 1;
@@ -201,8 +212,10 @@ __device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
         for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
             const int f = b >> (L - 2), g = b & (ng - 1);
             const int k = g & (hq - 1);
-            cx* y = buf + f * M + ((g - k) << 2) + k;
-            const cx x0 = y[0], x1 = y[hq], x2 = y[h], x3 = y[h + hq];
+            cx* y = buf + f * P;
+            const int y0 = ((g - k) << 2) + k;
+            const int i0 = fft_pad(y0), i1 = fft_pad(y0 + hq), i2 = fft_pad(y0 + h), i3 = fft_pad(y0 + h + hq);
+            const cx x0 = y[i0], x1 = y[i1], x2 = y[i2], x3 = y[i3];
             cx c0 = caddc(x0, x2), c2 = csubc(x0, x2), c1 = caddc(x1, x3), c3 = csubc(x1, x3);
             c3 = inv ? cmul_pi(c3) : cmul_mi(c3);
             if (hq > 1) {                            // per pass (see fft_dit)
@@ -211,21 +224,22 @@ __device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
                 twid(tw, k * s2, inv, v2h, v2l);
                 c2 = cmulc(c2, v1h, v1l);
                 c3 = cmulc(c3, v1h, v1l);
-                y[0] = caddc(c0, c1); y[hq] = cmulc(csubc(c0, c1), v2h, v2l);
-                y[h] = caddc(c2, c3); y[h + hq] = cmulc(csubc(c2, c3), v2h, v2l);
+                y[i0] = caddc(c0, c1); y[i1] = cmulc(csubc(c0, c1), v2h, v2l);
+                y[i2] = caddc(c2, c3); y[i3] = cmulc(csubc(c2, c3), v2h, v2l);
             } else {
-                y[0] = caddc(c0, c1); y[hq] = csubc(c0, c1);
-                y[h] = caddc(c2, c3); y[h + hq] = csubc(c2, c3);
+                y[i0] = caddc(c0, c1); y[i1] = csubc(c0, c1);
+                y[i2] = caddc(c2, c3); y[i3] = csubc(c2, c3);
             }
         }
         __syncthreads();
     }
     if (lh == 0) {                                   // last radix-2 stage of span 1
         for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
-            cx* x = buf + 2 * b;
-            const cx a = x[0], c = x[1];
-            x[0] = caddc(a, c);
-            x[1] = csubc(a, c);
+            cx* x = buf + (b >> (L - 1)) * P;
+            const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
+            const cx a = x[i0], c = x[i1];
+            x[i0] = caddc(a, c);
+            x[i1] = csubc(a, c);
         }
         __syncthreads();
     }
@@ -234,7 +248,7 @@ __device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
 // forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of nb sequences placed by placec()
 __device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const FftTabsF& t)
 {
-    const int M = f.m, L = 31 - __clz(M);
+    const int M = f.m, L = 31 - __clz(M), P = fft_pad_len(M);
     if (!f.bluestein) {
         fft_dit(buf, nb, L, tw, false);
         return;
@@ -242,14 +256,16 @@ __device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw,
     fft_dif(buf, nb, L, tw, false);
     for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
         const int ii = i & (M - 1);
-        buf[i] = cmulc(buf[i], t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
+        cx& z = buf[(i >> L) * P + fft_pad(ii)];
+        z = cmulc(z, t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
     }
     __syncthreads();
     fft_dit(buf, nb, L, tw, true);
     const float inv = 1.0f / (float)M;
     for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
         const int s = i / f.n, k = i - s * f.n;
-        buf[s * M + k] = cscale(cmulc(buf[s * M + k], t.chh[f.chirp + k], t.chl[f.chirp + k]), inv);
+        cx& z = buf[s * P + fft_pad(k)];
+        z = cscale(cmulc(z, t.chh[f.chirp + k], t.chl[f.chirp + k]), inv);
     }
     __syncthreads();
 }
@@ -291,7 +307,8 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * M * sizeof(cx));
+    const int P = fft_pad_len(M);
+    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
     stage_twiddles(tw, M, fftmax, tb);              // (the first __syncthreads below publishes it)
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
@@ -335,14 +352,14 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                     cx z = czero();
                     tc::f64_split_scaled(vn[u], 0, z.hr, z.lr);
                     if (g.start_s >= 0) tc::f64_split_scaled(vs[u], 0, z.hi, z.li);
-                    buf[s * M + placec(f, n)] = f.bluestein ? cmulc(z, cwh[u], cwl[u]) : z;
+                    buf[s * P + fft_pad(placec(f, n))] = f.bluestein ? cmulc(z, cwh[u], cwl[u]) : z;
                 }
             }
         }
         if (f.bluestein)
             for (int e = threadIdx.x; e < nb * (M - N); e += NT) {
                 const int s = e / (M - N), i = e - s * (M - N);
-                buf[s * M + N + i] = czero();
+                buf[s * P + fft_pad(N + i)] = czero();
             }
         __syncthreads();
         dftc_forward(buf, nb, f, tw, tb);
@@ -357,7 +374,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 #pragma unroll
             for (int s = 0; s < 2; s++) {
                 if (s >= nb) break;
-                const cx a = buf[s * M + j], b = cconjc(buf[s * M + jm]);
+                const cx a = buf[s * P + fft_pad(j)], b = cconjc(buf[s * P + fft_pad(jm)]);
                 // Xn = (a + conj b)/2, Xs = (a - conj b)/(2i)
                 cx Xn = cscale(caddc(a, b), 0.5f);
                 const cx d = cscale(csubc(a, b), 0.5f);
@@ -417,7 +434,8 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
-    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * M * sizeof(cx));
+    const int P = fft_pad_len(M);
+    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
     stage_twiddles(tw, M, fftmax, tb);              // (published by the __syncthreads before the FFT)
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
@@ -471,7 +489,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                     const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
                     const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
                     const cx z = cconjc(caddc(hn, cmul_pi(hs)));
-                    buf[s * M + placec(f, jt)] = chirp_in(f, tb, z, jt);
+                    buf[s * P + fft_pad(placec(f, jt))] = chirp_in(f, tb, z, jt);
                 }
             }
         };
@@ -541,13 +559,13 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         if (f.bluestein)
             for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
                 const int s = e / (M - N), i = e - s * (M - N);
-                buf[s * M + N + i] = czero();
+                buf[s * P + fft_pad(N + i)] = czero();
             }
         __syncthreads();
         dftc_forward(buf, nb, f, tw, tb);
         for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
             const int s = e / N, n = e - s * N;
-            const cx z = buf[s * M + n];               // conj of the inverse transform
+            const cx z = buf[s * P + fft_pad(n)];      // conj of the inverse transform
             double* mp = map + (long long)(mc0 + s) * npix;
             mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
             if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi) + tc::f32_to_f64(z.li));
@@ -568,13 +586,13 @@ static FftTabsF tabs(const sht_plan* p)
 }
 
 // FFT size classes of the plan: launch configuration per class (two map
-// columns per CTA while their buffers fit in 128 KB of shared memory), plus
-// the class's twiddles (M / 2 x 16 bytes)
+// columns per CTA while their unpadded buffers fit in 128 KB of shared
+// memory), the padded buffers plus the class's twiddles (M / 2 x 16 bytes)
 static void class_cfg(int M, int mmax, int& nt, int& mpc, size_t& sm)
 {
     nt = (M >= 4096 || mmax >= 1024) ? 512 : 256;
     mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
-    sm = (size_t)mpc * M * sizeof(cx) + (size_t)(M / 2) * sizeof(float4);
+    sm = (size_t)mpc * fft_pad_len(M) * sizeof(cx) + (size_t)(M / 2) * sizeof(float4);
 }
 
 static cudaError_t set_smem(const void* fn, const sht_plan* p)
