@@ -15,6 +15,7 @@ rank's time is used.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -451,6 +452,7 @@ def run_serving(n_req, load, device):
             "offered_requests_per_s": rate, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"],
             "maps_per_s": opened["maps_per_s"], "batches": opened["batches"],
             "saturation_maps_per_s": closed["maps_per_s"], "errors": opened["errors"] + closed["errors"],
+            "first_error": next((r.error for r in srv.completed if r.error), None),
             "peak_admitted_gb": srv.peak_used / 1e9,
             "workload": "Poisson stream; alm2map/map2alm 50/50; nside 64/128/256/512/1024 "
                         "(0.3/0.3/0.2/0.15/0.05); spin 2 in 30%; 1-64 maps per request (inputs from pools "
@@ -676,6 +678,11 @@ def main():
 
     serving = None
     if rank == 0 and a.serve_requests > 0:
+        # the serving run admits up to 150 GB of batches: release the step's
+        # plans (and their host-path staging buffers) and cached blocks first
+        plan = plan64 = None
+        gc.collect()
+        torch.cuda.empty_cache()
         serving = run_serving(a.serve_requests, a.serve_load, dev)
 
     if rank == 0:
