@@ -34,7 +34,7 @@ SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split
 # DRAM traffic (read + write) of one launch from an ncu capture of the same
 # kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
 # and lmax it grows in proportion to the map columns (profiles/k_leg_tc_nside512.md)
-TRAFFIC_NCU = {"k_leg_a2m_tc": 5.544e9, "k_leg_m2a_tc": 6.003e9}
+TRAFFIC_NCU = {"k_leg_a2m_tc": 5.557e9, "k_leg_m2a_tc": 6.000e9}
 TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
 
