@@ -86,11 +86,13 @@ def test_split_adjoints_and_iteration(orc, sht):
                   orc.map2alm(h, nside, lmax, niter=2)) < TOL
 
 
-@pytest.mark.parametrize("nside,lmax,nmaps", [(128, 300, 300), (64, 160, 1100)])
+@pytest.mark.parametrize("nside,lmax,nmaps", [(128, 300, 300), (64, 160, 1100), (64, 160, 1024)])
 def test_split_clusters_many_chunks(orc, sht, nside, lmax, nmaps):
     """Several column tiles per cluster and more K chunks than pipeline stages
     (stage reuse across the cluster); the oracle checks a few maps spread over
-    the column tiles (map columns are independent)."""
+    the column tiles (map columns are independent). 1024 maps = 16 column
+    tiles: clusters of 8, with the last work items (the highest m) in the
+    small-cluster launch that fills the SMs the large clusters leave idle."""
     a = inputs.gaussian_alm(nside + 5, nmaps, 1, lmax, cls=inputs.cl_inv_llp1(lmax))
     plan = sht.Plan(nside, lmax, None, 0, "split")
     pick = [0, nmaps // 2 + 1, nmaps - 1]
