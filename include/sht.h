@@ -25,7 +25,13 @@
  *     written as 0 on output; for spin 2, l < 2 is ignored / written as 0.
  *   - map2alm uses the constant pixel weight dsigma = 4 pi / Npix (Sec. 2.1).
  *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
- *     NULL = legacy default stream); nothing synchronises the host.
+ *     NULL = legacy default stream); nothing synchronises the host. A
+ *     split-precision contraction wide enough for clusters of 8 column tiles
+ *     (>= 1024 map columns) runs its last work items on a low-priority
+ *     internal stream of the device, forked from `stream` and joined back to
+ *     it with events inside the call, so work ordered after the call on
+ *     `stream` sees the complete result (environment SHT_FILL_FRAC=0 keeps
+ *     everything on `stream`).
  *   - `workspace` is caller-owned device memory of at least
  *     sht_workspace_bytes(plan, nmaps) bytes, 256-byte aligned. Concurrent
  *     calls on different streams need distinct workspaces.
