@@ -295,7 +295,7 @@ __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m,
 // of FWD_PB ring pairs of the class (neighbouring column pairs, which share
 // the cache lines of T, run together).
 // ---------------------------------------------------------------------------
-constexpr int FWD_PB = 64;
+constexpr int FWD_PB = 32;
 
 // NT threads; each thread owns m = threadIdx.x + jj NT, jj < 4 (mmax < 4 NT)
 template <int NT>
@@ -424,7 +424,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 // the IDFT of the Hermitian part. One launch per FFT size class; grid.x = pair
 // of map columns, grid.y = block of BWD_PB ring pairs of the class.
 // ---------------------------------------------------------------------------
-constexpr int BWD_PB = 16;
+constexpr int BWD_PB = 8;
 
 template <int NT>
 __global__ void __launch_bounds__(NT)
