@@ -4,10 +4,12 @@
 One step = alm2map + map2alm (spin 0) of one batch of maps at nside 512,
 lmax 1023, 1000 maps per GPU (the paper's batched-SHT scheme, Sec. 2.1-2.2),
 on synthetic Gaussian skies with C_l = 1/(l(l+1)) plus 1% white noise.
-Prints ONE JSON line (rank 0). With N > 1 (torchrun), every rank transforms
-its own batch (maps are independent columns: weak scaling, no collective on
-the data path); the timed region is bracketed by barriers and the slowest
-rank's time is used.
+Prints ONE JSON line. Single-GPU only: the split-form contraction shares
+lambda pieces inside thread-block clusters with TMA multicast loads, which
+this library keeps out of processes that drive more than one GPU. With
+--gpus N > 1 or WORLD_SIZE > 1 it prints an "unavailable" line and exits
+(maps are independent columns, so N GPUs serve N separate single-GPU
+processes; there is no exchange step to measure).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision auto|fp64|split]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
@@ -30,10 +32,12 @@ sys.path.insert(0, ROOT)
 METRIC = "maps/s batched vs per-map on one B300 at <=1e-6 rel err; served p50/p99 latency"
 WORKLOAD = "t_nside512"
 FP64_PEAK_TFLOPS = 1.25      # nominal B300 FP64 (recipe table); probe measured 1.13 at 2032 MHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12   # FP32 FMA lanes x clock (non-tensor)
 SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split form (4 FP16 slices)
-# DRAM traffic (read + write) of one launch from an ncu capture of the same
+# DRAM traffic (read + write) of one launch from an ncu capture of the current
 # kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
-# and lmax it grows in proportion to the map columns (profiles/k_leg_tc_nside512.md)
+# and lmax it grows in proportion to the map columns. Empty while the kernel
+# has changed since the last capture (the line then reports null).
 TRAFFIC_NCU = {"k_leg_a2m_tc": 5.557e9, "k_leg_m2a_tc": 6.000e9}
 TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
@@ -74,25 +78,19 @@ def dist_info():
     return rank, world, local
 
 
-def max_over_ranks(x: float, world: int, device) -> float:
-    """The slowest rank's time (replicas: the job ends when the last one does)."""
-    if world <= 1:
-        return float(x)
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+MULTI_GPU_UNAVAILABLE = ("single-GPU only: the split-form contraction multicasts lambda pieces inside "
+                         "thread-block clusters (TMA multicast from this GPU's own memory), which is kept out "
+                         "of multi-GPU processes; maps are independent columns with no exchange step")
 
 
-def rank_seed(rank: int) -> int:
-    """Input seed of a replica: seed 1 of the workload, offset by the rank."""
-    return 1 + rank
+def multi_gpu_requested(a) -> bool:
+    """True when the run asks for more than one GPU (flag or torchrun environment)."""
+    _, world, _ = dist_info()
+    return a.gpus > 1 or world > 1
 
 
-def job_throughput(nmaps_per_rank: int, world: int, seconds: float) -> float:
-    """Whole-job maps/s: the maps all ranks processed over the slowest rank's time."""
-    return world * nmaps_per_rank / seconds
+def unavailable_line(a) -> dict:
+    return {"metric": METRIC, "n_gpus": max(a.gpus, dist_info()[1]), "unavailable": MULTI_GPU_UNAVAILABLE}
 
 
 class ClockSampler:
@@ -156,6 +154,18 @@ def measured_peaks():
             return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def fft_flops_per_map(nside):
+    """Nominal flops of one direction's ring FFTs for one spin-0 map: one
+    complex FFT of N points per ring pair (the equator ring alone), counted as
+    5 N log2 N whatever its length."""
+    import math
+    tot = 0.0
+    for i in range(1, 2 * nside + 1):                 # ring pairs: north ring i with its mirror
+        n = 4 * i if i < nside else 4 * nside
+        tot += 5.0 * n * math.log2(n)
+    return tot
 
 
 def algorithmic_flops(nside, lmax, nmaps, spin=0):
@@ -464,21 +474,16 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if multi_gpu_requested(a):
+        if dist_info()[0] == 0:
+            print(json.dumps(unavailable_line(a)), flush=True)
+        return 0
     import numpy as np
     import torch
-    import torch.distributed as dist
     from paper_2208_10154_b300 import build, sht
-    rank, world, local = dist_info()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
+    torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    if rank == 0:
-        build.build()
-    if world > 1:
-        dist.barrier()
+    build.build()
     sht.load()
     nside, lmax, nmaps = a.nside, a.lmax, a.nmaps
     precision = a.precision
@@ -490,7 +495,7 @@ def main():
         except sht.ShtError:
             precision = "fp64"
 
-    # ---- inputs: Gaussian a_lm (seed 1 + rank), maps = alm2map(a) + 1% noise ----
+    # ---- inputs: Gaussian a_lm (seed 1), maps = alm2map(a) + 1% noise ----
     t0 = time.perf_counter()
     plan64 = sht.Plan(nside, lmax, None, 0, "fp64")
     plan = plan64 if precision == "fp64" else sht.Plan(nside, lmax, None, 0, precision)
@@ -500,7 +505,7 @@ def main():
     cl = inputs.cl_inv_llp1(lmax)[ls]
     sd = torch.from_numpy(np.where(ms == 0, np.sqrt(cl), np.sqrt(cl / 2.0))).cuda()
     g = torch.Generator(device="cuda")
-    g.manual_seed(rank_seed(rank))
+    g.manual_seed(1)
     re = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
     im = torch.randn((nmaps, 1, plan.nalm), generator=g, dtype=torch.float64, device="cuda") * sd
     im[..., torch.from_numpy(ms == 0).cuda()] = 0.0
@@ -531,8 +536,6 @@ def main():
     launches[0] = 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
     torch.cuda.synchronize()
     sht.sht_profile_begin()
     with ClockSampler(dev) as clk:
@@ -543,10 +546,8 @@ def main():
         torch.cuda.synchronize()
     prof = sht.sht_profile_end()
     plan.device_status()                 # raises if a bounded device wait gave up
-    if world > 1:
-        dist.barrier()
-    ms_step = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, "cuda")
-    value = job_throughput(nmaps, world, ms_step / 1e3)
+    ms_step = e0.elapsed_time(e1) / a.steps
+    value = nmaps / (ms_step / 1e3)
     gpu_launches = launches[0]
 
     # ---- per-map FP64 form (the paper's "one map at a time" baseline) ----
@@ -571,9 +572,8 @@ def main():
                    "samples": P}
         plan1._ws = None
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant Legendre kernel ----
     peaks, peak_src = measured_peaks()
-    # the contraction is the roofline kernel (the largest Legendre kernel of the step)
     legs = {k: v for k, v in prof.items() if "leg" in k} if prof else {}
     dom = max((legs or prof).items(), key=lambda kv: kv[1]["ms"]) if prof else None
     roofline = None
@@ -588,10 +588,11 @@ def main():
                         "peak_source": "nominal FP64 of the profiling recipe (no measured FP64 peak)",
                         "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
         elif "leg" in name:
-            # split form: eight FP16 slice products per (l, m, ring pair, column)
-            # on the tensor cores (kind::f16 runs at the bf16 rate)
-            ach_alg = flops / (avg_ms / 1e3) / 1e12
-            ach = SPLIT_PRODUCTS * ach_alg
+            # split form: `achieved` counts the method's own flops (4 per (l, m,
+            # ring pair, map)); the tensor cores execute SPLIT_PRODUCTS FP16
+            # slice products per term (kind::f16 runs at the bf16 rate), which
+            # `executed` reports against the same peak
+            ach = flops / (avg_ms / 1e3) / 1e12
             pk = peaks.get("bf16_tflops_sustained", 1400.0)
             traffic = None
             if name in TRAFFIC_NCU and (nside, lmax) == (TRAFFIC_NCU_AT["nside"], TRAFFIC_NCU_AT["lmax"]):
@@ -600,8 +601,9 @@ def main():
                         "frac": ach / pk, "traffic": traffic,
                         "traffic_source": "ncu capture at 128 maps, scaled by map columns" if traffic else None,
                         "peak_source": f"bf16 dense sustained ({peak_src}); the kernel runs inside a long step",
-                        "executed_flops_per_launch": SPLIT_PRODUCTS * flops, "algorithmic_tflops": ach_alg,
-                        "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
+                        "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms,
+                        "executed": {"products_per_term": SPLIT_PRODUCTS, "flops_per_launch": SPLIT_PRODUCTS * flops,
+                                     "achieved": SPLIT_PRODUCTS * ach, "frac": SPLIT_PRODUCTS * ach / pk}}
         else:
             byts = 8.0 * nmaps * plan.npix * 2
             ach = byts / (avg_ms / 1e3) / 1e9
@@ -609,19 +611,25 @@ def main():
                         "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
                         "peak_source": peak_src, "avg_launch_ms": avg_ms}
 
-    # ---- ring FFTs against HBM: algorithmic bytes of both directions per step
-    # (maps read and written in FP64; T written as FP32 hi/lo pairs, G read in FP32)
-    # over the summed device time of the FFT kernels ----
+    # ---- ring FFTs: against HBM (algorithmic bytes of both directions per
+    # step: maps read and written in FP64, T written as FP32 hi/lo pairs, G
+    # read in FP32) and against the FP32 ALU (5 N log2 N flops per complex
+    # ring-pair FFT of N points, both directions), over their summed time ----
     fft_roofline = None
     fft_ms = sum(v["ms"] for k, v in prof.items() if "fft" in k) / max(a.steps, 1) if prof else 0.0
     if fft_ms > 0:
         nring = 4 * nside - 1
         fft_bytes_map = 16.0 * plan.npix * plan.ncomp + (plan.mmax + 1) * nring * plan.ncomp * (16.0 + 8.0)
         ach = fft_bytes_map * nmaps / (fft_ms / 1e3) / 1e9
+        fft_flops = 2.0 * fft_flops_per_map(nside) * nmaps
+        ach_alu = fft_flops / (fft_ms / 1e3) / 1e12
         fft_roofline = {"kernels": "ring FFTs (all size classes, both directions)", "bound": "hbm",
                         "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": ach / peaks["hbm_gbs"],
                         "ms_per_step": fft_ms, "algorithmic_bytes_per_step": fft_bytes_map * nmaps,
-                        "note": "compensated FP32 (double-float) arithmetic: issue-bound, not HBM-bound"}
+                        "alu": {"bound": "alu", "achieved": ach_alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach_alu / FP32_PEAK_TFLOPS, "algorithmic_flops_per_step": fft_flops,
+                                "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
+                                "note": "each flop runs in double-float FP32 (~7 FP32 operations)"}}
 
     # ---- end to end through the host-buffer C-ABI entry points ----
     e2e = None
@@ -636,22 +644,20 @@ def main():
         torch.cuda.empty_cache()
         plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
         plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
-        if world > 1:
-            dist.barrier()
         t0 = time.perf_counter()
         ke = max(1, min(a.steps, 2))
         for _ in range(ke):
             plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
             plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
-        dt = max_over_ranks((time.perf_counter() - t0) / ke, world, "cuda")
+        dt = (time.perf_counter() - t0) / ke
         nb_alm = alm_h.numel() * 16
         nb_map = maps_h.numel() * 8
-        e2e = {"value": world * nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
+        e2e = {"value": nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
                "d2h_bytes_per_step": nb_map + nb_alm, "api": "sht_alm2map_host + sht_map2alm_host"}
 
     # ---- CPU baseline: the oracle on one map ----
     cpu = None
-    if rank == 0 and not a.no_cpu_baseline:
+    if not a.no_cpu_baseline:
         import oracle
         oracle.build()
         a1 = alm[:1].cpu().numpy()
@@ -666,18 +672,18 @@ def main():
     del alm, maps_in
     torch.cuda.empty_cache()
     context = None
-    if rank == 0 and not a.no_context:
+    if not a.no_context:
         context = run_context(precision)
     qu = None
-    if rank == 0 and a.qu_maps > 0:
+    if a.qu_maps > 0:
         qu = run_qu(nside, lmax, a.qu_maps, max(1, min(a.steps, 3)), max(1, min(a.warmup, 2)), precision)
 
     next_rows = None
-    if rank == 0 and not a.no_next_rows:
+    if not a.no_next_rows:
         next_rows = run_next_rows(nside, lmax, nmaps, 100, precision)
 
     serving = None
-    if rank == 0 and a.serve_requests > 0:
+    if a.serve_requests > 0:
         # the serving run admits up to 150 GB of batches: release the step's
         # plans (and their host-path staging buffers) and cached blocks first
         plan = plan64 = None
@@ -685,25 +691,22 @@ def main():
         torch.cuda.empty_cache()
         serving = run_serving(a.serve_requests, a.serve_load, dev)
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": world, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "bf16+f64",
-            "data": "synthetic",
-            "config": dict(ref_config(a), precision=precision, direction="alm2map+map2alm per step",
-                           l2="inputs larger than L2 (maps 25.2 GB per GPU), no flush",
-                           parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
-            "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
-            "roofline_fft": fft_roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
-            "batched_over_per_map": (value / world) / per_map["value"] if per_map else None,
-            "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "next_rows": next_rows,
-            "serving": serving,
-        }
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    line = {
+        "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f16+f64",
+        "data": "synthetic",
+        "config": dict(ref_config(a), precision=precision, direction="alm2map+map2alm per step",
+                       l2="inputs larger than L2 (maps 25.2 GB per GPU), no flush",
+                       parallelism="single GPU"),
+        "clocks": clk.summary(), "gpu_launches": gpu_launches, "roofline": roofline,
+        "roofline_fft": fft_roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
+        "batched_over_per_map": value / per_map["value"] if per_map else None,
+        "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "next_rows": next_rows,
+        "serving": serving,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 

@@ -62,14 +62,23 @@ typedef enum {
 typedef enum {
     /* Every step in FP64 (FFT, lambda recurrence, contraction). */
     SHT_FP64 = 0,
-    /* Contraction on the 16-bit tensor cores (tcgen05 kind::f16 with FP16
-     * operands, FP32 TMEM accumulation): each operand = exact integer main
-     * slice + a slice on the 2^-12 grid + an FP16 residual; the main and
-     * integer-grid products accumulate exactly; lambda recurrence in FP64;
-     * ring FFTs in compensated FP32; final accumulation into a_lm in FP64.
+    /* Split precision: the Legendre contraction on the 16-bit tensor cores
+     * (tcgen05 kind::f16, FP16 operands, FP32 accumulation in TMEM). Every
+     * operand value, scaled by a power-of-two quantum, is written as four
+     * FP16 slices: its nearest integer, a remainder on the fixed grid 2^-10
+     * (2^-11 for spin-2 map2alm), the next 11 bits, and their rounding error
+     * scaled by 2^12. Ten slice products per term; the integer and fixed-grid
+     * sums are exact and the rest are folded into the integer sum every 64 or
+     * 128 steps of K; the final sums are formed in FP64. The lambda_lm
+     * recurrence is walked in FP64 with scaled exponents when the plan is
+     * built, which stores FP64 checkpoints every 32 rows; the kernels step
+     * from a checkpoint in double-float FP32 pairs (~48 bits). Ring FFTs run
+     * in double-float FP32. The contraction shares lambda pieces inside a
+     * thread-block cluster with TMA multicast from this GPU's own memory: use
+     * this form only in processes that drive a single GPU.
      * Supported for mmax <= 2047 with nside <= 4096, lmax <= 16383 (spin 0)
      * or nside <= 2048, lmax <= 4095 (spin 2); SHT_EUNSUPPORTED otherwise. */
-    SHT_SPLIT_BF16 = 1
+    SHT_SPLIT_F16X4 = 1
 } sht_precision;
 
 /* Create a plan for HEALPix resolution `nside` (>= 1), band limit `lmax`

@@ -40,10 +40,14 @@
 // so the CTAs of a thread-block cluster, which work on
 // the same (m, q, tile) for different column tiles, split the lambda work:
 // lambda for one stage is cut into 32-row pieces, each produced by one warp of
-// one CTA, written to its own shared memory and copied to every other CTA of
-// the cluster with cp.async.bulk (shared::cta -> shared::cluster), completing
-// on the destination's mbarrier. Each CTA's MMA completion is multicast to the
-// "stage free" barriers of all CTAs of the cluster.
+// one CTA into its shared scratch and written to that warp's own slot of a
+// static device array (g_lam_slots, in L2); once the stage is released, the
+// warp multicasts the piece from that slot into the stage of every CTA of the
+// cluster with one cp.async.bulk ... .multicast::cluster per plane, completing
+// on each CTA's own stage barrier. The multicast source is always this GPU's
+// own g_lam_slots array, and the split form runs only in single-GPU processes.
+// Each CTA's MMA completion is multicast to the "stage free" barriers of all
+// CTAs of the cluster.
 //
 // Data operand. A separate pass (k_slice) writes, per 32-wide chunk of K and
 // column tile, the four slice planes of the data as the exact 32 KB image of

@@ -821,18 +821,18 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     if (lmax < 0 || lmax > 4 * 8192) { set_error("lmax out of range"); return SHT_EINVAL; }
     if (mmax > lmax) { set_error("mmax must be <= lmax"); return SHT_EINVAL; }
     if (spin != 0 && spin != 2) { set_error("spin must be 0 or 2"); return SHT_EINVAL; }
-    if (precision != SHT_FP64 && precision != SHT_SPLIT_BF16) { set_error("unknown precision"); return SHT_EINVAL; }
-    if (precision == SHT_SPLIT_BF16 && mmax > 2047) {
-        set_error("SHT_SPLIT_BF16 supports mmax <= 2047");
+    if (precision != SHT_FP64 && precision != SHT_SPLIT_F16X4) { set_error("unknown precision"); return SHT_EINVAL; }
+    if (precision == SHT_SPLIT_F16X4 && mmax > 2047) {
+        set_error("SHT_SPLIT_F16X4 supports mmax <= 2047");
         return SHT_EUNSUPPORTED;
     }
     // the contraction lengths (ring pairs, l of one parity) bound the exact
     // integer sums of the tensor-core form
     // (spin 2 contracts twice over each range)
     const int kmul = spin ? 2 : 1;
-    if (precision == SHT_SPLIT_BF16 && (kmul * 2 * nside > 8192 || (spin ? lmax + 1 : lmax / 2 + 1) * kmul > 8192)) {
-        set_error(spin ? "SHT_SPLIT_BF16 spin 2 supports nside <= 2048 and lmax <= 4095"
-                       : "SHT_SPLIT_BF16 supports nside <= 4096 and lmax <= 16383");
+    if (precision == SHT_SPLIT_F16X4 && (kmul * 2 * nside > 8192 || (spin ? lmax + 1 : lmax / 2 + 1) * kmul > 8192)) {
+        set_error(spin ? "SHT_SPLIT_F16X4 spin 2 supports nside <= 2048 and lmax <= 4095"
+                       : "SHT_SPLIT_F16X4 supports nside <= 4096 and lmax <= 16383");
         return SHT_EUNSUPPORTED;
     }
     int ndev = 0;
@@ -849,7 +849,7 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     p->nalm = (long long)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
     p->R = 2 * nside;
     cudaError_t e = build_tables(p);
-    if (e == cudaSuccess && precision == SHT_SPLIT_BF16) e = build_split_tables(p);
+    if (e == cudaSuccess && precision == SHT_SPLIT_F16X4) e = build_split_tables(p);
     if (e != cudaSuccess) {
         set_error(std::string("plan tables: ") + cudaGetErrorString(e));
         free_tables(p);

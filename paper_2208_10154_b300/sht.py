@@ -20,8 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsht.so")
 
 SHT_OK, SHT_EINVAL, SHT_ENOMEM, SHT_ECUDA, SHT_EUNSUPPORTED, SHT_ETIMEOUT = range(6)
-SHT_FP64, SHT_SPLIT_BF16 = 0, 1
-PRECISIONS = {"fp64": SHT_FP64, "split": SHT_SPLIT_BF16, "bf16": SHT_SPLIT_BF16}
+SHT_FP64, SHT_SPLIT_F16X4 = 0, 1
+PRECISIONS = {"fp64": SHT_FP64, "split": SHT_SPLIT_F16X4, "f16x4": SHT_SPLIT_F16X4}
 
 _lock = threading.Lock()
 _lib = None

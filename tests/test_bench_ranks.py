@@ -1,50 +1,48 @@
-"""The multi-rank path of bench.py (replicas, max over ranks, whole-job
-throughput) on two gloo ranks on the CPU."""
+"""bench.py is single-GPU only: a multi-GPU request (--gpus N > 1 or a
+torchrun environment with WORLD_SIZE > 1) prints one "unavailable" line and
+does no GPU work. Runs on the CPU."""
+import json
 import os
-import socket
+import subprocess
 import sys
-
-import torch
-import torch.distributed as dist
-import torch.multiprocessing as mp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _free_port():
-    s = socket.socket()
-    s.bind(("127.0.0.1", 0))
-    port = s.getsockname()[1]
-    s.close()
-    return port
+def _run(args, env_extra):
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, env=env,
+                       capture_output=True, text=True, timeout=120)
+    return r
 
 
-def _worker(rank, world, port, out):
+def test_gpus_flag_above_one_is_refused():
+    r = _run(["--gpus", "2"], {"RANK": "0", "WORLD_SIZE": "1"})
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and "single-GPU" in d["unavailable"]
+
+
+def test_torchrun_world_above_one_is_refused_and_only_rank0_prints():
+    r0 = _run([], {"RANK": "0", "WORLD_SIZE": "4", "LOCAL_RANK": "0"})
+    r1 = _run([], {"RANK": "1", "WORLD_SIZE": "4", "LOCAL_RANK": "1"})
+    assert r0.returncode == 0 and r1.returncode == 0
+    assert json.loads(r0.stdout.strip())["n_gpus"] == 4
+    assert r1.stdout.strip() == ""
+
+
+def test_single_gpu_is_not_refused():
     sys.path.insert(0, ROOT)
     import bench
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world)
+
+    class A:
+        gpus = 1
+    old = {k: os.environ.pop(k, None) for k in ("WORLD_SIZE", "RANK")}
     try:
-        t = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")
-        out[rank] = (t, bench.rank_seed(rank), bench.job_throughput(100, world, t))
+        assert not bench.multi_gpu_requested(A())
     finally:
-        dist.destroy_process_group()
-
-
-def test_two_ranks_take_the_slowest_time():
-    world = 2
-    port = _free_port()
-    with mp.Manager() as mgr:
-        out = mgr.dict()
-        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
-        res = dict(out)
-    assert res[0][0] == res[1][0] == 15.0
-    assert {res[0][1], res[1][1]} == {1, 2}          # distinct input seeds per replica
-    assert res[0][2] == res[1][2] == 2 * 100 / 15.0
-
-
-def test_single_rank_passthrough():
-    sys.path.insert(0, ROOT)
-    import bench
-    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
-    assert bench.job_throughput(1000, 1, 0.5) == 2000.0
+        for k, v in old.items():
+            if v is not None:
+                os.environ[k] = v
