@@ -488,3 +488,30 @@ def test_pure_e_gives_small_b(orc):
     T = orc.alm2map(a, nside, lmax, spin=2)
     b = orc.map2alm(T, nside, lmax, spin=2, niter=3)
     assert np.max(np.abs(b[:, 1])) < 1e-4 * np.max(np.abs(b[:, 0]))
+
+
+def test_spin2_impulse_fixes_the_eb_sign(orc):
+    """The overall sign of the E/B combination (Sec. 2.3, equ:alm-eb with
+    a_{+-2} = -(a_E +- i a_B)), fixed by the closed form
+    2Y_20 = -2Y_20 = sqrt(15/(32 pi)) sin^2(theta) (spin raising twice on
+    Y_20): a_E,20 = 1 gives Q = -sqrt(15/(32 pi)) sin^2 theta, U = 0, and
+    a_B,20 = 1 gives Q = 0, U = -sqrt(15/(32 pi)) sin^2 theta at every pixel
+    centre. Flipping both E/B signs together would pass the rotation, adjoint
+    and projection pins but fails this one. map2alm of those maps (with
+    Algorithm 2, band-limited input) must return +1 in the same slot."""
+    nside, lmax = 8, 7
+    th, _ = orc.pix_angles(nside)
+    y20 = math.sqrt(15.0 / (32.0 * math.pi)) * np.sin(th) ** 2
+    i20 = orc.alm_index(lmax, 2, 0)
+    for comp in (0, 1):
+        a = np.zeros((1, 2, orc.nalm(lmax)), dtype=complex)
+        a[0, comp, i20] = 1.0
+        for method in ("brute", "sep"):
+            QU = orc.alm2map(a, nside, lmax, spin=2, method=method)[0]
+            want_q = -y20 if comp == 0 else np.zeros_like(y20)
+            want_u = np.zeros_like(y20) if comp == 0 else -y20
+            np.testing.assert_allclose(QU[0], want_q, atol=1e-14)
+            np.testing.assert_allclose(QU[1], want_u, atol=1e-14)
+        back = orc.map2alm(QU[None], nside, lmax, spin=2, niter=4)[0]
+        assert abs(back[comp, i20] - 1.0) < 1e-6
+        assert abs(back[1 - comp, i20]) < 1e-6
