@@ -67,6 +67,8 @@ def _load():
                    "oracle_alm2map_sep", "oracle_map2alm_sep"):
             getattr(lib, fn).argtypes = [I, I, I, I, I, P, P]
         lib.oracle_map2alm_iter.argtypes = [I, I, I, I, I, P, P, I]
+        lib.oracle_map2alm_msel.argtypes = [I, I, I, I, I, P, I, P, P]
+        lib.oracle_alm2map_rings.argtypes = [I, I, I, I, I, P, I, P, P]
         lib.oracle_lambda_scaled.argtypes = [I, I, ctypes.c_double, P, P]
         lib.oracle_num_threads.restype = I
         lib.oracle_set_num_threads.argtypes = [I]
@@ -182,6 +184,46 @@ def map2alm(maps, nside: int, lmax: int, mmax: int | None = None, spin: int = 0,
         fn = "oracle_map2alm_brute" if method == "brute" else "oracle_map2alm_sep"
         getattr(lib, fn)(nside, lmax, mmax, spin, x.shape[0], _ptr(x), _ptr(out))
     return out
+
+
+def map2alm_msel(maps, nside: int, lmax: int, ms, mmax: int | None = None, spin: int = 0):
+    """map2alm restricted to the orders ``ms`` (separable tier, same formula):
+    a list, one complex128 array [nmaps, ncomp, lmax - m + 1] (l = m..lmax) per m."""
+    mmax = _check(nside, lmax, mmax, spin)
+    ms = np.ascontiguousarray(ms, dtype=np.int32)
+    if ms.size and (ms.min() < 0 or ms.max() > mmax):
+        raise ValueError("selected m outside 0..mmax")
+    ncomp = 2 if spin else 1
+    x = np.ascontiguousarray(maps, dtype=np.float64).reshape(-1, ncomp, npix(nside))
+    K = int(sum(lmax - int(m) + 1 for m in ms))
+    out = np.zeros((x.shape[0], ncomp, K), dtype=np.complex128)
+    _load().oracle_map2alm_msel(nside, lmax, mmax, spin, x.shape[0], _ptr(x), int(ms.size), _ptr(ms), _ptr(out))
+    res, o = [], 0
+    for m in ms:
+        res.append(out[..., o:o + lmax - int(m) + 1])
+        o += lmax - int(m) + 1
+    return res
+
+
+def alm2map_rings(alm, nside: int, lmax: int, rings, mmax: int | None = None, spin: int = 0):
+    """alm2map restricted to the 1-based rings ``rings`` (separable tier, same
+    formula): a list, one float64 array [nmaps, ncomp, N_ring] per ring."""
+    mmax = _check(nside, lmax, mmax, spin)
+    rings = np.ascontiguousarray(rings, dtype=np.int32)
+    if rings.size and (rings.min() < 1 or rings.max() > 4 * nside - 1):
+        raise ValueError("ring outside 1..4 nside - 1")
+    ncomp = 2 if spin else 1
+    a = np.ascontiguousarray(alm, dtype=np.complex128).reshape(-1, ncomp, nalm(lmax, mmax))
+    _, _, _, n, _ = ring_info(nside)
+    P = int(sum(int(n[r - 1]) for r in rings))
+    out = np.zeros((a.shape[0], ncomp, P))
+    _load().oracle_alm2map_rings(nside, lmax, mmax, spin, a.shape[0], _ptr(a), int(rings.size), _ptr(rings),
+                                 _ptr(out))
+    res, o = [], 0
+    for r in rings:
+        res.append(out[..., o:o + int(n[r - 1])])
+        o += int(n[r - 1])
+    return res
 
 
 def alm2map_adjoint(maps, nside, lmax, mmax=None, spin=0):

@@ -571,6 +571,33 @@ static void ring_dft_fwd(int nside, const double* x, int mlo, int mhi, double* F
     }
 }
 
+/* One ring of the backward DFT: x[n] = Re (and Im) of
+ * sum_m w_m G[m] e^{+i m (phi0 + 2 pi n / N)}, m = mlo..mhi, n = 0..N-1.
+ * wr/wi: the ring's unit-circle table; gr/gi: scratch of mhi - mlo + 1. */
+static void ring_bwd_one(const ring_t* r, const double* G, int mlo, int mhi, const double* wm,
+                         const double* wr, const double* wi, double* gr, double* gi,
+                         double* x, double* ximag)
+{
+    for (int m = mlo; m <= mhi; m++) {              /* fold in e^{i m phi0} and the weight */
+        const double* g = G + (long long)(m - mlo) * 2;
+        ld ph = (ld)m * r->phi0;
+        ld c = cosl(ph), s = sinl(ph);
+        gr[m - mlo] = (double)(wm[m - mlo] * (c * g[0] - s * g[1]));
+        gi[m - mlo] = (double)(wm[m - mlo] * (c * g[1] + s * g[0]));
+    }
+    for (int k = 0; k < r->n; k++) {
+        double sr = 0.0, si = 0.0;
+        long long mm = (((long long)mlo * k) % r->n + r->n) % r->n;   /* m k mod N */
+        for (int m = mlo; m <= mhi; m++) {
+            sr += gr[m - mlo] * wr[mm] - gi[m - mlo] * wi[mm];
+            si += gr[m - mlo] * wi[mm] + gi[m - mlo] * wr[mm];
+            mm += k; if (mm >= r->n) mm -= r->n;
+        }
+        x[k] = sr;
+        if (ximag) ximag[k] = si;
+    }
+}
+
 /* x[start_r + n] = sum_m G[r][m] e^{+i m (phi0 + 2 pi n/N)} with weights:
  * real_out: x = sum over m of Re(w_m G e^{i m phi}) where w_m is supplied per m. */
 static void ring_dft_bwd_real(int nside, const double* G, int mlo, int mhi,
@@ -589,26 +616,73 @@ static void ring_dft_bwd_real(int nside, const double* G, int mlo, int mhi,
             ring_t r;
             ring_geom(nside, i, &r);
             circle_table(r.n, wr, wi);
-            for (int m = mlo; m <= mhi; m++) {      /* fold in e^{i m phi0} and the weight */
-                const double* g = G + ((long long)(i - 1) * nm + (m - mlo)) * 2;
-                ld ph = (ld)m * r.phi0;
-                ld c = cosl(ph), s = sinl(ph);
-                gr[m - mlo] = (double)(wm[m - mlo] * (c * g[0] - s * g[1]));
-                gi[m - mlo] = (double)(wm[m - mlo] * (c * g[1] + s * g[0]));
-            }
-            for (int k = 0; k < r.n; k++) {
-                double sr = 0.0, si = 0.0;
-                long long mm = (((long long)mlo * k) % r.n + r.n) % r.n;   /* m k mod N */
-                for (int m = mlo; m <= mhi; m++) {
-                    sr += gr[m - mlo] * wr[mm] - gi[m - mlo] * wi[mm];
-                    si += gr[m - mlo] * wi[mm] + gi[m - mlo] * wr[mm];
-                    mm += k; if (mm >= r.n) mm -= r.n;
-                }
-                x[r.start + k] = sr;
-                if (ximag) ximag[r.start + k] = si;
-            }
+            ring_bwd_one(&r, G + (long long)(i - 1) * nm * 2, mlo, mhi, wm, wr, wi, gr, gi,
+                         x + r.start, ximag ? ximag + r.start : NULL);
         }
         free(wr); free(wi); free(gr); free(gi);
+    }
+}
+
+/* The sum over l of one m for spin 0 (separable map2alm): om[2 (l - m)] and
+ * om[2 (l - m) + 1] receive dsigma sum_rings lambda_lm(ring) F_ring(m), with
+ * F_ring(m) at F + ((ring - 1) fstride + fcol) * 2. lp, ar, ai: scratch. */
+static void m2a_spin0_m(int nside, int lmax, int m, const double* F, int fstride, int fcol, ld dsig,
+                        ld* lp, ld* ar, ld* ai, double* om)
+{
+    int nr = 4 * nside - 1;
+    for (int l = m; l <= lmax; l++) { ar[l] = 0.0L; ai[l] = 0.0L; }
+    for (int i = 1; i <= nr; i++) {
+        ring_t r;
+        ring_geom(nside, i, &r);
+        lambda_lm(lmax, m, r.cth, r.sth, lp);
+        const double* f = F + ((long long)(i - 1) * fstride + fcol) * 2;
+        for (int l = m; l <= lmax; l++) {
+            ar[l] += lp[l - m] * f[0];
+            ai[l] += lp[l - m] * f[1];
+        }
+    }
+    for (int l = m; l <= lmax; l++) {
+        om[2 * (l - m)] = (double)(dsig * ar[l]);
+        om[2 * (l - m) + 1] = (m == 0) ? 0.0 : (double)(dsig * ai[l]);
+    }
+}
+
+/* The same for spin 2: a_{+-2} from F(Q +- iU) and +-2 lambda, then E and B
+ * (Sec. 2.3 equ:alm-eb) into oE / oB at [2 (l - m)]; l < 2 is written as 0.
+ * lp, lq: scratch of lmax + 1; acc: scratch of 4 (lmax + 1). */
+static void m2a_spin2_m(int nside, int lmax, int m, const double* FQ, const double* FU, int fstride,
+                        int fcol, ld dsig, ld* lp, ld* lq, ld* acc, double* oE, double* oB)
+{
+    int nr = 4 * nside - 1;
+    int l0 = m > 2 ? m : 2;
+    for (int l = m; l <= lmax; l++) {
+        oE[2 * (l - m)] = oE[2 * (l - m) + 1] = oB[2 * (l - m)] = oB[2 * (l - m) + 1] = 0.0;
+    }
+    if (l0 > lmax) return;
+    memset(acc, 0, sizeof(ld) * 4 * (lmax + 1));
+    for (int i = 1; i <= nr; i++) {
+        ring_t r;
+        ring_geom(nside, i, &r);
+        slambda(lmax, m, 2, r.cth, r.chalf, r.shalf, lp);
+        slambda(lmax, m, -2, r.cth, r.chalf, r.shalf, lq);
+        const double* fq = FQ + ((long long)(i - 1) * fstride + fcol) * 2;
+        const double* fu = FU + ((long long)(i - 1) * fstride + fcol) * 2;
+        /* F(Q + iU) and F(Q - iU) */
+        ld pr = (ld)fq[0] - fu[1], pi = (ld)fq[1] + fu[0];
+        ld mr = (ld)fq[0] + fu[1], mi = (ld)fq[1] - fu[0];
+        for (int l = l0; l <= lmax; l++) {
+            ld* a = acc + 4 * l;
+            a[0] += lp[l - l0] * pr; a[1] += lp[l - l0] * pi;
+            a[2] += lq[l - l0] * mr; a[3] += lq[l - l0] * mi;
+        }
+    }
+    for (int l = l0; l <= lmax; l++) {
+        ld* a = acc + 4 * l;
+        ld pr = dsig * a[0], pi = dsig * a[1], mr = dsig * a[2], mi = dsig * a[3];
+        oE[2 * (l - m)] = (double)(-0.5L * (pr + mr));
+        oE[2 * (l - m) + 1] = (m == 0) ? 0.0 : (double)(-0.5L * (pi + mi));
+        oB[2 * (l - m)] = (double)(-0.5L * (pi - mi));
+        oB[2 * (l - m) + 1] = (m == 0) ? 0.0 : (double)(0.5L * (pr - mr));
     }
 }
 
@@ -632,24 +706,8 @@ void oracle_map2alm_sep(int nside, int lmax, int mmax, int spin, int nmaps,
                 ld* ar = (ld*)malloc(sizeof(ld) * (lmax + 1));
                 ld* ai = (ld*)malloc(sizeof(ld) * (lmax + 1));
 #pragma omp for schedule(dynamic)
-                for (int m = 0; m <= mmax; m++) {
-                    for (int l = m; l <= lmax; l++) { ar[l] = 0.0L; ai[l] = 0.0L; }
-                    for (int i = 1; i <= nr; i++) {
-                        ring_t r;
-                        ring_geom(nside, i, &r);
-                        lambda_lm(lmax, m, r.cth, r.sth, lp);
-                        const double* f = FQ + ((long long)(i - 1) * nm + m) * 2;
-                        for (int l = m; l <= lmax; l++) {
-                            ar[l] += lp[l - m] * f[0];
-                            ai[l] += lp[l - m] * f[1];
-                        }
-                    }
-                    for (int l = m; l <= lmax; l++) {
-                        long long q = aidx(lmax, l, m);
-                        o[2 * q] = (double)(dsig * ar[l]);
-                        o[2 * q + 1] = (m == 0) ? 0.0 : (double)(dsig * ai[l]);
-                    }
-                }
+                for (int m = 0; m <= mmax; m++)
+                    m2a_spin0_m(nside, lmax, m, FQ, nm, m, dsig, lp, ar, ai, o + 2 * aidx(lmax, m, m));
                 free(lp); free(ar); free(ai);
             }
         } else {
@@ -663,40 +721,9 @@ void oracle_map2alm_sep(int nside, int lmax, int mmax, int spin, int nmaps,
                 ld* lq = (ld*)malloc(sizeof(ld) * (lmax + 1));
                 ld* acc = (ld*)malloc(sizeof(ld) * 4 * (lmax + 1));
 #pragma omp for schedule(dynamic)
-                for (int m = 0; m <= mmax; m++) {
-                    int l0 = m > 2 ? m : 2;
-                    for (int l = 0; l <= lmax; l++) {
-                        long long q = l >= m ? aidx(lmax, l, m) : -1;
-                        if (q >= 0) { oE[2*q] = oE[2*q+1] = oB[2*q] = oB[2*q+1] = 0.0; }
-                    }
-                    if (l0 > lmax) continue;
-                    memset(acc, 0, sizeof(ld) * 4 * (lmax + 1));
-                    for (int i = 1; i <= nr; i++) {
-                        ring_t r;
-                        ring_geom(nside, i, &r);
-                        slambda(lmax, m, 2, r.cth, r.chalf, r.shalf, lp);
-                        slambda(lmax, m, -2, r.cth, r.chalf, r.shalf, lq);
-                        const double* fq = FQ + ((long long)(i - 1) * nm + m) * 2;
-                        const double* fu = FU + ((long long)(i - 1) * nm + m) * 2;
-                        /* F(Q + iU) and F(Q - iU) */
-                        ld pr = (ld)fq[0] - fu[1], pi = (ld)fq[1] + fu[0];
-                        ld mr = (ld)fq[0] + fu[1], mi = (ld)fq[1] - fu[0];
-                        for (int l = l0; l <= lmax; l++) {
-                            ld* a = acc + 4 * l;
-                            a[0] += lp[l - l0] * pr; a[1] += lp[l - l0] * pi;
-                            a[2] += lq[l - l0] * mr; a[3] += lq[l - l0] * mi;
-                        }
-                    }
-                    for (int l = l0; l <= lmax; l++) {
-                        long long q = aidx(lmax, l, m);
-                        ld* a = acc + 4 * l;
-                        ld pr = dsig * a[0], pi = dsig * a[1], mr = dsig * a[2], mi = dsig * a[3];
-                        oE[2 * q] = (double)(-0.5L * (pr + mr));
-                        oE[2 * q + 1] = (m == 0) ? 0.0 : (double)(-0.5L * (pi + mi));
-                        oB[2 * q] = (double)(-0.5L * (pi - mi));
-                        oB[2 * q + 1] = (m == 0) ? 0.0 : (double)(0.5L * (pr - mr));
-                    }
-                }
+                for (int m = 0; m <= mmax; m++)
+                    m2a_spin2_m(nside, lmax, m, FQ, FU, nm, m, dsig, lp, lq, acc,
+                                oE + 2 * aidx(lmax, m, m), oB + 2 * aidx(lmax, m, m));
                 free(lp); free(lq); free(acc);
             }
         }
@@ -705,90 +732,181 @@ void oracle_map2alm_sep(int nside, int lmax, int mmax, int spin, int nmaps,
     if (FU) free(FU);
 }
 
+/* G of one ring for the separable alm2map (before the backward DFT).
+ * spin 0: G[m] = sum_l a_lm lambda_lm(ring), m = 0..mmax (Im of m = 0 dropped);
+ * spin 2: G[m + mmax] = sum_l a_{2,lm} 2lambda_lm(ring), m = -mmax..mmax, with
+ * a_{2,lm} = -(a_E + i a_B) and a_{X,l,-m} = (-1)^m conj(a_{X,lm}). lp: scratch. */
+static void a2m_ring_G(int lmax, int mmax, int spin, const ring_t* r, const double* a, const double* aB,
+                       ld* lp, double* G)
+{
+    if (spin == 0) {
+        for (int m = 0; m <= mmax; m++) {
+            lambda_lm(lmax, m, r->cth, r->sth, lp);
+            ld sr = 0.0L, si = 0.0L;
+            for (int l = m; l <= lmax; l++) {
+                const double* c = a + 2 * aidx(lmax, l, m);
+                sr += lp[l - m] * c[0];
+                if (m) si += lp[l - m] * c[1];
+            }
+            G[2 * m] = (double)sr; G[2 * m + 1] = (double)si;
+        }
+        return;
+    }
+    for (int m = -mmax; m <= mmax; m++) {
+        int am = abs(m);
+        int l0 = am > 2 ? am : 2;
+        ld sr = 0.0L, si = 0.0L;
+        if (l0 <= lmax) {
+            slambda(lmax, m, 2, r->cth, r->chalf, r->shalf, lp);
+            for (int l = l0; l <= lmax; l++) {
+                const double* e = a + 2 * aidx(lmax, l, am);
+                const double* b = aB + 2 * aidx(lmax, l, am);
+                ld er = e[0], ei = e[1], br = b[0], bi = b[1];
+                if (m == 0) { ei = 0.0L; bi = 0.0L; }
+                if (m < 0) {
+                    ld sg = (am & 1) ? -1.0L : 1.0L;
+                    er = sg * er; ei = -sg * ei; br = sg * br; bi = -sg * bi;
+                }
+                ld a2r = -(er - bi), a2i = -(ei + br);
+                sr += lp[l - l0] * a2r;
+                si += lp[l - l0] * a2i;
+            }
+        }
+        G[2 * (m + mmax)] = (double)sr; G[2 * (m + mmax) + 1] = (double)si;
+    }
+}
+
 void oracle_alm2map_sep(int nside, int lmax, int mmax, int spin, int nmaps,
                         const double* alm, double* map)
 {
     long long npix = oracle_npix(nside);
     long long nalm = oracle_nalm(lmax, mmax);
     int nr = 4 * nside - 1;
-    if (spin == 0) {
-        int nm = mmax + 1;
-        double* G = (double*)malloc(sizeof(double) * 2 * (size_t)nr * nm);
-        double* wm = (double*)malloc(sizeof(double) * nm);
-        for (int m = 0; m <= mmax; m++) wm[m] = m ? 2.0 : 1.0;
-        for (int j = 0; j < nmaps; j++) {
-            const double* a = alm + (long long)j * nalm * 2;
+    int nm = spin ? 2 * mmax + 1 : mmax + 1;
+    int mlo = spin ? -mmax : 0;
+    double* G = (double*)malloc(sizeof(double) * 2 * (size_t)nr * nm);
+    double* wm = (double*)malloc(sizeof(double) * nm);
+    for (int k = 0; k < nm; k++) wm[k] = (spin || k == 0) ? 1.0 : 2.0;
+    for (int j = 0; j < nmaps; j++) {
+        const double* a = alm + (long long)j * (spin ? 2 : 1) * nalm * 2;
+        const double* aB = spin ? a + nalm * 2 : NULL;
 #pragma omp parallel
-            {
-                ld* lp = (ld*)malloc(sizeof(ld) * (lmax + 1));
+        {
+            ld* lp = (ld*)malloc(sizeof(ld) * (lmax + 1));
 #pragma omp for schedule(dynamic)
-                for (int i = 1; i <= nr; i++) {
-                    ring_t r;
-                    ring_geom(nside, i, &r);
-                    for (int m = 0; m <= mmax; m++) {
-                        lambda_lm(lmax, m, r.cth, r.sth, lp);
-                        ld sr = 0.0L, si = 0.0L;
-                        for (int l = m; l <= lmax; l++) {
-                            const double* c = a + 2 * aidx(lmax, l, m);
-                            sr += lp[l - m] * c[0];
-                            if (m) si += lp[l - m] * c[1];
-                        }
-                        double* g = G + ((long long)(i - 1) * nm + m) * 2;
-                        g[0] = (double)sr; g[1] = (double)si;
-                    }
-                }
-                free(lp);
+            for (int i = 1; i <= nr; i++) {
+                ring_t r;
+                ring_geom(nside, i, &r);
+                a2m_ring_G(lmax, mmax, spin, &r, a, aB, lp, G + (long long)(i - 1) * nm * 2);
             }
+            free(lp);
+        }
+        if (spin == 0)
             ring_dft_bwd_real(nside, G, 0, mmax, wm, map + (long long)j * npix, NULL);
-        }
-        free(G); free(wm);
-    } else {
-        int nm = 2 * mmax + 1;
-        double* G = (double*)malloc(sizeof(double) * 2 * (size_t)nr * nm);
-        double* wm = (double*)malloc(sizeof(double) * nm);
-        for (int m = 0; m < nm; m++) wm[m] = 1.0;
-        for (int j = 0; j < nmaps; j++) {
-            const double* aE = alm + ((long long)j * 2 + 0) * nalm * 2;
-            const double* aB = alm + ((long long)j * 2 + 1) * nalm * 2;
-#pragma omp parallel
-            {
-                ld* lp = (ld*)malloc(sizeof(ld) * (lmax + 1));
-#pragma omp for schedule(dynamic)
-                for (int i = 1; i <= nr; i++) {
-                    ring_t r;
-                    ring_geom(nside, i, &r);
-                    for (int m = -mmax; m <= mmax; m++) {
-                        int am = abs(m);
-                        int l0 = am > 2 ? am : 2;
-                        ld sr = 0.0L, si = 0.0L;
-                        if (l0 <= lmax) {
-                            slambda(lmax, m, 2, r.cth, r.chalf, r.shalf, lp);
-                            for (int l = l0; l <= lmax; l++) {
-                                const double* e = aE + 2 * aidx(lmax, l, am);
-                                const double* b = aB + 2 * aidx(lmax, l, am);
-                                ld er = e[0], ei = e[1], br = b[0], bi = b[1];
-                                if (m == 0) { ei = 0.0L; bi = 0.0L; }
-                                if (m < 0) {
-                                    ld sg = (am & 1) ? -1.0L : 1.0L;
-                                    er = sg * er; ei = -sg * ei; br = sg * br; bi = -sg * bi;
-                                }
-                                ld a2r = -(er - bi), a2i = -(ei + br);
-                                sr += lp[l - l0] * a2r;
-                                si += lp[l - l0] * a2i;
-                            }
-                        }
-                        double* g = G + ((long long)(i - 1) * nm + (m + mmax)) * 2;
-                        g[0] = (double)sr; g[1] = (double)si;
-                    }
-                }
-                free(lp);
-            }
-            ring_dft_bwd_real(nside, G, -mmax, mmax, wm,
-                              map + ((long long)j * 2 + 0) * npix,
+        else
+            ring_dft_bwd_real(nside, G, mlo, mmax, wm, map + ((long long)j * 2 + 0) * npix,
                               map + ((long long)j * 2 + 1) * npix);
-        }
-        free(G); free(wm);
     }
+    free(G); free(wm);
+}
+
+/* Sampled outputs of the separable tier, for checks at sizes where the full
+ * transform is too slow; every value is the same formula as above.
+ *
+ * map2alm restricted to the orders ms[0..nsel-1]: out [nmaps][ncomp][K][2]
+ * with K = sum_k (lmax - ms[k] + 1), the coefficients l = m..lmax of each
+ * selected m in selection order. */
+void oracle_map2alm_msel(int nside, int lmax, int mmax, int spin, int nmaps, const double* map,
+                         int nsel, const int* ms, double* out)
+{
+    long long npix = oracle_npix(nside);
+    int nr = 4 * nside - 1;
+    int ncomp = spin ? 2 : 1;
+    ld dsig = 4.0L * PI_L / (ld)npix;
+    long long K = 0;
+    long long* off = (long long*)malloc(sizeof(long long) * (nsel + 1));
+    for (int k = 0; k < nsel; k++) { off[k] = K; K += lmax - ms[k] + 1; }
+    double* FQ = (double*)malloc(sizeof(double) * 2 * (size_t)nr * nsel);
+    double* FU = (double*)malloc(sizeof(double) * 2 * (size_t)nr * nsel);
+    double* col = (double*)malloc(sizeof(double) * 2 * (size_t)nr);
+    (void)mmax;
+    for (int j = 0; j < nmaps; j++) {
+        for (int c = 0; c < ncomp; c++) {
+            double* F = c ? FU : FQ;
+            for (int k = 0; k < nsel; k++) {        /* F[ring][k] for the selected orders */
+                ring_dft_fwd(nside, map + ((long long)j * ncomp + c) * npix, ms[k], ms[k], col);
+                for (int i = 0; i < nr; i++) {
+                    F[((long long)i * nsel + k) * 2] = col[2 * i];
+                    F[((long long)i * nsel + k) * 2 + 1] = col[2 * i + 1];
+                }
+            }
+        }
+#pragma omp parallel
+        {
+            ld* lp = (ld*)malloc(sizeof(ld) * (lmax + 1));
+            ld* lq = (ld*)malloc(sizeof(ld) * (lmax + 1));
+            ld* acc = (ld*)malloc(sizeof(ld) * 4 * (lmax + 1));
+#pragma omp for schedule(dynamic)
+            for (int k = 0; k < nsel; k++) {
+                double* o0 = out + (((long long)j * ncomp + 0) * K + off[k]) * 2;
+                if (spin == 0) {
+                    m2a_spin0_m(nside, lmax, ms[k], FQ, nsel, k, dsig, lp, lq, acc, o0);
+                } else {
+                    double* o1 = out + (((long long)j * ncomp + 1) * K + off[k]) * 2;
+                    m2a_spin2_m(nside, lmax, ms[k], FQ, FU, nsel, k, dsig, lp, lq, acc, o0, o1);
+                }
+            }
+            free(lp); free(lq); free(acc);
+        }
+    }
+    free(FQ); free(FU); free(col); free(off);
+}
+
+/* alm2map restricted to the rings rings[0..nsel-1] (1-based): out
+ * [nmaps][ncomp][P] with P = sum_k N(rings[k]), the pixels of each selected
+ * ring in RING order, rings in selection order. */
+void oracle_alm2map_rings(int nside, int lmax, int mmax, int spin, int nmaps, const double* alm,
+                          int nsel, const int* rings, double* out)
+{
+    long long nalm = oracle_nalm(lmax, mmax);
+    int ncomp = spin ? 2 : 1;
+    int nm = spin ? 2 * mmax + 1 : mmax + 1;
+    int mlo = spin ? -mmax : 0;
+    long long P = 0;
+    long long* off = (long long*)malloc(sizeof(long long) * (nsel + 1));
+    for (int k = 0; k < nsel; k++) {
+        ring_t r;
+        ring_geom(nside, rings[k], &r);
+        off[k] = P;
+        P += r.n;
+    }
+    double* wm = (double*)malloc(sizeof(double) * nm);
+    for (int k = 0; k < nm; k++) wm[k] = (spin || k == 0) ? 1.0 : 2.0;
+    for (int j = 0; j < nmaps; j++) {
+        const double* a = alm + (long long)j * ncomp * nalm * 2;
+        const double* aB = spin ? a + nalm * 2 : NULL;
+#pragma omp parallel
+        {
+            ld* lp = (ld*)malloc(sizeof(ld) * (lmax + 1));
+            double* G = (double*)malloc(sizeof(double) * 2 * nm);
+            double* wr = (double*)malloc(sizeof(double) * 4 * nside);
+            double* wi = (double*)malloc(sizeof(double) * 4 * nside);
+            double* gr = (double*)malloc(sizeof(double) * nm);
+            double* gi = (double*)malloc(sizeof(double) * nm);
+#pragma omp for schedule(dynamic)
+            for (int k = 0; k < nsel; k++) {
+                ring_t r;
+                ring_geom(nside, rings[k], &r);
+                a2m_ring_G(lmax, mmax, spin, &r, a, aB, lp, G);
+                circle_table(r.n, wr, wi);
+                double* x0 = out + ((long long)j * ncomp + 0) * P + off[k];
+                double* x1 = spin ? out + ((long long)j * ncomp + 1) * P + off[k] : NULL;
+                ring_bwd_one(&r, G, mlo, spin ? mmax : mmax, wm, wr, wi, gr, gi, x0, x1);
+            }
+            free(lp); free(G); free(wr); free(wi); free(gr); free(gi);
+        }
+    }
+    free(wm); free(off);
 }
 
 /* Traditional (Jacobi) iteration, Algorithm 2, in its pixel-domain form:

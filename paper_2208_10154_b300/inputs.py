@@ -97,3 +97,37 @@ def workload_cls(w: dict) -> np.ndarray:
     if w.get("spin", 0) == 2:
         return np.stack([base, w.get("bb_frac", 1.0) * base])
     return base[None, :]
+
+
+def gaussian_alm_torch(seed: int, nmaps: int, ncomp: int, lmax: int, mmax: int | None = None, cls=None,
+                       device="cuda"):
+    """The same sky recipe as ``gaussian_alm``, drawn on ``device`` with a
+    seeded ``torch.Generator`` (for batches too large to draw on the host):
+    complex128 tensor [nmaps, ncomp, nalm]. Not bit-identical to the numpy
+    draw; parity tests copy the columns they check to the host."""
+    import torch
+    mmax = lmax if mmax is None else mmax
+    n = nalm(lmax, mmax)
+    cls = cl_inv_llp1(lmax) if cls is None else np.asarray(cls, dtype=np.float64)
+    if cls.ndim == 1:
+        cls = np.broadcast_to(cls, (ncomp, lmax + 1))
+    ls, ms = lm_arrays(lmax, mmax)
+    sd = np.stack([np.where(ms == 0, np.sqrt(cls[c][ls]), np.sqrt(cls[c][ls] / 2.0)) for c in range(ncomp)])
+    sd = torch.from_numpy(sd).to(device)[None]
+    m0 = torch.from_numpy(ms == 0).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    re = torch.randn((nmaps, ncomp, n), generator=g, dtype=torch.float64, device=device) * sd
+    im = torch.randn((nmaps, ncomp, n), generator=g, dtype=torch.float64, device=device) * sd
+    im[..., m0] = 0.0
+    out = torch.complex(re, im)
+    del re, im
+    return out.contiguous()
+
+
+def white_noise_torch(seed: int, shape, device="cuda"):
+    """Unit Gaussian noise of ``shape`` (float64) from a seeded torch.Generator."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randn(tuple(shape), generator=g, dtype=torch.float64, device=device)

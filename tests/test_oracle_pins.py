@@ -515,3 +515,24 @@ def test_spin2_impulse_fixes_the_eb_sign(orc):
         back = orc.map2alm(QU[None], nside, lmax, spin=2, niter=4)[0]
         assert abs(back[comp, i20] - 1.0) < 1e-6
         assert abs(back[1 - comp, i20]) < 1e-6
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_sampled_tiers_equal_full_transform(orc, spin):
+    """The sampled forms used at full size (map2alm for chosen m, alm2map on
+    chosen rings) return exactly the corresponding entries of the full
+    separable transform, which the pins above tie to the mathematics."""
+    nside, lmax, mmax = 8, 23, 20
+    ncomp = 2 if spin else 1
+    a = inputs.gaussian_alm(5, 2, ncomp, lmax, mmax)
+    full = orc.alm2map(a, nside, lmax, mmax, spin)
+    _, _, _, n, st = orc.ring_info(nside)
+    rings = [1, 3, 8, 16, 20, 31]
+    for k, r in enumerate(orc.alm2map_rings(a, nside, lmax, rings, mmax, spin)):
+        assert np.array_equal(r, full[..., st[rings[k] - 1]:st[rings[k] - 1] + n[rings[k] - 1]])
+    x = np.random.default_rng(2).standard_normal(full.shape)
+    af = orc.map2alm(x, nside, lmax, mmax, spin)
+    ms = [0, 1, 7, 20]
+    for k, blk in enumerate(orc.map2alm_msel(x, nside, lmax, ms, mmax, spin)):
+        i0 = orc.alm_index(lmax, ms[k], ms[k])
+        assert np.array_equal(blk, af[..., i0:i0 + lmax - ms[k] + 1])
