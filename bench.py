@@ -61,10 +61,11 @@ def parse():
                     help="skip the context run (nside 256, lmax 767, 1000 maps, Legendre only)")
     ap.add_argument("--no-next-rows", action="store_true",
                     help="skip the compact-storage and E-projection measurements")
-    ap.add_argument("--serve-requests", type=int, default=300,
-                    help="requests of the serving measurement (0: skip)")
-    ap.add_argument("--serve-load", type=float, default=0.8,
-                    help="offered load of the open-loop serving run, as a fraction of closed-loop saturation")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests of the serving measurement, drawn from the serving workload's mix (0: skip)")
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95",
+                    help="offered loads of the open-loop serving runs, as fractions of closed-loop saturation")
+    ap.add_argument("--serve-no-graphs", action="store_true")
     a = ap.parse_args()
     if a.lmax is None:
         a.lmax = 2 * a.nside - 1
@@ -220,12 +221,7 @@ def ref_config(a):
 
 
 # ----------------------------------------------------------------------------
-# Serving: a Poisson stream of mixed requests through the continuous-batching
-# server. Request mix of the serving workload, scaled to finish in seconds:
-# alm2map / map2alm 50/50, nside {64, 128, 256, 512} with weights
-# {0.3, 0.3, 0.2, 0.15} (renormalised), spin 2 for 30% of the nside <= 128
-# requests, maps per request uniform in 1..64, seed 3. Spin-0 requests run in
-# the split form, spin-2 in the FP64 form (the split form is spin 0 only).
+# Serving workload (request mix; see serving_spec)
 SERVE_NSIDES = [64, 128, 256, 512, 1024]
 SERVE_W = [0.3, 0.3, 0.2, 0.15, 0.05]
 
@@ -400,19 +396,34 @@ def run_context(precision, steps=3):
     return out
 
 
-def run_serving(n_req, load, device):
+def serving_spec(n_req, seed=3):
+    """Requests of the serving workload: op alm2map / map2alm 50/50, spin 2
+    with probability 0.3, nside from {64, 128, 256, 512, 1024} with weights
+    {0.3, 0.3, 0.2, 0.15, 0.05}, lmax = 2 nside - 1, maps uniform in 1..256."""
     import numpy as np
-    import torch
-    from paper_2208_10154_b300.serving import GpuExecutor, Request, Server
-    rng = np.random.default_rng(3)
+    rng = np.random.default_rng(seed)
     w = np.array(SERVE_W) / np.sum(SERVE_W)
     spec = []
     for _ in range(n_req):
         nside = int(rng.choice(SERVE_NSIDES, p=w))
         spin = 2 if rng.random() < 0.3 else 0
         op = "alm2map" if rng.random() < 0.5 else "map2alm"
-        spec.append((op, nside, spin, int(rng.integers(1, 65))))
-    # one input pool per (op, nside, spin) of 64 maps; a request takes its first n
+        spec.append((op, nside, spin, int(rng.integers(1, 257))))
+    return spec, rng
+
+
+def run_serving(n_req, loads, device, use_graphs=True):
+    """The serving workload through the continuous-batching server: closed
+    loop (all requests at once: saturation), then Poisson arrivals at each
+    offered load (a fraction of saturation). Inputs: one pool of maps per
+    (op, nside, spin), 256 maps (64 for nside >= 512); a request of n maps
+    takes the pool's first n, or repeats of the pool passed as a list of
+    pieces. Results are dropped as requests finish (the caller would take
+    them); the split form within its limits, HBM budget 150 GB."""
+    import numpy as np
+    import torch
+    from paper_2208_10154_b300.serving import GpuExecutor, Request, Server
+    spec, rng = serving_spec(n_req)
     pool = {}
     g = torch.Generator(device="cuda")
     g.manual_seed(3)
@@ -422,51 +433,84 @@ def run_serving(n_req, load, device):
             continue
         ncomp = 2 if spin else 1
         lmax = 2 * nside - 1
+        npool = 64 if nside >= 512 else 256
         if op == "alm2map":
             nalm = (lmax + 1) * (lmax + 2) // 2
-            x = torch.randn((64, ncomp, nalm, 2), generator=g, dtype=torch.float64, device="cuda")
+            x = torch.randn((npool, ncomp, nalm, 2), generator=g, dtype=torch.float64, device="cuda")
             pool[k] = torch.view_as_complex(x).contiguous()
+            del x
         else:
-            pool[k] = torch.randn((64, ncomp, 12 * nside * nside), generator=g, dtype=torch.float64, device="cuda")
-    ex = GpuExecutor(device=device, slots=4)
-    srv = Server(ex, hbm_budget=150e9, max_batch_maps=256, slots=4)
-    for op, nside, spin, _ in spec:                       # plans and kernels warm
-        srv.submit(Request(op=op, nside=nside, spin=spin, data=pool[(op, nside, spin)][:1]))
-    srv.run_until_idle()
-    torch.cuda.synchronize()
+            pool[k] = torch.randn((npool, ncomp, 12 * nside * nside), generator=g, dtype=torch.float64,
+                                  device="cuda")
 
-    def run(arrivals):
+    def data(k, n):
+        p = pool[k]
+        if n <= p.shape[0]:
+            return p[:n]
+        q, r = divmod(n, p.shape[0])
+        return [p] * q + ([p[:r]] if r else [])
+
+    budget = 150e9
+    ex = GpuExecutor(device=device, slots=4, use_graphs=use_graphs, mem_cap=budget)
+
+    def drop(r):
+        r.result = None
+    srv = Server(ex, hbm_budget=budget, max_batch_maps=256, slots=4, on_complete=drop)
+
+    def run(sp, arrivals):
         srv.completed.clear()
         srv.nbatches = 0
+        srv.peak_used = 0.0
         t0 = time.perf_counter()
         i = 0
-        while i < len(spec) or not srv.idle():
+        while i < len(sp) or not srv.idle():
             now = time.perf_counter() - t0
-            while i < len(spec) and arrivals[i] <= now:
-                op, nside, spin, n = spec[i]
-                srv.submit(Request(op=op, nside=nside, spin=spin, data=pool[(op, nside, spin)][:n],
+            while i < len(sp) and arrivals[i] <= now:
+                op, nside, spin, n = sp[i]
+                srv.submit(Request(op=op, nside=nside, spin=spin, data=data((op, nside, spin), n),
                                    t_arrival=t0 + arrivals[i]))
                 i += 1
             if not srv.step():
                 time.sleep(1e-4)
         torch.cuda.synchronize()
-        return srv.stats()
+        st = srv.stats()
+        st["peak_admitted_gb"] = srv.peak_used / 1e9
+        return st
 
-    closed = run(np.zeros(len(spec)))                      # all at once: saturation
-    # requests/s at saturation = maps/s / mean maps per request
+    warm = spec[:min(len(spec), 64)]                       # plans, kernel attributes, graphs
+    run(warm, np.zeros(len(warm)))
+    closed = run(spec, np.zeros(len(spec)))
     mean_maps = sum(s[3] for s in spec) / len(spec)
-    rate = load * closed["maps_per_s"] / mean_maps
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(spec)))
-    opened = run(arrivals)
-    return {"requests": opened["requests"], "offered_load": load,
-            "offered_requests_per_s": rate, "p50_ms": opened["p50_ms"], "p99_ms": opened["p99_ms"],
-            "maps_per_s": opened["maps_per_s"], "batches": opened["batches"],
-            "saturation_maps_per_s": closed["maps_per_s"], "errors": opened["errors"] + closed["errors"],
-            "first_error": next((r.error for r in srv.completed if r.error), None),
-            "peak_admitted_gb": srv.peak_used / 1e9,
-            "workload": "Poisson stream; alm2map/map2alm 50/50; nside 64/128/256/512/1024 "
-                        "(0.3/0.3/0.2/0.15/0.05); spin 2 in 30%; 1-64 maps per request (inputs from pools "
-                        "of 64 maps); split form"}
+    out = {"requests": len(spec), "saturation": {k: closed.get(k) for k in (
+               "maps_per_s", "p50_ms", "p99_ms", "batches", "errors", "first_error", "peak_admitted_gb")},
+           "open_loop": [], "graphs": use_graphs, "graph_replays": ex.graph_replays,
+           "workload": "serving mix: Poisson arrivals; alm2map/map2alm 50/50; nside 64/128/256/512/1024 "
+                       "(0.3/0.3/0.2/0.15/0.05), lmax = 2 nside - 1; spin 2 in 30%; 1-256 maps per request; "
+                       "split form; HBM budget 150 GB; seed 3; "
+                       f"{len(spec)} of the workload's 20000 requests"}
+    errors = closed.get("errors", 0) or 0
+    first = closed.get("first_error")
+    peak = closed.get("peak_admitted_gb", 0.0) or 0.0
+    for load in loads:
+        rate = load * closed["maps_per_s"] / mean_maps
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(spec)))
+        o = run(spec, arrivals)
+        out["open_loop"].append({"offered_load": load, "offered_requests_per_s": rate,
+                                 "p50_ms": o.get("p50_ms"), "p99_ms": o.get("p99_ms"),
+                                 "maps_per_s": o.get("maps_per_s"), "batches": o.get("batches"),
+                                 "errors": o.get("errors"), "first_error": o.get("first_error"),
+                                 "peak_admitted_gb": o.get("peak_admitted_gb")})
+        errors += o.get("errors", 0) or 0
+        first = first or o.get("first_error")
+        peak = max(peak, o.get("peak_admitted_gb", 0.0) or 0.0)
+    ref = next((x for x in out["open_loop"] if x["offered_load"] == 0.8), out["open_loop"][-1] if loads else {})
+    out.update({"p50_ms": ref.get("p50_ms"), "p99_ms": ref.get("p99_ms"), "maps_per_s": ref.get("maps_per_s"),
+                "errors": errors, "first_error": first, "peak_admitted_gb": peak,
+                "resident_gb_at_end": ex.resident_bytes() / 1e9})
+    del srv, ex, pool
+    gc.collect()
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -689,7 +733,8 @@ def main():
         plan = plan64 = None
         gc.collect()
         torch.cuda.empty_cache()
-        serving = run_serving(a.serve_requests, a.serve_load, dev)
+        serving = run_serving(a.serve_requests, [float(x) for x in a.serve_loads.split(",") if x],
+                              dev, use_graphs=not a.serve_no_graphs)
 
     line = {
         "metric": METRIC, "value": value, "unit": "maps/s", "n_gpus": 1, "steps": a.steps,

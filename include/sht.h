@@ -113,6 +113,13 @@ int       sht_plan_precision(const sht_plan* plan);
 long long sht_plan_npix(const sht_plan* plan);
 long long sht_plan_nalm(const sht_plan* plan);
 
+/* Device memory the plan holds while it lives (bytes): its resident tables
+ * (ring geometry, recurrence and FFT tables; in the split form also the FP64
+ * recurrence checkpoints) plus the staging buffers of the host-buffer entry
+ * points once they have been used. For HBM admission (no counterpart in the
+ * paper). 0 for a NULL plan. */
+size_t    sht_plan_device_bytes(const sht_plan* plan);
+
 /* Backward transform (Sec. 2.1 equ:backward equ, equ:mm backward; spin 2:
  * equ:aeab mat form inv). alm [nmaps][ncomp][nalm] (complex double, device)
  * -> map [nmaps][ncomp][npix] (double, device). Real field:

@@ -887,6 +887,10 @@ int sht_plan_spin(const sht_plan* p) { return p ? p->spin : 0; }
 int sht_plan_precision(const sht_plan* p) { return p ? p->precision : 0; }
 long long sht_plan_npix(const sht_plan* p) { return p ? p->npix : 0; }
 long long sht_plan_nalm(const sht_plan* p) { return p ? p->nalm : 0; }
+size_t sht_plan_device_bytes(const sht_plan* p)
+{
+    return p ? p->table_bytes + p->host_dev_in_bytes + p->host_dev_out_bytes + p->host_ws_bytes : 0;
+}
 
 static sht_status check_call(const sht_plan* p, const void* in, const void* out, int nmaps,
                              void* ws, size_t wsb, int niter)

@@ -5,9 +5,10 @@ server keeps plans (ring, recurrence and FFT tables) resident, groups the
 pending requests that share a plan key and an operation into one batch (the
 map columns are the GEMM's N side, so a batch fills the tensor-core tiles that
 single requests leave empty), admits a batch only while the device memory it
-needs (workspace + batch buffers) fits the HBM budget and a stream slot is
-free, runs it asynchronously, and hands every request its own slice of the
-batch output. Batches that arrive while others run are admitted as slots and
+needs (workspace, staging and output buffers), on top of what the executor
+keeps resident (plans, captured graphs) and the batches already running, fits
+the HBM budget and a stream slot is free, runs it asynchronously, and hands
+every request its own slice of the batch output. Batches that arrive while others run are admitted as slots and
 memory free up (continuous batching); the results of a request do not depend
 on what it was batched with (map columns are independent in every kernel).
 
@@ -18,7 +19,7 @@ with zero maps up to their bucket.
 The scheduling logic is independent of the GPU: `Server` drives an executor
 object (`GpuExecutor` on a device; tests use a CPU fake) through four calls:
 `prepare(key)`, `batch_bytes(key, n)`, `launch(key, inputs) -> handle` and
-`poll(handle) -> outputs or None`.
+`poll(handle) -> outputs or None`, plus optionally `resident_bytes()`.
 """
 from __future__ import annotations
 
@@ -33,7 +34,8 @@ class Request:
     op: str                      # "alm2map" or "map2alm"
     nside: int
     spin: int
-    data: object                 # alm [n, ncomp, nalm] complex128 / maps [n, ncomp, npix] float64
+    data: object                 # alm [n, ncomp, nalm] complex128 / maps [n, ncomp, npix] float64,
+                                 # or a list of such arrays (concatenated along the first axis)
     nmaps: int = 0
     lmax: int = -1               # default 2 nside - 1
     t_arrival: float = 0.0
@@ -61,12 +63,13 @@ class Server:
     """Continuous-batching scheduler over an executor (see module docstring)."""
 
     def __init__(self, executor, hbm_budget: float = 150e9, max_batch_maps: int = 256, slots: int = 4,
-                 precision_for=None):
+                 precision_for=None, on_complete=None):
         self.ex = executor
         self.budget = float(hbm_budget)
         self.max_batch = int(max_batch_maps)
         self.slots = int(slots)
         self.precision_for = precision_for or (lambda req: "auto")
+        self.on_complete = on_complete               # called with each finished request
         self.pending = collections.OrderedDict()     # key -> deque of requests (FIFO per key)
         self.inflight: list[_Batch] = []
         self.used = 0.0
@@ -82,7 +85,8 @@ class Server:
         if req.op not in ("alm2map", "map2alm"):
             raise ValueError(f"unknown operation {req.op}")
         if not req.nmaps:
-            req.nmaps = int(req.data.shape[0])
+            parts = req.data if isinstance(req.data, (list, tuple)) else [req.data]
+            req.nmaps = int(sum(int(x.shape[0]) for x in parts))
         if not req.t_arrival:
             req.t_arrival = time.perf_counter()
         key = req.key(self.precision_for(req))
@@ -111,8 +115,7 @@ class Server:
             now = time.perf_counter()
             for r, o in zip(b.reqs, outs):
                 r.result, r.t_done = o, now
-                r.done.set()
-                self.completed.append(r)
+                self._finish(r)
             self.inflight.remove(b)
             self.used -= b.nbytes
             progressed = True
@@ -132,7 +135,7 @@ class Server:
             self.ex.prepare(key)
             nbytes = self.ex.batch_bytes(key, n)
             # (a batch larger than the whole budget still runs, alone)
-            if self.used + nbytes > self.budget and self.inflight:
+            if self.used + self._resident() + nbytes > self.budget and self.inflight:
                 with self.lock:                       # put back, in order
                     for r in reversed(reqs):
                         q.appendleft(r)
@@ -144,18 +147,28 @@ class Server:
             try:
                 handle = self.ex.launch(key, [r.data for r in reqs])
             except Exception as e:                    # a failed batch fails its requests, not the server
+                msg = f"{type(e).__name__}: {e}"
                 for r in reqs:
-                    r.error, r.t_done = str(e), time.perf_counter()
-                    r.done.set()
-                    self.completed.append(r)
+                    r.error, r.t_done = msg, time.perf_counter()
+                    self._finish(r)
                 progressed = True
                 continue
             self.inflight.append(_Batch(key, reqs, nbytes, handle, now))
             self.used += nbytes
-            self.peak_used = max(self.peak_used, self.used)
+            self.peak_used = max(self.peak_used, self.used + self._resident())
             self.nbatches += 1
             progressed = True
         return progressed
+
+    def _resident(self) -> float:
+        f = getattr(self.ex, "resident_bytes", None)
+        return float(f()) if f else 0.0
+
+    def _finish(self, r):
+        r.done.set()
+        self.completed.append(r)
+        if self.on_complete is not None:
+            self.on_complete(r)
 
     def idle(self) -> bool:
         with self.lock:
@@ -187,8 +200,9 @@ class Server:
     def stats(self) -> dict:
         lat = sorted((r.t_done - r.t_arrival) for r in self.completed if r.t_done is not None and not r.error)
         maps = sum(r.nmaps for r in self.completed if not r.error)
+        errs = [r.error for r in self.completed if r.error]
         if not lat:
-            return {"requests": 0}
+            return {"requests": 0, "errors": len(errs), "first_error": errs[0] if errs else None}
         t0 = min(r.t_arrival for r in self.completed)
         t1 = max(r.t_done for r in self.completed)
 
@@ -197,14 +211,25 @@ class Server:
         return {"requests": len(lat), "maps": maps, "batches": self.nbatches,
                 "p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "maps_per_s": maps / max(t1 - t0, 1e-9),
                 "peak_admitted_bytes": self.peak_used,
-                "errors": sum(1 for r in self.completed if r.error)}
+                "errors": len(errs), "first_error": errs[0] if errs else None}
 
 
 class GpuExecutor:
-    """Runs batches on one GPU with libsht: resident plans, one CUDA stream per
-    slot, optional CUDA-graph replay per (key, bucket)."""
+    """Runs batches on one GPU with libsht: resident plans (LRU), one CUDA
+    stream per slot, optional CUDA-graph replay per (key, batch bucket).
 
-    def __init__(self, device: int = 0, slots: int = 4, use_graphs: bool = False, plan_cache: int = 32):
+    Memory. A batch of n maps is run as consecutive library calls of at most
+    `chunk` maps on its stream, with one workspace sized for the chunk, so
+    that workspace + input staging + the batch output stay within `mem_cap`
+    (the server's HBM budget). Each request's result is a view of the batch
+    output (no copies). Graphs are kept only for batch buckets whose static
+    buffers (input, output, workspace) are at most `graph_max_bytes`, up to
+    `graph_cache_bytes` in all (LRU); a captured graph serves one batch at a
+    time (a batch that finds its graph busy runs without it). Plans and graph
+    buffers are reported by `resident_bytes()` for admission."""
+
+    def __init__(self, device: int = 0, slots: int = 4, use_graphs: bool = False, plan_cache: int = 32,
+                 mem_cap: float = 150e9, graph_max_bytes: float = 4e9, graph_cache_bytes: float = 24e9):
         import torch
         from . import sht
         self.torch, self.sht = torch, sht
@@ -214,8 +239,14 @@ class GpuExecutor:
         self.plans = collections.OrderedDict()
         self.plan_cache = plan_cache
         self.use_graphs = use_graphs
-        self.graphs = {}
+        self.mem_cap = float(mem_cap)
+        self.graph_max_bytes = float(graph_max_bytes)
+        self.graph_cache_bytes = float(graph_cache_bytes)
+        self.graphs = collections.OrderedDict()      # (key, bucket) -> (graph, xin, yout, ws, bytes)
+        self.graph_busy = set()
+        self.graph_replays = 0
 
+    # ------------------------------------------------------------- plans
     def _precision(self, key):
         op, nside, lmax, spin, prec = key
         if prec != "auto":
@@ -229,17 +260,39 @@ class GpuExecutor:
         if pk not in self.plans:
             self.plans[pk] = self.sht.Plan(pk[0], pk[1], None, pk[2], pk[3], device=self.device)
             while len(self.plans) > self.plan_cache:
-                self.plans.popitem(last=False)
+                old, _ = self.plans.popitem(last=False)
+                for gk in [g for g in self.graphs if g[0][1:4] == old[:3] and g not in self.graph_busy]:
+                    del self.graphs[gk]
         self.plans.move_to_end(pk)
         return self.plans[pk]
 
-    def _plan(self, key):
-        return self.prepare(key)
+    _plan = prepare
+
+    def resident_bytes(self) -> float:
+        return float(sum(p.device_bytes() for p in self.plans.values())
+                     + sum(v[4] for v in self.graphs.values()))
+
+    # ------------------------------------------------------------ memory
+    @staticmethod
+    def _sizes(p, op):
+        """(input, output) bytes per map of one operation."""
+        alm_b, map_b = p.ncomp * p.nalm * 16, p.ncomp * p.npix * 8
+        return (alm_b, map_b) if op == "alm2map" else (map_b, alm_b)
+
+    def _chunk(self, p, op, n):
+        """Maps per library call: all n if they fit the memory cap, else the
+        largest halving of n that does (at least 1)."""
+        ib, ob = self._sizes(p, op)
+        c = n
+        while c > 1 and p.workspace_bytes(c) + c * ib + n * ob > self.mem_cap:
+            c = (c + 1) // 2
+        return c
 
     def batch_bytes(self, key, n):
         p = self._plan(key)
-        io = n * p.ncomp * (p.npix * 8 + p.nalm * 16)
-        return p.workspace_bytes(n) + io
+        ib, ob = self._sizes(p, key[0])
+        c = self._chunk(p, key[0], n)
+        return p.workspace_bytes(c) + c * ib + n * ob
 
     @staticmethod
     def _bucket(n):
@@ -248,62 +301,140 @@ class GpuExecutor:
             b *= 2
         return b
 
+    # ------------------------------------------------------------ launch
     def launch(self, key, inputs):
         torch = self.torch
         p = self._plan(key)
         op = key[0]
+        dev = f"cuda:{self.device}"
         sid = self.free_streams.pop() if self.free_streams else 0
         st = self.streams[sid]
-        counts = [int(x.shape[0]) for x in inputs]
+        counts, pieces = [], []
+        for x in inputs:
+            parts = list(x) if isinstance(x, (list, tuple)) else [x]
+            counts.append(sum(int(t.shape[0]) for t in parts))
+            pieces.extend(parts)
         n = sum(counts)
+        ib, ob = self._sizes(p, op)
+        out_len = p.npix if op == "alm2map" else p.nalm
+        out_dt = torch.float64 if op == "alm2map" else torch.complex128
+        gk = None
         with torch.cuda.stream(st):
-            xs = [x.to(f"cuda:{self.device}", non_blocking=True) for x in inputs]
+            pieces = [t.to(dev, non_blocking=True) for t in pieces]
             if self.use_graphs:
-                out = self._replay(key, p, op, xs, n, st)
+                gk = self._graph_for(key, p, op, n, st)
+            if gk is not None:
+                out = self._replay(gk, pieces, n, out_len, out_dt)
             else:
-                x = xs[0] if len(xs) == 1 else torch.cat(xs, dim=0)
-                ws = torch.empty(p.workspace_bytes(n) + 256, dtype=torch.uint8, device=x.device)
+                out = torch.empty((n, p.ncomp, out_len), dtype=out_dt, device=dev)
+                c = self._chunk(p, op, n)
+                ws = torch.empty(p.workspace_bytes(c) + 256, dtype=torch.uint8, device=dev)
                 ws = ws[(-ws.data_ptr()) % 256:]
-                out = p.alm2map(x, workspace=ws) if op == "alm2map" else p.map2alm(x, workspace=ws)
+                stage = None
+                for c0 in range(0, n, c):
+                    c1 = min(n, c0 + c)
+                    x = self._rows(pieces, c0, c1)
+                    if x is None:                      # rows span several pieces: gather
+                        if stage is None:
+                            in_len = p.nalm if op == "alm2map" else p.npix
+                            in_dt = torch.complex128 if op == "alm2map" else torch.float64
+                            stage = torch.empty((c, p.ncomp, in_len), dtype=in_dt, device=dev)
+                        x = stage[:c1 - c0]
+                        self._gather(pieces, c0, c1, x)
+                    if op == "alm2map":
+                        p.alm2map(x, out=out[c0:c1], workspace=ws)
+                    else:
+                        p.map2alm(x, out=out[c0:c1], workspace=ws)
             outs, o = [], 0
-            for c in counts:
-                outs.append(out[o:o + c].clone())
-                o += c
+            for cnt in counts:
+                outs.append(out[o:o + cnt])
+                o += cnt
             ev = torch.cuda.Event()
             ev.record(st)
         # buffers allocated on st are only reused by later work on st: stream order keeps them valid
-        return (ev, outs, sid)
+        return (ev, outs, sid, gk)
 
-    def _replay(self, key, p, op, xs, n, st):
+    @staticmethod
+    def _rows(pieces, c0, c1):
+        """Rows c0..c1 of the concatenated pieces as one contiguous view, or None."""
+        o = 0
+        for t in pieces:
+            k = int(t.shape[0])
+            if o <= c0 and c1 <= o + k:
+                v = t[c0 - o:c1 - o]
+                return v if v.is_contiguous() else None
+            o += k
+        return None
+
+    @staticmethod
+    def _gather(pieces, c0, c1, dst):
+        o = 0
+        for t in pieces:
+            k = int(t.shape[0])
+            a, b = max(c0, o), min(c1, o + k)
+            if a < b:
+                dst[a - c0:b - c0].copy_(t[a - o:b - o])
+            o += k
+
+    # ------------------------------------------------------------ graphs
+    def _graph_for(self, key, p, op, n, st):
+        """The (key, bucket) graph to replay for n maps, captured on first
+        use; None if its buffers exceed the limits or it is busy."""
         torch = self.torch
         b = self._bucket(n)
         gk = (key, b)
+        if gk in self.graph_busy:
+            return None
+        ib, ob = self._sizes(p, op)
+        nbytes = p.workspace_bytes(b) + b * (ib + ob)
+        if nbytes > self.graph_max_bytes:
+            return None
         if gk not in self.graphs:
+            while self.graphs and sum(v[4] for v in self.graphs.values()) + nbytes > self.graph_cache_bytes:
+                old = next((g for g in self.graphs if g not in self.graph_busy), None)
+                if old is None:
+                    return None
+                del self.graphs[old]
+            dev = f"cuda:{self.device}"
             shape_in = (b, p.ncomp, p.nalm if op == "alm2map" else p.npix)
             dt_in = torch.complex128 if op == "alm2map" else torch.float64
-            xin = torch.zeros(shape_in, dtype=dt_in, device=f"cuda:{self.device}")
-            ws = torch.empty(p.workspace_bytes(b) + 256, dtype=torch.uint8, device=xin.device)
+            xin = torch.zeros(shape_in, dtype=dt_in, device=dev)
+            yout = torch.empty((b, p.ncomp, p.npix if op == "alm2map" else p.nalm),
+                               dtype=torch.float64 if op == "alm2map" else torch.complex128, device=dev)
+            ws = torch.empty(p.workspace_bytes(b) + 256, dtype=torch.uint8, device=dev)
             ws = ws[(-ws.data_ptr()) % 256:]
-            run = (lambda: p.alm2map(xin, workspace=ws)) if op == "alm2map" else (lambda: p.map2alm(xin, workspace=ws))
+            if op == "alm2map":
+                def run():
+                    p.alm2map(xin, out=yout, workspace=ws)
+            else:
+                def run():
+                    p.map2alm(xin, out=yout, workspace=ws)
             run()                                      # warm-up outside the capture (sets kernel attributes)
-            torch.cuda.current_stream().synchronize()
+            st.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=st, capture_error_mode="thread_local"):
-                yout = run()
-            self.graphs[gk] = (g, xin, yout, ws)
-        g, xin, yout, ws = self.graphs[gk]
-        o = 0
-        for x in xs:
-            xin[o:o + x.shape[0]].copy_(x)
-            o += x.shape[0]
-        if o < b:
-            xin[o:].zero_()
+                run()
+            self.graphs[gk] = (g, xin, yout, ws, nbytes)
+        self.graphs.move_to_end(gk)
+        self.graph_busy.add(gk)
+        return gk
+
+    def _replay(self, gk, pieces, n, out_len, out_dt):
+        torch = self.torch
+        g, xin, yout, ws, _ = self.graphs[gk]
+        self._gather(pieces, 0, n, xin[:n])
+        if n < xin.shape[0]:
+            xin[n:].zero_()
         g.replay()
-        return yout[:n]
+        self.graph_replays += 1
+        # the graph's output buffer is reused by its next replay: copy out
+        return yout[:n].clone()
 
     def poll(self, handle):
-        ev, outs, sid = handle
+        ev, outs, sid, gk = handle
         if not ev.query():
             return None
         self.free_streams.append(sid)
+        if gk is not None:
+            self.graph_busy.discard(gk)
         return outs

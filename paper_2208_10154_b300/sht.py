@@ -61,6 +61,8 @@ def load() -> ctypes.CDLL:
             f = getattr(lib, "sht_plan_" + n)
             f.argtypes = [P]
             f.restype = LL
+        lib.sht_plan_device_bytes.argtypes = [P]
+        lib.sht_plan_device_bytes.restype = S
         lib.sht_alm2map.argtypes = [P, P, P, I, P, S, P]
         lib.sht_map2alm.argtypes = [P, P, P, I, I, P, S, P]
         lib.sht_alm2map_adjoint.argtypes = [P, P, P, I, P, S, P]
@@ -204,6 +206,10 @@ class Plan:
     def device_status(self) -> int:
         """0 if every bounded device wait of this plan's kernels succeeded; raises otherwise."""
         return sht_plan_device_status(self.handle)
+
+    def device_bytes(self) -> int:
+        """Device memory held by the plan itself (tables, host-path staging)."""
+        return int(load().sht_plan_device_bytes(self.handle))
 
     def workspace_bytes(self, nmaps: int, niter: int = 0) -> int:
         return sht_workspace_bytes(self.handle, nmaps, niter)

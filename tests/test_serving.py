@@ -111,15 +111,49 @@ def test_batches_finishing_out_of_order():
     assert srv.completed != reqs                      # retired out of order
 
 
+def test_executor_rows_and_gather_cpu():
+    """Row ranges of a list of pieces: a contiguous view when the range lies
+    in one piece, else a gather in order (GpuExecutor helpers, CPU tensors)."""
+    import torch
+    from paper_2208_10154_b300.serving import GpuExecutor
+    pieces = [torch.arange(3 * 2 * 4, dtype=torch.float64).reshape(3, 2, 4) + 100 * i for i in range(3)]
+    cat = torch.cat(pieces)
+    v = GpuExecutor._rows(pieces, 3, 5)
+    assert v is not None and torch.equal(v, cat[3:5])
+    assert GpuExecutor._rows(pieces, 2, 4) is None
+    dst = torch.empty((5, 2, 4), dtype=torch.float64)
+    GpuExecutor._gather(pieces, 2, 7, dst)
+    assert torch.equal(dst, cat[2:7])
+
+
+def test_executor_chunk_fits_the_cap():
+    """Chunk selection: the whole batch when it fits, else halvings until
+    workspace + staging + output fit the memory cap."""
+    from paper_2208_10154_b300.serving import GpuExecutor
+
+    class P:
+        ncomp, nalm, npix = 1, 10, 100
+
+        def workspace_bytes(self, n):
+            return 1000 * n
+    ex = GpuExecutor.__new__(GpuExecutor)
+    ex.mem_cap = 1e9
+    assert ex._chunk(P(), "alm2map", 64) == 64
+    ex.mem_cap = 64 * 800 + 8 * (1000 + 160)            # output of 64 maps + 8 maps of the rest
+    c = ex._chunk(P(), "alm2map", 64)
+    assert c == 8 and 1000 * c + 160 * c + 64 * 800 <= ex.mem_cap
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("graphs", [False, True])
-def test_gpu_results_same_alone_and_in_the_mix(graphs):
+@pytest.mark.parametrize("graphs,chunked", [(False, False), (True, False), (False, True)])
+def test_gpu_results_same_alone_and_in_the_mix(graphs, chunked):
     import torch
     from paper_2208_10154_b300 import build, inputs, sht
     from paper_2208_10154_b300.serving import GpuExecutor
     build.build()
     rng = np.random.default_rng(7)
-    ex = GpuExecutor(slots=3, use_graphs=graphs)
+    # chunked: a memory cap that forces batches through several library calls
+    ex = GpuExecutor(slots=3, use_graphs=graphs, mem_cap=2e6 if chunked else 150e9)
     srv = Server(ex, hbm_budget=4e9, max_batch_maps=16, slots=3)
     reqs = []
     for i in range(18):
@@ -134,13 +168,16 @@ def test_gpu_results_same_alone_and_in_the_mix(graphs):
             data = torch.from_numpy(a).cuda()
         else:
             data = torch.from_numpy(rng.standard_normal((n, ncomp, 12 * nside * nside))).cuda()
+        if chunked and n > 1:                         # a request given as a list of pieces
+            data = [data[:1], data[1:]]
         reqs.append(srv.submit(Request(op=op, nside=nside, spin=spin, data=data)))
     srv.run_until_idle()
     torch.cuda.synchronize()
     assert srv.stats()["errors"] == 0
     for r in reqs:
         p = ex.prepare(r.key("auto"))
-        alone = p.alm2map(r.data) if r.op == "alm2map" else p.map2alm(r.data)
+        x = torch.cat(list(r.data)) if isinstance(r.data, list) else r.data
+        alone = p.alm2map(x) if r.op == "alm2map" else p.map2alm(x)
         d = (r.result - alone).abs().max().item()
         s = alone.abs().max().item()
         assert d <= 1e-12 * s, (r.op, r.nside, r.spin, d, s)
