@@ -932,6 +932,96 @@ void oracle_map2alm_iter(int nside, int lmax, int mmax, int spin, int nmaps,
     free(res); free(da);
 }
 
+/* Immediate (Gauss-Seidel) iteration, Algorithm 3, spin 0. The ring
+ * spectra F of the residual map S - alm2map(a) are kept per ring (the full
+ * DFT, bins j = 0..N-1, no phase). Each pass walks m = 0..mmax in order:
+ *   T_m(ring)  = e^{-i m phi0} F_{m mod N}                 (remap)
+ *   c_lm       = dsigma sum_rings lambda_lm T_m             (this order's correction)
+ *   a_lm      += c_lm                                       (updated at once)
+ *   S_m(ring)  = sum_l c_lm lambda_lm                       (its synthesis)
+ *   F_{ m mod N} -= (w_m / 2) N S_m e^{+i m phi0},
+ *   F_{-m mod N} -= (w_m / 2) N conj(S_m) e^{-i m phi0}     (w_0 = 1, w_m = 2)
+ * so every later order sharing a bin with m (aliasing on rings with
+ * N <= 2 mmax) already sees the update. a starts at 0 and F at the DFT of
+ * the map; npass >= 1 passes (npass = 1 is one sweep, not the plain
+ * quadrature: without aliasing the two coincide). */
+void oracle_map2alm_immediate(int nside, int lmax, int mmax, int nmaps, const double* map, double* alm,
+                              int npass)
+{
+    long long npix = oracle_npix(nside);
+    long long nalm = oracle_nalm(lmax, mmax);
+    int nr = 4 * nside - 1;
+    ld dsig = 4.0L * PI_L / (ld)npix;
+    ld* F = (ld*)malloc(sizeof(ld) * 2 * (size_t)npix);      /* ring r's bins at start_r */
+    ld* lam = (ld*)malloc(sizeof(ld) * (size_t)nr * (lmax + 1));
+    ld* c = (ld*)malloc(sizeof(ld) * 2 * (lmax + 1));
+    ring_t* rg = (ring_t*)malloc(sizeof(ring_t) * nr);
+    for (int i = 1; i <= nr; i++) ring_geom(nside, i, &rg[i - 1]);
+    for (int j = 0; j < nmaps; j++) {
+        const double* x = map + (long long)j * npix;
+        double* o = alm + (long long)j * nalm * 2;
+        memset(o, 0, sizeof(double) * 2 * nalm);
+#pragma omp parallel for schedule(dynamic)
+        for (int i = 0; i < nr; i++) {                      /* F = DFT of each ring */
+            const ring_t* r = &rg[i];
+            for (int b = 0; b < r->n; b++) {
+                ld sr = 0.0L, si = 0.0L;
+                for (int k = 0; k < r->n; k++) {
+                    long long t = ((long long)b * k) % r->n;
+                    ld a = -2.0L * PI_L * (ld)t / r->n;
+                    sr += x[r->start + k] * cosl(a);
+                    si += x[r->start + k] * sinl(a);
+                }
+                F[2 * (r->start + b)] = sr;
+                F[2 * (r->start + b) + 1] = si;
+            }
+        }
+        for (int pass = 0; pass < npass; pass++) {
+            for (int m = 0; m <= mmax; m++) {
+                int nl = lmax - m + 1;
+#pragma omp parallel for schedule(dynamic)
+                for (int i = 0; i < nr; i++)
+                    lambda_lm(lmax, m, rg[i].cth, rg[i].sth, lam + (long long)i * (lmax + 1));
+                /* remap and correction */
+                for (int l = 0; l < nl; l++) { c[2 * l] = 0.0L; c[2 * l + 1] = 0.0L; }
+                for (int i = 0; i < nr; i++) {
+                    const ring_t* r = &rg[i];
+                    int b = m % r->n;
+                    ld fr = F[2 * (r->start + b)], fi = F[2 * (r->start + b) + 1];
+                    ld ph = -(ld)m * r->phi0, cph = cosl(ph), sph = sinl(ph);
+                    ld tr = cph * fr - sph * fi, ti = cph * fi + sph * fr;
+                    const ld* lp = lam + (long long)i * (lmax + 1);
+                    for (int l = 0; l < nl; l++) { c[2 * l] += lp[l] * tr; c[2 * l + 1] += lp[l] * ti; }
+                }
+                for (int l = 0; l < nl; l++) {
+                    c[2 * l] *= dsig;
+                    c[2 * l + 1] = (m == 0) ? 0.0L : c[2 * l + 1] * dsig;
+                    long long q = aidx(lmax, m + l, m);
+                    o[2 * q] += (double)c[2 * l];
+                    o[2 * q + 1] += (double)c[2 * l + 1];
+                }
+                /* synthesis of the correction, removed from the residual's bins */
+                ld w = (m == 0) ? 1.0L : 2.0L;
+                for (int i = 0; i < nr; i++) {
+                    const ring_t* r = &rg[i];
+                    const ld* lp = lam + (long long)i * (lmax + 1);
+                    ld sr = 0.0L, si = 0.0L;
+                    for (int l = 0; l < nl; l++) { sr += lp[l] * c[2 * l]; si += lp[l] * c[2 * l + 1]; }
+                    ld ph = (ld)m * r->phi0, cph = cosl(ph), sph = sinl(ph);
+                    ld ur = cph * sr - sph * si, ui = cph * si + sph * sr;     /* S e^{i m phi0} */
+                    ld f = 0.5L * w * (ld)r->n;
+                    int b1 = m % r->n, b2 = (r->n - b1) % r->n;
+                    F[2 * (r->start + b1)] -= f * ur;
+                    F[2 * (r->start + b1) + 1] -= f * ui;
+                    F[2 * (r->start + b2)] -= f * ur;
+                    F[2 * (r->start + b2) + 1] += f * ui;
+                }
+            }
+        }
+    }
+    free(F); free(lam); free(c); free(rg);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

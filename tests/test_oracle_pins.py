@@ -536,3 +536,54 @@ def test_sampled_tiers_equal_full_transform(orc, spin):
     for k, blk in enumerate(orc.map2alm_msel(x, nside, lmax, ms, mmax, spin)):
         i0 = orc.alm_index(lmax, ms[k], ms[k])
         assert np.array_equal(blk, af[..., i0:i0 + lmax - ms[k] + 1])
+
+
+# ------------------------------------------------- Algorithm 3 (immediate)
+def _gs_pixel(orc, x, nside, lmax, npass, mmax):
+    """Algorithm 3 read as a block Gauss-Seidel sweep over m in the pixel
+    domain: for each m in order, a_m += map2alm(S - alm2map(a))_m with the
+    residual recomputed from the current a (every earlier order updated)."""
+    a = np.zeros((x.shape[0], 1, orc.nalm(lmax, mmax)), dtype=complex)
+    for _ in range(npass):
+        for m in range(mmax + 1):
+            r = x - orc.alm2map(a, nside, lmax, mmax)
+            c = orc.map2alm_msel(r, nside, lmax, [m], mmax)[0]
+            i0 = orc.alm_index(lmax, m, m)
+            a[..., i0:i0 + lmax - m + 1] += c
+    return a
+
+
+@pytest.mark.parametrize("nside,lmax,mmax,npass", [(4, 15, 15, 2), (8, 20, 12, 2), (2, 7, 7, 3)])
+def test_immediate_fourier_domain_equals_pixel_definition(orc, nside, lmax, mmax, npass):
+    """The oracle's Algorithm 3 keeps the residual as ring spectra and updates
+    them after every order (aliased bins included); it must equal the
+    pixel-domain sweep, here with lmax up to 4 nside - 1 (heavy aliasing)."""
+    x = np.random.default_rng(nside).standard_normal((2, 1, 12 * nside * nside))
+    got = orc.map2alm_immediate(x, nside, lmax, npass, mmax)
+    assert rel(got, _gs_pixel(orc, x, nside, lmax, npass, mmax)) < 1e-13
+
+
+def test_immediate_without_aliasing_equals_traditional(orc):
+    """With mmax = 1 no two orders share a ring bin, so the orders decouple and
+    npass sweeps of Algorithm 3 equal Algorithm 2 with npass - 1 refinements."""
+    nside, lmax, mmax = 4, 5, 1
+    x = np.random.default_rng(0).standard_normal((2, 1, 12 * nside * nside))
+    for npass in (1, 2, 3):
+        g = orc.map2alm_immediate(x, nside, lmax, npass, mmax)
+        j = orc.map2alm(x, nside, lmax, mmax, niter=npass - 1)
+        assert rel(g, j) < 1e-13
+
+
+@pytest.mark.parametrize("nside,lmax", [(16, 40), (32, 80)])
+def test_immediate_more_accurate_for_lmax_below_3nside(orc, nside, lmax):
+    """Sec. 4: for band-limited maps with 2 nside < lmax < 3 nside the
+    immediate mode (Algorithm 3) is more accurate than the traditional one
+    (Algorithm 2) after the same number of passes, and both converge."""
+    a = inputs.gaussian_alm(3, 2, 1, lmax, cls=inputs.cl_inv_llp1(lmax))
+    x = orc.alm2map(a, nside, lmax)
+    eg, ej = [], []
+    for npass in (1, 2, 3, 4):
+        eg.append(rel(orc.map2alm_immediate(x, nside, lmax, npass), a))
+        ej.append(rel(orc.map2alm(x, nside, lmax, niter=npass - 1), a))
+    assert all(g < j for g, j in zip(eg[1:], ej[1:])), (eg, ej)
+    assert eg[-1] < 0.05 * eg[0]
