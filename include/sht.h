@@ -139,7 +139,26 @@ sht_status sht_alm2map(sht_plan* plan, const void* alm, void* map, int nmaps,
 sht_status sht_map2alm(sht_plan* plan, const void* map, void* alm, int nmaps, int niter,
                        void* workspace, size_t workspace_bytes, void* stream);
 
-/* Adjoints in real parameters (Re a_l0; Re, Im a_lm for m > 0), used by the
+/* Forward transform with the immediate iteration of Algorithm 3 (Sec. 4):
+ * the orders m are refined one after another inside each pass, and every
+ * order sees the corrections of the orders before it that share its ring
+ * bins (aliasing on rings of N <= 2 mmax pixels), where Algorithm 2 updates
+ * all orders together after the pass. Read as a block Gauss-Seidel sweep on
+ * the ring spectra of the residual, starting from a = 0:
+ *   for m = 0..mmax:  a_m += map2alm(T - alm2map(a))_m
+ * with the residual kept in the Fourier domain (no FFT inside a pass).
+ * npass >= 1 sweeps (npass = 1 is one sweep; without aliasing it equals the
+ * plain quadrature and npass sweeps equal Algorithm 2 with npass - 1
+ * refinements). For lmax between 2 nside and 3 nside it converges faster
+ * than Algorithm 2. FP64 spin-0 plans only (SHT_EUNSUPPORTED otherwise).
+ * Three kernel launches per order and pass (the orders depend on each
+ * other in sequence). Layouts as sht_map2alm; needs
+ * sht_workspace_bytes_immediate(plan, nmaps) bytes of workspace. */
+sht_status sht_map2alm_immediate(sht_plan* plan, const void* map, void* alm, int nmaps, int npass,
+                                 void* workspace, size_t workspace_bytes, void* stream);
+size_t     sht_workspace_bytes_immediate(const sht_plan* plan, int nmaps);
+
+/* Adjoints in real parameters/* Adjoints in real parameters (Re a_l0; Re, Im a_lm for m > 0), used by the
  * autograd wrappers. The paper has no adjoints; these are the exact
  * transposes of the two linear maps above:
  *   alm2map_adjoint(h)_lm = (Npix / 4 pi) map2alm(h)_lm * (1 if m = 0 [real

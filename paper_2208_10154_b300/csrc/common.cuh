@@ -137,6 +137,7 @@ struct sht_plan {
     // Legendre work lists (m, q, tile, 0) for the FP64 kernels
     int4* work_m2a = nullptr; int nwork_m2a = 0;
     int4* work_a2m = nullptr; int nwork_a2m = 0;
+    std::vector<int> m2a_off, a2m_off;   // first work item of each order m (mmax + 2 entries)
     // staging for the host-buffer entry points (allocated lazily)
     void* pin_in = nullptr;
     void* pin_out = nullptr;
@@ -180,6 +181,14 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
                                     cudaStream_t st);
 cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
+// one order m only (its work items); map2alm may add into alm
+cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                          double scale0, double scale, int m, bool accum, cudaStream_t st);
+cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m,
+                                          cudaStream_t st);
+// Fourier-domain residual of order m only: D[m] = T[m] - F(G)[m] (FP64)
+cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, const double* G, double* D, int nmaps,
+                                        int m, cudaStream_t st);
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
 int legendre_f64_row_tile();

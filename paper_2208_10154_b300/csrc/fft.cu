@@ -435,6 +435,71 @@ k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const Pa
     }
 }
 
+// The same residual for one order m only (Algorithm 3 updates the
+// coefficients order by order): D[m] = T[m] - F(G)[m], with F(G)[m] =
+// f sigma^{k0} [B(j) + sigma_j conj(B(j'))] folded from the current G of
+// every order that shares the ring bin j = m mod N (and its mirror j').
+// FP64. grid = (ring pair, column blocks of 128)
+__global__ void __launch_bounds__(128)
+k_alias_residual_order(const double2* __restrict__ T, const double2* __restrict__ G, double2* __restrict__ D,
+                       const PairGeom* __restrict__ pairs, int R_, int mmax, long long ncol, int nmc, int m)
+{
+    const int p = blockIdx.x;
+    const int mc = blockIdx.y * blockDim.x + threadIdx.x;
+    if (mc >= nmc) return;
+    const PairGeom g = pairs[p];
+    const int N = g.n;
+    const bool neg = g.phi0 != 0.0;
+    const bool eq = g.start_s < 0;
+    const long long qs = (long long)R_ * ncol;
+    auto idx = [&](int mm, int slot) -> long long {
+        return (((long long)mm * 2 + slot) * qs + (long long)p * ncol + (long long)mc * 2) >> 1;
+    };
+    auto fold = [&](int j, int slot) -> double2 {
+        double2 b = make_double2(0.0, 0.0);
+        double sk = 1.0;
+        for (int mm = j; mm <= mmax; mm += N) {
+            double2 v = G[idx(mm, slot)];
+            if (eq) {
+                const double2 o = G[idx(mm, 1)];
+                v.x += o.x;
+                v.y += o.y;
+            }
+            const double w = (mm ? 2.0 : 1.0) * sk;
+            b.x += w * v.x;
+            b.y += w * v.y;
+            if (neg) sk = -sk;
+        }
+        return b;
+    };
+    const int j = m % N, jp = (N - j) % N, k0 = m / N;
+    const double sj = (neg && j) ? -1.0 : 1.0;
+    const double fk = (eq ? 0.5 : 1.0) * (double)N * ((neg && (k0 & 1)) ? -1.0 : 1.0);
+    for (int slot = 0; slot < (eq ? 1 : 2); slot++) {
+        const double2 Bj = fold(j, slot);
+        const double2 Bc = (jp == j) ? Bj : fold(jp, slot);
+        const double xr = Bj.x + sj * Bc.x, xi = Bj.y - sj * Bc.y;
+        for (int s2 = 0; s2 < (eq ? 2 : 1); s2++) {
+            const long long i = idx(m, eq ? s2 : slot);
+            const double2 t = T[i];
+            D[i] = make_double2(t.x - fk * xr, t.y - fk * xi);
+        }
+    }
+}
+
+cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, const double* G, double* D, int nmaps,
+                                        int m, cudaStream_t st)
+{
+    const int nmc = nmaps * p->ncomp;
+    dim3 grid(p->R, (nmc + 127) / 128);
+    prof_start("k_alias_residual_order", st);
+    k_alias_residual_order<<<grid, 128, 0, st>>>((const double2*)T, (const double2*)G, (double2*)D, p->t.pairs,
+                                                 p->R, p->mmax, ncols(p, nmaps), nmc, m);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // column maxima of T[m][q][p][c] (FP32 hi/lo) over the ring pairs, as float
 // bits: the quanta of the split map2alm. grid = ((mmax + 1) * 2, column
 // blocks of 256)

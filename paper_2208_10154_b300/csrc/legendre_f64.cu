@@ -41,6 +41,7 @@ struct LegArgs {
     int ncomp;
     double scale;      // output scale for m > 0
     double scale0;     // output scale for m = 0
+    int accum;         // map2alm: add into alm instead of overwriting
 };
 
 __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
@@ -201,7 +202,8 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
             int reim = (int)(cg & 1);
             double v = (m == 0 ? a.scale0 : a.scale) * acc[i][j];
             if ((m == 0 && reim) || (a.spin && l < 2)) v = 0.0;
-            alm[(mc * a.nalm + d_alm_index(a.lmax, l, m)) * 2 + reim] = v;
+            double* dst = alm + (mc * a.nalm + d_alm_index(a.lmax, l, m)) * 2 + reim;
+            if (a.accum) *dst += v; else *dst = v;
         }
     }
 }
@@ -367,22 +369,54 @@ static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double sca
     a.ncol = ncols(p, nmaps); a.nalm = p->nalm; a.ncomp = p->ncomp;
     a.scale = scale;
     a.scale0 = scale0;
+    a.accum = 0;
     return a;
 }
 
-cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
-                                    double scale0, double scale, cudaStream_t st)
+// work items [w0, w0 + nwork) of the plan's list (the list runs over m in
+// order, so one order's items are one range); accum adds into alm
+static cudaError_t launch_m2a_range(const sht_plan* p, const double* T, double* alm, int nmaps, double scale0,
+                                    double scale, int w0, int nwork, bool accum, cudaStream_t st)
 {
-    const int4* work = p->work_m2a;
-    int nwork = p->nwork_m2a;
-    if (nwork == 0) return cudaSuccess;
+    if (nwork <= 0) return cudaSuccess;
     size_t sm = (size_t)(2 * M2A_TK * M2A_TL + 2 * M2A_TK * M2A_TN) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     long long nc = ncols(p, nmaps);
     dim3 grid((unsigned)nwork, (unsigned)((nc + M2A_TN - 1) / M2A_TN));
+    LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a + w0);
+    a.accum = accum ? 1 : 0;
     prof_start("k_leg_m2a_f64", st);
-    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, make_args(p, nmaps, scale0, scale, work));
+    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, a);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                    double scale0, double scale, cudaStream_t st)
+{
+    return launch_m2a_range(p, T, alm, nmaps, scale0, scale, 0, p->nwork_m2a, false, st);
+}
+
+cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                          double scale0, double scale, int m, bool accum, cudaStream_t st)
+{
+    const int w0 = p->m2a_off[m];
+    return launch_m2a_range(p, T, alm, nmaps, scale0, scale, w0, p->m2a_off[m + 1] - w0, accum, st);
+}
+
+static cudaError_t launch_a2m_range(const sht_plan* p, const double* alm, double* G, int nmaps, double scale0,
+                                    double scale, int w0, int nwork, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    size_t sm = (size_t)(A2M_TK * A2M_TP + A2M_TK * A2M_TN) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_a2m_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    long long nc = ncols(p, nmaps);
+    dim3 grid((unsigned)nwork, (unsigned)((nc + A2M_TN - 1) / A2M_TN));
+    prof_start("k_leg_a2m_f64", st);
+    k_leg_a2m_f64<<<grid, 256, sm, st>>>(alm, G, make_args(p, nmaps, scale0, scale, p->work_a2m + w0));
     prof_stop(st);
     count_launch();
     return cudaGetLastError();
@@ -391,19 +425,14 @@ cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* 
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
                                     double scale0, double scale, cudaStream_t st)
 {
-    const int4* work = p->work_a2m;
-    int nwork = p->nwork_a2m;
-    if (nwork == 0) return cudaSuccess;
-    size_t sm = (size_t)(A2M_TK * A2M_TP + A2M_TK * A2M_TN) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_leg_a2m_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    long long nc = ncols(p, nmaps);
-    dim3 grid((unsigned)nwork, (unsigned)((nc + A2M_TN - 1) / A2M_TN));
-    prof_start("k_leg_a2m_f64", st);
-    k_leg_a2m_f64<<<grid, 256, sm, st>>>(alm, G, make_args(p, nmaps, scale0, scale, work));
-    prof_stop(st);
-    count_launch();
-    return cudaGetLastError();
+    return launch_a2m_range(p, alm, G, nmaps, scale0, scale, 0, p->nwork_a2m, st);
+}
+
+cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m,
+                                          cudaStream_t st)
+{
+    const int w0 = p->a2m_off[m];
+    return launch_a2m_range(p, alm, G, nmaps, 1.0, 1.0, w0, p->a2m_off[m + 1] - w0, st);
 }
 
 int legendre_f64_row_tile() { return M2A_TL; }

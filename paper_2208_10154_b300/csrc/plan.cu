@@ -373,13 +373,20 @@ static cudaError_t build_tables(sht_plan* p)
     {
         int TL = legendre_f64_row_tile(), TP = legendre_f64_pair_tile();
         std::vector<int4> w1, w2;
-        for (int m = 0; m <= mmax; m++)
+        p->m2a_off.assign(mmax + 2, 0);
+        p->a2m_off.assign(mmax + 2, 0);
+        for (int m = 0; m <= mmax; m++) {
+            p->m2a_off[m] = (int)w1.size();
+            p->a2m_off[m] = (int)w2.size();
             for (int q = 0; q < 2; q++) {
                 int lf = m + q;
                 int nrows = (lmax >= lf) ? (lmax - lf) / 2 + 1 : 0;
                 for (int t = 0; t * TL < nrows; t++) w1.push_back(make_int4(m, q, t, 0));
                 for (int t = 0; t * TP < R; t++) w2.push_back(make_int4(m, q, t, 0));
             }
+        }
+        p->m2a_off[mmax + 1] = (int)w1.size();
+        p->a2m_off[mmax + 1] = (int)w2.size();
         p->nwork_m2a = (int)w1.size();
         p->nwork_a2m = (int)w2.size();
         if ((e = upload(&p->work_m2a, w1, &acc)) != cudaSuccess) return e;
@@ -1008,6 +1015,57 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) { set_error(std::string("map2alm iteration: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    return SHT_OK;
+}
+
+// Algorithm 3 (immediate iteration), FP64 spin-0 plans: ring spectra T of
+// the map, the current coefficients' spectra G and the residual D of one
+// order at a time, each [m][q][p][c] in FP64.
+size_t sht_workspace_bytes_immediate(const sht_plan* p, int nmaps)
+{
+    if (!p || nmaps < 1) return 0;
+    const size_t n = (size_t)(p->mmax + 1) * 2 * (size_t)p->R * (size_t)ncols(p, nmaps) * sizeof(double);
+    return 3 * round_up(n, 256);
+}
+
+sht_status sht_map2alm_immediate(sht_plan* p, const void* map, void* alm, int nmaps, int npass, void* ws,
+                                 size_t wsb, void* stream)
+{
+    t_err.clear();
+    reset_launches();
+    if (!p) { set_error("plan is NULL"); return SHT_EINVAL; }
+    if (p->precision != SHT_FP64 || p->spin != 0) {
+        set_error("the immediate iteration is built for FP64 spin-0 plans");
+        return SHT_EUNSUPPORTED;
+    }
+    if (nmaps < 1) { set_error("nmaps must be >= 1"); return SHT_EINVAL; }
+    if (npass < 1) { set_error("npass must be >= 1"); return SHT_EINVAL; }
+    if (!map || !alm) { set_error("data pointer is NULL"); return SHT_EINVAL; }
+    if (((uintptr_t)map & 15) || ((uintptr_t)alm & 15)) { set_error("data pointers must be 16-byte aligned"); return SHT_EINVAL; }
+    const size_t need = sht_workspace_bytes_immediate(p, nmaps);
+    if (!ws || wsb < need) { set_error("workspace too small: need " + std::to_string(need) + " bytes"); return SHT_EINVAL; }
+    if ((uintptr_t)ws & 255) { set_error("workspace must be 256-byte aligned"); return SHT_EINVAL; }
+    cudaSetDevice(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t tb = need / 3;
+    double* T = (double*)ws;
+    double* G = (double*)((char*)ws + tb);
+    double* D = (double*)((char*)ws + 2 * tb);
+    const double dsig = 4.0 * PI_D / (double)p->npix;
+    // a = 0, so the coefficients' spectra G = 0 and the first residual is T
+    cudaError_t e = launch_fft_forward_f64(p, (const double*)map, T, nmaps, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(alm, 0, (size_t)nmaps * p->nalm * 2 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, tb, st);
+    // each order m in turn: its residual from the current G of every order
+    // sharing its ring bins, its correction added to a at once, and its G
+    // recomputed from the updated a, so the orders after it see the update
+    for (int pass = 0; pass < npass && e == cudaSuccess; pass++)
+        for (int m = 0; m <= p->mmax && e == cudaSuccess; m++) {
+            e = launch_alias_residual_order(p, T, G, D, nmaps, m, st);
+            if (e == cudaSuccess) e = launch_legendre_m2a_f64_order(p, D, (double*)alm, nmaps, dsig, dsig, m, true, st);
+            if (e == cudaSuccess) e = launch_legendre_a2m_f64_order(p, (const double*)alm, G, nmaps, m, st);
+        }
+    if (e != cudaSuccess) { set_error(std::string("immediate iteration: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
 }
 

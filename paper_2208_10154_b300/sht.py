@@ -69,6 +69,10 @@ def load() -> ctypes.CDLL:
         lib.sht_map2alm_adjoint.argtypes = [P, P, P, I, P, S, P]
         lib.sht_alm2map_host.argtypes = [P, P, P, I, P]
         lib.sht_map2alm_host.argtypes = [P, P, P, I, I, P]
+        lib.sht_map2alm_immediate.argtypes = [P, P, P, I, I, P, S, P]
+        lib.sht_map2alm_immediate.restype = I
+        lib.sht_workspace_bytes_immediate.argtypes = [P, I]
+        lib.sht_workspace_bytes_immediate.restype = S
         lib.sht_alm_to_square.argtypes = [P, P, P, I, P]
         lib.sht_square_to_alm.argtypes = [P, P, P, I, P]
         lib.sht_eb_project.argtypes = [P, P, P, I, I, I, P, S, P]
@@ -253,6 +257,22 @@ class Plan:
         ws, wsb = self._workspace(nmaps, niter, workspace)
         sht_map2alm(self.handle, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                     nmaps, int(niter), ctypes.c_void_p(ws.data_ptr()), wsb, _stream())
+        return out
+
+    def map2alm_immediate(self, maps: torch.Tensor, npass: int, out=None) -> torch.Tensor:
+        """Algorithm 3 (immediate iteration): npass >= 1 Gauss-Seidel sweeps
+        over m from a = 0 (FP64 spin-0 plans)."""
+        maps = self._in(maps, torch.float64, self.npix)
+        nmaps = maps.numel() // (self.ncomp * self.npix)
+        if out is None:
+            out = torch.empty((nmaps, self.ncomp, self.nalm), dtype=torch.complex128, device=maps.device)
+        lib = load()
+        need = lib.sht_workspace_bytes_immediate(self.handle, nmaps)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=maps.device)
+        off = (-ws.data_ptr()) % 256
+        _check(lib.sht_map2alm_immediate(self.handle, ctypes.c_void_p(maps.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), nmaps, int(npass),
+                                         ctypes.c_void_p(ws.data_ptr() + off), need, _stream()))
         return out
 
     def alm2map_adjoint(self, maps: torch.Tensor, out=None, workspace=None) -> torch.Tensor:

@@ -88,6 +88,7 @@ def spin0_oracle(orc):
 @pytest.mark.parametrize("prec", ["fp64", "split"])
 def test_spin0_nside512_1000_maps(sht, spin0_oracle, prec):
     ref = spin0_oracle
+    NAME = "spin 0, nside 512, lmax 1023, 1000 maps"
     plan = sht.Plan(NS0, LM0, None, 0, prec)
     alm = inputs.gaussian_alm_torch(101, NM0, 1, LM0)
     maps = plan.alm2map(alm)
@@ -108,6 +109,7 @@ def test_spin0_nside512_1000_maps(sht, spin0_oracle, prec):
     plan.close()
     del maps, out, plan
     _free()
+    print(f"\n{NAME} {prec}: alm2map {err_a2m:.3e}, map2alm {err_m2a:.3e} (bar {TOL[prec]:.0e})")
     assert err_a2m < TOL[prec], ("alm2map", prec, err_a2m)
     assert err_m2a < TOL[prec], ("map2alm", prec, err_m2a)
 
@@ -173,6 +175,7 @@ def spin2_oracle(orc):
 def test_spin2_nside1024_200_pairs(orc, sht, spin2_oracle, prec):
     ref = spin2_oracle
     _, _, _, n, st = orc.ring_info(NS2)
+    NAME = "spin 2, nside 1024, lmax 2047, 200 pairs"
     plan = sht.Plan(NS2, LM2, None, 2, prec)
     cl = inputs.cl_inv_llp1(LM2)
     alm = inputs.gaussian_alm_torch(201, NP2, 2, LM2, cls=np.stack([cl, 0.01 * cl]))
@@ -204,5 +207,6 @@ def test_spin2_nside1024_200_pairs(orc, sht, spin2_oracle, prec):
     plan.close()
     del out, plan
     _free()
+    print(f"\n{NAME} {prec}: alm2map {err_a2m:.3e}, map2alm {err_m2a:.3e} (bar {TOL[prec]:.0e})")
     assert err_a2m < TOL[prec], ("alm2map", prec, err_a2m)
     assert err_m2a < TOL[prec], ("map2alm", prec, err_m2a)
