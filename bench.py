@@ -28,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving run allocates and frees batches of very different sizes on
+# several streams: growable segments keep the allocator from fragmenting
+os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
 
 METRIC = "maps/s batched vs per-map on one B300 at <=1e-6 rel err; served p50/p99 latency"
 WORKLOAD = "t_nside512"
@@ -685,6 +688,7 @@ def main():
         mo_h = torch.empty(maps_in.shape, dtype=torch.float64, pin_memory=True)
         ao_h = torch.empty(alm.shape, dtype=torch.complex128, pin_memory=True)
         del maps_out, alm_out, ws
+        maps_out = alm_out = ws = None
         torch.cuda.empty_cache()
         plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
         plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
@@ -713,7 +717,8 @@ def main():
         cpu = {"value": 1.0 / dt, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"1 map (alm2map + map2alm, nside {nside}, lmax {lmax}), separable tier"}
 
-    del alm, maps_in
+    del alm, maps_in, maps_out, alm_out, ws
+    gc.collect()
     torch.cuda.empty_cache()
     context = None
     if not a.no_context:
