@@ -139,6 +139,24 @@ sht_status sht_alm2map(sht_plan* plan, const void* alm, void* map, int nmaps,
 sht_status sht_map2alm(sht_plan* plan, const void* map, void* alm, int nmaps, int niter,
                        void* workspace, size_t workspace_bytes, void* stream);
 
+/* E-only or B-only transforms of spin-2 plans (the paper's remark that
+ * pipelines needing one of a_E, a_B should get it without the other,
+ * Sec. 3.1; equ:aeab mat form keeps one block row). which = 0: E, 1: B.
+ * sht_map2alm_eb: Q/U maps [nmaps][2][npix] -> that component's a_lm
+ * [nmaps][1][nalm]; the ring FFTs of Q and U run in full, the Legendre
+ * contraction forms only the kept component (half of the spin-2 work).
+ * Workspace: sht_workspace_bytes(plan, nmaps).
+ * sht_alm2map_eb: one component's a_lm [nmaps][1][nalm] -> Q/U maps
+ * [nmaps][2][npix] with the other component zero (the full spin-2
+ * synthesis, no saving). Workspace: sht_workspace_bytes_eb(plan, nmaps).
+ * SHT_EINVAL for spin-0 plans or another `which`. Otherwise as
+ * sht_map2alm / sht_alm2map. */
+sht_status sht_map2alm_eb(sht_plan* plan, const void* map, void* alm, int nmaps, int which,
+                          void* workspace, size_t workspace_bytes, void* stream);
+sht_status sht_alm2map_eb(sht_plan* plan, const void* alm, void* map, int nmaps, int which,
+                          void* workspace, size_t workspace_bytes, void* stream);
+size_t     sht_workspace_bytes_eb(const sht_plan* plan, int nmaps);
+
 /* Forward transform with the immediate iteration of Algorithm 3 (Sec. 4):
  * the orders m are refined one after another inside each pass, and every
  * order sees the corrections of the orders before it that share its ring
@@ -216,8 +234,9 @@ sht_status sht_square_to_alm(const sht_plan* plan, const void* sq, void* alm, in
 
 /* Pixel-domain E or B projection of Q/U maps (Sec. 2.3, equ:aeab mat form
  * pixel): out = alm2map(keep(map2alm(map, niter))), keep = the E (which = 0)
- * or B (which = 1) component of every a_lm, the other set to zero. Spin-2
- * plans only (SHT_EINVAL otherwise). map, out: double [nmaps][2][npix]
+ * or B (which = 1) component of every a_lm, the other set to zero. With
+ * niter = 0 the analysis forms only the kept component (sht_map2alm_eb).
+ * Spin-2 plans only (SHT_EINVAL otherwise). map, out: double [nmaps][2][npix]
  * (device, distinct); the result is the band-limited E- (B-) part of the
  * input, within the accuracy of the plan's precision and niter. Needs
  * sht_workspace_bytes_project(plan, nmaps, niter) bytes of workspace. */

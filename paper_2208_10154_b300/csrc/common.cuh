@@ -181,6 +181,11 @@ cudaError_t launch_fft_backward_f64(const sht_plan* p, const double* G, double* 
                                     cudaStream_t st);
 cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
+// [nmaps][2][nalm] a_lm with component `which` copied from [nmaps][1][nalm], the other zero
+cudaError_t expand_component(const sht_plan* p, const void* one, void* full, int nmaps, int which, cudaStream_t st);
+// spin-2 map2alm of one component (csel = 1: E, 2: B) into alm [nmaps][1][nalm]
+cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                         double scale0, double scale, int csel, cudaStream_t st);
 // one order m only (its work items); map2alm may add into alm
 cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
                                           double scale0, double scale, int m, bool accum, cudaStream_t st);
@@ -197,9 +202,11 @@ int legendre_f64_pair_tile();
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st);
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st);
-// (each runs the slicing pass into `img`, split_img_bytes long, then the contraction)
+// (each runs the slicing pass into `img`, split_img_bytes long, then the contraction;
+// csel = 1 / 2: spin-2 map2alm of the E / B component only, alm [nmaps][1][nalm])
 cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, uint8_t* img,
-                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st);
+                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st,
+                                   int csel = 0);
 cudaError_t launch_legendre_a2m_tc(const sht_plan* p, const float2* A2, const float* colmax, uint8_t* img,
                                    float* G, int nmaps, float s0, float s1, cudaStream_t st);
 size_t split_img_bytes(const sht_plan* p, int nmaps);

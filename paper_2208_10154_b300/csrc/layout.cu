@@ -122,7 +122,7 @@ size_t sht_workspace_bytes_project(const sht_plan* p, int nmaps, int niter)
 {
     if (!p || nmaps < 1 || niter < 0) return 0;
     const size_t alm_b = (size_t)nmaps * p->ncomp * (size_t)p->nalm * 2 * sizeof(double);
-    return round256(alm_b) + sht_workspace_bytes_iter(p, nmaps, niter);
+    return round256(alm_b) + round256(alm_b / 2) + sht_workspace_bytes_iter(p, nmaps, niter);
 }
 
 sht_status sht_eb_project(sht_plan* p, const void* map, void* out, int nmaps, int which, int niter, void* ws,
@@ -139,16 +139,25 @@ sht_status sht_eb_project(sht_plan* p, const void* map, void* out, int nmaps, in
     cudaSetDevice(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t row = (size_t)p->nalm * 2 * sizeof(double);        // one component of one map
-    const size_t alm_b = round256((size_t)nmaps * 2 * row);
+    const size_t alm_b = round256((size_t)nmaps * 2 * row), one_b = round256((size_t)nmaps * row);
     char* alm = (char*)ws;
-    void* tws = (char*)ws + alm_b;
-    const size_t twsb = wsb - alm_b;
-    s = sht_map2alm(p, map, alm, nmaps, niter, tws, twsb, stream);
-    if (s != SHT_OK) return s;
+    char* one = alm + alm_b;
+    void* tws = one + one_b;
+    const size_t twsb = wsb - alm_b - one_b;
+    cudaError_t e;
+    if (niter == 0) {
+        // only the kept component is formed (half of the spin-2 contraction)
+        s = sht_map2alm_eb(p, map, one, nmaps, which, tws, twsb, stream);
+        if (s != SHT_OK) return s;
+        e = expand_component(p, one, alm, nmaps, which, st);
+    } else {
+        s = sht_map2alm(p, map, alm, nmaps, niter, tws, twsb, stream);
+        if (s != SHT_OK) return s;
+        // zero the other component of every map: rows of `row` bytes, 2 rows apart
+        e = cudaMemset2DAsync(alm + (size_t)(1 - which) * row, 2 * row, 0, row, (size_t)nmaps, st);
+    }
     const int launches = sht_last_launch_count();
-    // zero the other component of every map: rows of `row` bytes, 2 rows apart
-    const cudaError_t e = cudaMemset2DAsync(alm + (size_t)(1 - which) * row, 2 * row, 0, row, (size_t)nmaps, st);
-    if (e != cudaSuccess) { set_error(std::string("eb_project memset: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    if (e != cudaSuccess) { set_error(std::string("eb_project copy: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     s = sht_alm2map(p, alm, out, nmaps, tws, twsb, stream);
     count_launch(launches);
     return s;

@@ -42,6 +42,11 @@ struct LegArgs {
     double scale;      // output scale for m > 0
     double scale0;     // output scale for m = 0
     int accum;         // map2alm: add into alm instead of overwriting
+    // spin-2 map2alm of one component: csel = 1 (E) / 2 (B) keeps the two
+    // columns per map that form it (ncol = output columns); pcol = columns
+    // of T. csel = 0: pcol = ncol.
+    long long pcol;
+    int csel;
 };
 
 __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
@@ -70,7 +75,7 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
     const int nrows = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
     const int r0 = rt * M2A_TL;
     const int ntypes = a.spin ? 2 : 1;
-    const long long qstride = (long long)a.R * a.ncol;
+    const long long qstride = (long long)a.R * a.pcol;     // T holds every data column
     const double* Tq = T + ((long long)m * 2 + q) * qstride;
     const double* To = T + ((long long)m * 2 + (1 - q)) * qstride;
     const int tx = tid & 7, ty = tid >> 3;
@@ -158,11 +163,12 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
             long long cg = c0 + c;
             double v0 = 0.0, v1 = 0.0;
             if (p < a.R && cg < a.ncol) {
-                v0 = Tq[(long long)p * a.ncol + cg];
+                const long long pc = a.csel == 0 ? cg : ((cg >> 1) << 2) + (cg & 1) + (a.csel == 2 ? 2 : 0);
+                v0 = Tq[(long long)p * a.pcol + pc];
                 if (a.spin) {
-                    long long base = cg & ~3LL;
-                    int wsel = (int)(cg & 3);
-                    const double* o = To + (long long)p * a.ncol + base;
+                    long long base = pc & ~3LL;
+                    int wsel = (int)(pc & 3);
+                    const double* o = To + (long long)p * a.pcol + base;
                     v1 = (wsel == 0) ? -o[3] : (wsel == 1) ? o[2] : (wsel == 2) ? o[1] : -o[0];
                 }
             }
@@ -370,6 +376,8 @@ static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double sca
     a.scale = scale;
     a.scale0 = scale0;
     a.accum = 0;
+    a.pcol = a.ncol;
+    a.csel = 0;
     return a;
 }
 
@@ -397,6 +405,25 @@ cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* 
                                     double scale0, double scale, cudaStream_t st)
 {
     return launch_m2a_range(p, T, alm, nmaps, scale0, scale, 0, p->nwork_m2a, false, st);
+}
+
+cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, double* alm, int nmaps,
+                                         double scale0, double scale, int csel, cudaStream_t st)
+{
+    const int nwork = p->nwork_m2a;
+    if (nwork <= 0) return cudaSuccess;
+    size_t sm = (size_t)(2 * M2A_TK * M2A_TL + 2 * M2A_TK * M2A_TN) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a);
+    a.csel = csel;
+    a.ncol = a.pcol / 2;
+    dim3 grid((unsigned)nwork, (unsigned)((a.ncol + M2A_TN - 1) / M2A_TN));
+    prof_start("k_leg_m2a_f64", st);
+    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, a);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,

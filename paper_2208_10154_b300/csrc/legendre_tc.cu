@@ -126,7 +126,12 @@ struct TcArgs {
     int* err;
     int lmax, mmax, R;
     int ntile;                 // column tiles of 128
-    long long ncol, nalm;
+    long long ncol, nalm;      // ncol: columns of the contraction (output columns)
+    // spin-2 map2alm of one component: csel = 1 (E) or 2 (B) keeps, per map,
+    // the two columns that form it; pcol = the columns of the data (row
+    // stride of T and the column maxima). csel = 0: all columns, pcol = ncol.
+    long long pcol;
+    int csel;
     float Q;                   // integer range of the main slices
     double fs0, fs1;           // map2alm: output factor (dsigma times any adjoint weight), m = 0 / m > 0
     float s0, s1;              // alm2map: extra output scale for m = 0 / m > 0
@@ -380,6 +385,13 @@ __device__ __forceinline__ void rescale(double& cur, double& prev, int& E)
 __device__ __forceinline__ int perm_src(int c) { return (c & ~3) | (3 - (c & 3)); }
 __device__ __forceinline__ float perm_sign(int c) { return ((c & 3) == 0 || (c & 3) == 3) ? -1.0f : 1.0f; }
 
+// data column (in T and the column maxima) of contraction column j: itself,
+// or for one spin-2 component (E: Xr, Xi of each group of four; B: Yr, Yi)
+__device__ __forceinline__ long long phys_col(const TcArgs& a, long long j)
+{
+    return a.csel == 0 ? j : ((j >> 1) << 2) + (j & 1) + (a.csel == 2 ? 2 : 0);
+}
+
 // quantum exponent of data column c0 + c of (m, q). Spin 2 also bounds the
 // other slot, permuted: map2alm slices T_q +- P(T_{1-q}) (bounded by the sum),
 // alm2map slices a_l or P(a_l) (bounded by the larger).
@@ -388,9 +400,10 @@ __device__ __forceinline__ int col_quantum(const TcArgs& a, int m, int q, long l
 {
     const long long cg = c0 + c;
     if (cg >= a.ncol) return 0;
-    float mx = a.colmax[((long long)m * 2 + q) * a.ncol + cg];
+    const long long pc = phys_col(a, cg);
+    float mx = a.colmax[((long long)m * 2 + q) * a.pcol + pc];
     if (S2) {
-        const float mo = a.colmax[((long long)m * 2 + (1 - q)) * a.ncol + (c0 + perm_src(c))];
+        const float mo = a.colmax[((long long)m * 2 + (1 - q)) * a.pcol + perm_src((int)(pc & 3)) + (pc & ~3LL)];
         mx = M2A ? mx + mo : fmaxf(mx, mo);
     }
     return quantum_exp(mx, a.Q);
@@ -1051,14 +1064,19 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
     const long long c0 = (long long)blockIdx.y * TC_M;
     const long long cg = c0 + t;
     const bool cok = cg < a.ncol;
+    const long long pc = phys_col(a, cg);           // the column in T / A2
     const int l_first = m + q;
     const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
     const int K = M2A ? a.R : (S2 ? a.lmax - m + 1 : nl);
     constexpr bool TWO = S2 && M2A;                 // map2alm spin 2 reads both slots
+    // one spin-2 component: this thread reads the permuted partner column of
+    // the other slot itself (its lane does not hold it)
+    const long long pc1 = (TWO && a.csel) ? perm_src((int)(pc & 3)) + (pc & ~3LL) : pc;
     float2 buf[TWO ? 2 * KC : KC];
 #pragma unroll
     for (int h = 0; h < (TWO ? 2 : 1); h++) {
         const int slot = h ? 1 - q : q;
+        const long long col = h ? pc1 : pc;
 #pragma unroll
         for (int i = 0; i < KC; i++) {
             const int k = u * KC + i;
@@ -1067,7 +1085,7 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
                 long long row;
                 if (M2A) row = ((long long)m * 2 + slot) * a.R + k;
                 else row = S2 ? a_idx(a.lmax, m + k, m) : a_idx(a.lmax, l_first + 2 * k, m);
-                x = __ldg(raw + row * a.ncol + cg);
+                x = __ldg(raw + row * a.pcol + col);
             }
             buf[h * KC + i] = x;
         }
@@ -1075,7 +1093,8 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
     const int ce = col_quantum<M2A, S2>(a, m, q, c0, t);
     const float csc = __int_as_float((127 - ce) << 23);   // 2^-ce (exact scaling)
     const int psrc = (lane & ~3) | (3 - (lane & 3));     // spin 2: lane of the permuted column
-    const float sgp = perm_sign(t);
+    const float sgp = perm_sign((int)(pc & 3));
+    const bool direct = a.csel != 0;
 #pragma unroll
     for (int sub = 0; sub < (TWO ? 2 : 1); sub++) {
         uint8_t* A = img + ((long long)(w.w + sub) * a.ntile + blockIdx.y) * A_BYTES;
@@ -1094,6 +1113,7 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
                     float2 x1;
                     x1.x = __shfl_sync(0xffffffffu, buf[KC + r].x, psrc);
                     x1.y = __shfl_sync(0xffffffffu, buf[KC + r].y, psrc);
+                    if (direct) x1 = buf[KC + r];
                     const float sb = sub ? -sgp : sgp;
                     const float bh = sb * x1.x;
                     const float s1 = x0.x + bh;
@@ -1310,6 +1330,7 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.err = p->s.err;
     a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;
     a.ncol = ncols(p, nmaps); a.nalm = p->nalm;
+    a.pcol = a.ncol; a.csel = 0;
     a.ntile = (int)((a.ncol + TC_M - 1) / TC_M);
     a.img = nullptr; a.img_base = nullptr; a.sunits = nullptr;
     a.Q = Q;
@@ -1470,10 +1491,15 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
 
 // (the slicing pass writes the image that the contraction then reads, in stream order)
 cudaError_t launch_legendre_m2a_tc(const sht_plan* p, const float2* T, const float* colmax, uint8_t* img,
-                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st)
+                                   double* alm, int nmaps, double fs0, double fs1, cudaStream_t st, int csel)
 {
     if (p->s.nwork_m2a == 0) return cudaSuccess;
     TcArgs a = make_tc(p, nmaps, colmax, p->s.Q_m2a);
+    if (csel) {                      // one spin-2 component: half the columns
+        a.csel = csel;
+        a.ncol = a.pcol / 2;
+        a.ntile = (int)((a.ncol + TC_M - 1) / TC_M);
+    }
     a.fs0 = fs0; a.fs1 = fs1;
     a.work = p->s.work_m2a;
     a.img = img; a.img_base = p->s.img_base_m2a; a.sunits = p->s.sunits_m2a;

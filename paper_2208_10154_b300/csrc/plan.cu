@@ -744,6 +744,17 @@ __global__ void k_add(double* __restrict__ a, const double* __restrict__ d, long
 }
 static int ew_grid(long long n) { long long b = (n + 255) / 256; return (int)std::min<long long>(b, 148 * 16); }
 
+// [nmaps][2][nalm] a_lm with component `which` from one [nmaps][1][nalm], the other zero
+cudaError_t expand_component(const sht_plan* p, const void* one, void* full, int nmaps, int which, cudaStream_t st)
+{
+    const size_t row = (size_t)p->nalm * 2 * sizeof(double);
+    cudaError_t e = cudaMemset2DAsync((char*)full + (size_t)(1 - which) * row, 2 * row, 0, row, (size_t)nmaps, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync((char*)full + (size_t)which * row, 2 * row, one, row, row, (size_t)nmaps,
+                              cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
 }  // namespace sht
 
 using namespace sht;
@@ -1016,6 +1027,72 @@ sht_status sht_map2alm(sht_plan* p, const void* map, void* alm, int nmaps, int n
     }
     if (e != cudaSuccess) { set_error(std::string("map2alm iteration: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;
+}
+
+// E-only / B-only transforms of spin-2 plans (Sec. 3.1: pipelines that need
+// one of a_E, a_B). map2alm: the ring FFTs of Q and U, then a contraction
+// over the two columns per map that form the kept component (half of the
+// spin-2 contraction). alm2map from one component: the other is zero.
+static sht_status check_eb(const sht_plan* p, int which)
+{
+    if (p->spin != 2) { set_error("E/B transforms need a spin-2 plan"); return SHT_EINVAL; }
+    if (which != 0 && which != 1) { set_error("which must be 0 (E) or 1 (B)"); return SHT_EINVAL; }
+    return SHT_OK;
+}
+
+sht_status sht_map2alm_eb(sht_plan* p, const void* map, void* alm, int nmaps, int which, void* ws, size_t wsb,
+                          void* stream)
+{
+    sht_status s = check_call(p, map, alm, nmaps, ws, wsb, 0);
+    if (s != SHT_OK) return s;
+    if ((s = check_eb(p, which)) != SHT_OK) return s;
+    cudaSetDevice(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const double dsig = 4.0 * PI_D / (double)p->npix;
+    cudaError_t e;
+    if (p->precision == SHT_FP64) {
+        double* T = (double*)ws;
+        e = launch_fft_forward_f64(p, (const double*)map, T, nmaps, st);
+        if (e == cudaSuccess)
+            e = launch_legendre_m2a_f64_comp(p, T, (double*)alm, nmaps, dsig, dsig, which + 1, st);
+    } else {
+        float2* T = (float2*)ws;
+        unsigned int* cm = (unsigned int*)((char*)ws + round_up(tbuf_bytes(p, nmaps), 256));
+        e = launch_fft_forward_split(p, (const double*)map, T, cm, nmaps, st);
+        if (e == cudaSuccess)
+            e = launch_legendre_m2a_tc(p, T, (const float*)cm, (uint8_t*)ws + img_offset(p, nmaps), (double*)alm,
+                                       nmaps, dsig, dsig, st, which + 1);
+    }
+    if (e != cudaSuccess) { set_error(std::string("map2alm_eb launch: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    return SHT_OK;
+}
+
+size_t sht_workspace_bytes_eb(const sht_plan* p, int nmaps)
+{
+    if (!p || nmaps < 1) return 0;
+    return round_up((size_t)nmaps * 2 * (size_t)p->nalm * 2 * sizeof(double), 256) + ws_bytes(p, nmaps, 0);
+}
+
+sht_status sht_alm2map_eb(sht_plan* p, const void* alm, void* map, int nmaps, int which, void* ws, size_t wsb,
+                          void* stream)
+{
+    t_err.clear();
+    reset_launches();
+    if (!p) { set_error("plan is NULL"); return SHT_EINVAL; }
+    sht_status s = check_eb(p, which);
+    if (s != SHT_OK) return s;
+    if (nmaps < 1) { set_error("nmaps must be >= 1"); return SHT_EINVAL; }
+    if (!alm || !map) { set_error("data pointer is NULL"); return SHT_EINVAL; }
+    if (((uintptr_t)alm & 15) || ((uintptr_t)map & 15)) { set_error("data pointers must be 16-byte aligned"); return SHT_EINVAL; }
+    const size_t need = sht_workspace_bytes_eb(p, nmaps);
+    if (!ws || wsb < need) { set_error("workspace too small: need " + std::to_string(need) + " bytes"); return SHT_EINVAL; }
+    if ((uintptr_t)ws & 255) { set_error("workspace must be 256-byte aligned"); return SHT_EINVAL; }
+    cudaSetDevice(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t fb = round_up((size_t)nmaps * 2 * (size_t)p->nalm * 2 * sizeof(double), 256);
+    cudaError_t e = expand_component(p, alm, ws, nmaps, which, st);
+    if (e != cudaSuccess) { set_error(std::string("alm2map_eb copy: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
+    return do_alm2map(p, (const double*)ws, (double*)map, nmaps, (char*)ws + fb, 1.0, 1.0, st);
 }
 
 // Algorithm 3 (immediate iteration), FP64 spin-0 plans: ring spectra T of

@@ -69,6 +69,12 @@ def load() -> ctypes.CDLL:
         lib.sht_map2alm_adjoint.argtypes = [P, P, P, I, P, S, P]
         lib.sht_alm2map_host.argtypes = [P, P, P, I, P]
         lib.sht_map2alm_host.argtypes = [P, P, P, I, I, P]
+        lib.sht_map2alm_eb.argtypes = [P, P, P, I, I, P, S, P]
+        lib.sht_map2alm_eb.restype = I
+        lib.sht_alm2map_eb.argtypes = [P, P, P, I, I, P, S, P]
+        lib.sht_alm2map_eb.restype = I
+        lib.sht_workspace_bytes_eb.argtypes = [P, I]
+        lib.sht_workspace_bytes_eb.restype = S
         lib.sht_map2alm_immediate.argtypes = [P, P, P, I, I, P, S, P]
         lib.sht_map2alm_immediate.restype = I
         lib.sht_workspace_bytes_immediate.argtypes = [P, I]
@@ -257,6 +263,33 @@ class Plan:
         ws, wsb = self._workspace(nmaps, niter, workspace)
         sht_map2alm(self.handle, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                     nmaps, int(niter), ctypes.c_void_p(ws.data_ptr()), wsb, _stream())
+        return out
+
+    def map2alm_eb(self, maps: torch.Tensor, which: str = "E", out=None, workspace=None) -> torch.Tensor:
+        """One component (E or B) of the spin-2 map2alm: [nmaps, 2, npix] -> [nmaps, 1, nalm]."""
+        maps = self._in(maps, torch.float64, self.npix)
+        nmaps = maps.numel() // (2 * self.npix)
+        if out is None:
+            out = torch.empty((nmaps, 1, self.nalm), dtype=torch.complex128, device=maps.device)
+        ws, wsb = self._workspace(nmaps, 0, workspace)
+        _check(load().sht_map2alm_eb(self.handle, ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     nmaps, {"E": 0, "B": 1}[which], ctypes.c_void_p(ws.data_ptr()), wsb,
+                                     _stream()))
+        return out
+
+    def alm2map_eb(self, alm: torch.Tensor, which: str = "E", out=None) -> torch.Tensor:
+        """Q/U maps [nmaps, 2, npix] from one component's a_lm [nmaps, 1, nalm] (the other zero)."""
+        alm = self._in(alm, torch.complex128, self.nalm)
+        nmaps = alm.numel() // self.nalm
+        if out is None:
+            out = torch.empty((nmaps, 2, self.npix), dtype=torch.float64, device=alm.device)
+        lib = load()
+        need = lib.sht_workspace_bytes_eb(self.handle, nmaps)
+        ws = torch.empty(need + 256, dtype=torch.uint8, device=alm.device)
+        off = (-ws.data_ptr()) % 256
+        _check(lib.sht_alm2map_eb(self.handle, ctypes.c_void_p(alm.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                  nmaps, {"E": 0, "B": 1}[which], ctypes.c_void_p(ws.data_ptr() + off), need,
+                                  _stream()))
         return out
 
     def map2alm_immediate(self, maps: torch.Tensor, npass: int, out=None) -> torch.Tensor:
