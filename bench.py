@@ -273,6 +273,23 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
     prof = sht.sht_profile_end()
     ms = e0.elapsed_time(e1) / steps
     status = plan.device_status()
+    # E-only map2alm (Sec. 3.1: one of a_E, a_B) beside the full spin-2 map2alm
+    e_only = plan.map2alm_eb(maps, "E", workspace=ws)
+    torch.cuda.synchronize()
+    t_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_ev[0].record()
+    plan.map2alm(maps, out=alm_out, workspace=ws)
+    t_ev[1].record()
+    plan.map2alm_eb(maps, "E", out=e_only, workspace=ws)
+    t_ev[2].record()
+    plan.map2alm_eb(maps, "B", out=e_only, workspace=ws)
+    t_ev[3].record()
+    torch.cuda.synchronize()
+    t_full, t_e, t_b = (t_ev[i].elapsed_time(t_ev[i + 1]) for i in range(3))
+    eb_only = {"pairs": npairs, "map2alm_full_ms": t_full, "map2alm_E_ms": t_e, "map2alm_B_ms": t_b,
+               "E_over_full": t_e / t_full, "device_status": plan.device_status(),
+               "note": "ring FFTs of Q and U in full; the Legendre contraction forms one component"}
+    del e_only
     # per-pair FP64 form
     p64 = sht.Plan(nside, lmax, None, 2, "fp64")
     a1 = alm[:1].contiguous()
@@ -292,7 +309,7 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
            "config": {"workload": "qu", "nside": nside, "lmax": lmax, "npairs": npairs, "spin": 2,
                       "precision": precision, "cl": "EE 1/(l(l+1)), BB 0.01 EE", "seed": 2},
            "per_map": {"value": per, "unit": "Q/U map pairs/s", "form": "fp64, one pair"},
-           "batched_over_per_map": npairs / (ms / 1e3) / per, "device_status": status,
+           "batched_over_per_map": npairs / (ms / 1e3) / per, "device_status": status, "eb_only": eb_only,
            "kernels": {k: {"launches": v["launches"], "ms": v["ms"] / steps} for k, v in prof.items()}}
     del plan, p64, ws, maps, alm, alm_out
     torch.cuda.empty_cache()

@@ -128,11 +128,16 @@ class Server:
                 if key is None:
                     break
                 q = self.pending[key]
+            self.ex.prepare(key)
+            room = self.budget - self._resident()
+            with self.lock:
+                # grow the batch while it stays within max_batch maps and
+                # within the memory left beside the resident plans
                 reqs, n = [], 0
-                while q and (not reqs or n + q[0].nmaps <= self.max_batch):
+                while q and (not reqs or (n + q[0].nmaps <= self.max_batch
+                                          and self.ex.batch_bytes(key, n + q[0].nmaps) <= room)):
                     reqs.append(q.popleft())
                     n += reqs[-1].nmaps
-            self.ex.prepare(key)
             nbytes = self.ex.batch_bytes(key, n)
             # (a batch larger than the whole budget still runs, alone)
             if self.used + self._resident() + nbytes > self.budget and self.inflight:
@@ -280,11 +285,13 @@ class GpuExecutor:
         return (alm_b, map_b) if op == "alm2map" else (map_b, alm_b)
 
     def _chunk(self, p, op, n):
-        """Maps per library call: all n if they fit the memory cap, else the
-        largest halving of n that does (at least 1)."""
+        """Maps per library call: all n if they fit the memory cap (less what
+        the executor keeps resident), else the largest halving of n that does
+        (at least 1)."""
         ib, ob = self._sizes(p, op)
+        cap = self.mem_cap - self.resident_bytes()
         c = n
-        while c > 1 and p.workspace_bytes(c) + c * ib + n * ob > self.mem_cap:
+        while c > 1 and p.workspace_bytes(c) + c * ib + n * ob > cap:
             c = (c + 1) // 2
         return c
 

@@ -64,6 +64,24 @@ def test_admission_respects_budget_and_slots():
     assert srv.peak_used <= 1000
 
 
+def test_batches_fit_the_budget_beside_resident_memory():
+    """A batch grows only while it fits the budget left beside what the
+    executor keeps resident; the admitted total never exceeds the budget."""
+    class Resident(FakeExecutor):
+        def resident_bytes(self):
+            return 400.0
+    rng = np.random.default_rng(5)
+    ex = Resident(lag=2, bytes_per_map=100)
+    srv = Server(ex, hbm_budget=1000, max_batch_maps=64, slots=2)
+    for i in range(6):
+        srv.submit(_req("alm2map", 8, 3, rng))
+    while not srv.idle():
+        srv.step()
+        assert srv.used + 400.0 <= 1000
+    assert all(n <= 6 for _, n in ex.launched)       # (1000 - 400) / 100 maps per batch
+    assert srv.peak_used <= 1000
+
+
 def test_continuous_admission_while_busy():
     rng = np.random.default_rng(2)
     ex = FakeExecutor(lag=5)
@@ -137,6 +155,7 @@ def test_executor_chunk_fits_the_cap():
         def workspace_bytes(self, n):
             return 1000 * n
     ex = GpuExecutor.__new__(GpuExecutor)
+    ex.resident_bytes = lambda: 0.0
     ex.mem_cap = 1e9
     assert ex._chunk(P(), "alm2map", 64) == 64
     ex.mem_cap = 64 * 800 + 8 * (1000 + 160)            # output of 64 maps + 8 maps of the rest
