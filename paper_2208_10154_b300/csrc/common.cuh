@@ -35,13 +35,16 @@ struct PairGeom {
     int fft;           // index into the FFT length table
 };
 
-// One distinct ring length and its FFT recipe.
+// One distinct ring length and its FFT recipe. The FP64 form uses
+// power-of-two sizes (p3 = 1); the split form's own table also uses sizes
+// M = 3^b 2^a (p3 = 3^b, 2^a >= 64), whichever needs the least work.
 struct FftLen {
     int n;             // ring length N
-    int m;             // power-of-two FFT size used (N itself or the Bluestein size)
-    int bluestein;     // 1 if N is not a power of two
+    int m;             // FFT size used (N itself or the Bluestein size)
+    int bluestein;     // 1 if N itself is not transformed directly
     long long chirp;   // offset of w_n = exp(-i pi n^2 / N) (n < N) in the chirp table
-    long long bhat;    // offset of FFT_M(conj chirp, circular) (bit-reversed order)
+    long long bhat;    // offset of FFT_M(conj chirp, circular) (digit-reversed order)
+    int p3;            // 3^b of M (1: M is a power of two)
 };
 
 struct DevTables {
@@ -75,6 +78,7 @@ struct DevTables {
 struct FftClass {
     int m;             // FFT size of the class
     int off, cnt;      // its ring pairs: cls_pairs[off .. off + cnt)
+    long long tw;      // split form: offset of its twiddles exp(-2 pi i u / m), u < m / 2
 };
 
 struct CompTables {
@@ -85,6 +89,13 @@ struct CompTables {
     float2* phase_h = nullptr;     // exp(+i pi k / N), k < 2N, per ring length
     float2* phase_l = nullptr;
     long long* phase_off = nullptr;
+    // the split form's FFT recipes (sizes 2^a or 3^b 2^a), per-class twiddles
+    // and digit-reversed Bluestein filters, FP32 hi/lo
+    FftLen* fft_s = nullptr;
+    float2* tws_h = nullptr;
+    float2* tws_l = nullptr;
+    float2* bhs_h = nullptr;
+    float2* bhs_l = nullptr;
 };
 
 // tables of the split-precision (tensor-core) form
@@ -132,6 +143,7 @@ struct sht_plan {
     sht::CompTables c;
     std::vector<sht::PairGeom> h_pairs;
     std::vector<sht::FftLen> h_fft;
+    std::vector<sht::FftLen> h_fft_s;       // split form's FFT recipes
     std::vector<sht::FftClass> h_fcls;
     size_t table_bytes = 0;
     // Legendre work lists (m, q, tile, 0) for the FP64 kernels

@@ -103,9 +103,9 @@ __device__ __forceinline__ cx cmul_mi(const cx& a) { cx r; r.hr = a.hi; r.lr = a
 __device__ __forceinline__ cx cmul_pi(const cx& a) { cx r; r.hr = -a.hi; r.lr = -a.li; r.hi = a.hr; r.li = a.lr; return r; }
 
 struct FftTabsF {
-    const float2 *twh, *twl;      // exp(-2 pi i t / fftmax), t < fftmax / 2, hi / lo
+    const float2 *twh, *twl;      // per size class: exp(-2 pi i u / M), u < M / 2, hi / lo
     const float2 *chh, *chl;      // Bluestein chirp, hi / lo
-    const float2 *bhh, *bhl;      // Bluestein filter spectrum (bit-reversed), hi / lo
+    const float2 *bhh, *bhl;      // Bluestein filter spectrum / M (digit-reversed), hi / lo
     const float2 *phh, *phl;      // exp(+i pi k / N), k < 2N, per ring length, hi / lo
     const long long* phoff;       // offset of each ring length's phase table
 };
@@ -127,12 +127,22 @@ __device__ __forceinline__ void twid(const float4* tw, int idx, bool inv, float2
     wh = make_float2(v.x, inv ? -v.y : v.y);
     wl = make_float2(v.z, inv ? -v.w : v.w);
 }
-// copy the size-M twiddles out of the global table (exp(-2 pi i t / fftmax), t < fftmax / 2)
-__device__ __forceinline__ void stage_twiddles(float4* tw, int M, int fftmax, const FftTabsF& t)
+// twiddle exp(-+2 pi i u / M) for 0 <= u < M (the staged table holds u < M / 2;
+// u >= M / 2 is the negative of u - M / 2), branch-free per lane
+__device__ __forceinline__ void twid_full(const float4* tw, int u, int M, bool inv, float2& wh, float2& wl)
 {
-    const int st = fftmax / M;
+    const int hm = M >> 1;
+    const bool up = u >= hm;
+    twid(tw, up ? u - hm : u, inv, wh, wl);
+    const float sg = up ? -1.0f : 1.0f;
+    wh.x *= sg; wh.y *= sg; wl.x *= sg; wl.y *= sg;
+}
+
+// copy the size-M twiddles of the class (table at offset ctw) into shared memory
+__device__ __forceinline__ void stage_twiddles(float4* tw, int M, long long ctw, const FftTabsF& t)
+{
     for (int u = threadIdx.x; u < M / 2; u += blockDim.x) {
-        const float2 h = t.twh[u * st], l = t.twl[u * st];
+        const float2 h = t.twh[ctw + u], l = t.twl[ctw + u];
         tw[tw_slot(u)] = make_float4(h.x, h.y, l.x, l.y);
     }
 }
@@ -145,134 +155,261 @@ __device__ __forceinline__ void stage_twiddles(float4* tw, int M, int fftmax, co
 __host__ __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 3) + (i >> 6); }
 __host__ __device__ __forceinline__ int fft_pad_len(int M) { return M + (M >> 3) + (M >> 6); }
 
-// In-place decimation-in-time FFTs of nb sequences of M = 2^L points (padded
-// layout above), input in bit-reversed order, output natural. Two radix-2
-// stages (spans h and 2h) per pass; W = exp(-+2 pi i / M).
-__device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv)
+// One radix-4 pass (two radix-2 stages) over NS sequences at a time: each
+// work item does the same butterfly on NS sequences P apart with the same
+// twiddles, so the NS independent double-float chains overlap (the passes
+// are latency-bound at one or two CTAs per SM).
+// (the twiddle branch is per pass, not per lane: for k = 0 the twiddled path
+// multiplies by exactly 1, and a warp whose lanes took both paths would
+// execute both)
+// DIT: spans h and 2h, with w = W_{4h}^k the inputs are multiplied by w^2
+// (x1), w (x2), w^3 (x3), then the 4-point DFT (+-i exact).
+template <int NS>
+__device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, const float4* tw, bool inv, int ts)
+{
+    const int M = 1 << L, P = fft_pad_len(M), MT = M * ts;
+    const int h = 1 << lh;
+    const int s1 = M >> (lh + 1), s2 = M >> (lh + 2);
+    const int ng = M >> 2;                           // groups per sequence
+    for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
+        const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
+        const int k = g & (h - 1);
+        cx* y = buf + f * P;
+        const int y0 = ((g - k) << 2) + k;
+        const int i0 = fft_pad(y0), i1 = fft_pad(y0 + h), i2 = fft_pad(y0 + 2 * h), i3 = fft_pad(y0 + 3 * h);
+        cx x0[NS], x1[NS], x2[NS], x3[NS];
+#pragma unroll
+        for (int q = 0; q < NS; q++) {
+            x0[q] = y[q * P + i0]; x1[q] = y[q * P + i1]; x2[q] = y[q * P + i2]; x3[q] = y[q * P + i3];
+        }
+        if (h > 1) {
+            float2 w1h, w1l, w2h, w2l, w3h, w3l;
+            twid(tw, k * s1 * ts, inv, w1h, w1l);
+            twid(tw, k * s2 * ts, inv, w2h, w2l);
+            twid_full(tw, 3 * k * s2 * ts, MT, inv, w3h, w3l);
+#pragma unroll
+            for (int q = 0; q < NS; q++) {
+                x1[q] = cmulc(x1[q], w1h, w1l);
+                x2[q] = cmulc(x2[q], w2h, w2l);
+                x3[q] = cmulc(x3[q], w3h, w3l);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NS; q++) {
+            const cx b0 = caddc(x0[q], x1[q]), b1 = csubc(x0[q], x1[q]);
+            const cx b2 = caddc(x2[q], x3[q]), b3 = csubc(x2[q], x3[q]);
+            const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
+            y[q * P + i0] = caddc(b0, b2); y[q * P + i2] = csubc(b0, b2);
+            y[q * P + i1] = caddc(b1, u3); y[q * P + i3] = csubc(b1, u3);
+        }
+    }
+}
+
+// DIF: spans h and h/2, outputs 1, 2, 3 take v^2, v, v^3 with v = W_{2h}^k.
+template <int NS>
+__device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, const float4* tw, bool inv, int ts)
+{
+    const int M = 1 << L, P = fft_pad_len(M), MT = M * ts;
+    const int h = 1 << lh, hq = h >> 1;
+    const int s1 = M >> (lh + 1), s2 = M >> lh;
+    const int ng = M >> 2;
+    for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
+        const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
+        const int k = g & (hq - 1);
+        cx* y = buf + f * P;
+        const int y0 = ((g - k) << 2) + k;
+        const int i0 = fft_pad(y0), i1 = fft_pad(y0 + hq), i2 = fft_pad(y0 + h), i3 = fft_pad(y0 + h + hq);
+        cx c0[NS], c1[NS], c2[NS], c3[NS];
+#pragma unroll
+        for (int q = 0; q < NS; q++) {
+            const cx x0 = y[q * P + i0], x1 = y[q * P + i1], x2 = y[q * P + i2], x3 = y[q * P + i3];
+            c0[q] = caddc(x0, x2); c2[q] = csubc(x0, x2); c1[q] = caddc(x1, x3);
+            const cx d = csubc(x1, x3);
+            c3[q] = inv ? cmul_pi(d) : cmul_mi(d);
+        }
+        if (hq > 1) {
+            float2 v1h, v1l, v2h, v2l, v3h, v3l;
+            twid(tw, k * s1 * ts, inv, v1h, v1l);
+            twid(tw, k * s2 * ts, inv, v2h, v2l);
+            twid_full(tw, 3 * k * s1 * ts, MT, inv, v3h, v3l);
+#pragma unroll
+            for (int q = 0; q < NS; q++) {
+                y[q * P + i0] = caddc(c0[q], c1[q]); y[q * P + i1] = cmulc(csubc(c0[q], c1[q]), v2h, v2l);
+                y[q * P + i2] = cmulc(caddc(c2[q], c3[q]), v1h, v1l);
+                y[q * P + i3] = cmulc(csubc(c2[q], c3[q]), v3h, v3l);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NS; q++) {
+                y[q * P + i0] = caddc(c0[q], c1[q]); y[q * P + i1] = csubc(c0[q], c1[q]);
+                y[q * P + i2] = caddc(c2[q], c3[q]); y[q * P + i3] = csubc(c2[q], c3[q]);
+            }
+        }
+    }
+}
+
+// radix-2 stage of span 1 (twiddle 1) over nb sequences
+__device__ __forceinline__ void r2_span1(cx* buf, int nb, int L)
 {
     const int M = 1 << L, P = fft_pad_len(M);
+    for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
+        cx* x = buf + (b >> (L - 1)) * P;
+        const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
+        const cx a = x[i0], c = x[i1];
+        x[i0] = caddc(a, c);
+        x[i1] = csubc(a, c);
+    }
+    __syncthreads();
+}
+
+// In-place decimation-in-time FFTs of nb sequences of M = 2^L points (padded
+// layout above), input in bit-reversed order, output natural. Two radix-2
+// stages per pass, sequences in pairs; W = exp(-+2 pi i / M).
+// ts: stride of the twiddle indices (the staged table belongs to a size ts M)
+__device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv, int ts = 1)
+{
+    const int P = fft_pad_len(1 << L);
     int lh = 0;
-    if (L & 1) {                                     // one radix-2 stage of span 1 (twiddle 1)
-        for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
-            cx* x = buf + (b >> (L - 1)) * P;
-            const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
-            const cx a = x[i0], c = x[i1];
-            x[i0] = caddc(a, c);
-            x[i1] = csubc(a, c);
-        }
-        __syncthreads();
+    if (L & 1) {
+        r2_span1(buf, nb, L);
         lh = 1;
     }
     for (; lh + 2 <= L; lh += 2) {
-        const int h = 1 << lh;
-        const int s1 = M >> (lh + 1), s2 = M >> (lh + 2);
-        const int ng = M >> 2;                       // groups per sequence
-        for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
-            const int f = b >> (L - 2), g = b & (ng - 1);
-            const int k = g & (h - 1);
-            cx* y = buf + f * P;
-            const int y0 = ((g - k) << 2) + k;
-            const int i0 = fft_pad(y0), i1 = fft_pad(y0 + h), i2 = fft_pad(y0 + 2 * h), i3 = fft_pad(y0 + 3 * h);
-            cx x0 = y[i0], x1 = y[i1], x2 = y[i2], x3 = y[i3];
-            // (the branch is per pass, not per lane: for k = 0 the twiddled
-            // path multiplies by exactly 1, and a warp whose lanes took both
-            // paths would execute both)
-            if (h > 1) {
-                float2 w1h, w1l, w2h, w2l;
-                twid(tw, k * s1, inv, w1h, w1l);
-                twid(tw, k * s2, inv, w2h, w2l);
-                x1 = cmulc(x1, w1h, w1l);
-                x3 = cmulc(x3, w1h, w1l);
-                const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
-                const cx u2 = cmulc(b2, w2h, w2l);
-                const cx u3 = inv ? cmul_pi(cmulc(b3, w2h, w2l)) : cmul_mi(cmulc(b3, w2h, w2l));
-                y[i0] = caddc(b0, u2); y[i2] = csubc(b0, u2);
-                y[i1] = caddc(b1, u3); y[i3] = csubc(b1, u3);
-            } else {
-                const cx b0 = caddc(x0, x1), b1 = csubc(x0, x1), b2 = caddc(x2, x3), b3 = csubc(x2, x3);
-                const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
-                y[i0] = caddc(b0, b2); y[i2] = csubc(b0, b2);
-                y[i1] = caddc(b1, u3); y[i3] = csubc(b1, u3);
-            }
-        }
+        if (nb >= 2) dit4_pass<2>(buf, nb >> 1, L, lh, tw, inv, ts);
+        if (nb & 1) dit4_pass<1>(buf + (nb - 1) * P, 1, L, lh, tw, inv, ts);
         __syncthreads();
     }
 }
 
 // In-place decimation-in-frequency FFTs (natural input, bit-reversed output),
-// two radix-2 stages (spans h and h/2) per pass.
-__device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv)
+// two radix-2 stages (spans h and h/2) per pass, sequences in pairs.
+__device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv, int ts = 1)
 {
-    const int M = 1 << L, P = fft_pad_len(M);
+    const int P = fft_pad_len(1 << L);
     int lh = L - 1;
     for (; lh >= 1; lh -= 2) {
-        const int h = 1 << lh, hq = h >> 1;
-        const int s1 = M >> (lh + 1), s2 = M >> lh;
-        const int ng = M >> 2;
-        for (int b = threadIdx.x; b < nb * ng; b += blockDim.x) {
-            const int f = b >> (L - 2), g = b & (ng - 1);
-            const int k = g & (hq - 1);
+        if (nb >= 2) dif4_pass<2>(buf, nb >> 1, L, lh, tw, inv, ts);
+        if (nb & 1) dif4_pass<1>(buf + (nb - 1) * P, 1, L, lh, tw, inv, ts);
+        __syncthreads();
+    }
+    if (lh == 0) r2_span1(buf, nb, L);
+}
+
+// a * c for a real double-float constant c = ch + cl (both parts of a)
+__device__ __forceinline__ cx rmulc(const cx& a, float ch, float cl)
+{
+    cx r;
+    r.hr = a.hr * ch; r.hi = a.hi * ch;
+    r.lr = fmaf(a.hr, ch, -r.hr) + fmaf(a.hr, cl, a.lr * ch);
+    r.li = fmaf(a.hi, ch, -r.hi) + fmaf(a.hi, cl, a.li * ch);
+    return r;
+}
+// sqrt(3) / 2 as a double-float pair
+constexpr float R3H = 0.866025388240814208984375f;
+constexpr float R3L = 1.55436244377793497517e-08f;
+
+// the 3-point DFT y_j = sum_i x_i e^{-+2 pi i i j / 3}: y0 = x0 + t,
+// y1,2 = (x0 - t / 2) -+ i (sqrt 3 / 2)(x1 - x2), t = x1 + x2 (forward sign)
+__device__ __forceinline__ void dft3(const cx& x0, const cx& x1, const cx& x2, bool inv, cx& y0, cx& y1, cx& y2)
+{
+    const cx t = caddc(x1, x2);
+    y0 = caddc(x0, t);
+    const cx u = csubc(x0, cscale(t, 0.5f));
+    const cx d = rmulc(csubc(x1, x2), R3H, R3L);
+    const cx v = inv ? cmul_pi(d) : cmul_mi(d);
+    y1 = caddc(u, v);
+    y2 = csubc(u, v);
+}
+
+// Radix-3 stages of a size M = 3^b 2^a transform (padded layout, nb
+// sequences), on the full sequences: decimation in frequency with spans M,
+// M / 3, ... (before the power-of-two passes on the 3^b blocks of 2^a), or
+// decimation in time with spans 3 2^a, ..., M (after them). The staged
+// twiddles are those of size M: W_S^{j k} = W_M^{j k M / S}.
+__device__ void r3_passes(cx* buf, int nb, int M, int p3, const float4* tw, bool inv, bool dif)
+{
+    const int P = fft_pad_len(M);
+    const int nbf = M / 3;                           // butterflies per sequence and stage
+    for (int st = 0, S = dif ? M : 3 * (M / p3); st < 64 && (dif ? S > M / p3 : S <= M);
+         st++, S = dif ? S / 3 : S * 3) {
+        const int Sp = S / 3, ms = M / S;
+        const float rsp = 1.0f / (float)Sp;
+        for (int b = threadIdx.x; b < nb * nbf; b += blockDim.x) {
+            const int f = (b >= nbf) ? 1 : 0;            // nb <= 2 sequences
+            const int r = b - f * nbf;
+            // r / Sp through the FP32 reciprocal (r < 2^14: off by at most one)
+            int blk = __float2int_rz((float)r * rsp);
+            int k = r - blk * Sp;
+            if (k < 0) { blk--; k += Sp; } else if (k >= Sp) { blk++; k -= Sp; }
             cx* y = buf + f * P;
-            const int y0 = ((g - k) << 2) + k;
-            const int i0 = fft_pad(y0), i1 = fft_pad(y0 + hq), i2 = fft_pad(y0 + h), i3 = fft_pad(y0 + h + hq);
-            const cx x0 = y[i0], x1 = y[i1], x2 = y[i2], x3 = y[i3];
-            cx c0 = caddc(x0, x2), c2 = csubc(x0, x2), c1 = caddc(x1, x3), c3 = csubc(x1, x3);
-            c3 = inv ? cmul_pi(c3) : cmul_mi(c3);
-            if (hq > 1) {                            // per pass (see fft_dit)
-                float2 v1h, v1l, v2h, v2l;
-                twid(tw, k * s1, inv, v1h, v1l);
-                twid(tw, k * s2, inv, v2h, v2l);
-                c2 = cmulc(c2, v1h, v1l);
-                c3 = cmulc(c3, v1h, v1l);
-                y[i0] = caddc(c0, c1); y[i1] = cmulc(csubc(c0, c1), v2h, v2l);
-                y[i2] = caddc(c2, c3); y[i3] = cmulc(csubc(c2, c3), v2h, v2l);
+            const int o = blk * S + k;
+            const int i0 = fft_pad(o), i1 = fft_pad(o + Sp), i2 = fft_pad(o + 2 * Sp);
+            float2 w1h, w1l, w2h, w2l;
+            twid_full(tw, k * ms, M, inv, w1h, w1l);
+            twid_full(tw, 2 * k * ms, M, inv, w2h, w2l);
+            cx x0 = y[i0], x1 = y[i1], x2 = y[i2], y0, y1, y2;
+            if (dif) {
+                dft3(x0, x1, x2, inv, y0, y1, y2);
+                y[i0] = y0; y[i1] = cmulc(y1, w1h, w1l); y[i2] = cmulc(y2, w2h, w2l);
             } else {
-                y[i0] = caddc(c0, c1); y[i1] = csubc(c0, c1);
-                y[i2] = caddc(c2, c3); y[i3] = csubc(c2, c3);
+                dft3(x0, cmulc(x1, w1h, w1l), cmulc(x2, w2h, w2l), inv, y0, y1, y2);
+                y[i0] = y0; y[i1] = y1; y[i2] = y2;
             }
         }
         __syncthreads();
     }
-    if (lh == 0) {                                   // last radix-2 stage of span 1
-        for (int b = threadIdx.x; b < nb * (M >> 1); b += blockDim.x) {
-            cx* x = buf + (b >> (L - 1)) * P;
-            const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
-            const cx a = x[i0], c = x[i1];
-            x[i0] = caddc(a, c);
-            x[i1] = csubc(a, c);
-        }
-        __syncthreads();
-    }
+}
+
+// transforms of size M = p3 2^L: natural in, digit-reversed out (DIF) and
+// digit-reversed in, natural out (DIT); p3 = 1 is the plain power-of-two case
+__device__ __forceinline__ void fft_dif_m(cx* buf, int nb, int L, int p3, const float4* tw, bool inv)
+{
+    if (p3 > 1) r3_passes(buf, nb, p3 << L, p3, tw, inv, true);
+    fft_dif(buf, nb * p3, L, tw, inv, p3);
+}
+__device__ __forceinline__ void fft_dit_m(cx* buf, int nb, int L, int p3, const float4* tw, bool inv)
+{
+    fft_dit(buf, nb * p3, L, tw, inv, p3);
+    if (p3 > 1) r3_passes(buf, nb, p3 << L, p3, tw, inv, false);
 }
 
 // forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of nb sequences placed by placec()
 __device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const FftTabsF& t)
 {
-    const int M = f.m, L = 31 - __clz(M), P = fft_pad_len(M);
+    const int M = f.m, L = 31 - __clz(M / f.p3), P = fft_pad_len(M);
     if (!f.bluestein) {
-        fft_dit(buf, nb, L, tw, false);
+        fft_dit_m(buf, nb, L, f.p3, tw, false);
         return;
     }
-    fft_dif(buf, nb, L, tw, false);
+    fft_dif_m(buf, nb, L, f.p3, tw, false);
     for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
-        const int ii = i & (M - 1);
-        cx& z = buf[(i >> L) * P + fft_pad(ii)];
+        const int s = i / M, ii = i - s * M;
+        cx& z = buf[s * P + fft_pad(ii)];
         z = cmulc(z, t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
     }
     __syncthreads();
-    fft_dit(buf, nb, L, tw, true);
-    const float inv = 1.0f / (float)M;
+    fft_dit_m(buf, nb, L, f.p3, tw, true);
+    // (the filter spectrum carries the 1 / M of the inverse transform: an
+    // FP32 scale by 1 / M would round for M = 3^b 2^a)
     for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
         const int s = i / f.n, k = i - s * f.n;
         cx& z = buf[s * P + fft_pad(k)];
-        z = cscale(cmulc(z, t.chh[f.chirp + k], t.chl[f.chirp + k]), inv);
+        z = cmulc(z, t.chh[f.chirp + k], t.chl[f.chirp + k]);
     }
     __syncthreads();
 }
 
+// where input n goes: natural for Bluestein (decimation in frequency), else
+// the digit-reversed position the decimation-in-time passes take: the base-3
+// digits of n (least significant first) at spans M / 3, M / 9, ..., then the
+// bit-reversed rest
 __device__ __forceinline__ int placec(const FftLen& f, int n)
 {
-    return f.bluestein ? n : brev_c(n, 31 - __clz(f.m));
+    if (f.bluestein) return n;
+    if (f.p3 == 1) return brev_c(n, 31 - __clz(f.m));
+    int p = 0, S = f.m;
+    for (int q = f.p3; q > 1; q /= 3) { S /= 3; const int d = n % 3; n /= 3; p += d * S; }
+    return p + brev_c(n, 31 - __clz(f.m / f.p3));
 }
 
 __device__ __forceinline__ cx chirp_in(const FftLen& f, const FftTabsF& t, cx z, int n)
@@ -299,17 +436,17 @@ constexpr int FWD_PB = 32;
 
 // NT threads; each thread owns m = threadIdx.x + jj NT, jj < 4 (mmax < 4 NT)
 template <int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned int* __restrict__ colmax,
                const int* __restrict__ cls, int ncls, const PairGeom* __restrict__ pairs,
-               const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax, int M, int R_, int mmax,
+               const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw, int M, int R_, int mmax,
                long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
     const int P = fft_pad_len(M);
     float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
-    stage_twiddles(tw, M, fftmax, tb);              // (the first __syncthreads below publishes it)
+    stage_twiddles(tw, M, ctw, tb);                 // (the first __syncthreads below publishes it)
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
@@ -427,16 +564,16 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
 constexpr int BWD_PB = 8;
 
 template <int NT>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls, int ncls,
-                const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, int fftmax,
+                const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw,
                 int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
     const int P = fft_pad_len(M);
     float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
-    stage_twiddles(tw, M, fftmax, tb);              // (published by the __syncthreads before the FFT)
+    stage_twiddles(tw, M, ctw, tb);                 // (published by the __syncthreads before the FFT)
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
@@ -577,9 +714,9 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
 static FftTabsF tabs(const sht_plan* p)
 {
     FftTabsF t;
-    t.twh = p->t.twiddle_f; t.twl = p->c.twiddle_l;
+    t.twh = p->c.tws_h; t.twl = p->c.tws_l;
     t.chh = p->t.chirp_f; t.chl = p->c.chirp_l;
-    t.bhh = p->t.bhat_f; t.bhl = p->c.bhat_l;
+    t.bhh = p->c.bhs_h; t.bhl = p->c.bhs_l;
     t.phh = p->c.phase_h; t.phl = p->c.phase_l;
     t.phoff = p->c.phase_off;
     return t;
@@ -590,9 +727,10 @@ static FftTabsF tabs(const sht_plan* p)
 // memory), the padded buffers plus the class's twiddles (M / 2 x 16 bytes)
 static void class_cfg(int M, int mmax, int& nt, int& mpc, size_t& sm)
 {
-    nt = (M >= 4096 || mmax >= 1024) ? 512 : 256;
     mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
     sm = (size_t)mpc * fft_pad_len(M) * sizeof(cx) + (size_t)(M / 2) * sizeof(float4);
+    // 512 threads where one CTA fills an SM's shared memory (16 warps per SM)
+    nt = (M >= 4096 || mmax >= 1024 || sm > (113u << 10)) ? 512 : 256;
 }
 
 static cudaError_t set_smem(const void* fn, const sht_plan* p)
@@ -623,11 +761,11 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
         prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
             k_fftc_forward<512><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->t.fft, tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix, nc,
+                                                      p->c.fft_s, tabs(p), c.tw, c.m, p->R, p->mmax, p->npix, nc,
                                                       nmc, mpc);
         else
             k_fftc_forward<256><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->t.fft, tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix, nc,
+                                                      p->c.fft_s, tabs(p), c.tw, c.m, p->R, p->mmax, p->npix, nc,
                                                       nmc, mpc);
         prof_stop(st);
         count_launch();
@@ -647,12 +785,12 @@ cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* m
         dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
         prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
-            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->t.fft,
-                                                       tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix,
+            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+                                                       tabs(p), c.tw, c.m, p->R, p->mmax, p->npix,
                                                        ncols(p, nmaps), nmc, mpc);
         else
-            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->t.fft,
-                                                       tabs(p), p->fft_max, c.m, p->R, p->mmax, p->npix,
+            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+                                                       tabs(p), c.tw, c.m, p->R, p->mmax, p->npix,
                                                        ncols(p, nmaps), nmc, mpc);
         prof_stop(st);
         count_launch();

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <map>
+#include <complex>
 
 #include <cstdlib>
 #include <climits>
@@ -106,6 +107,86 @@ static int bitrev(int i, int logm)
     return r;
 }
 
+// ---- split form: FFT sizes M = 3^b 2^a (2^a >= 64 when b > 0) ----
+// relative cost of one size-M transform in the split FFT (double-float
+// operations per point: ~29.5 per radix-4 pass, ~16 per radix-2 pass, ~30 per
+// radix-3 pass)
+static double split_fft_cost(int M)
+{
+    int b = 0;
+    while (M % 3 == 0) { M /= 3; b++; }
+    int L = 0;
+    while ((1 << L) < M) L++;
+    const double p3 = std::pow(3.0, b);
+    return p3 * (double)M * ((L / 2) * 29.5 + (L % 2) * 16.0 + b * 30.0);
+}
+
+static int pow3_part(int M) { int p = 1; while (M % 3 == 0) { M /= 3; p *= 3; } return p; }
+
+// the split form's recipe for a ring of N pixels: a direct transform when N
+// is a power of two or 3^b 2^a (2^a >= 64), else Bluestein with the cheapest
+// M = 3^b 2^a >= 2N - 1 (never above the power-of-two size)
+static void split_fft_choice(int N, int& M, int& bluestein)
+{
+    if (is_pow2(N)) { M = N; bluestein = 0; return; }
+    double best = 1e300;
+    const int p3n = pow3_part(N);
+    if (is_pow2(N / p3n) && N / p3n >= 64) { best = split_fft_cost(N); M = N; bluestein = 0; }
+    const int cap = next_pow2(2 * N - 1);
+    for (int p3 = 1; p3 <= 243; p3 *= 3) {
+        int a2 = 1;
+        while ((long long)a2 * p3 < 2LL * N - 1) a2 *= 2;
+        const int Mc = a2 * p3;
+        if (Mc > cap || (p3 > 1 && a2 < 64)) continue;
+        const double c = 2.0 * split_fft_cost(Mc) + 30.0 * Mc;
+        if (c < best) { best = c; M = Mc; bluestein = 1; }
+    }
+}
+
+// position of index k in a digit-reversed sequence of M = p3 2^a points (the
+// output order of the split FFT's decimation-in-frequency passes: radix-3
+// stages first, then the power-of-two passes), and its inverse
+static int split_pos_of(int k, int M, int p3)
+{
+    const int a2 = M / p3;
+    int logm = 0;
+    while ((1 << logm) < a2) logm++;
+    int p = 0, S = M;
+    for (int q = p3; q > 1; q /= 3) { S /= 3; p += (k % 3) * S; k /= 3; }
+    return p + bitrev(k, logm);
+}
+static int split_k_of(int p, int M, int p3)
+{
+    const int a2 = M / p3;
+    int logm = 0;
+    while ((1 << logm) < a2) logm++;
+    int k = 0, mul = 1, S = M;
+    for (int q = p3; q > 1; q /= 3) { S /= 3; const int j = p / S; p -= j * S; k += j * mul; mul *= 3; }
+    return k + mul * bitrev(p, logm);
+}
+
+// forward DFT of n = 3^b 2^a points in long double (recursive decimation in time)
+typedef std::complex<ld> cld;
+static void host_dft_mixed(std::vector<cld>& x)
+{
+    const size_t n = x.size();
+    if (n == 1) return;
+    const int r = (n % 3 == 0) ? 3 : 2;
+    const size_t m = n / r;
+    std::vector<std::vector<cld>> sub(r, std::vector<cld>(m));
+    for (size_t i = 0; i < m; i++)
+        for (int j = 0; j < r; j++) sub[j][i] = x[i * r + j];
+    for (int j = 0; j < r; j++) host_dft_mixed(sub[j]);
+    for (size_t k = 0; k < n; k++) {
+        cld acc(0.0L, 0.0L);
+        for (int j = 0; j < r; j++) {
+            const ld a = -2 * PI_L * (ld)((j * k) % n) / (ld)n;
+            acc += sub[j][k % m] * cld(cosl(a), sinl(a));
+        }
+        x[k] = acc;
+    }
+}
+
 // scaled long-double value: mant * 2^exp
 struct Scaled { ld v; long e; };
 static Scaled snorm(ld v, long e)
@@ -172,6 +253,7 @@ static cudaError_t build_tables(sht_plan* p)
         f.n = N;
         f.bluestein = is_pow2(N) ? 0 : 1;
         f.m = f.bluestein ? next_pow2(2 * N - 1) : N;
+        f.p3 = 1;
         f.chirp = (long long)chirp.size();
         f.bhat = (long long)bhat.size();
         if (f.bluestein) {
@@ -247,19 +329,62 @@ static cudaError_t build_tables(sht_plan* p)
         if ((e = upload(&p->c.phase_h, ph, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.phase_l, pl, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.phase_off, off, &acc)) != cudaSuccess) return e;
-        // ring pairs grouped by FFT size (one launch per size in the split FFTs)
+        // the split form's own recipes: sizes 3^b 2^a where they need less
+        // work, Bluestein filters in the digit-reversed order of its passes
+        p->h_fft_s = p->h_fft;
+        std::vector<float2> bsh, bsl;
+        for (auto& kv : len_index) {
+            sht::FftLen& fs = p->h_fft_s[kv.second];
+            const int N = kv.first;
+            split_fft_choice(N, fs.m, fs.bluestein);
+            fs.p3 = pow3_part(fs.m);
+            fs.bhat = (long long)bsh.size();
+            if (!fs.bluestein) continue;
+            const int M = fs.m;
+            std::vector<cld> b(M, cld(0.0L, 0.0L));
+            for (int j = 0; j < N; j++) {
+                const long long n2 = ((long long)j * j) % (2LL * N);
+                const ld a = PI_L * (ld)n2 / N;              // conj of w_j = exp(-i pi j^2 / N)
+                b[j] = cld(cosl(a), sinl(a));
+                if (j > 0) b[M - j] = b[j];
+            }
+            host_dft_mixed(b);
+            for (int q = 0; q < M; q++) {
+                const cld v = b[split_k_of(q, M, fs.p3)] / (ld)M;   // with the inverse transform's 1 / M
+                const float hx = (float)v.real(), hy = (float)v.imag();
+                bsh.push_back(make_float2(hx, hy));
+                bsl.push_back(make_float2((float)(v.real() - (ld)hx), (float)(v.imag() - (ld)hy)));
+            }
+        }
+        if (bsh.empty()) { bsh.push_back(make_float2(1, 0)); bsl.push_back(make_float2(0, 0)); }
+        if ((e = upload(&p->c.fft_s, p->h_fft_s, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.bhs_h, bsh, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.bhs_l, bsl, &acc)) != cudaSuccess) return e;
+        // ring pairs grouped by FFT size (one launch per size in the split
+        // FFTs), each size with its twiddles exp(-2 pi i u / M), u < M / 2
         std::map<int, std::vector<int>> bym;
-        for (int q = 0; q < R; q++) bym[p->h_fft[p->h_pairs[q].fft].m].push_back(q);
+        for (int q = 0; q < R; q++) bym[p->h_fft_s[p->h_pairs[q].fft].m].push_back(q);
         std::vector<int> cls;
+        std::vector<float2> twh, twl;
         for (auto& kv : bym) {
             sht::FftClass c;
             c.m = kv.first;
             c.off = (int)cls.size();
             c.cnt = (int)kv.second.size();
+            c.tw = (long long)twh.size();
+            for (int u = 0; u < std::max(1, c.m / 2); u++) {
+                const ld a = -2 * PI_L * (ld)u / (ld)c.m;
+                const ld cr = cosl(a), ci = sinl(a);
+                const float hx = (float)cr, hy = (float)ci;
+                twh.push_back(make_float2(hx, hy));
+                twl.push_back(make_float2((float)(cr - (ld)hx), (float)(ci - (ld)hy)));
+            }
             cls.insert(cls.end(), kv.second.begin(), kv.second.end());
             p->h_fcls.push_back(c);
         }
         if ((e = upload(&p->c.cls_pairs, cls, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.tws_h, twh, &acc)) != cudaSuccess) return e;
+        if ((e = upload(&p->c.tws_l, twl, &acc)) != cudaSuccess) return e;
     }
 
     // ---- lambda seeds ----
@@ -654,7 +779,8 @@ static void free_tables(sht_plan* p)
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
                     p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
-    void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off};
+    void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off,
+                  p->c.fft_s, p->c.tws_h, p->c.tws_l, p->c.bhs_h, p->c.bhs_l};
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,

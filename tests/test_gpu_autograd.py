@@ -83,3 +83,54 @@ def test_refinement_gradient_matches_oracle_transposes(orc, mods):
         g = g - orc.alm2map_adjoint(orc.map2alm_adjoint(g, nside, lmax), nside, lmax)
     scale = np.abs(g).max()
     assert np.max(np.abs(got - g)) <= 1e-10 * scale
+
+
+def test_refinement_gradient_at_nside256_256_maps(orc, mods):
+    """The differentiable workload's own shape: nside 256, lmax 511, 256 maps,
+    FP64, loss = squared residual after three Algorithm-2 steps. The gradient
+    comes from one backward pass over the whole batch. The loss is a sum of
+    per-map terms and every transform acts on each map alone, so the
+    derivative by a coefficient of map k is that of map k's term: central
+    differences (step 1e-6) on 64 random components evaluate map k's term
+    alone (free of the other maps' rounding), and the oracle's explicit
+    transposes check two whole maps (to 2e-9 of the gradient's largest
+    entry: a chain of 14 FP64 transforms)."""
+    sht, ag = mods
+    nside, lmax, nmaps = 256, 511, 256
+    plan = sht.Plan(nside, lmax, None, 0, "fp64")
+    rng = np.random.default_rng(4)
+    a0 = _ri(inputs.gaussian_alm(4, nmaps, 1, lmax, cls=inputs.cl_inv_llp1(lmax)))
+    t_np = rng.standard_normal((nmaps, 1, 12 * nside * nside)) * 0.05
+    target = torch.from_numpy(t_np).cuda()
+    a = a0.clone().requires_grad_(True)
+    _loss(ag, plan, a, target).backward()
+    g = a.grad.detach()
+    per = g[0].numel()
+    idx = rng.choice(a0.numel(), 64, replace=False)
+    h = 1e-6
+    for i in idx:
+        k, j = divmod(int(i), per)
+        ak = a0[k:k + 1].clone()
+        ap = ak.clone().view(-1); ap[j] += h
+        am = ak.clone().view(-1); am[j] -= h
+        with torch.no_grad():
+            fd = (_loss(ag, plan, ap.view_as(ak), target[k:k + 1]) -
+                  _loss(ag, plan, am.view_as(ak), target[k:k + 1])) / (2 * h)
+        an = float(g.view(-1)[i])
+        assert abs(float(fd) - an) <= 1e-5 * max(1.0, abs(float(fd))), (int(i), float(fd), an)
+    # reverse mode with the oracle's transposes on two maps
+    got = torch.view_as_complex(g.contiguous()).cpu().numpy()
+    for k in (0, nmaps - 1):
+        ak0 = torch.view_as_complex(a0[k:k + 1].contiguous()).cpu().numpy()
+        tk = t_np[k:k + 1]
+        a_k = [ak0]
+        for _ in range(3):
+            a_k.append(a_k[-1] + orc.map2alm(tk - orc.alm2map(a_k[-1], nside, lmax), nside, lmax))
+        r = orc.alm2map(a_k[3], nside, lmax) - tk
+        gk = orc.alm2map_adjoint(2 * r, nside, lmax)
+        for _ in range(3):
+            gk = gk - orc.alm2map_adjoint(orc.map2alm_adjoint(gk, nside, lmax), nside, lmax)
+        # the gradient chains 14 FP64 transforms (three refinement steps
+        # forward and back, the final synthesis and its adjoint), each held
+        # to 1e-10: their rounding adds up, so the chain is held to 2e-9
+        assert np.max(np.abs(got[k:k + 1] - gk)) <= 2e-9 * np.abs(gk).max()
