@@ -471,11 +471,11 @@ def run_serving(n_req, loads, device, use_graphs=True):
         return [p] * q + ([p[:r]] if r else [])
 
     budget = 150e9
-    ex = GpuExecutor(device=device, slots=4, use_graphs=use_graphs, mem_cap=budget)
+    ex = GpuExecutor(device=device, slots=4, use_graphs=use_graphs, mem_cap=budget, small_slots=2)
 
     def drop(r):
         r.result = None
-    srv = Server(ex, hbm_budget=budget, max_batch_maps=256, slots=4, on_complete=drop)
+    srv = Server(ex, hbm_budget=budget, max_batch_maps=256, slots=6, on_complete=drop)
 
     def run(sp, arrivals):
         srv.completed.clear()
@@ -497,7 +497,9 @@ def run_serving(n_req, loads, device, use_graphs=True):
         st["peak_admitted_gb"] = srv.peak_used / 1e9
         return st
 
-    warm = spec[:min(len(spec), 64)]                       # plans, kernel attributes, graphs
+    for op, nside, spin, _ in spec:                         # every plan before any timing
+        ex.prepare(Request(op=op, nside=nside, spin=spin, data=pool[(op, nside, spin)][:1]).key("auto"))
+    warm = spec[:min(len(spec), 64)]                       # kernel attributes, first graphs
     run(warm, np.zeros(len(warm)))
     closed = run(spec, np.zeros(len(spec)))
     mean_maps = sum(s[3] for s in spec) / len(spec)
@@ -695,7 +697,11 @@ def main():
                                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
                                 "note": "each flop runs in double-float FP32 (~7 FP32 operations)"}}
 
-    # ---- end to end through the host-buffer C-ABI entry points ----
+    # ---- end to end through the host-buffer C-ABI entry points: the two
+    # directions of a step from two host threads, one plan each (the host
+    # entry points are not for concurrent calls on one plan), so that the
+    # host->device copies of one overlap the device->host copies of the
+    # other (PCIe is full duplex) ----
     e2e = None
     if not a.no_e2e:
         alm_h = torch.empty(alm.shape, dtype=torch.complex128, pin_memory=True)
@@ -707,18 +713,45 @@ def main():
         del maps_out, alm_out, ws
         maps_out = alm_out = ws = None
         torch.cuda.empty_cache()
-        plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
-        plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
+        plan_b = sht.Plan(nside, lmax, None, 0, precision)
+        sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+        errs = []
+
+        def a2m():
+            try:
+                with torch.cuda.stream(sa):
+                    plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
+            except Exception as ex:                  # surfaced after the join
+                errs.append(ex)
+
+        def m2a():
+            try:
+                with torch.cuda.stream(sb):
+                    plan_b.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
+            except Exception as ex:
+                errs.append(ex)
+
+        def both():
+            th = [threading.Thread(target=a2m), threading.Thread(target=m2a)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            if errs:
+                raise errs[0]
+        both()                                       # staging buffers, kernel attributes
         t0 = time.perf_counter()
         ke = max(1, min(a.steps, 2))
         for _ in range(ke):
-            plan.alm2map_host(alm_h.numpy(), out_host=mo_h.numpy())
-            plan.map2alm_host(maps_h.numpy(), out_host=ao_h.numpy())
+            both()
         dt = (time.perf_counter() - t0) / ke
         nb_alm = alm_h.numel() * 16
         nb_map = maps_h.numel() * 8
         e2e = {"value": nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
-               "d2h_bytes_per_step": nb_map + nb_alm, "api": "sht_alm2map_host + sht_map2alm_host"}
+               "d2h_bytes_per_step": nb_map + nb_alm, "api": "sht_alm2map_host + sht_map2alm_host",
+               "directions": "concurrent: two host threads, one plan each"}
+        plan_b.close()
+        del plan_b
 
     # ---- CPU baseline: the oracle on one map ----
     cpu = None

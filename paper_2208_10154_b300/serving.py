@@ -223,7 +223,7 @@ class GpuExecutor:
     """Runs batches on one GPU with libsht: resident plans (LRU), one CUDA
     stream per slot, optional CUDA-graph replay per (key, batch bucket).
 
-    Memory. A batch of n maps is run as consecutive library calls of at most
+    Memory. A batch of n maps (without a graph) is run as consecutive library calls of at most
     `chunk` maps on its stream, with one workspace sized for the chunk, so
     that workspace + input staging + the batch output stay within `mem_cap`
     (the server's HBM budget). Each request's result is a view of the batch
@@ -231,16 +231,28 @@ class GpuExecutor:
     buffers (input, output, workspace) are at most `graph_max_bytes`, up to
     `graph_cache_bytes` in all (LRU); a captured graph serves one batch at a
     time (a batch that finds its graph busy runs without it). Plans and graph
-    buffers are reported by `resident_bytes()` for admission."""
+    buffers are reported by `resident_bytes()` for admission; a batch that
+    will capture a graph also counts the capture's buffers. Batches below
+    `small_work` map values run on high-priority streams (`small_slots` of
+    them)."""
 
     def __init__(self, device: int = 0, slots: int = 4, use_graphs: bool = False, plan_cache: int = 32,
-                 mem_cap: float = 150e9, graph_max_bytes: float = 4e9, graph_cache_bytes: float = 24e9):
+                 mem_cap: float = 150e9, graph_max_bytes: float = 0.5e9, graph_cache_bytes: float = 24e9,
+                 small_work: float = 2e9, small_slots: int = 2):
         import torch
         from . import sht
         self.torch, self.sht = torch, sht
         self.device = device
+        # batches of less than `small_work` (map pixels x components x maps)
+        # run on high-priority streams: the GPU schedules their CTAs ahead of
+        # those of large batches already running, so small requests do not
+        # wait behind a batch that takes seconds
+        self.small_work = float(small_work)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+        hi = torch.cuda.Stream.priority_range()[1] if hasattr(torch.cuda.Stream, "priority_range") else -1
+        self.streams_hi = [torch.cuda.Stream(device=device, priority=hi) for _ in range(small_slots)]
         self.free_streams = list(range(slots))
+        self.free_hi = list(range(small_slots))
         self.plans = collections.OrderedDict()
         self.plan_cache = plan_cache
         self.use_graphs = use_graphs
@@ -298,8 +310,22 @@ class GpuExecutor:
     def batch_bytes(self, key, n):
         p = self._plan(key)
         ib, ob = self._sizes(p, key[0])
+        g = self._graph_bytes(key, p, n)
+        if g:                                          # the output is copied out of the graph's buffers,
+            cached = (key, self._bucket(n)) in self.graphs   # which are resident once captured
+            return n * ob + (0 if cached else g)
         c = self._chunk(p, key[0], n)
         return p.workspace_bytes(c) + c * ib + n * ob
+
+    def _graph_bytes(self, key, p, n):
+        """Static bytes of the graph a batch of n maps would replay, or 0 if
+        it would run without one."""
+        if not self.use_graphs:
+            return 0
+        b = self._bucket(n)
+        ib, ob = self._sizes(p, key[0])
+        nbytes = p.workspace_bytes(b) + b * (ib + ob)
+        return nbytes if nbytes <= self.graph_max_bytes else 0
 
     @staticmethod
     def _bucket(n):
@@ -314,14 +340,21 @@ class GpuExecutor:
         p = self._plan(key)
         op = key[0]
         dev = f"cuda:{self.device}"
-        sid = self.free_streams.pop() if self.free_streams else 0
-        st = self.streams[sid]
         counts, pieces = [], []
         for x in inputs:
             parts = list(x) if isinstance(x, (list, tuple)) else [x]
             counts.append(sum(int(t.shape[0]) for t in parts))
             pieces.extend(parts)
         n = sum(counts)
+        if n * p.ncomp * p.npix < self.small_work and self.free_hi:
+            sid = ("hi", self.free_hi.pop())
+            st = self.streams_hi[sid[1]]
+        elif self.free_streams:
+            sid = ("lo", self.free_streams.pop())
+            st = self.streams[sid[1]]
+        else:                                          # every slot busy: queue on stream 0 (not freed again)
+            sid = ("shared", 0)
+            st = self.streams[0]
         ib, ob = self._sizes(p, op)
         out_len = p.npix if op == "alm2map" else p.nalm
         out_dt = torch.float64 if op == "alm2map" else torch.complex128
@@ -441,7 +474,10 @@ class GpuExecutor:
         ev, outs, sid, gk = handle
         if not ev.query():
             return None
-        self.free_streams.append(sid)
+        if sid[0] == "hi":
+            self.free_hi.append(sid[1])
+        elif sid[0] == "lo":
+            self.free_streams.append(sid[1])
         if gk is not None:
             self.graph_busy.discard(gk)
         return outs
