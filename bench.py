@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--per-map-samples", type=int, default=4)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--qu1024-pairs", type=int, default=200,
+                    help="Q/U pairs of the spin-2 measurement at nside 1024, lmax 2047 (0 skips it)")
     ap.add_argument("--qu-maps", type=int, default=500,
                     help="Q/U map pairs of the spin-2 (polarization) measurement at the same nside; 0 skips it")
     ap.add_argument("--no-context", action="store_true",
@@ -776,6 +778,11 @@ def main():
     qu = None
     if a.qu_maps > 0:
         qu = run_qu(nside, lmax, a.qu_maps, max(1, min(a.steps, 3)), max(1, min(a.warmup, 2)), precision)
+    qu1024 = None
+    if a.qu1024_pairs > 0:
+        gc.collect()
+        torch.cuda.empty_cache()
+        qu1024 = run_qu(1024, 2047, a.qu1024_pairs, 2, 1, precision)
 
     next_rows = None
     if not a.no_next_rows:
@@ -803,7 +810,8 @@ def main():
         "roofline_fft": fft_roofline,
         "cpu_baseline": cpu, "e2e": e2e, "per_map": per_map,
         "batched_over_per_map": value / per_map["value"] if per_map else None,
-        "kernels": prof, "plan_create_s": plan_s, "qu": qu, "context": context, "next_rows": next_rows,
+        "kernels": prof, "plan_create_s": plan_s, "qu": qu, "qu_nside1024": qu1024, "context": context,
+        "next_rows": next_rows,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
