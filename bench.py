@@ -174,6 +174,41 @@ def fft_flops_per_map(nside):
     return tot
 
 
+def host_link_gbs(host_buf, torch):
+    """Copy bandwidth between pinned host memory and the GPU (GB/s): host to
+    device alone, device to host alone, and both at once on two streams (the
+    ceiling of the end-to-end measurement)."""
+    n = min(host_buf.numel(), 1 << 30)                # up to 8 GB of float64
+    h_in = host_buf.view(-1)[:n]
+    h_out = torch.empty(n, dtype=host_buf.dtype, pin_memory=True)
+    d_a = torch.empty(n, dtype=host_buf.dtype, device="cuda")
+    d_b = torch.empty(n, dtype=host_buf.dtype, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nbytes = n * host_buf.element_size()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+    d_a.copy_(h_in, non_blocking=True)
+    h_out.copy_(d_b, non_blocking=True)
+    t_h2d = timed(lambda: d_a.copy_(h_in, non_blocking=True))
+    t_d2h = timed(lambda: h_out.copy_(d_b, non_blocking=True))
+
+    def both():
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+    t_both = timed(both)
+    out = {"h2d_gbs": nbytes / t_h2d / 1e9, "d2h_gbs": nbytes / t_d2h / 1e9,
+           "both_gbs": 2 * nbytes / t_both / 1e9, "bytes_per_copy": nbytes}
+    del h_out, d_a, d_b
+    return out
+
+
 def algorithmic_flops(nside, lmax, nmaps, spin=0):
     """Legendre contraction flops per transform (4 per (l, m, ring pair) per map
     for spin 0; x4 for a spin-2 Q/U pair)."""
@@ -751,7 +786,9 @@ def main():
         nb_map = maps_h.numel() * 8
         e2e = {"value": nmaps / dt, "unit": "maps/s", "h2d_bytes_per_step": nb_alm + nb_map,
                "d2h_bytes_per_step": nb_map + nb_alm, "api": "sht_alm2map_host + sht_map2alm_host",
-               "directions": "concurrent: two host threads, one plan each"}
+               "directions": "concurrent: two host threads, one plan each",
+               "host_link": host_link_gbs(maps_h, torch)}
+        e2e["host_link"]["e2e_gbs"] = (nb_alm + nb_map) * 2 / dt / 1e9
         plan_b.close()
         del plan_b
 

@@ -190,7 +190,9 @@ sht_status sht_map2alm_adjoint(sht_plan* plan, const void* alm, void* map, int n
                                void* workspace, size_t workspace_bytes, void* stream);
 
 /* End-to-end variants on HOST buffers (pageable or pinned): the library
- * moves the batch in chunks through two device buffer pairs, overlapping
+ * moves the batch in chunks (sized so that the call holds at most 48 GB of
+ * device memory; environment SHT_HOST_CHUNK_GB sets another limit) through
+ * two device buffer pairs, overlapping
  * chunk k's transform (on `stream`) with chunk k+1's host->device copy and
  * chunk k-1's device->host copy (two plan-owned copy streams); pageable
  * buffers are staged through plan-owned pinned buffers. Returns after the

@@ -1313,7 +1313,12 @@ static sht_status host_call(sht_plan* p, const void* in_host, void* out_host, in
     const size_t alm_b = (size_t)p->ncomp * p->nalm * 2 * sizeof(double);
     const size_t in_b = to_map ? alm_b : map_b, out_b = to_map ? map_b : alm_b;
     int chunk = nmaps;
-    const size_t cap = (size_t)24 << 30;
+    // device memory of one call: two buffer pairs and a workspace of a chunk
+    size_t cap = (size_t)48 << 30;
+    if (const char* env = std::getenv("SHT_HOST_CHUNK_GB")) {
+        const long long g = std::atoll(env);
+        if (g >= 1) cap = (size_t)g << 30;
+    }
     while (chunk > 1 && 2 * (size_t)chunk * (in_b + out_b) + ws_bytes(p, chunk, niter) > cap) chunk = (chunk + 1) / 2;
     if (const char* env = std::getenv("SHT_HOST_CHUNK_MAPS")) {      // smaller chunks (tests)
         const int c = std::atoi(env);
