@@ -103,6 +103,7 @@ __device__ __forceinline__ cx cmul_mi(const cx& a) { cx r; r.hr = a.hi; r.lr = a
 __device__ __forceinline__ cx cmul_pi(const cx& a) { cx r; r.hr = -a.hi; r.lr = -a.li; r.hi = a.hr; r.li = a.lr; return r; }
 
 struct FftTabsF {
+    const float4* twp;            // per size class: per-pass radix-4 twiddles (hi re, hi im, lo re, lo im)
     const float2 *twh, *twl;      // per size class: exp(-2 pi i u / M), u < M / 2, hi / lo
     const float2 *chh, *chl;      // Bluestein chirp, hi / lo
     const float2 *bhh, *bhl;      // Bluestein filter spectrum / M (digit-reversed), hi / lo
@@ -147,6 +148,27 @@ __device__ __forceinline__ void stage_twiddles(float4* tw, int M, long long ctw,
     }
 }
 
+// the class's per-pass radix-4 twiddles (n float4 at offset ctwp) into shared memory
+__device__ __forceinline__ void stage_pass_twiddles(float4* twp, int n, long long ctwp, const FftTabsF& t)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) twp[i] = t.twp[ctwp + i];
+}
+
+// Per-pass twiddles: for the radix-4 pass of span h of a 2^L-point transform
+// (decimation in time) and k < h, the three factors W^{k M / 2h},
+// W^{k M / 4h}, W^{3 k M / 4h} sit at slots 3 (off(h) + k) + 0, 1, 2 with
+// off(h) = (h - 1 - (L & 1)) / 3 (the spans are 2^(L & 1), 4 times that, ...);
+// consecutive k are 48 bytes apart, which keeps a warp's 16-byte reads on
+// distinct banks. The decimation-in-frequency pass of span 2h uses the same
+// three factors.
+__device__ __forceinline__ int twp_off(int L, int h) { return (h - 1 - (L & 1)) / 3; }
+__device__ __forceinline__ void twp_get(const float4* e, int t, bool inv, float2& wh, float2& wl)
+{
+    const float4 v = e[t];
+    wh = make_float2(v.x, inv ? -v.y : v.y);
+    wl = make_float2(v.z, inv ? -v.w : v.w);
+}
+
 // Transform buffers in shared memory: sequence s of a size-M class starts at
 // s * fft_pad_len(M), and its point i sits at fft_pad(i). One 16-byte slot of
 // padding per 8 points and one more per 64 keep the 16-byte accesses of a
@@ -165,12 +187,12 @@ __host__ __device__ __forceinline__ int fft_pad_len(int M) { return M + (M >> 3)
 // DIT: spans h and 2h, with w = W_{4h}^k the inputs are multiplied by w^2
 // (x1), w (x2), w^3 (x3), then the 4-point DFT (+-i exact).
 template <int NS>
-__device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, const float4* tw, bool inv, int ts)
+__device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, const float4* twp, bool inv)
 {
-    const int M = 1 << L, P = fft_pad_len(M), MT = M * ts;
+    const int M = 1 << L, P = fft_pad_len(M);
     const int h = 1 << lh;
-    const int s1 = M >> (lh + 1), s2 = M >> (lh + 2);
     const int ng = M >> 2;                           // groups per sequence
+    const float4* tp = twp + 3 * twp_off(L, h);
     for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
         const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
         const int k = g & (h - 1);
@@ -184,9 +206,10 @@ __device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, co
         }
         if (h > 1) {
             float2 w1h, w1l, w2h, w2l, w3h, w3l;
-            twid(tw, k * s1 * ts, inv, w1h, w1l);
-            twid(tw, k * s2 * ts, inv, w2h, w2l);
-            twid_full(tw, 3 * k * s2 * ts, MT, inv, w3h, w3l);
+            const float4* e = tp + 3 * k;
+            twp_get(e, 0, inv, w1h, w1l);
+            twp_get(e, 1, inv, w2h, w2l);
+            twp_get(e, 2, inv, w3h, w3l);
 #pragma unroll
             for (int q = 0; q < NS; q++) {
                 x1[q] = cmulc(x1[q], w1h, w1l);
@@ -207,12 +230,12 @@ __device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, co
 
 // DIF: spans h and h/2, outputs 1, 2, 3 take v^2, v, v^3 with v = W_{2h}^k.
 template <int NS>
-__device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, const float4* tw, bool inv, int ts)
+__device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, const float4* twp, bool inv)
 {
-    const int M = 1 << L, P = fft_pad_len(M), MT = M * ts;
+    const int M = 1 << L, P = fft_pad_len(M);
     const int h = 1 << lh, hq = h >> 1;
-    const int s1 = M >> (lh + 1), s2 = M >> lh;
     const int ng = M >> 2;
+    const float4* tp = twp + 3 * twp_off(L, hq);
     for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
         const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
         const int k = g & (hq - 1);
@@ -228,10 +251,13 @@ __device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, co
             c3[q] = inv ? cmul_pi(d) : cmul_mi(d);
         }
         if (hq > 1) {
+            // v = W^{k M / 2h}: outputs 1, 2, 3 take v^2, v, v^3, the DIT
+            // factors 0, 1, 2 of span hq
             float2 v1h, v1l, v2h, v2l, v3h, v3l;
-            twid(tw, k * s1 * ts, inv, v1h, v1l);
-            twid(tw, k * s2 * ts, inv, v2h, v2l);
-            twid_full(tw, 3 * k * s1 * ts, MT, inv, v3h, v3l);
+            const float4* e = tp + 3 * k;
+            twp_get(e, 1, inv, v1h, v1l);
+            twp_get(e, 0, inv, v2h, v2l);
+            twp_get(e, 2, inv, v3h, v3l);
 #pragma unroll
             for (int q = 0; q < NS; q++) {
                 y[q * P + i0] = caddc(c0[q], c1[q]); y[q * P + i1] = cmulc(csubc(c0[q], c1[q]), v2h, v2l);
@@ -265,8 +291,8 @@ __device__ __forceinline__ void r2_span1(cx* buf, int nb, int L)
 // In-place decimation-in-time FFTs of nb sequences of M = 2^L points (padded
 // layout above), input in bit-reversed order, output natural. Two radix-2
 // stages per pass, sequences in pairs; W = exp(-+2 pi i / M).
-// ts: stride of the twiddle indices (the staged table belongs to a size ts M)
-__device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv, int ts = 1)
+// twp: the per-pass twiddles of the 2^L-point transform
+__device__ void fft_dit(cx* buf, int nb, int L, const float4* twp, bool inv)
 {
     const int P = fft_pad_len(1 << L);
     int lh = 0;
@@ -275,21 +301,21 @@ __device__ void fft_dit(cx* buf, int nb, int L, const float4* tw, bool inv, int 
         lh = 1;
     }
     for (; lh + 2 <= L; lh += 2) {
-        if (nb >= 2) dit4_pass<2>(buf, nb >> 1, L, lh, tw, inv, ts);
-        if (nb & 1) dit4_pass<1>(buf + (nb - 1) * P, 1, L, lh, tw, inv, ts);
+        if (nb >= 2) dit4_pass<2>(buf, nb >> 1, L, lh, twp, inv);
+        if (nb & 1) dit4_pass<1>(buf + (nb - 1) * P, 1, L, lh, twp, inv);
         __syncthreads();
     }
 }
 
 // In-place decimation-in-frequency FFTs (natural input, bit-reversed output),
 // two radix-2 stages (spans h and h/2) per pass, sequences in pairs.
-__device__ void fft_dif(cx* buf, int nb, int L, const float4* tw, bool inv, int ts = 1)
+__device__ void fft_dif(cx* buf, int nb, int L, const float4* twp, bool inv)
 {
     const int P = fft_pad_len(1 << L);
     int lh = L - 1;
     for (; lh >= 1; lh -= 2) {
-        if (nb >= 2) dif4_pass<2>(buf, nb >> 1, L, lh, tw, inv, ts);
-        if (nb & 1) dif4_pass<1>(buf + (nb - 1) * P, 1, L, lh, tw, inv, ts);
+        if (nb >= 2) dif4_pass<2>(buf, nb >> 1, L, lh, twp, inv);
+        if (nb & 1) dif4_pass<1>(buf + (nb - 1) * P, 1, L, lh, twp, inv);
         __syncthreads();
     }
     if (lh == 0) r2_span1(buf, nb, L);
@@ -361,38 +387,40 @@ __device__ void r3_passes(cx* buf, int nb, int M, int p3, const float4* tw, bool
 }
 
 // transforms of size M = p3 2^L: natural in, digit-reversed out (DIF) and
-// digit-reversed in, natural out (DIT); p3 = 1 is the plain power-of-two case
-__device__ __forceinline__ void fft_dif_m(cx* buf, int nb, int L, int p3, const float4* tw, bool inv)
+// digit-reversed in, natural out (DIT); p3 = 1 is the plain power-of-two case.
+// tw: the size-M twiddles of the radix-3 stages (p3 > 1 only), twp: the
+// per-pass twiddles of the 2^L-point part
+__device__ __forceinline__ void fft_dif_m(cx* buf, int nb, int L, int p3, const float4* tw, const float4* twp, bool inv)
 {
     if (p3 > 1) r3_passes(buf, nb, p3 << L, p3, tw, inv, true);
-    fft_dif(buf, nb * p3, L, tw, inv, p3);
+    fft_dif(buf, nb * p3, L, twp, inv);
 }
-__device__ __forceinline__ void fft_dit_m(cx* buf, int nb, int L, int p3, const float4* tw, bool inv)
+__device__ __forceinline__ void fft_dit_m(cx* buf, int nb, int L, int p3, const float4* tw, const float4* twp, bool inv)
 {
-    fft_dit(buf, nb * p3, L, tw, inv, p3);
+    fft_dit(buf, nb * p3, L, twp, inv);
     if (p3 > 1) r3_passes(buf, nb, p3 << L, p3, tw, inv, false);
 }
 
-// forward DFT (Z_k = sum z_n e^{-2 pi i k n / N}) of nb sequences placed by placec()
-__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const FftTabsF& t)
+__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const float4* twp,
+                             const FftTabsF& t)
 {
     const int M = f.m, L = 31 - __clz(M / f.p3), P = fft_pad_len(M);
     if (!f.bluestein) {
-        fft_dit_m(buf, nb, L, f.p3, tw, false);
+        fft_dit_m(buf, nb, L, f.p3, tw, twp, false);
         return;
     }
-    fft_dif_m(buf, nb, L, f.p3, tw, false);
+    fft_dif_m(buf, nb, L, f.p3, tw, twp, false);
     for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
-        const int s = i / M, ii = i - s * M;
+        const int s = (i >= M) ? 1 : 0, ii = i - s * M;   // nb <= 2 sequences
         cx& z = buf[s * P + fft_pad(ii)];
         z = cmulc(z, t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
     }
     __syncthreads();
-    fft_dit_m(buf, nb, L, f.p3, tw, true);
+    fft_dit_m(buf, nb, L, f.p3, tw, twp, true);
     // (the filter spectrum carries the 1 / M of the inverse transform: an
     // FP32 scale by 1 / M would round for M = 3^b 2^a)
     for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
-        const int s = i / f.n, k = i - s * f.n;
+        const int s = (i >= f.n) ? 1 : 0, k = i - s * f.n;
         cx& z = buf[s * P + fft_pad(k)];
         z = cmulc(z, t.chh[f.chirp + k], t.chl[f.chirp + k]);
     }
@@ -439,14 +467,21 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned int* __restrict__ colmax,
                const int* __restrict__ cls, int ncls, const PairGeom* __restrict__ pairs,
-               const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw, int M, int R_, int mmax,
+               const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw, long long ctwp, int ntwp, int M,
+               int R_, int mmax,
                long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
     const int P = fft_pad_len(M);
-    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
-    stage_twiddles(tw, M, ctw, tb);                 // (the first __syncthreads below publishes it)
+    // shared memory: the transform buffers, the per-pass twiddles, and for
+    // sizes 3^b 2^a the size-M twiddles of the radix-3 stages
+    // (ntwp < 0: the per-pass twiddles do not fit and stay in global memory)
+    float4* twp_s = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
+    float4* tw = twp_s + max(ntwp, 0);
+    const float4* twp = (ntwp >= 0) ? twp_s : tb.twp + ctwp;
+    if (ntwp > 0) stage_pass_twiddles(twp_s, ntwp, ctwp, tb);   // (the first __syncthreads below publishes them)
+    if (M % 3 == 0) stage_twiddles(tw, M, ctw, tb);
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
@@ -474,7 +509,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                 vn[u] = 0.0; vs[u] = 0.0;
                 cwh[u] = make_float2(1.0f, 0.0f); cwl[u] = make_float2(0.0f, 0.0f);
                 if (e < nb * N) {
-                    const int s = e / N, n = e - s * N;
+                    const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
                     const double* mp = map + (long long)(mc0 + s) * npix;
                     vn[u] = mp[g.start_n + n];
                     if (g.start_s >= 0) vs[u] = mp[g.start_s + n];
@@ -485,7 +520,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
             for (int u = 0; u < FWD_UB; u++) {
                 const int e = e0 + u * NT;
                 if (e < nb * N) {
-                    const int s = e / N, n = e - s * N;
+                    const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
                     cx z = czero();
                     tc::f64_split_scaled(vn[u], 0, z.hr, z.lr);
                     if (g.start_s >= 0) tc::f64_split_scaled(vs[u], 0, z.hi, z.li);
@@ -495,11 +530,11 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         }
         if (f.bluestein)
             for (int e = threadIdx.x; e < nb * (M - N); e += NT) {
-                const int s = e / (M - N), i = e - s * (M - N);
+                const int s = (e >= M - N) ? 1 : 0, i = e - s * (M - N);
                 buf[s * P + fft_pad(N + i)] = czero();
             }
         __syncthreads();
-        dftc_forward(buf, nb, f, tw, tb);
+        dftc_forward(buf, nb, f, tw, twp, tb);
 #pragma unroll
         for (int jj = 0; jj < FWD_MJ; jj++) {
             const int m = threadIdx.x + jj * NT;
@@ -567,13 +602,17 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls, int ncls,
                 const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw,
+                long long ctwp, int ntwp,
                 int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
     const int P = fft_pad_len(M);
-    float4* tw = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
-    stage_twiddles(tw, M, ctw, tb);                 // (published by the __syncthreads before the FFT)
+    float4* twp_s = reinterpret_cast<float4*>(smem_raw + (size_t)mpc * P * sizeof(cx));
+    float4* tw = twp_s + max(ntwp, 0);
+    const float4* twp = (ntwp >= 0) ? twp_s : tb.twp + ctwp;
+    if (ntwp > 0) stage_pass_twiddles(twp_s, ntwp, ctwp, tb);   // (published by the __syncthreads before the FFT)
+    if (M % 3 == 0) stage_twiddles(tw, M, ctw, tb);
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
@@ -695,13 +734,13 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         }
         if (f.bluestein)
             for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
-                const int s = e / (M - N), i = e - s * (M - N);
+                const int s = (e >= M - N) ? 1 : 0, i = e - s * (M - N);
                 buf[s * P + fft_pad(N + i)] = czero();
             }
         __syncthreads();
-        dftc_forward(buf, nb, f, tw, tb);
+        dftc_forward(buf, nb, f, tw, twp, tb);
         for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
-            const int s = e / N, n = e - s * N;
+            const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
             const cx z = buf[s * P + fft_pad(n)];      // conj of the inverse transform
             double* mp = map + (long long)(mc0 + s) * npix;
             mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
@@ -714,6 +753,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
 static FftTabsF tabs(const sht_plan* p)
 {
     FftTabsF t;
+    t.twp = p->c.twp;
     t.twh = p->c.tws_h; t.twl = p->c.tws_l;
     t.chh = p->t.chirp_f; t.chl = p->c.chirp_l;
     t.bhh = p->c.bhs_h; t.bhl = p->c.bhs_l;
@@ -725,20 +765,28 @@ static FftTabsF tabs(const sht_plan* p)
 // FFT size classes of the plan: launch configuration per class (two map
 // columns per CTA while their unpadded buffers fit in 128 KB of shared
 // memory), the padded buffers plus the class's twiddles (M / 2 x 16 bytes)
-static void class_cfg(int M, int mmax, int& nt, int& mpc, size_t& sm)
+// Launch configuration of a size class: two map columns per CTA while their
+// unpadded buffers fit in 128 KB, the per-pass twiddles staged in shared
+// memory when everything fits in 227 KB (else read from global memory), the
+// size-M twiddles for sizes 3^b 2^a; 512 threads where one CTA fills an SM's
+// shared memory (16 warps per SM).
+static void class_cfg(const FftClass& c, int mmax, int& nt, int& mpc, size_t& sm, bool& twp_smem,
+                      bool allow_smem_twp = true)
 {
+    const int M = c.m;
     mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
-    sm = (size_t)mpc * fft_pad_len(M) * sizeof(cx) + (size_t)(M / 2) * sizeof(float4);
-    // 512 threads where one CTA fills an SM's shared memory (16 warps per SM)
+    sm = (size_t)mpc * fft_pad_len(M) * sizeof(cx) + ((M % 3 == 0) ? (size_t)(M / 2) * sizeof(float4) : 0);
+    twp_smem = allow_smem_twp && sm + (size_t)c.twp_n * sizeof(float4) <= (227u << 10);
+    if (twp_smem) sm += (size_t)c.twp_n * sizeof(float4);
     nt = (M >= 4096 || mmax >= 1024 || sm > (113u << 10)) ? 512 : 256;
 }
 
-static cudaError_t set_smem(const void* fn, const sht_plan* p)
+static cudaError_t set_smem(const void* fn, const sht_plan* p, bool allow_smem_twp = true)
 {
     size_t mx = 0;
     for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm;
-        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        int nt, mpc; size_t sm; bool ts;
+        class_cfg(c, p->mmax, nt, mpc, sm, ts, allow_smem_twp);
         mx = std::max(mx, sm);
     }
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
@@ -755,17 +803,18 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
     e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm;
-        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        int nt, mpc; size_t sm; bool ts;
+        class_cfg(c, p->mmax, nt, mpc, sm, ts);
+        const int ntwp = ts ? c.twp_n : -1;          // < 0: per-pass twiddles from global memory
         dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + FWD_PB - 1) / FWD_PB);
         prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
             k_fftc_forward<512><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->c.fft_s, tabs(p), c.tw, c.m, p->R, p->mmax, p->npix, nc,
+                                                      p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix, nc,
                                                       nmc, mpc);
         else
             k_fftc_forward<256><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->c.fft_s, tabs(p), c.tw, c.m, p->R, p->mmax, p->npix, nc,
+                                                      p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix, nc,
                                                       nmc, mpc);
         prof_stop(st);
         count_launch();
@@ -775,22 +824,25 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
 
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
 {
-    cudaError_t e = set_smem((const void*)k_fftc_backward<256>, p);
-    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_backward<512>, p);
+    // (the backward kernels read the per-pass twiddles from global memory:
+    // their G and phase loads keep more of the L1 that way; measured)
+    cudaError_t e = set_smem((const void*)k_fftc_backward<256>, p, false);
+    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_backward<512>, p, false);
     if (e != cudaSuccess) return e;
     const int nmc = nmaps * p->ncomp;
     for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm;
-        class_cfg(c.m, p->mmax, nt, mpc, sm);
+        int nt, mpc; size_t sm; bool ts;
+        class_cfg(c, p->mmax, nt, mpc, sm, ts, false);
+        const int ntwp = ts ? c.twp_n : -1;          // < 0: per-pass twiddles from global memory
         dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
         prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
         if (nt == 512)
             k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
-                                                       tabs(p), c.tw, c.m, p->R, p->mmax, p->npix,
+                                                       tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
                                                        ncols(p, nmaps), nmc, mpc);
         else
             k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
-                                                       tabs(p), c.tw, c.m, p->R, p->mmax, p->npix,
+                                                       tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
                                                        ncols(p, nmaps), nmc, mpc);
         prof_stop(st);
         count_launch();

@@ -366,12 +366,37 @@ static cudaError_t build_tables(sht_plan* p)
         for (int q = 0; q < R; q++) bym[p->h_fft_s[p->h_pairs[q].fft].m].push_back(q);
         std::vector<int> cls;
         std::vector<float2> twh, twl;
+        std::vector<float4> twp;
         for (auto& kv : bym) {
             sht::FftClass c;
             c.m = kv.first;
             c.off = (int)cls.size();
             c.cnt = (int)kv.second.size();
             c.tw = (long long)twh.size();
+            // per-pass twiddles of the power-of-two part Ms = 2^La: for each
+            // radix-4 pass of span h (decimation in time: h = 2^lh, lh = La & 1,
+            // La & 1 + 2, ..., h <= Ms / 4) and k < h, the three factors
+            // W^{k Ms / 2h}, W^{k Ms / 4h}, W^{3 k Ms / 4h} (W = e^{-2 pi i / Ms});
+            // the decimation-in-frequency pass of span 2h uses the same three
+            c.twp = (long long)twp.size();
+            {
+                const int Ms = c.m / pow3_part(c.m);
+                int La = 0;
+                while ((1 << La) < Ms) La++;
+                for (int lh = (La & 1); lh + 2 <= La; lh += 2) {
+                    const int h = 1 << lh, s1 = Ms >> (lh + 1), s2 = Ms >> (lh + 2);
+                    for (int k = 0; k < h; k++) {
+                        const long long us[3] = {(long long)k * s1, (long long)k * s2, 3LL * k * s2};
+                        for (long long u : us) {
+                            const ld a = -2 * PI_L * (ld)u / (ld)Ms;
+                            const ld cr = cosl(a), ci = sinl(a);
+                            const float hx = (float)cr, hy = (float)ci;
+                            twp.push_back(make_float4(hx, hy, (float)(cr - (ld)hx), (float)(ci - (ld)hy)));
+                        }
+                    }
+                }
+            }
+            c.twp_n = (int)(twp.size() - c.twp);
             for (int u = 0; u < std::max(1, c.m / 2); u++) {
                 const ld a = -2 * PI_L * (ld)u / (ld)c.m;
                 const ld cr = cosl(a), ci = sinl(a);
@@ -383,6 +408,8 @@ static cudaError_t build_tables(sht_plan* p)
             p->h_fcls.push_back(c);
         }
         if ((e = upload(&p->c.cls_pairs, cls, &acc)) != cudaSuccess) return e;
+        if (twp.empty()) twp.push_back(make_float4(1, 0, 0, 0));
+        if ((e = upload(&p->c.twp, twp, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.tws_h, twh, &acc)) != cudaSuccess) return e;
         if ((e = upload(&p->c.tws_l, twl, &acc)) != cudaSuccess) return e;
     }
@@ -780,7 +807,7 @@ static void free_tables(sht_plan* p)
                     p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
     void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off,
-                  p->c.fft_s, p->c.tws_h, p->c.tws_l, p->c.bhs_h, p->c.bhs_l};
+                  p->c.fft_s, p->c.twp, p->c.tws_h, p->c.tws_l, p->c.bhs_h, p->c.bhs_l};
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,
