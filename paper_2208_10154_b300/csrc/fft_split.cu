@@ -448,7 +448,7 @@ __device__ __forceinline__ cx chirp_in(const FftLen& f, const FftTabsF& t, cx z,
 // e^{sgn i pi k / N} for k = m mod 2N (hi/lo)
 __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m, bool neg, float2& ph, float2& pl)
 {
-    long long o = t.phoff[fidx] + (m % (2 * N));
+    long long o = t.phoff[fidx] + ((m < 2 * N) ? m : m % (2 * N));
     ph = t.phh[o]; pl = t.phl[o];
     if (neg) { ph.y = -ph.y; pl.y = -pl.y; }
 }
@@ -539,7 +539,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         for (int jj = 0; jj < FWD_MJ; jj++) {
             const int m = threadIdx.x + jj * NT;
             if (m > mmax) break;
-            const int j = m % N, jm = j ? N - j : 0;
+            const int j = (m < N) ? m : m % N, jm = j ? N - j : 0;
             float2 ph, pl;
             if (g.phi0 != 0.0) phase(tb, g.fft, N, m, true, ph, pl);
             float4 ev[2], ov[2];
@@ -653,7 +653,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         };
         // bins j and N - j of both columns into the transform buffer
         auto emit = [&](int j, const cx (&Bn)[2][2], const cx (&Bs)[2][2]) {
-            const int jj[2] = {j, (N - j) % N};
+            const int jj[2] = {j, (j ? N - j : 0)};
 #pragma unroll
             for (int t = 0; t < 2; t++) {
                 const int jt = jj[t];
@@ -681,7 +681,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                     const int j = j0 + u * NT;
 #pragma unroll
                     for (int t = 0; t < 2; t++) {
-                        const int m = t ? (N - j) % N : j;
+                        const int m = t ? (j ? N - j : 0) : j;
                         E[u][t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); O[u][t] = E[u][t];
                         PH[u][t] = make_float2(1.0f, 0.0f); PL[u][t] = make_float2(0.0f, 0.0f);
                         if (j <= N / 2 && m <= mmax) {
@@ -697,7 +697,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                     cx Bn[2][2], Bs[2][2];                 // [bin j / N - j][column]
 #pragma unroll
                     for (int t = 0; t < 2; t++) {
-                        const int m = t ? (N - j) % N : j;
+                        const int m = t ? (j ? N - j : 0) : j;
 #pragma unroll
                         for (int s = 0; s < 2; s++) {
                             Bn[t][s] = czero(); Bs[t][s] = czero();
@@ -709,7 +709,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
             }
         } else {
             for (int j = threadIdx.x; j <= N / 2; j += NT) {
-                const int jj[2] = {j, (N - j) % N};
+                const int jj[2] = {j, (j ? N - j : 0)};
                 cx Bn[2][2], Bs[2][2];                     // [bin j / N - j][column]
 #pragma unroll
                 for (int t = 0; t < 2; t++) {
