@@ -45,6 +45,7 @@ struct FftLen {
     long long chirp;   // offset of w_n = exp(-i pi n^2 / N) (n < N) in the chirp table
     long long bhat;    // offset of FFT_M(conj chirp, circular) (digit-reversed order)
     int p3;            // 3^b of M (1: M is a power of two)
+    int bexp = 0;      // split form, Bluestein: max_k |filter_k| <= 2^bexp (filter with the 1 / M)
 };
 
 struct DevTables {

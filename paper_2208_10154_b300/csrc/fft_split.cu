@@ -98,6 +98,114 @@ __device__ __forceinline__ float cim(const cx& a) { return a.hi + a.li; }
 
 __device__ __forceinline__ int brev_c(int i, int logm) { return (int)(__brev((unsigned)i) >> (32 - logm)); }
 
+// ---- grid arithmetic: the transforms proper ----------------------------
+// Inside a transform a value is hi + lo with hi an integer-valued FP32 number
+// and lo an FP32 correction of a few units. The sequence is first scaled by
+// a power of two 2^-K such that every partial sum of the transform stays
+// below 2^20 in magnitude (the complex L1 bound: at most N nonzero points of
+// components below max, 2 sqrt(2) N max). Then the hi parts of a sum are
+// integers below 2^24 and add exactly, so an addition is two packed FP32
+// additions with no error term; a product rounds hi w to an integer inside
+// the FMA (adding 1.5 2^23 puts the units digit at the last place) and keeps
+// the remainder hi w - round(hi w), exact to 2^-25, with the lo terms in lo.
+// The only rounding left is that of lo, a few units times 2^-24: relative to
+// values of typical size (2^8 .. 2^14 units) an error of ~2^-32 per step.
+constexpr float GRND = 12582912.0f;      // 1.5 * 2^23
+
+__device__ __forceinline__ cx gadd(const cx& a, const cx& b)
+{
+    using namespace tc;
+    cx s;
+    up2(f2_add(pk2(a.hr, a.hi), pk2(b.hr, b.hi)), s.hr, s.hi);
+    up2(f2_add(pk2(a.lr, a.li), pk2(b.lr, b.li)), s.lr, s.li);
+    return s;
+}
+__device__ __forceinline__ cx gsub(const cx& a, const cx& b)
+{
+    using namespace tc;
+    cx s;
+    up2(f2_sub(pk2(a.hr, a.hi), pk2(b.hr, b.hi)), s.hr, s.hi);
+    up2(f2_sub(pk2(a.lr, a.li), pk2(b.lr, b.li)), s.lr, s.li);
+    return s;
+}
+// x * w, w = wh + wl a hi/lo twiddle, |x| <= 2^22. Lane 0 the real part,
+// lane 1 the imaginary part: hi = round(xr w) + round(xi (-wy, wx)).
+__device__ __forceinline__ cx gmul(const cx& x, float2 wh, float2 wl)
+{
+    using namespace tc;
+    const unsigned long long CC = pk2(GRND, GRND);
+    const unsigned long long WH = pk2(wh.x, wh.y), WS = pk2(-wh.y, wh.x);
+    const unsigned long long XR = pk2(x.hr, x.hr), XI = pk2(x.hi, x.hi);
+    const unsigned long long T1 = f2_fma(XR, WH, CC), T2 = f2_fma(XI, WS, CC);
+    const unsigned long long N1 = f2_sub(CC, T1), N2 = f2_sub(CC, T2);    // -round(xr w), -round(xi ws)
+    const unsigned long long H = f2_sub(f2_sub(T1, CC), N2);             // integers: exact
+    unsigned long long L = f2_fma(XR, WH, N1);                           // xr w - round(xr w)
+    L = f2_fma(pk2(x.lr, x.lr), WH, L);
+    L = f2_fma(pk2(x.li, x.li), WS, L);
+    L = f2_fma(XR, pk2(wl.x, wl.y), L);
+    L = f2_fma(XI, pk2(-wl.y, wl.x), L);
+    L = f2_add(L, f2_fma(XI, WS, N2));
+    cx t;
+    up2(H, t.hr, t.hi);
+    up2(L, t.lr, t.li);
+    return t;
+}
+// x * c for a real c = ch + cl (|x| <= 2^22)
+__device__ __forceinline__ cx gmulr(const cx& x, float ch, float cl)
+{
+    using namespace tc;
+    const unsigned long long CC = pk2(GRND, GRND), C = pk2(ch, ch);
+    const unsigned long long XH = pk2(x.hr, x.hi);
+    const unsigned long long T = f2_fma(XH, C, CC);
+    unsigned long long L = f2_fma(XH, C, f2_sub(CC, T));
+    L = f2_fma(pk2(x.lr, x.li), C, f2_fma(XH, pk2(cl, cl), L));
+    cx t;
+    up2(f2_sub(T, CC), t.hr, t.hi);
+    up2(L, t.lr, t.li);
+    return t;
+}
+// a double-float value (hi + lo, normalised) times sc = 2^-K onto the grid
+// (|hi sc| <= 2^22); the scaling is exact, the remainder too
+__device__ __forceinline__ cx gquant(const cx& x, float sc)
+{
+    using namespace tc;
+    const unsigned long long CC = pk2(GRND, GRND), S = pk2(sc, sc);
+    const unsigned long long XH = pk2(x.hr, x.hi);
+    const unsigned long long T = f2_fma(XH, S, CC);
+    const unsigned long long L = f2_fma(pk2(x.lr, x.li), S, f2_fma(XH, S, f2_sub(CC, T)));
+    cx t;
+    up2(f2_sub(T, CC), t.hr, t.hi);
+    up2(L, t.lr, t.li);
+    return t;
+}
+// 2^k as an FP32 (k clamped to the normal range)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + min(max(k, -126), 127)) << 23); }
+// |hi| of both components as the larger FP32 bit pattern (order-preserving)
+__device__ __forceinline__ unsigned absbits(const cx& z)
+{
+    return max(__float_as_uint(z.hr) & 0x7FFFFFFFu, __float_as_uint(z.hi) & 0x7FFFFFFFu);
+}
+// block-wide maxima of v0 (sequence 0) and v1 (sequence 1) into red[0], red[1]
+// (every thread of the block calls this, outside divergent code)
+__device__ __forceinline__ void red_max2(unsigned* red, unsigned v0, unsigned v1)
+{
+    v0 = __reduce_max_sync(0xffffffffu, v0);
+    v1 = __reduce_max_sync(0xffffffffu, v1);
+    if ((threadIdx.x & 31) == 0) {
+        if (v0) atomicMax(red, v0);
+        if (v1) atomicMax(red + 1, v1);
+    }
+}
+// grid exponent K of a sequence of at most N nonzero points whose largest
+// component has the FP32 bit pattern mb: |x| < 2^(E - 126) for the exponent
+// field E, so 4 N max 2^-K <= 2^20 with K = E + ceil(log2 N) - 144
+__device__ __forceinline__ int grid_k(unsigned mb, int N)
+{
+    const int E = (int)(mb >> 23);
+    if (E == 0) return 0;
+    return max(E + (32 - __clz(N - 1)) - 144, -126);
+}
+
 // a * (-i) and a * (+i): component swaps, exact
 __device__ __forceinline__ cx cmul_mi(const cx& a) { cx r; r.hr = a.hi; r.lr = a.li; r.hi = -a.hr; r.li = -a.lr; return r; }
 __device__ __forceinline__ cx cmul_pi(const cx& a) { cx r; r.hr = -a.hi; r.lr = -a.li; r.hi = a.hr; r.li = a.lr; return r; }
@@ -212,18 +320,18 @@ __device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, co
             twp_get(e, 2, inv, w3h, w3l);
 #pragma unroll
             for (int q = 0; q < NS; q++) {
-                x1[q] = cmulc(x1[q], w1h, w1l);
-                x2[q] = cmulc(x2[q], w2h, w2l);
-                x3[q] = cmulc(x3[q], w3h, w3l);
+                x1[q] = gmul(x1[q], w1h, w1l);
+                x2[q] = gmul(x2[q], w2h, w2l);
+                x3[q] = gmul(x3[q], w3h, w3l);
             }
         }
 #pragma unroll
         for (int q = 0; q < NS; q++) {
-            const cx b0 = caddc(x0[q], x1[q]), b1 = csubc(x0[q], x1[q]);
-            const cx b2 = caddc(x2[q], x3[q]), b3 = csubc(x2[q], x3[q]);
+            const cx b0 = gadd(x0[q], x1[q]), b1 = gsub(x0[q], x1[q]);
+            const cx b2 = gadd(x2[q], x3[q]), b3 = gsub(x2[q], x3[q]);
             const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
-            y[q * P + i0] = caddc(b0, b2); y[q * P + i2] = csubc(b0, b2);
-            y[q * P + i1] = caddc(b1, u3); y[q * P + i3] = csubc(b1, u3);
+            y[q * P + i0] = gadd(b0, b2); y[q * P + i2] = gsub(b0, b2);
+            y[q * P + i1] = gadd(b1, u3); y[q * P + i3] = gsub(b1, u3);
         }
     }
 }
@@ -246,8 +354,8 @@ __device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, co
 #pragma unroll
         for (int q = 0; q < NS; q++) {
             const cx x0 = y[q * P + i0], x1 = y[q * P + i1], x2 = y[q * P + i2], x3 = y[q * P + i3];
-            c0[q] = caddc(x0, x2); c2[q] = csubc(x0, x2); c1[q] = caddc(x1, x3);
-            const cx d = csubc(x1, x3);
+            c0[q] = gadd(x0, x2); c2[q] = gsub(x0, x2); c1[q] = gadd(x1, x3);
+            const cx d = gsub(x1, x3);
             c3[q] = inv ? cmul_pi(d) : cmul_mi(d);
         }
         if (hq > 1) {
@@ -260,15 +368,15 @@ __device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, co
             twp_get(e, 2, inv, v3h, v3l);
 #pragma unroll
             for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = caddc(c0[q], c1[q]); y[q * P + i1] = cmulc(csubc(c0[q], c1[q]), v2h, v2l);
-                y[q * P + i2] = cmulc(caddc(c2[q], c3[q]), v1h, v1l);
-                y[q * P + i3] = cmulc(csubc(c2[q], c3[q]), v3h, v3l);
+                y[q * P + i0] = gadd(c0[q], c1[q]); y[q * P + i1] = gmul(gsub(c0[q], c1[q]), v2h, v2l);
+                y[q * P + i2] = gmul(gadd(c2[q], c3[q]), v1h, v1l);
+                y[q * P + i3] = gmul(gsub(c2[q], c3[q]), v3h, v3l);
             }
         } else {
 #pragma unroll
             for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = caddc(c0[q], c1[q]); y[q * P + i1] = csubc(c0[q], c1[q]);
-                y[q * P + i2] = caddc(c2[q], c3[q]); y[q * P + i3] = csubc(c2[q], c3[q]);
+                y[q * P + i0] = gadd(c0[q], c1[q]); y[q * P + i1] = gsub(c0[q], c1[q]);
+                y[q * P + i2] = gadd(c2[q], c3[q]); y[q * P + i3] = gsub(c2[q], c3[q]);
             }
         }
     }
@@ -282,8 +390,8 @@ __device__ __forceinline__ void r2_span1(cx* buf, int nb, int L)
         cx* x = buf + (b >> (L - 1)) * P;
         const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
         const cx a = x[i0], c = x[i1];
-        x[i0] = caddc(a, c);
-        x[i1] = csubc(a, c);
+        x[i0] = gadd(a, c);
+        x[i1] = gsub(a, c);
     }
     __syncthreads();
 }
@@ -321,30 +429,22 @@ __device__ void fft_dif(cx* buf, int nb, int L, const float4* twp, bool inv)
     if (lh == 0) r2_span1(buf, nb, L);
 }
 
-// a * c for a real double-float constant c = ch + cl (both parts of a)
-__device__ __forceinline__ cx rmulc(const cx& a, float ch, float cl)
-{
-    cx r;
-    r.hr = a.hr * ch; r.hi = a.hi * ch;
-    r.lr = fmaf(a.hr, ch, -r.hr) + fmaf(a.hr, cl, a.lr * ch);
-    r.li = fmaf(a.hi, ch, -r.hi) + fmaf(a.hi, cl, a.li * ch);
-    return r;
-}
 // sqrt(3) / 2 as a double-float pair
 constexpr float R3H = 0.866025388240814208984375f;
 constexpr float R3L = 1.55436244377793497517e-08f;
 
-// the 3-point DFT y_j = sum_i x_i e^{-+2 pi i i j / 3}: y0 = x0 + t,
-// y1,2 = (x0 - t / 2) -+ i (sqrt 3 / 2)(x1 - x2), t = x1 + x2 (forward sign)
+// the 3-point DFT y_j = sum_i x_i e^{-+2 pi i i j / 3} on the grid: y0 = x0 + t,
+// y1,2 = (x0 - t / 2) -+ i (sqrt 3 / 2)(x1 - x2), t = x1 + x2 (forward sign);
+// t / 2 is rounded back onto the grid like a product
 __device__ __forceinline__ void dft3(const cx& x0, const cx& x1, const cx& x2, bool inv, cx& y0, cx& y1, cx& y2)
 {
-    const cx t = caddc(x1, x2);
-    y0 = caddc(x0, t);
-    const cx u = csubc(x0, cscale(t, 0.5f));
-    const cx d = rmulc(csubc(x1, x2), R3H, R3L);
+    const cx t = gadd(x1, x2);
+    y0 = gadd(x0, t);
+    const cx u = gsub(x0, gmulr(t, 0.5f, 0.0f));
+    const cx d = gmulr(gsub(x1, x2), R3H, R3L);
     const cx v = inv ? cmul_pi(d) : cmul_mi(d);
-    y1 = caddc(u, v);
-    y2 = csubc(u, v);
+    y1 = gadd(u, v);
+    y2 = gsub(u, v);
 }
 
 // Radix-3 stages of a size M = 3^b 2^a transform (padded layout, nb
@@ -376,9 +476,9 @@ __device__ void r3_passes(cx* buf, int nb, int M, int p3, const float4* tw, bool
             cx x0 = y[i0], x1 = y[i1], x2 = y[i2], y0, y1, y2;
             if (dif) {
                 dft3(x0, x1, x2, inv, y0, y1, y2);
-                y[i0] = y0; y[i1] = cmulc(y1, w1h, w1l); y[i2] = cmulc(y2, w2h, w2l);
+                y[i0] = y0; y[i1] = gmul(y1, w1h, w1l); y[i2] = gmul(y2, w2h, w2l);
             } else {
-                dft3(x0, cmulc(x1, w1h, w1l), cmulc(x2, w2h, w2l), inv, y0, y1, y2);
+                dft3(x0, gmul(x1, w1h, w1l), gmul(x2, w2h, w2l), inv, y0, y1, y2);
                 y[i0] = y0; y[i1] = y1; y[i2] = y2;
             }
         }
@@ -401,30 +501,108 @@ __device__ __forceinline__ void fft_dit_m(cx* buf, int nb, int L, int p3, const 
     if (p3 > 1) r3_passes(buf, nb, p3 << L, p3, tw, inv, false);
 }
 
-__device__ void dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const float4* twp,
-                             const FftTabsF& t)
+// The forward DFTs of the nb sequences in buf, which hold double-float
+// values at their input positions (natural order for Bluestein, the
+// digit-reversed order of the passes otherwise). red[0], red[1]: the largest
+// |component| of each sequence (block-reduced and published by the caller);
+// red[2], red[3] zero on entry. Output in natural order on the grid, true
+// values (hi + lo) 2^k of the returned exponents (x: sequence 0, y: 1).
+__device__ __noinline__ int2 dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const float4* twp,
+                             const FftTabsF& t, unsigned* red)
 {
     const int M = f.m, L = 31 - __clz(M / f.p3), P = fft_pad_len(M);
+    const int K0 = grid_k(red[0], f.n), K1 = grid_k(red[1], f.n);
+    const float sc0 = pow2f(-K0), sc1 = pow2f(-K1);
+    // onto the grid; Bluestein: times the chirp, zero beyond N (the table
+    // loads of DUB points per thread are in flight before the first is used)
+    constexpr int DUB = 4;
+    if (!f.bluestein)
+        for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
+            const int s = (i >= M) ? 1 : 0, ii = i - s * M;   // nb <= 2 sequences
+            cx& z = buf[s * P + fft_pad(ii)];
+            z = gquant(z, s ? sc1 : sc0);
+        }
+    else
+    for (int i0 = threadIdx.x; i0 < nb * M; i0 += DUB * blockDim.x) {
+        float2 ch[DUB], cl[DUB];
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            const int s = (i >= M) ? 1 : 0, ii = i - s * M;   // nb <= 2 sequences
+            ch[u] = make_float2(1.0f, 0.0f); cl[u] = make_float2(0.0f, 0.0f);
+            if (i < nb * M && ii < f.n) { ch[u] = t.chh[f.chirp + ii]; cl[u] = t.chl[f.chirp + ii]; }
+        }
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nb * M) break;
+            const int s = (i >= M) ? 1 : 0, ii = i - s * M;
+            cx& z = buf[s * P + fft_pad(ii)];
+            z = (ii < f.n) ? gmul(gquant(z, s ? sc1 : sc0), ch[u], cl[u]) : czero();
+        }
+    }
+    __syncthreads();
     if (!f.bluestein) {
         fft_dit_m(buf, nb, L, f.p3, tw, twp, false);
-        return;
+        return make_int2(K0, K1);
     }
     fft_dif_m(buf, nb, L, f.p3, tw, twp, false);
+    // the filter product Y = Z b / M is rescaled by 2^-D so that the inverse
+    // transform's partial sums (at most M terms of components below
+    // sqrt(2) max|Z| 2^bexp) stay below 2^20 too
+    unsigned m0 = 0, m1 = 0;
     for (int i = threadIdx.x; i < nb * M; i += blockDim.x) {
-        const int s = (i >= M) ? 1 : 0, ii = i - s * M;   // nb <= 2 sequences
-        cx& z = buf[s * P + fft_pad(ii)];
-        z = cmulc(z, t.bhh[f.bhat + ii], t.bhl[f.bhat + ii]);
+        const int s = (i >= M) ? 1 : 0, ii = i - s * M;
+        const unsigned v = absbits(buf[s * P + fft_pad(ii)]);
+        if (s) m1 = max(m1, v); else m0 = max(m0, v);
+    }
+    red_max2(red + 2, m0, m1);
+    __syncthreads();
+    const int lgm = 32 - __clz(M - 1);
+    const int e0 = (int)(red[2] >> 23), e1 = (int)(red[3] >> 23);
+    const int D0 = e0 ? e0 - 126 + lgm + f.bexp + 2 - 20 : 0, D1 = e1 ? e1 - 126 + lgm + f.bexp + 2 - 20 : 0;
+    const float fs0 = pow2f(-D0), fs1 = pow2f(-D1);
+    for (int i0 = threadIdx.x; i0 < nb * M; i0 += DUB * blockDim.x) {
+        float2 bh[DUB], bl[DUB];
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            const int s = (i >= M) ? 1 : 0, ii = i - s * M;   // nb <= 2 sequences
+            if (i < nb * M) { bh[u] = t.bhh[f.bhat + ii]; bl[u] = t.bhl[f.bhat + ii]; }
+        }
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nb * M) break;
+            const int s = (i >= M) ? 1 : 0, ii = i - s * M;
+            cx& z = buf[s * P + fft_pad(ii)];
+            const float fsc = s ? fs1 : fs0;
+            z = gmul(z, make_float2(bh[u].x * fsc, bh[u].y * fsc), make_float2(bl[u].x * fsc, bl[u].y * fsc));
+        }
     }
     __syncthreads();
     fft_dit_m(buf, nb, L, f.p3, tw, twp, true);
     // (the filter spectrum carries the 1 / M of the inverse transform: an
     // FP32 scale by 1 / M would round for M = 3^b 2^a)
-    for (int i = threadIdx.x; i < nb * f.n; i += blockDim.x) {
-        const int s = (i >= f.n) ? 1 : 0, k = i - s * f.n;
-        cx& z = buf[s * P + fft_pad(k)];
-        z = cmulc(z, t.chh[f.chirp + k], t.chl[f.chirp + k]);
+    for (int i0 = threadIdx.x; i0 < nb * f.n; i0 += DUB * blockDim.x) {
+        float2 ch[DUB], cl[DUB];
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            const int s = (i >= f.n) ? 1 : 0, k = i - s * f.n;
+            if (i < nb * f.n) { ch[u] = t.chh[f.chirp + k]; cl[u] = t.chl[f.chirp + k]; }
+        }
+#pragma unroll
+        for (int u = 0; u < DUB; u++) {
+            const int i = i0 + u * blockDim.x;
+            if (i >= nb * f.n) break;
+            const int s = (i >= f.n) ? 1 : 0, k = i - s * f.n;
+            cx& z = buf[s * P + fft_pad(k)];
+            z = gmul(z, ch[u], cl[u]);
+        }
     }
     __syncthreads();
+    return make_int2(K0 + D0, K1 + D1);
 }
 
 // where input n goes: natural for Bluestein (decimation in frequency), else
@@ -438,11 +616,6 @@ __device__ __forceinline__ int placec(const FftLen& f, int n)
     int p = 0, S = f.m;
     for (int q = f.p3; q > 1; q /= 3) { S /= 3; const int d = n % 3; n /= 3; p += d * S; }
     return p + brev_c(n, 31 - __clz(f.m / f.p3));
-}
-
-__device__ __forceinline__ cx chirp_in(const FftLen& f, const FftTabsF& t, cx z, int n)
-{
-    return f.bluestein ? cmulc(z, t.chh[f.chirp + n], t.chl[f.chirp + n]) : z;
 }
 
 // e^{sgn i pi k / N} for k = m mod 2N (hi/lo)
@@ -462,7 +635,8 @@ __device__ __forceinline__ void phase(const FftTabsF& t, int fidx, int N, int m,
 // ---------------------------------------------------------------------------
 constexpr int FWD_PB = 32;
 
-// NT threads; each thread owns m = threadIdx.x + jj NT, jj < 4 (mmax < 4 NT)
+// NT threads; in the epilogue lane pairs own m = threadIdx.x / 2 + jj NT / 2,
+// jj < 8 (mmax < 4 NT)
 template <int NT>
 __global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned int* __restrict__ colmax,
@@ -482,38 +656,40 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
     const float4* twp = (ntwp >= 0) ? twp_s : tb.twp + ctwp;
     if (ntwp > 0) stage_pass_twiddles(twp_s, ntwp, ctwp, tb);   // (the first __syncthreads below publishes them)
     if (M % 3 == 0) stage_twiddles(tw, M, ctw, tb);
+    __shared__ unsigned red[4];                    // per ring pair: largest |component| of each sequence
+    if (threadIdx.x < 4) red[threadIdx.x] = 0u;
+    __syncthreads();
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
-    constexpr int FWD_MJ = 4;
-    float mx[FWD_MJ][2][4];
+    // epilogue: lanes 2k and 2k + 1 take the two columns of one order m, so
+    // that a warp's T stores cover whole 32-byte sectors
+    constexpr int FWD_MJ = 8;
+    const int es = threadIdx.x & 1, et = threadIdx.x >> 1, ent = NT / 2;
+    float mx[FWD_MJ][4];
 #pragma unroll
-    for (int j = 0; j < FWD_MJ; j++)
-#pragma unroll
-        for (int s = 0; s < 2; s++) mx[j][s][0] = mx[j][s][1] = mx[j][s][2] = mx[j][s][3] = 0.0f;
+    for (int j = 0; j < FWD_MJ; j++) mx[j][0] = mx[j][1] = mx[j][2] = mx[j][3] = 0.0f;
     const int iend = min(ncls, (int)(blockIdx.y + 1) * FWD_PB);
     for (int ip = blockIdx.y * FWD_PB; ip < iend; ip++) {
         const int p = cls[ip];
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
         const int N = g.n;
-        // the ring's samples (and Bluestein chirps) in batches of FWD_UB per
-        // thread: every load of a batch is in flight before the first is used
+        // the ring's samples in batches of FWD_UB per thread: every load of a
+        // batch is in flight before the first is used
         constexpr int FWD_UB = 4;
+        unsigned m0 = 0, m1 = 0;
         for (int e0 = threadIdx.x; e0 < nb * N; e0 += FWD_UB * NT) {
             double vn[FWD_UB], vs[FWD_UB];
-            float2 cwh[FWD_UB], cwl[FWD_UB];
 #pragma unroll
             for (int u = 0; u < FWD_UB; u++) {
                 const int e = e0 + u * NT;
                 vn[u] = 0.0; vs[u] = 0.0;
-                cwh[u] = make_float2(1.0f, 0.0f); cwl[u] = make_float2(0.0f, 0.0f);
                 if (e < nb * N) {
                     const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
                     const double* mp = map + (long long)(mc0 + s) * npix;
                     vn[u] = mp[g.start_n + n];
                     if (g.start_s >= 0) vs[u] = mp[g.start_s + n];
-                    if (f.bluestein) { cwh[u] = tb.chh[f.chirp + n]; cwl[u] = tb.chl[f.chirp + n]; }
                 }
             }
 #pragma unroll
@@ -524,69 +700,70 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                     cx z = czero();
                     tc::f64_split_scaled(vn[u], 0, z.hr, z.lr);
                     if (g.start_s >= 0) tc::f64_split_scaled(vs[u], 0, z.hi, z.li);
-                    buf[s * P + fft_pad(placec(f, n))] = f.bluestein ? cmulc(z, cwh[u], cwl[u]) : z;
+                    buf[s * P + fft_pad(placec(f, n))] = z;
+                    const unsigned v = absbits(z);
+                    if (s) m1 = max(m1, v); else m0 = max(m0, v);
                 }
             }
         }
-        if (f.bluestein)
-            for (int e = threadIdx.x; e < nb * (M - N); e += NT) {
-                const int s = (e >= M - N) ? 1 : 0, i = e - s * (M - N);
-                buf[s * P + fft_pad(N + i)] = czero();
-            }
+        red_max2(red, m0, m1);
         __syncthreads();
-        dftc_forward(buf, nb, f, tw, twp, tb);
+        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red);
+        // the bins hold 2^-K times the spectrum; E and O below are twice the
+        // true ones (the halvings of the split fold into the output scale)
+        const float osc0 = pow2f(kq.x - 1), osc1 = pow2f(kq.y - 1);
+        if (threadIdx.x < 4) red[threadIdx.x] = 0u;    // (read by every thread before the syncs above)
+        // the phases of this lane's orders first (all loads in flight)
+        float2 PH[FWD_MJ], PL[FWD_MJ];
 #pragma unroll
         for (int jj = 0; jj < FWD_MJ; jj++) {
-            const int m = threadIdx.x + jj * NT;
-            if (m > mmax) break;
-            const int j = (m < N) ? m : m % N, jm = j ? N - j : 0;
-            float2 ph, pl;
-            if (g.phi0 != 0.0) phase(tb, g.fft, N, m, true, ph, pl);
-            float4 ev[2], ov[2];
+            const int m = et + jj * ent;
+            PH[jj] = make_float2(1.0f, 0.0f); PL[jj] = make_float2(0.0f, 0.0f);
+            if (m <= mmax && g.phi0 != 0.0) phase(tb, g.fft, N, m, true, PH[jj], PL[jj]);
+        }
+        const float osc = es ? osc1 : osc0;
 #pragma unroll
-            for (int s = 0; s < 2; s++) {
-                if (s >= nb) break;
-                const cx a = buf[s * P + fft_pad(j)], b = cconjc(buf[s * P + fft_pad(jm)]);
-                // Xn = (a + conj b)/2, Xs = (a - conj b)/(2i)
-                cx Xn = cscale(caddc(a, b), 0.5f);
-                const cx d = cscale(csubc(a, b), 0.5f);
+        for (int jj = 0; jj < FWD_MJ; jj++) {
+            const int m = et + jj * ent;
+            if (m > mmax) break;
+            if (es < nb) {
+                const int j = (m < N) ? m : m % N, jm = j ? N - j : 0;
+                const cx a = buf[es * P + fft_pad(j)], b = cconjc(buf[es * P + fft_pad(jm)]);
+                // 2 Xn = a + conj b, 2 Xs = (a - conj b) / i
+                cx Xn = gadd(a, b);
+                const cx d = gsub(a, b);
                 cx Xs; Xs.hr = d.hi; Xs.lr = d.li; Xs.hi = -d.hr; Xs.li = -d.lr;
-                if (g.phi0 != 0.0) { Xn = cmulc(Xn, ph, pl); Xs = cmulc(Xs, ph, pl); }
-                const cx E = caddc(Xn, Xs), O = csubc(Xn, Xs);
+                if (g.phi0 != 0.0) { Xn = gmul(Xn, PH[jj], PL[jj]); Xs = gmul(Xs, PH[jj], PL[jj]); }
+                const cx E = gadd(Xn, Xs), O = gsub(Xn, Xs);
                 float2 e2, o2, el, ol;
                 two_sum(E.hr, E.lr, e2.x, el.x); two_sum(E.hi, E.li, e2.y, el.y);
                 two_sum(O.hr, O.lr, o2.x, ol.x); two_sum(O.hi, O.li, o2.y, ol.y);
+                e2.x *= osc; e2.y *= osc; el.x *= osc; el.y *= osc;
+                o2.x *= osc; o2.y *= osc; ol.x *= osc; ol.y *= osc;
+                mx[jj][0] = fmaxf(mx[jj][0], fabsf(e2.x));
+                mx[jj][1] = fmaxf(mx[jj][1], fabsf(e2.y));
+                mx[jj][2] = fmaxf(mx[jj][2], fabsf(o2.x));
+                mx[jj][3] = fmaxf(mx[jj][3], fabsf(o2.y));
                 // T keeps hi and lo: (Re hi, Re lo, Im hi, Im lo) per complex column
-                ev[s] = make_float4(e2.x, el.x, e2.y, el.y);
-                ov[s] = make_float4(o2.x, ol.x, o2.y, ol.y);
-                mx[jj][s][0] = fmaxf(mx[jj][s][0], fabsf(e2.x));
-                mx[jj][s][1] = fmaxf(mx[jj][s][1], fabsf(e2.y));
-                mx[jj][s][2] = fmaxf(mx[jj][s][2], fabsf(o2.x));
-                mx[jj][s][3] = fmaxf(mx[jj][s][3], fabsf(o2.y));
+                float4* t0 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + mc0 * 2);
+                float4* t1 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 1) * qstride + (long long)p * ncol + mc0 * 2);
+                t0[es] = make_float4(e2.x, el.x, e2.y, el.y);
+                t1[es] = make_float4(o2.x, ol.x, o2.y, ol.y);
             }
-            float4* t0 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 0) * qstride + (long long)p * ncol + mc0 * 2);
-            float4* t1 = reinterpret_cast<float4*>(T + ((long long)m * 2 + 1) * qstride + (long long)p * ncol + mc0 * 2);
-            t0[0] = ev[0];
-            t1[0] = ov[0];
-            if (nb == 2) { t0[1] = ev[1]; t1[1] = ov[1]; }
         }
         __syncthreads();
     }
 #pragma unroll
     for (int jj = 0; jj < FWD_MJ; jj++) {
-        const int m = threadIdx.x + jj * NT;
-        if (m > mmax) break;
-#pragma unroll
-        for (int s = 0; s < 2; s++) {
-            if (s >= nb) break;
-            const long long col = (long long)(mc0 + s) * 2;
-            unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
-            unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
-            if (mx[jj][s][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][s][0]));
-            if (mx[jj][s][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][s][1]));
-            if (mx[jj][s][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][s][2]));
-            if (mx[jj][s][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][s][3]));
-        }
+        const int m = et + jj * ent;
+        if (m > mmax || es >= nb) break;
+        const long long col = (long long)(mc0 + es) * 2;
+        unsigned int* c0 = colmax + ((long long)m * 2 + 0) * ncol + col;
+        unsigned int* c1 = colmax + ((long long)m * 2 + 1) * ncol + col;
+        if (mx[jj][0] > 0.0f) atomicMax(c0, __float_as_uint(mx[jj][0]));
+        if (mx[jj][1] > 0.0f) atomicMax(c0 + 1, __float_as_uint(mx[jj][1]));
+        if (mx[jj][2] > 0.0f) atomicMax(c1, __float_as_uint(mx[jj][2]));
+        if (mx[jj][3] > 0.0f) atomicMax(c1 + 1, __float_as_uint(mx[jj][3]));
     }
 }
 
@@ -613,6 +790,9 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
     const float4* twp = (ntwp >= 0) ? twp_s : tb.twp + ctwp;
     if (ntwp > 0) stage_pass_twiddles(twp_s, ntwp, ctwp, tb);   // (published by the __syncthreads before the FFT)
     if (M % 3 == 0) stage_twiddles(tw, M, ctw, tb);
+    __shared__ unsigned red[4];                    // per ring pair: largest |component| of each sequence
+    if (threadIdx.x < 4) red[threadIdx.x] = 0u;
+    __syncthreads();
     const int mc0 = blockIdx.x * mpc;
     const int nb = min(mpc, nmc - mc0);
     const long long qstride = (long long)R_ * ncol;
@@ -652,6 +832,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
             if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
         };
         // bins j and N - j of both columns into the transform buffer
+        unsigned m0 = 0, m1 = 0;
         auto emit = [&](int j, const cx (&Bn)[2][2], const cx (&Bs)[2][2]) {
             const int jj[2] = {j, (j ? N - j : 0)};
 #pragma unroll
@@ -665,7 +846,9 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                     const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
                     const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
                     const cx z = cconjc(caddc(hn, cmul_pi(hs)));
-                    buf[s * P + fft_pad(placec(f, jt))] = chirp_in(f, tb, z, jt);
+                    buf[s * P + fft_pad(placec(f, jt))] = z;
+                    const unsigned v = absbits(z);
+                    if (s) m1 = max(m1, v); else m0 = max(m0, v);
                 }
             }
         };
@@ -732,19 +915,18 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                 emit(j, Bn, Bs);
             }
         }
-        if (f.bluestein)
-            for (int e = threadIdx.x; e < nb * (M - N); e += blockDim.x) {
-                const int s = (e >= M - N) ? 1 : 0, i = e - s * (M - N);
-                buf[s * P + fft_pad(N + i)] = czero();
-            }
+        red_max2(red, m0, m1);
         __syncthreads();
-        dftc_forward(buf, nb, f, tw, twp, tb);
+        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red);
+        const float osc0 = pow2f(kq.x), osc1 = pow2f(kq.y);
+        if (threadIdx.x < 4) red[threadIdx.x] = 0u;    // (read by every thread before the syncs above)
         for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
             const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
-            const cx z = buf[s * P + fft_pad(n)];      // conj of the inverse transform
+            const cx z = buf[s * P + fft_pad(n)];      // conj of the inverse transform, times 2^-K
+            const float osc = s ? osc1 : osc0;
             double* mp = map + (long long)(mc0 + s) * npix;
-            mp[g.start_n + n] = tc::f32_to_f64(z.hr) + tc::f32_to_f64(z.lr);
-            if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi) + tc::f32_to_f64(z.li));
+            mp[g.start_n + n] = tc::f32_to_f64(z.hr * osc) + tc::f32_to_f64(z.lr * osc);
+            if (g.start_s >= 0) mp[g.start_s + n] = -(tc::f32_to_f64(z.hi * osc) + tc::f32_to_f64(z.li * osc));
         }
         __syncthreads();                               // buf is rewritten by the next ring pair
     }
@@ -762,60 +944,61 @@ static FftTabsF tabs(const sht_plan* p)
     return t;
 }
 
-// FFT size classes of the plan: launch configuration per class (two map
-// columns per CTA while their unpadded buffers fit in 128 KB of shared
-// memory), the padded buffers plus the class's twiddles (M / 2 x 16 bytes)
 // Launch configuration of a size class: two map columns per CTA while their
-// unpadded buffers fit in 128 KB, the per-pass twiddles staged in shared
-// memory when everything fits in 227 KB (else read from global memory), the
-// size-M twiddles for sizes 3^b 2^a; 512 threads where one CTA fills an SM's
-// shared memory (16 warps per SM).
-static void class_cfg(const FftClass& c, int mmax, int& nt, int& mpc, size_t& sm, bool& twp_smem,
-                      bool allow_smem_twp = true)
+// unpadded buffers fit in 128 KB; the per-pass twiddles staged in shared
+// memory when everything fits in 227 KB (else read from global memory); the
+// size-M twiddles for sizes 3^b 2^a; 512 threads where one CTA fills an
+// SM's shared memory (16 warps per SM).
+struct ClassCfg {
+    int nt, mpc;
+    size_t sm;
+    bool twp_smem;
+};
+static ClassCfg class_cfg(const FftClass& c, int mmax, bool fwd)
 {
+    ClassCfg k;
     const int M = c.m;
-    mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
-    sm = (size_t)mpc * fft_pad_len(M) * sizeof(cx) + ((M % 3 == 0) ? (size_t)(M / 2) * sizeof(float4) : 0);
-    twp_smem = allow_smem_twp && sm + (size_t)c.twp_n * sizeof(float4) <= (227u << 10);
-    if (twp_smem) sm += (size_t)c.twp_n * sizeof(float4);
-    nt = (M >= 4096 || mmax >= 1024 || sm > (113u << 10)) ? 512 : 256;
+    k.mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
+    size_t sm = (size_t)k.mpc * fft_pad_len(M) * sizeof(cx) + ((M % 3 == 0) ? (size_t)(M / 2) * sizeof(float4) : 0);
+    // (the backward kernels read the per-pass twiddles from global memory:
+    // their G and phase loads keep more of the L1 that way; measured)
+    k.twp_smem = fwd && sm + (size_t)c.twp_n * sizeof(float4) <= (227u << 10);
+    if (k.twp_smem) sm += (size_t)c.twp_n * sizeof(float4);
+    k.sm = sm;
+    k.nt = (M >= 4096 || mmax >= 1024 || sm > (113u << 10)) ? 512 : 256;
+    return k;
 }
 
-static cudaError_t set_smem(const void* fn, const sht_plan* p, bool allow_smem_twp = true)
+static cudaError_t set_smem(const void* fn, const sht_plan* p, bool fwd)
 {
     size_t mx = 0;
-    for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm; bool ts;
-        class_cfg(c, p->mmax, nt, mpc, sm, ts, allow_smem_twp);
-        mx = std::max(mx, sm);
-    }
+    for (const FftClass& c : p->h_fcls) mx = std::max(mx, class_cfg(c, p->mmax, fwd).sm);
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st)
 {
-    cudaError_t e = set_smem((const void*)k_fftc_forward<256>, p);
-    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_forward<512>, p);
+    cudaError_t e = set_smem((const void*)k_fftc_forward<256>, p, true);
+    if (e == cudaSuccess) e = set_smem((const void*)k_fftc_forward<512>, p, true);
     if (e != cudaSuccess) return e;
     const long long nc = ncols(p, nmaps);
     const int nmc = nmaps * p->ncomp;
     e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm; bool ts;
-        class_cfg(c, p->mmax, nt, mpc, sm, ts);
-        const int ntwp = ts ? c.twp_n : -1;          // < 0: per-pass twiddles from global memory
-        dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + FWD_PB - 1) / FWD_PB);
+        const ClassCfg k = class_cfg(c, p->mmax, true);
+        const int ntwp = k.twp_smem ? c.twp_n : -1;  // < 0: per-pass twiddles from global memory
+        dim3 grid((nmc + k.mpc - 1) / k.mpc, (c.cnt + FWD_PB - 1) / FWD_PB);
         prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
-        if (nt == 512)
-            k_fftc_forward<512><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix, nc,
-                                                      nmc, mpc);
+        if (k.nt == 512)
+            k_fftc_forward<512><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+                                                          p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
+                                                          p->npix, nc, nmc, k.mpc);
         else
-            k_fftc_forward<256><<<grid, nt, sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
-                                                      p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix, nc,
-                                                      nmc, mpc);
+            k_fftc_forward<256><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+                                                          p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
+                                                          p->npix, nc, nmc, k.mpc);
         prof_stop(st);
         count_launch();
     }
@@ -824,26 +1007,23 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
 
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
 {
-    // (the backward kernels read the per-pass twiddles from global memory:
-    // their G and phase loads keep more of the L1 that way; measured)
     cudaError_t e = set_smem((const void*)k_fftc_backward<256>, p, false);
     if (e == cudaSuccess) e = set_smem((const void*)k_fftc_backward<512>, p, false);
     if (e != cudaSuccess) return e;
     const int nmc = nmaps * p->ncomp;
     for (const FftClass& c : p->h_fcls) {
-        int nt, mpc; size_t sm; bool ts;
-        class_cfg(c, p->mmax, nt, mpc, sm, ts, false);
-        const int ntwp = ts ? c.twp_n : -1;          // < 0: per-pass twiddles from global memory
-        dim3 grid((nmc + mpc - 1) / mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
+        const ClassCfg k = class_cfg(c, p->mmax, false);
+        const int ntwp = k.twp_smem ? c.twp_n : -1;  // < 0: per-pass twiddles from global memory
+        dim3 grid((nmc + k.mpc - 1) / k.mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
         prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
-        if (nt == 512)
-            k_fftc_backward<512><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
-                                                       tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
-                                                       ncols(p, nmaps), nmc, mpc);
+        if (k.nt == 512)
+            k_fftc_backward<512><<<grid, k.nt, k.sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+                                                           tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
+                                                           ncols(p, nmaps), nmc, k.mpc);
         else
-            k_fftc_backward<256><<<grid, nt, sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
-                                                       tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
-                                                       ncols(p, nmaps), nmc, mpc);
+            k_fftc_backward<256><<<grid, k.nt, k.sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+                                                           tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
+                                                           ncols(p, nmaps), nmc, k.mpc);
         prof_stop(st);
         count_launch();
     }

@@ -349,6 +349,9 @@ static cudaError_t build_tables(sht_plan* p)
                 if (j > 0) b[M - j] = b[j];
             }
             host_dft_mixed(b);
+            ld bmax = 0.0L;
+            for (int q = 0; q < M; q++) bmax = std::max(bmax, std::abs(b[q]) / (ld)M);
+            fs.bexp = (bmax > 0.0L) ? (int)ceill(log2l(bmax)) : 0;
             for (int q = 0; q < M; q++) {
                 const cld v = b[split_k_of(q, M, fs.p3)] / (ld)M;   // with the inverse transform's 1 / M
                 const float hx = (float)v.real(), hy = (float)v.imag();

@@ -62,3 +62,17 @@ def test_eb_projection_needs_spin2(sht):
     plan = sht.Plan(8, 15, None, 0, "fp64")
     with pytest.raises(Exception):
         plan.eb_project(torch.zeros((1, 1, 12 * 64), dtype=torch.float64, device="cuda"))
+
+
+def test_plan_device_bytes_counts_tables_and_host_staging(sht):
+    """sht_plan_device_bytes (HBM admission): the split plan's FP64
+    checkpoints make it larger than the FP64 plan, and the host-buffer entry
+    points' device buffers are added once used."""
+    import numpy as np
+    p64 = sht.Plan(32, 63, None, 0, "fp64")
+    psp = sht.Plan(32, 63, None, 0, "split")
+    b64, bsp = p64.device_bytes(), psp.device_bytes()
+    assert 0 < b64 < bsp
+    a = np.zeros((2, 1, p64.nalm), dtype=np.complex128)
+    p64.alm2map_host(a)
+    assert p64.device_bytes() > b64
