@@ -643,7 +643,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                const int* __restrict__ cls, int ncls, const PairGeom* __restrict__ pairs,
                const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw, long long ctwp, int ntwp, int M,
                int R_, int mmax,
-               long long npix, long long ncol, int nmc, int mpc)
+               long long npix, long long ncol, int nmc, int mpc, int pf)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
@@ -675,6 +675,15 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
         const int N = g.n;
+        // the next ring pair's rows into L2 while this one is transformed (pf:
+        // the map is 16-byte aligned; rows start at even pixels, N = 4i)
+        if (pf && ip + 1 < iend && threadIdx.x < 2 * nb) {
+            const PairGeom gn = pairs[cls[ip + 1]];
+            const int s = threadIdx.x >> 1, r = threadIdx.x & 1;
+            if (!r || gn.start_s >= 0)
+                tc::prefetch_l2_bulk(map + (long long)(mc0 + s) * npix + (r ? gn.start_s : gn.start_n),
+                                     (uint32_t)gn.n * 8u);
+        }
         // the ring's samples in batches of FWD_UB per thread: every load of a
         // batch is in flight before the first is used
         constexpr int FWD_UB = 4;
@@ -979,6 +988,11 @@ static cudaError_t set_smem(const void* fn, const sht_plan* p, bool fwd)
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st)
 {
+    // the bulk L2 prefetches of the map rows want 16-byte aligned rows of a
+    // multiple of 16 bytes: an aligned map, even row starts, even N
+    int pf = ((uintptr_t)map & 15) == 0;
+    for (const PairGeom& g : p->h_pairs)
+        if ((g.start_n & 1) || (g.start_s >= 0 && (g.start_s & 1)) || (g.n & 1)) pf = 0;
     cudaError_t e = set_smem((const void*)k_fftc_forward<256>, p, true);
     if (e == cudaSuccess) e = set_smem((const void*)k_fftc_forward<512>, p, true);
     if (e != cudaSuccess) return e;
@@ -994,11 +1008,11 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
         if (k.nt == 512)
             k_fftc_forward<512><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
-                                                          p->npix, nc, nmc, k.mpc);
+                                                          p->npix, nc, nmc, k.mpc, pf);
         else
             k_fftc_forward<256><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
-                                                          p->npix, nc, nmc, k.mpc);
+                                                          p->npix, nc, nmc, k.mpc, pf);
         prof_stop(st);
         count_launch();
     }
