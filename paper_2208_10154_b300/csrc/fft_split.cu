@@ -4,10 +4,11 @@
 // signal RMS (5.96e-7 worst over 4e5 outputs), too close to the 1e-6 bar of
 // the split form, and FP64 arithmetic runs at ~1/64 of FP32 on this GPU. So
 // every complex value is carried as an unevaluated sum hi + lo of two FP32
-// numbers: butterfly additions are error-free (TwoSum, their rounding error
-// goes to lo), products use FMA and a hi/lo twiddle, and lo is propagated in
-// plain FP32. This halves the FFT error (6e-8 RMS) for ~4x the FP32 work.
-// Phases e^{+-i pi m / N} come from a hi/lo table per ring length.
+// numbers. Outside the transforms (loading, bin assembly) these are
+// double-float pairs (TwoSum additions, FMA products with hi/lo constants);
+// inside, a fixed-grid form (below) makes every addition exact at the cost
+// of two packed FP32 additions. Phases e^{+-i pi m / N} come from a hi/lo
+// table per ring length.
 //
 // Structure (Sec. 2.1 eq:mm; Appendix A.1 for m -> bin m mod N) is that of
 // fft.cu: one complex FFT of x_north + i x_south per ring pair, power-of-two
@@ -100,16 +101,20 @@ __device__ __forceinline__ int brev_c(int i, int logm) { return (int)(__brev((un
 
 // ---- grid arithmetic: the transforms proper ----------------------------
 // Inside a transform a value is hi + lo with hi an integer-valued FP32 number
-// and lo an FP32 correction of a few units. The sequence is first scaled by
-// a power of two 2^-K such that every partial sum of the transform stays
-// below 2^20 in magnitude (the complex L1 bound: at most N nonzero points of
-// components below max, 2 sqrt(2) N max). Then the hi parts of a sum are
-// integers below 2^24 and add exactly, so an addition is two packed FP32
-// additions with no error term; a product rounds hi w to an integer inside
-// the FMA (adding 1.5 2^23 puts the units digit at the last place) and keeps
-// the remainder hi w - round(hi w), exact to 2^-25, with the lo terms in lo.
-// The only rounding left is that of lo, a few units times 2^-24: relative to
-// values of typical size (2^8 .. 2^14 units) an error of ~2^-32 per step.
+// and lo an FP32 correction of at most a few units. The sequence is first
+// scaled by a power of two 2^-K such that every partial sum of the transform
+// stays below 2^hb in magnitude (the complex L1 bound: at most N nonzero
+// points of components below max, 2 sqrt(2) N max; hb = 21 for the forward
+// transforms, whose epilogue doubles the bins before a product, 22 for the
+// backward ones). Then the hi parts of a sum are integers below 2^24 and add
+// exactly, so an addition is two packed FP32 additions with no error term; a
+// product rounds hi w to an integer inside the FMA (adding 1.5 2^23 puts the
+// units digit at the last place; |hi w| <= 2^22) and keeps the remainder
+// hi w - round(hi w), exact to 2^-25, with the lo terms in lo. Every pass
+// moves the integer part of lo back into hi (grenorm), so lo stays below a
+// few units and its FP32 rounding near 2^-23 units per step (without it lo
+// sums the remainders of every product upstream, and at N = 2048 that alone
+// doubled the split form's alm2map error).
 constexpr float GRND = 12582912.0f;      // 1.5 * 2^23
 
 __device__ __forceinline__ cx gadd(const cx& a, const cx& b)
@@ -178,6 +183,18 @@ __device__ __forceinline__ cx gquant(const cx& x, float sc)
     up2(L, t.lr, t.li);
     return t;
 }
+// the integer part of lo moved into hi (exact): keeps |lo| <= 1/2 so that
+// the FP32 rounding of lo stays at 2^-25 units however many products fed it
+__device__ __forceinline__ cx grenorm(const cx& x)
+{
+    using namespace tc;
+    const unsigned long long CC = pk2(GRND, GRND), XL = pk2(x.lr, x.li);
+    const unsigned long long G = f2_sub(f2_add(XL, CC), CC);
+    cx r;
+    up2(f2_add(pk2(x.hr, x.hi), G), r.hr, r.hi);
+    up2(f2_sub(XL, G), r.lr, r.li);
+    return r;
+}
 // 2^k as an FP32 (k clamped to the normal range)
 __device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + min(max(k, -126), 127)) << 23); }
 // |hi| of both components as the larger FP32 bit pattern (order-preserving)
@@ -198,12 +215,12 @@ __device__ __forceinline__ void red_max2(unsigned* red, unsigned v0, unsigned v1
 }
 // grid exponent K of a sequence of at most N nonzero points whose largest
 // component has the FP32 bit pattern mb: |x| < 2^(E - 126) for the exponent
-// field E, so 4 N max 2^-K <= 2^20 with K = E + ceil(log2 N) - 144
-__device__ __forceinline__ int grid_k(unsigned mb, int N)
+// field E, so 4 N max 2^-K <= 2^hb with K = E + ceil(log2 N) - 124 - hb
+__device__ __forceinline__ int grid_k(unsigned mb, int N, int hb)
 {
     const int E = (int)(mb >> 23);
     if (E == 0) return 0;
-    return max(E + (32 - __clz(N - 1)) - 144, -126);
+    return max(E + (32 - __clz(N - 1)) - 124 - hb, -126);
 }
 
 // a * (-i) and a * (+i): component swaps, exact
@@ -330,8 +347,8 @@ __device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, co
             const cx b0 = gadd(x0[q], x1[q]), b1 = gsub(x0[q], x1[q]);
             const cx b2 = gadd(x2[q], x3[q]), b3 = gsub(x2[q], x3[q]);
             const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
-            y[q * P + i0] = gadd(b0, b2); y[q * P + i2] = gsub(b0, b2);
-            y[q * P + i1] = gadd(b1, u3); y[q * P + i3] = gsub(b1, u3);
+            y[q * P + i0] = grenorm(gadd(b0, b2)); y[q * P + i2] = grenorm(gsub(b0, b2));
+            y[q * P + i1] = grenorm(gadd(b1, u3)); y[q * P + i3] = grenorm(gsub(b1, u3));
         }
     }
 }
@@ -368,15 +385,16 @@ __device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, co
             twp_get(e, 2, inv, v3h, v3l);
 #pragma unroll
             for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = gadd(c0[q], c1[q]); y[q * P + i1] = gmul(gsub(c0[q], c1[q]), v2h, v2l);
-                y[q * P + i2] = gmul(gadd(c2[q], c3[q]), v1h, v1l);
-                y[q * P + i3] = gmul(gsub(c2[q], c3[q]), v3h, v3l);
+                y[q * P + i0] = grenorm(gadd(c0[q], c1[q]));
+                y[q * P + i1] = grenorm(gmul(gsub(c0[q], c1[q]), v2h, v2l));
+                y[q * P + i2] = grenorm(gmul(gadd(c2[q], c3[q]), v1h, v1l));
+                y[q * P + i3] = grenorm(gmul(gsub(c2[q], c3[q]), v3h, v3l));
             }
         } else {
 #pragma unroll
             for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = gadd(c0[q], c1[q]); y[q * P + i1] = gsub(c0[q], c1[q]);
-                y[q * P + i2] = gadd(c2[q], c3[q]); y[q * P + i3] = gsub(c2[q], c3[q]);
+                y[q * P + i0] = grenorm(gadd(c0[q], c1[q])); y[q * P + i1] = grenorm(gsub(c0[q], c1[q]));
+                y[q * P + i2] = grenorm(gadd(c2[q], c3[q])); y[q * P + i3] = grenorm(gsub(c2[q], c3[q]));
             }
         }
     }
@@ -390,8 +408,8 @@ __device__ __forceinline__ void r2_span1(cx* buf, int nb, int L)
         cx* x = buf + (b >> (L - 1)) * P;
         const int i = (b & ((M >> 1) - 1)) * 2, i0 = fft_pad(i), i1 = fft_pad(i + 1);
         const cx a = x[i0], c = x[i1];
-        x[i0] = gadd(a, c);
-        x[i1] = gsub(a, c);
+        x[i0] = grenorm(gadd(a, c));
+        x[i1] = grenorm(gsub(a, c));
     }
     __syncthreads();
 }
@@ -476,10 +494,10 @@ __device__ void r3_passes(cx* buf, int nb, int M, int p3, const float4* tw, bool
             cx x0 = y[i0], x1 = y[i1], x2 = y[i2], y0, y1, y2;
             if (dif) {
                 dft3(x0, x1, x2, inv, y0, y1, y2);
-                y[i0] = y0; y[i1] = gmul(y1, w1h, w1l); y[i2] = gmul(y2, w2h, w2l);
+                y[i0] = grenorm(y0); y[i1] = grenorm(gmul(y1, w1h, w1l)); y[i2] = grenorm(gmul(y2, w2h, w2l));
             } else {
                 dft3(x0, gmul(x1, w1h, w1l), gmul(x2, w2h, w2l), inv, y0, y1, y2);
-                y[i0] = y0; y[i1] = y1; y[i2] = y2;
+                y[i0] = grenorm(y0); y[i1] = grenorm(y1); y[i2] = grenorm(y2);
             }
         }
         __syncthreads();
@@ -508,10 +526,10 @@ __device__ __forceinline__ void fft_dit_m(cx* buf, int nb, int L, int p3, const 
 // red[2], red[3] zero on entry. Output in natural order on the grid, true
 // values (hi + lo) 2^k of the returned exponents (x: sequence 0, y: 1).
 __device__ __noinline__ int2 dftc_forward(cx* buf, int nb, const FftLen& f, const float4* tw, const float4* twp,
-                             const FftTabsF& t, unsigned* red)
+                             const FftTabsF& t, unsigned* red, int hb)
 {
     const int M = f.m, L = 31 - __clz(M / f.p3), P = fft_pad_len(M);
-    const int K0 = grid_k(red[0], f.n), K1 = grid_k(red[1], f.n);
+    const int K0 = grid_k(red[0], f.n, hb), K1 = grid_k(red[1], f.n, hb);
     const float sc0 = pow2f(-K0), sc1 = pow2f(-K1);
     // onto the grid; Bluestein: times the chirp, zero beyond N (the table
     // loads of DUB points per thread are in flight before the first is used)
@@ -560,7 +578,7 @@ __device__ __noinline__ int2 dftc_forward(cx* buf, int nb, const FftLen& f, cons
     __syncthreads();
     const int lgm = 32 - __clz(M - 1);
     const int e0 = (int)(red[2] >> 23), e1 = (int)(red[3] >> 23);
-    const int D0 = e0 ? e0 - 126 + lgm + f.bexp + 2 - 20 : 0, D1 = e1 ? e1 - 126 + lgm + f.bexp + 2 - 20 : 0;
+    const int D0 = e0 ? e0 - 126 + lgm + f.bexp + 2 - hb : 0, D1 = e1 ? e1 - 126 + lgm + f.bexp + 2 - hb : 0;
     const float fs0 = pow2f(-D0), fs1 = pow2f(-D1);
     for (int i0 = threadIdx.x; i0 < nb * M; i0 += DUB * blockDim.x) {
         float2 bh[DUB], bl[DUB];
@@ -717,7 +735,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         }
         red_max2(red, m0, m1);
         __syncthreads();
-        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red);
+        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red, 21);
         // the bins hold 2^-K times the spectrum; E and O below are twice the
         // true ones (the halvings of the split fold into the output scale)
         const float osc0 = pow2f(kq.x - 1), osc1 = pow2f(kq.y - 1);
@@ -840,25 +858,28 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
             tn = cscale(tn, w); ts = cscale(ts, w);
             if (g.phi0 != 0.0) { tn = cmulc(tn, ph, pl); ts = cmulc(ts, ph, pl); }
         };
-        // bins j and N - j of both columns into the transform buffer
+        // bins j and N - j of both columns into the transform buffer. With
+        // hn = B(j) + conj(B(N - j)) and hs likewise (twice the Hermitian parts
+        // of the two rings), bin j takes conj(hn + i hs) and bin N - j, whose
+        // Hermitian parts are the conjugates, hn - i hs (conjugated input: the
+        // forward transform gives the inverse; the 1/2 goes to the output scale)
         unsigned m0 = 0, m1 = 0;
         auto emit = [&](int j, const cx (&Bn)[2][2], const cx (&Bs)[2][2]) {
-            const int jj[2] = {j, (j ? N - j : 0)};
+            const int jm = j ? N - j : 0;
 #pragma unroll
-            for (int t = 0; t < 2; t++) {
-                const int jt = jj[t];
-                if (t == 1 && jt == jj[0]) break;
-#pragma unroll
-                for (int s = 0; s < 2; s++) {
-                    if (s >= nb) break;
-                    // H(j) = (B(j) + conj(B(N-j))) / 2 ; z = Hn + i Hs ; store conj(z)
-                    const cx hn = cscale(caddc(Bn[t][s], cconjc(Bn[1 - t][s])), 0.5f);
-                    const cx hs = cscale(caddc(Bs[t][s], cconjc(Bs[1 - t][s])), 0.5f);
-                    const cx z = cconjc(caddc(hn, cmul_pi(hs)));
-                    buf[s * P + fft_pad(placec(f, jt))] = z;
-                    const unsigned v = absbits(z);
-                    if (s) m1 = max(m1, v); else m0 = max(m0, v);
+            for (int s = 0; s < 2; s++) {
+                if (s >= nb) break;
+                const cx hn = caddc(Bn[0][s], cconjc(Bn[1][s]));
+                const cx hs = cmul_pi(caddc(Bs[0][s], cconjc(Bs[1][s])));
+                const cx z = cconjc(caddc(hn, hs));
+                buf[s * P + fft_pad(placec(f, j))] = z;
+                unsigned v = absbits(z);
+                if (jm != j) {
+                    const cx z1 = csubc(hn, hs);
+                    buf[s * P + fft_pad(placec(f, jm))] = z1;
+                    v = max(v, absbits(z1));
                 }
+                if (s) m1 = max(m1, v); else m0 = max(m0, v);
             }
         };
         if (N > mmax) {
@@ -926,8 +947,8 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         }
         red_max2(red, m0, m1);
         __syncthreads();
-        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red);
-        const float osc0 = pow2f(kq.x), osc1 = pow2f(kq.y);
+        const int2 kq = dftc_forward(buf, nb, f, tw, twp, tb, red, 22);
+        const float osc0 = pow2f(kq.x - 1), osc1 = pow2f(kq.y - 1);
         if (threadIdx.x < 4) red[threadIdx.x] = 0u;    // (read by every thread before the syncs above)
         for (int e = threadIdx.x; e < nb * N; e += blockDim.x) {
             const int s = (e >= N) ? 1 : 0, n = e - s * N;     // nb <= 2 sequences
