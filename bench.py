@@ -266,10 +266,34 @@ SERVE_NSIDES = [64, 128, 256, 512, 1024]
 SERVE_W = [0.3, 0.3, 0.2, 0.15, 0.05]
 
 
-def run_qu(nside, lmax, npairs, steps, warmup, precision):
+def time_eb_only(plan, maps, alm_out, ws, npairs):
+    """E-only and B-only spin-2 map2alm beside the full one (events on the current stream)."""
+    import torch
+    e_only = plan.map2alm_eb(maps, "E", workspace=ws)
+    torch.cuda.synchronize()
+    t_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_ev[0].record()
+    plan.map2alm(maps, out=alm_out, workspace=ws)
+    t_ev[1].record()
+    plan.map2alm_eb(maps, "E", out=e_only, workspace=ws)
+    t_ev[2].record()
+    plan.map2alm_eb(maps, "B", out=e_only, workspace=ws)
+    t_ev[3].record()
+    torch.cuda.synchronize()
+    t_full, t_e, t_b = (t_ev[i].elapsed_time(t_ev[i + 1]) for i in range(3))
+    eb_only = {"pairs": npairs, "map2alm_full_ms": t_full, "map2alm_E_ms": t_e, "map2alm_B_ms": t_b,
+               "E_over_full": t_e / t_full, "device_status": plan.device_status(),
+               "note": "ring FFTs of Q and U in full; the Legendre contraction forms one component"}
+    del e_only
+    return eb_only
+
+
+def run_qu(nside, lmax, npairs, steps, warmup, precision, eb=True):
     """Spin-2 (Q/U <-> E/B) alm2map + map2alm of `npairs` Q/U map pairs per step,
     E/B a_lm Gaussian with C_EE = 1/(l(l+1)), C_BB = 0.01 C_EE, beside the
-    per-pair FP64 form; kernel times from libsht's own profiler."""
+    per-pair FP64 form; kernel times from libsht's own profiler. eb: also time
+    the E-only / B-only map2alm (its output does not fit beside the nside-1024
+    batch)."""
     import torch
     from paper_2208_10154_b300 import sht
     plan = sht.Plan(nside, lmax, None, 2, precision)
@@ -311,22 +335,9 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision):
     ms = e0.elapsed_time(e1) / steps
     status = plan.device_status()
     # E-only map2alm (Sec. 3.1: one of a_E, a_B) beside the full spin-2 map2alm
-    e_only = plan.map2alm_eb(maps, "E", workspace=ws)
-    torch.cuda.synchronize()
-    t_ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    t_ev[0].record()
-    plan.map2alm(maps, out=alm_out, workspace=ws)
-    t_ev[1].record()
-    plan.map2alm_eb(maps, "E", out=e_only, workspace=ws)
-    t_ev[2].record()
-    plan.map2alm_eb(maps, "B", out=e_only, workspace=ws)
-    t_ev[3].record()
-    torch.cuda.synchronize()
-    t_full, t_e, t_b = (t_ev[i].elapsed_time(t_ev[i + 1]) for i in range(3))
-    eb_only = {"pairs": npairs, "map2alm_full_ms": t_full, "map2alm_E_ms": t_e, "map2alm_B_ms": t_b,
-               "E_over_full": t_e / t_full, "device_status": plan.device_status(),
-               "note": "ring FFTs of Q and U in full; the Legendre contraction forms one component"}
-    del e_only
+    eb_only = None
+    if eb:
+        eb_only = time_eb_only(plan, maps, alm_out, ws, npairs)
     # per-pair FP64 form
     p64 = sht.Plan(nside, lmax, None, 2, "fp64")
     a1 = alm[:1].contiguous()
@@ -807,6 +818,10 @@ def main():
                "sample": f"1 map (alm2map + map2alm, nside {nside}, lmax {lmax}), separable tier"}
 
     del alm, maps_in, maps_out, alm_out, ws
+    # the step's plans hold the host entry points' device buffers (up to 48 GB)
+    for pl in {id(plan): plan, id(plan64): plan64}.values():
+        pl.close()
+    del plan, plan64
     gc.collect()
     torch.cuda.empty_cache()
     context = None
@@ -819,7 +834,7 @@ def main():
     if a.qu1024_pairs > 0:
         gc.collect()
         torch.cuda.empty_cache()
-        qu1024 = run_qu(1024, 2047, a.qu1024_pairs, 2, 1, precision)
+        qu1024 = run_qu(1024, 2047, a.qu1024_pairs, 2, 1, precision, eb=False)
 
     next_rows = None
     if not a.no_next_rows:
