@@ -279,14 +279,11 @@ __device__ __forceinline__ void stage_pass_twiddles(float4* twp, int n, long lon
     for (int i = threadIdx.x; i < n; i += blockDim.x) twp[i] = t.twp[ctwp + i];
 }
 
-// Per-pass twiddles: for the radix-4 pass of span h of a 2^L-point transform
-// (decimation in time) and k < h, the three factors W^{k M / 2h},
-// W^{k M / 4h}, W^{3 k M / 4h} sit at slots 3 (off(h) + k) + 0, 1, 2 with
-// off(h) = (h - 1 - (L & 1)) / 3 (the spans are 2^(L & 1), 4 times that, ...);
-// consecutive k are 48 bytes apart, which keeps a warp's 16-byte reads on
-// distinct banks. The decimation-in-frequency pass of span 2h uses the same
-// three factors.
-__device__ __forceinline__ int twp_off(int L, int h) { return (h - 1 - (L & 1)) / 3; }
+// Per-pass twiddles: the radix-8 pass of span h of a 2^L-point transform
+// (h = 2^(L mod 3), 8 times that, ...) takes, for k < h, the seven factors
+// W_{8h}^{k e}, e = 1 .. 7, at slots off(h) + 7 k + e - 1 with
+// off(h) = h - 2^(L mod 3) (the sum of 7 h' over the smaller spans); 7 is odd,
+// so a warp's 16-byte reads of consecutive k fall on distinct banks.
 __device__ __forceinline__ void twp_get(const float4* e, int t, bool inv, float2& wh, float2& wl)
 {
     const float4 v = e[t];
@@ -302,100 +299,137 @@ __device__ __forceinline__ void twp_get(const float4* e, int t, bool inv, float2
 __host__ __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 3) + (i >> 6); }
 __host__ __device__ __forceinline__ int fft_pad_len(int M) { return M + (M >> 3) + (M >> 6); }
 
-// One radix-4 pass (two radix-2 stages) over NS sequences at a time: each
-// work item does the same butterfly on NS sequences P apart with the same
-// twiddles, so the NS independent double-float chains overlap (the passes
-// are latency-bound at one or two CTAs per SM).
-// (the twiddle branch is per pass, not per lane: for k = 0 the twiddled path
-// multiplies by exactly 1, and a warp whose lanes took both paths would
-// execute both)
-// DIT: spans h and 2h, with w = W_{4h}^k the inputs are multiplied by w^2
-// (x1), w (x2), w^3 (x3), then the 4-point DFT (+-i exact).
-template <int NS>
-__device__ __forceinline__ void dit4_pass(cx* buf, int nitems, int L, int lh, const float4* twp, bool inv)
+// 1/sqrt(2) as a double-float pair
+constexpr float R2H = 0.707106769084930419921875f;
+constexpr float R2L = 1.21016175477703189729e-08f;
+
+// x * W_8 and x * W_8^3 (W_8 = e^{-+i pi / 4}): the sums are exact on the
+// grid, then one product by 1/sqrt(2)
+__device__ __forceinline__ cx mul_w8(const cx& x, bool inv)
+{
+    cx t;                                          // x (1 -+ i)
+    if (!inv) { t.hr = x.hr + x.hi; t.lr = x.lr + x.li; t.hi = x.hi - x.hr; t.li = x.li - x.lr; }
+    else      { t.hr = x.hr - x.hi; t.lr = x.lr - x.li; t.hi = x.hi + x.hr; t.li = x.li + x.lr; }
+    return gmulr(t, R2H, R2L);
+}
+__device__ __forceinline__ cx mul_w83(const cx& x, bool inv)
+{
+    cx t;                                          // x (-1 -+ i)
+    if (!inv) { t.hr = x.hi - x.hr; t.lr = x.li - x.lr; t.hi = -(x.hr + x.hi); t.li = -(x.lr + x.li); }
+    else      { t.hr = -(x.hr + x.hi); t.lr = -(x.lr + x.li); t.hi = x.hr - x.hi; t.li = x.lr - x.li; }
+    return gmulr(t, R2H, R2L);
+}
+
+// the 8-point DFT X_m = sum_j x_j W_8^{j m} of x in natural order (three
+// radix-2 stages, W_8^2 = -+i exact)
+__device__ __forceinline__ void dft8(cx (&x)[8], bool inv)
+{
+    const cx a0 = gadd(x[0], x[4]), b0 = gsub(x[0], x[4]);
+    const cx a1 = gadd(x[1], x[5]), b1 = gsub(x[1], x[5]);
+    const cx a2 = gadd(x[2], x[6]), b2 = gsub(x[2], x[6]);
+    const cx a3 = gadd(x[3], x[7]), b3 = gsub(x[3], x[7]);
+    const cx c0 = gadd(a0, a2), c2 = gsub(a0, a2), c1 = gadd(a1, a3);
+    const cx c3 = inv ? cmul_pi(gsub(a1, a3)) : cmul_mi(gsub(a1, a3));
+    x[0] = gadd(c0, c1); x[4] = gsub(c0, c1);
+    x[2] = gadd(c2, c3); x[6] = gsub(c2, c3);
+    const cx d1 = mul_w8(b1, inv), d3 = mul_w83(b3, inv);
+    const cx d2 = inv ? cmul_pi(b2) : cmul_mi(b2);
+    const cx e0 = gadd(b0, d2), e2 = gsub(b0, d2), e1 = gadd(d1, d3);
+    const cx e3 = inv ? cmul_pi(gsub(d1, d3)) : cmul_mi(gsub(d1, d3));
+    x[1] = gadd(e0, e1); x[5] = gsub(e0, e1);
+    x[3] = gadd(e2, e3); x[7] = gsub(e2, e3);
+}
+
+// One radix-8 pass (three radix-2 stages) over nseq sequences of M = 2^L
+// points (padded layout, P apart), span h of the last stage merged in.
+// Decimation in time: the points y0 + j h hold sub-transforms in bit-reversed
+// order, so the one at j takes W_{8h}^{k rev(j)} before the 8-point DFT, whose
+// output m goes to y0 + m h. (the twiddle branch is per pass, not per lane)
+__device__ __forceinline__ void dit8_pass(cx* buf, int nseq, int L, int h, const float4* tp, bool inv)
 {
     const int M = 1 << L, P = fft_pad_len(M);
-    const int h = 1 << lh;
-    const int ng = M >> 2;                           // groups per sequence
-    const float4* tp = twp + 3 * twp_off(L, h);
-    for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
-        const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
+    const int ng = M >> 3;
+    constexpr int rev[8] = {0, 4, 2, 6, 1, 5, 3, 7};
+    for (int b = threadIdx.x; b < nseq * ng; b += blockDim.x) {
+        const int f = b >> (L - 3), g = b & (ng - 1);
         const int k = g & (h - 1);
         cx* y = buf + f * P;
-        const int y0 = ((g - k) << 2) + k;
-        const int i0 = fft_pad(y0), i1 = fft_pad(y0 + h), i2 = fft_pad(y0 + 2 * h), i3 = fft_pad(y0 + 3 * h);
-        cx x0[NS], x1[NS], x2[NS], x3[NS];
+        const int y0 = ((g - k) << 3) + k;
+        int ix[8];
+        cx x[8];
 #pragma unroll
-        for (int q = 0; q < NS; q++) {
-            x0[q] = y[q * P + i0]; x1[q] = y[q * P + i1]; x2[q] = y[q * P + i2]; x3[q] = y[q * P + i3];
-        }
+        for (int j = 0; j < 8; j++) { ix[j] = fft_pad(y0 + j * h); x[j] = y[ix[j]]; }
         if (h > 1) {
-            float2 w1h, w1l, w2h, w2l, w3h, w3l;
-            const float4* e = tp + 3 * k;
-            twp_get(e, 0, inv, w1h, w1l);
-            twp_get(e, 1, inv, w2h, w2l);
-            twp_get(e, 2, inv, w3h, w3l);
+            const float4* e = tp + 7 * k - 1;
 #pragma unroll
-            for (int q = 0; q < NS; q++) {
-                x1[q] = gmul(x1[q], w1h, w1l);
-                x2[q] = gmul(x2[q], w2h, w2l);
-                x3[q] = gmul(x3[q], w3h, w3l);
+            for (int j = 1; j < 8; j++) {
+                float2 wh, wl;
+                twp_get(e, rev[j], inv, wh, wl);
+                x[j] = gmul(x[j], wh, wl);
             }
         }
+        cx z[8];
 #pragma unroll
-        for (int q = 0; q < NS; q++) {
-            const cx b0 = gadd(x0[q], x1[q]), b1 = gsub(x0[q], x1[q]);
-            const cx b2 = gadd(x2[q], x3[q]), b3 = gsub(x2[q], x3[q]);
-            const cx u3 = inv ? cmul_pi(b3) : cmul_mi(b3);
-            y[q * P + i0] = grenorm(gadd(b0, b2)); y[q * P + i2] = grenorm(gsub(b0, b2));
-            y[q * P + i1] = grenorm(gadd(b1, u3)); y[q * P + i3] = grenorm(gsub(b1, u3));
-        }
+        for (int j = 0; j < 8; j++) z[rev[j]] = x[j];
+        dft8(z, inv);
+#pragma unroll
+        for (int j = 0; j < 8; j++) y[ix[j]] = grenorm(z[j]);
     }
 }
 
-// DIF: spans h and h/2, outputs 1, 2, 3 take v^2, v, v^3 with v = W_{2h}^k.
-template <int NS>
-__device__ __forceinline__ void dif4_pass(cx* buf, int nitems, int L, int lh, const float4* twp, bool inv)
+// Decimation in frequency: the 8-point DFT of the points y0 + j h (natural
+// order), output m times W_{8h}^{k m} to y0 + rev(m) h.
+__device__ __forceinline__ void dif8_pass(cx* buf, int nseq, int L, int h, const float4* tp, bool inv)
 {
     const int M = 1 << L, P = fft_pad_len(M);
-    const int h = 1 << lh, hq = h >> 1;
-    const int ng = M >> 2;
-    const float4* tp = twp + 3 * twp_off(L, hq);
-    for (int b = threadIdx.x; b < nitems * ng; b += blockDim.x) {
-        const int f = (b >> (L - 2)) * NS, g = b & (ng - 1);
-        const int k = g & (hq - 1);
+    const int ng = M >> 3;
+    constexpr int rev[8] = {0, 4, 2, 6, 1, 5, 3, 7};
+    for (int b = threadIdx.x; b < nseq * ng; b += blockDim.x) {
+        const int f = b >> (L - 3), g = b & (ng - 1);
+        const int k = g & (h - 1);
         cx* y = buf + f * P;
-        const int y0 = ((g - k) << 2) + k;
-        const int i0 = fft_pad(y0), i1 = fft_pad(y0 + hq), i2 = fft_pad(y0 + h), i3 = fft_pad(y0 + h + hq);
-        cx c0[NS], c1[NS], c2[NS], c3[NS];
+        const int y0 = ((g - k) << 3) + k;
+        int ix[8];
+        cx x[8];
 #pragma unroll
-        for (int q = 0; q < NS; q++) {
-            const cx x0 = y[q * P + i0], x1 = y[q * P + i1], x2 = y[q * P + i2], x3 = y[q * P + i3];
-            c0[q] = gadd(x0, x2); c2[q] = gsub(x0, x2); c1[q] = gadd(x1, x3);
-            const cx d = gsub(x1, x3);
-            c3[q] = inv ? cmul_pi(d) : cmul_mi(d);
+        for (int j = 0; j < 8; j++) { ix[j] = fft_pad(y0 + j * h); x[j] = y[ix[j]]; }
+        dft8(x, inv);
+        if (h > 1) {
+            const float4* e = tp + 7 * k - 1;
+#pragma unroll
+            for (int m = 1; m < 8; m++) {
+                float2 wh, wl;
+                twp_get(e, m, inv, wh, wl);
+                x[m] = gmul(x[m], wh, wl);
+            }
         }
-        if (hq > 1) {
-            // v = W^{k M / 2h}: outputs 1, 2, 3 take v^2, v, v^3, the DIT
-            // factors 0, 1, 2 of span hq
-            float2 v1h, v1l, v2h, v2l, v3h, v3l;
-            const float4* e = tp + 3 * k;
-            twp_get(e, 1, inv, v1h, v1l);
-            twp_get(e, 0, inv, v2h, v2l);
-            twp_get(e, 2, inv, v3h, v3l);
 #pragma unroll
-            for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = grenorm(gadd(c0[q], c1[q]));
-                y[q * P + i1] = grenorm(gmul(gsub(c0[q], c1[q]), v2h, v2l));
-                y[q * P + i2] = grenorm(gmul(gadd(c2[q], c3[q]), v1h, v1l));
-                y[q * P + i3] = grenorm(gmul(gsub(c2[q], c3[q]), v3h, v3l));
-            }
+        for (int m = 0; m < 8; m++) y[ix[rev[m]]] = grenorm(x[m]);
+    }
+}
+
+// radix-4 pass of spans 1 and 2 (no twiddles), decimation in time (bit-
+// reversed sub-transforms of length 1 at y0 .. y0 + 3) or in frequency
+// (natural input, bit-reversed output), over nseq sequences
+__device__ __forceinline__ void r4_span1(cx* buf, int nseq, int L, bool inv, bool dif)
+{
+    const int M = 1 << L, P = fft_pad_len(M);
+    for (int b = threadIdx.x; b < nseq * (M >> 2); b += blockDim.x) {
+        cx* y = buf + (b >> (L - 2)) * P;
+        const int y0 = (b & ((M >> 2) - 1)) << 2;
+        const int i0 = fft_pad(y0), i1 = fft_pad(y0 + 1), i2 = fft_pad(y0 + 2), i3 = fft_pad(y0 + 3);
+        const cx x0 = y[i0], x1 = y[i1], x2 = y[i2], x3 = y[i3];
+        if (!dif) {
+            // x1 and x2 are the bit-reversed sub-transforms 2 and 1
+            const cx b0 = gadd(x0, x1), b1 = gsub(x0, x1), b2 = gadd(x2, x3), d = gsub(x2, x3);
+            const cx b3 = inv ? cmul_pi(d) : cmul_mi(d);
+            y[i0] = grenorm(gadd(b0, b2)); y[i2] = grenorm(gsub(b0, b2));
+            y[i1] = grenorm(gadd(b1, b3)); y[i3] = grenorm(gsub(b1, b3));
         } else {
-#pragma unroll
-            for (int q = 0; q < NS; q++) {
-                y[q * P + i0] = grenorm(gadd(c0[q], c1[q])); y[q * P + i1] = grenorm(gsub(c0[q], c1[q]));
-                y[q * P + i2] = grenorm(gadd(c2[q], c3[q])); y[q * P + i3] = grenorm(gsub(c2[q], c3[q]));
-            }
+            const cx c0 = gadd(x0, x2), c2 = gsub(x0, x2), c1 = gadd(x1, x3), d = gsub(x1, x3);
+            const cx c3 = inv ? cmul_pi(d) : cmul_mi(d);
+            y[i0] = grenorm(gadd(c0, c1)); y[i1] = grenorm(gsub(c0, c1));
+            y[i2] = grenorm(gadd(c2, c3)); y[i3] = grenorm(gsub(c2, c3));
         }
     }
 }
@@ -415,36 +449,31 @@ __device__ __forceinline__ void r2_span1(cx* buf, int nb, int L)
 }
 
 // In-place decimation-in-time FFTs of nb sequences of M = 2^L points (padded
-// layout above), input in bit-reversed order, output natural. Two radix-2
-// stages per pass, sequences in pairs; W = exp(-+2 pi i / M).
-// twp: the per-pass twiddles of the 2^L-point transform
+// layout above), input in bit-reversed order, output natural: one radix-2 or
+// radix-4 pass of span 1 for L = 1, 2 mod 3, then radix-8 passes.
+// twp: the per-pass twiddles of the 2^L-point transform; W = exp(-+2 pi i / M).
 __device__ void fft_dit(cx* buf, int nb, int L, const float4* twp, bool inv)
 {
-    const int P = fft_pad_len(1 << L);
-    int lh = 0;
-    if (L & 1) {
-        r2_span1(buf, nb, L);
-        lh = 1;
-    }
-    for (; lh + 2 <= L; lh += 2) {
-        if (nb >= 2) dit4_pass<2>(buf, nb >> 1, L, lh, twp, inv);
-        if (nb & 1) dit4_pass<1>(buf + (nb - 1) * P, 1, L, lh, twp, inv);
+    const int r0 = L % 3;
+    if (r0 == 1) r2_span1(buf, nb, L);
+    if (r0 == 2) { r4_span1(buf, nb, L, inv, false); __syncthreads(); }
+    for (int h = 1 << r0; 8 * h <= (1 << L); h <<= 3) {
+        dit8_pass(buf, nb, L, h, twp + (h - (1 << r0)), inv);
         __syncthreads();
     }
 }
 
-// In-place decimation-in-frequency FFTs (natural input, bit-reversed output),
-// two radix-2 stages (spans h and h/2) per pass, sequences in pairs.
+// In-place decimation-in-frequency FFTs (natural input, bit-reversed output):
+// radix-8 passes from span M / 8 down, then the radix-4 or radix-2 pass of span 1.
 __device__ void fft_dif(cx* buf, int nb, int L, const float4* twp, bool inv)
 {
-    const int P = fft_pad_len(1 << L);
-    int lh = L - 1;
-    for (; lh >= 1; lh -= 2) {
-        if (nb >= 2) dif4_pass<2>(buf, nb >> 1, L, lh, twp, inv);
-        if (nb & 1) dif4_pass<1>(buf + (nb - 1) * P, 1, L, lh, twp, inv);
+    const int r0 = L % 3;
+    for (int h = (1 << L) >> 3; h >= (1 << r0); h >>= 3) {
+        dif8_pass(buf, nb, L, h, twp + (h - (1 << r0)), inv);
         __syncthreads();
     }
-    if (lh == 0) r2_span1(buf, nb, L);
+    if (r0 == 2) { r4_span1(buf, nb, L, inv, true); __syncthreads(); }
+    if (r0 == 1) r2_span1(buf, nb, L);
 }
 
 // sqrt(3) / 2 as a double-float pair
@@ -704,7 +733,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         }
         // the ring's samples in batches of FWD_UB per thread: every load of a
         // batch is in flight before the first is used
-        constexpr int FWD_UB = 4;
+        constexpr int FWD_UB = 8;
         unsigned m0 = 0, m1 = 0;
         for (int e0 = threadIdx.x; e0 < nb * N; e0 += FWD_UB * NT) {
             double vn[FWD_UB], vs[FWD_UB];

@@ -376,28 +376,25 @@ static cudaError_t build_tables(sht_plan* p)
             c.off = (int)cls.size();
             c.cnt = (int)kv.second.size();
             c.tw = (long long)twh.size();
-            // per-pass twiddles of the power-of-two part Ms = 2^La: for each
-            // radix-4 pass of span h (decimation in time: h = 2^lh, lh = La & 1,
-            // La & 1 + 2, ..., h <= Ms / 4) and k < h, the three factors
-            // W^{k Ms / 2h}, W^{k Ms / 4h}, W^{3 k Ms / 4h} (W = e^{-2 pi i / Ms});
-            // the decimation-in-frequency pass of span 2h uses the same three
+            // per-pass twiddles of the power-of-two part Ms = 2^La: its
+            // transforms run one radix-2 (La = 1 mod 3) or radix-4 (La = 2
+            // mod 3) pass of span 1, which needs none, and radix-8 passes of
+            // spans h = 2^(La mod 3), 8 times that, ..., h <= Ms / 8; for each
+            // such h and k < h, the seven factors W_{8h}^{k e}, e = 1 .. 7
+            // (decimation in time and in frequency use the same ones)
             c.twp = (long long)twp.size();
             {
                 const int Ms = c.m / pow3_part(c.m);
                 int La = 0;
                 while ((1 << La) < Ms) La++;
-                for (int lh = (La & 1); lh + 2 <= La; lh += 2) {
-                    const int h = 1 << lh, s1 = Ms >> (lh + 1), s2 = Ms >> (lh + 2);
-                    for (int k = 0; k < h; k++) {
-                        const long long us[3] = {(long long)k * s1, (long long)k * s2, 3LL * k * s2};
-                        for (long long u : us) {
-                            const ld a = -2 * PI_L * (ld)u / (ld)Ms;
+                for (int h = 1 << (La % 3); 8 * h <= Ms; h *= 8)
+                    for (int k = 0; k < h; k++)
+                        for (int e = 1; e <= 7; e++) {
+                            const ld a = -2 * PI_L * (ld)((long long)k * e) / (ld)(8 * h);
                             const ld cr = cosl(a), ci = sinl(a);
                             const float hx = (float)cr, hy = (float)ci;
                             twp.push_back(make_float4(hx, hy, (float)(cr - (ld)hx), (float)(ci - (ld)hy)));
                         }
-                    }
-                }
             }
             c.twp_n = (int)(twp.size() - c.twp);
             for (int u = 0; u < std::max(1, c.m / 2); u++) {
