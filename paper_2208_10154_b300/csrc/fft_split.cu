@@ -1020,8 +1020,10 @@ static ClassCfg class_cfg(const FftClass& c, int mmax, bool fwd)
     k.mpc = (2 * (size_t)M * sizeof(cx) <= (128u << 10)) ? 2 : 1;
     size_t sm = (size_t)k.mpc * fft_pad_len(M) * sizeof(cx) + ((M % 3 == 0) ? (size_t)(M / 2) * sizeof(float4) : 0);
     // (the backward kernels read the per-pass twiddles from global memory:
-    // their G and phase loads keep more of the L1 that way; measured)
-    k.twp_smem = fwd && sm + (size_t)c.twp_n * sizeof(float4) <= (227u << 10);
+    // their G and phase loads keep more of the L1 that way; so do the forward
+    // ones for tables above 40 KB, M >= 4096; measured)
+    k.twp_smem = fwd && (size_t)c.twp_n * sizeof(float4) <= (40u << 10) &&
+                 sm + (size_t)c.twp_n * sizeof(float4) <= (227u << 10);
     if (k.twp_smem) sm += (size_t)c.twp_n * sizeof(float4);
     k.sm = sm;
     k.nt = (M >= 4096 || mmax >= 1024 || sm > (113u << 10)) ? 512 : 256;
