@@ -158,6 +158,9 @@ class Server:
                     self._finish(r)
                 progressed = True
                 continue
+            # a graph captured by this launch is resident from now on (and in
+            # _resident()): the batch itself keeps only what batch_bytes now says
+            nbytes = min(nbytes, self.ex.batch_bytes(key, n))
             self.inflight.append(_Batch(key, reqs, nbytes, handle, now))
             self.used += nbytes
             self.peak_used = max(self.peak_used, self.used + self._resident())

@@ -82,6 +82,35 @@ def test_batches_fit_the_budget_beside_resident_memory():
     assert srv.peak_used <= 1000
 
 
+def test_graph_captured_at_launch_is_counted_once():
+    """A batch that captures a CUDA graph is admitted with the graph's bytes;
+    once launched those bytes are resident (reported by resident_bytes) and
+    no longer the batch's, so the admitted peak stays within the budget."""
+    class Graphs(FakeExecutor):
+        def __init__(self):
+            super().__init__(lag=2, bytes_per_map=100)
+            self.cached = set()
+
+        def resident_bytes(self):
+            return 150.0 * len(self.cached)
+
+        def batch_bytes(self, key, n):
+            return n * self.bpm + (0 if key in self.cached else 150)
+
+        def launch(self, key, inputs):
+            self.cached.add(key)
+            return super().launch(key, inputs)
+    rng = np.random.default_rng(6)
+    ex = Graphs()
+    srv = Server(ex, hbm_budget=1000, max_batch_maps=8, slots=2)
+    for i in range(8):
+        srv.submit(_req("alm2map", 8 * (1 + i % 2), 4, rng))
+    while not srv.idle():
+        srv.step()
+        assert srv.used + ex.resident_bytes() <= 1000
+    assert srv.peak_used <= 1000
+
+
 def test_continuous_admission_while_busy():
     rng = np.random.default_rng(2)
     ex = FakeExecutor(lag=5)
