@@ -743,7 +743,7 @@ def main():
                         "alu": {"bound": "alu", "achieved": ach_alu, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": ach_alu / FP32_PEAK_TFLOPS, "algorithmic_flops_per_step": fft_flops,
                                 "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz",
-                                "note": "each flop runs in double-float FP32 (~7 FP32 operations)"}}
+                                "note": "each flop runs as several compensated FP32 operations"}}
 
     # ---- end to end through the host-buffer C-ABI entry points: the two
     # directions of a step from two host threads, one plan each (the host
