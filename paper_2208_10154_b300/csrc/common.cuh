@@ -19,6 +19,7 @@
 #include <cstddef>
 #include <string>
 #include <vector>
+#include <mutex>
 
 #include "../../include/sht.h"
 
@@ -166,6 +167,14 @@ struct sht_plan {
     // the host entry points' copy streams and their events (created lazily)
     cudaStream_t hp_h2d = nullptr, hp_d2h = nullptr;
     cudaEvent_t hp_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // split FFTs: helper streams that run size classes beside the caller's
+    // stream, forked and joined with events (made with the plan; one call's
+    // fork / launch / join sequence at a time under fft_mu)
+    static constexpr int FFT_AUX = 2;
+    cudaStream_t fft_aux[FFT_AUX] = {nullptr, nullptr};
+    cudaEvent_t fft_fork = nullptr;
+    cudaEvent_t fft_join[FFT_AUX] = {nullptr, nullptr};
+    mutable std::mutex fft_mu;
 };
 
 namespace sht {

@@ -18,6 +18,9 @@
 // round trip), and the rings are launched in classes of equal FFT size so the
 // shared-memory footprint and thread count fit each size.
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -1037,6 +1040,65 @@ static cudaError_t set_smem(const void* fn, const sht_plan* p, bool fwd)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
 }
 
+// The size classes of a transform run beside one another: each class goes,
+// in decreasing order of work (ring pairs x M log M), to whichever of the
+// caller's stream and the plan's helper streams has the least work queued so
+// far; the helpers are forked from and joined back into the caller's stream
+// with events, so the call is ordered on `st` as a whole (and can be
+// captured into a CUDA graph). The classes write disjoint ring pairs (the
+// forward ones' column maxima with atomicMax).
+struct ClassOrder {
+    int n = 0;
+    std::vector<int> idx;
+    std::vector<int> stream;   // 0: the caller's stream, 1 + i: helper i
+};
+static ClassOrder class_order(const sht_plan* p)
+{
+    ClassOrder o;
+    const int nc = (int)p->h_fcls.size();
+    std::vector<std::pair<double, int>> w;
+    for (int i = 0; i < nc; i++) {
+        const FftClass& c = p->h_fcls[i];
+        w.push_back({(double)c.cnt * c.m * std::log2((double)std::max(c.m, 2)), i});
+    }
+    std::sort(w.begin(), w.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first;
+    });
+    const bool aux = p->fft_fork != nullptr && p->fft_aux[sht_plan::FFT_AUX - 1] != nullptr;
+    double load[1 + sht_plan::FFT_AUX] = {0.0};
+    for (auto& kv : w) {
+        int s = 0;
+        if (aux)
+            for (int j = 1; j <= sht_plan::FFT_AUX; j++) if (load[j] < load[s]) s = j;
+        load[s] += kv.first;
+        o.idx.push_back(kv.second);
+        o.stream.push_back(s);
+        o.n++;
+    }
+    return o;
+}
+static cudaError_t fork_aux(const sht_plan* p, const ClassOrder& o, cudaStream_t st)
+{
+    bool any = false;
+    for (int i = 0; i < o.n; i++) any = any || o.stream[i] > 0;
+    if (!any) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(p->fft_fork, st);
+    for (int j = 0; j < sht_plan::FFT_AUX && e == cudaSuccess; j++) e = cudaStreamWaitEvent(p->fft_aux[j], p->fft_fork, 0);
+    return e;
+}
+static cudaError_t join_aux(const sht_plan* p, const ClassOrder& o, cudaStream_t st)
+{
+    bool any = false;
+    for (int i = 0; i < o.n; i++) any = any || o.stream[i] > 0;
+    if (!any) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < sht_plan::FFT_AUX && e == cudaSuccess; j++) {
+        e = cudaEventRecord(p->fft_join[j], p->fft_aux[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->fft_join[j], 0);
+    }
+    return e;
+}
+
 cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float2* T,
                                      unsigned int* colmax, int nmaps, cudaStream_t st)
 {
@@ -1052,23 +1114,30 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
     const int nmc = nmaps * p->ncomp;
     e = cudaMemsetAsync(colmax, 0, (size_t)(p->mmax + 1) * 2 * nc * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    for (const FftClass& c : p->h_fcls) {
+    std::lock_guard<std::mutex> lk(p->fft_mu);
+    const ClassOrder o = class_order(p);
+    prof_start("k_fftc_forward", st);
+    if ((e = fork_aux(p, o, st)) != cudaSuccess) return e;
+    for (int i = 0; i < o.n; i++) {
+        const FftClass& c = p->h_fcls[o.idx[i]];
+        cudaStream_t ss = o.stream[i] ? p->fft_aux[o.stream[i] - 1] : st;
         const ClassCfg k = class_cfg(c, p->mmax, true);
         const int ntwp = k.twp_smem ? c.twp_n : -1;  // < 0: per-pass twiddles from global memory
         dim3 grid((nmc + k.mpc - 1) / k.mpc, (c.cnt + FWD_PB - 1) / FWD_PB);
-        prof_start(("k_fftc_forward_M" + std::to_string(c.m)).c_str(), st);
         if (k.nt == 512)
-            k_fftc_forward<512><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+            k_fftc_forward<512><<<grid, k.nt, k.sm, ss>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
                                                           p->npix, nc, nmc, k.mpc, pf);
         else
-            k_fftc_forward<256><<<grid, k.nt, k.sm, st>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
+            k_fftc_forward<256><<<grid, k.nt, k.sm, ss>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
                                                           p->npix, nc, nmc, k.mpc, pf);
-        prof_stop(st);
         count_launch();
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = join_aux(p, o, st);
+    prof_stop(st);
+    return e;
 }
 
 cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* map, int nmaps, cudaStream_t st)
@@ -1077,23 +1146,30 @@ cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* m
     if (e == cudaSuccess) e = set_smem((const void*)k_fftc_backward<512>, p, false);
     if (e != cudaSuccess) return e;
     const int nmc = nmaps * p->ncomp;
-    for (const FftClass& c : p->h_fcls) {
+    std::lock_guard<std::mutex> lk(p->fft_mu);
+    const ClassOrder o = class_order(p);
+    prof_start("k_fftc_backward", st);
+    if ((e = fork_aux(p, o, st)) != cudaSuccess) return e;
+    for (int i = 0; i < o.n; i++) {
+        const FftClass& c = p->h_fcls[o.idx[i]];
+        cudaStream_t ss = o.stream[i] ? p->fft_aux[o.stream[i] - 1] : st;
         const ClassCfg k = class_cfg(c, p->mmax, false);
         const int ntwp = k.twp_smem ? c.twp_n : -1;  // < 0: per-pass twiddles from global memory
         dim3 grid((nmc + k.mpc - 1) / k.mpc, (c.cnt + BWD_PB - 1) / BWD_PB);
-        prof_start(("k_fftc_backward_M" + std::to_string(c.m)).c_str(), st);
         if (k.nt == 512)
-            k_fftc_backward<512><<<grid, k.nt, k.sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+            k_fftc_backward<512><<<grid, k.nt, k.sm, ss>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
                                                            tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
                                                            ncols(p, nmaps), nmc, k.mpc);
         else
-            k_fftc_backward<256><<<grid, k.nt, k.sm, st>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
+            k_fftc_backward<256><<<grid, k.nt, k.sm, ss>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
                                                            tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
                                                            ncols(p, nmaps), nmc, k.mpc);
-        prof_stop(st);
         count_launch();
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = join_aux(p, o, st);
+    prof_stop(st);
+    return e;
 }
 
 }  // namespace sht

@@ -816,6 +816,11 @@ static void free_tables(sht_plan* p)
     for (cudaEvent_t ev : p->hp_ev) if (ev) cudaEventDestroy(ev);
     if (p->hp_h2d) cudaStreamDestroy(p->hp_h2d);
     if (p->hp_d2h) cudaStreamDestroy(p->hp_d2h);
+    for (int i = 0; i < sht_plan::FFT_AUX; i++) {
+        if (p->fft_aux[i]) cudaStreamDestroy(p->fft_aux[i]);
+        if (p->fft_join[i]) cudaEventDestroy(p->fft_join[i]);
+    }
+    if (p->fft_fork) cudaEventDestroy(p->fft_fork);
     if (p->pin_in) cudaFreeHost(p->pin_in);
     if (p->pin_out) cudaFreeHost(p->pin_out);
 }
@@ -1021,6 +1026,15 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     p->R = 2 * nside;
     cudaError_t e = build_tables(p);
     if (e == cudaSuccess && precision == SHT_SPLIT_F16X4) e = build_split_tables(p);
+    // the split FFTs' helper streams and events, made here rather than at the
+    // first call (which may be under stream capture)
+    if (e == cudaSuccess && precision == SHT_SPLIT_F16X4) {
+        e = cudaEventCreateWithFlags(&p->fft_fork, cudaEventDisableTiming);
+        for (int i = 0; i < sht_plan::FFT_AUX && e == cudaSuccess; i++) {
+            e = cudaStreamCreateWithFlags(&p->fft_aux[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fft_join[i], cudaEventDisableTiming);
+        }
+    }
     if (e != cudaSuccess) {
         set_error(std::string("plan tables: ") + cudaGetErrorString(e));
         free_tables(p);
