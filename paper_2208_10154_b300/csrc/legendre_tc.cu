@@ -1052,12 +1052,16 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
 //   alm2map: rows = the l of slot q (spin 0: l = m + q + 2k) or all l >= m
 //            (spin 2: a_l for l - m of parity q, P(a_l) otherwise; the sign
 //            sigma_l of the v- chunks is carried by lambda).
-// grid.x = unit (m, q, u, image chunk), grid.y = column tile; one column per thread
+// grid.x = unit (m, q, u, image chunk), grid.y = column tile; one column per
+// thread. The image is built in shared memory and then copied out 16 bytes
+// per lane, so that a warp's stores cover 512 contiguous bytes (direct stores
+// of a row's 16-byte chunks would hit 32 half sectors per instruction).
 // ===========================================================================
 template <bool M2A, bool S2>
 __global__ void __launch_bounds__(TC_M)
 k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
 {
+    __shared__ __align__(128) uint8_t simg[A_BYTES];
     const int4 w = a.sunits[blockIdx.x];
     const int m = w.x, q = w.y, u = w.z;
     const int t = threadIdx.x, lane = t & 31;
@@ -1097,7 +1101,8 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
     const bool direct = a.csel != 0;
 #pragma unroll
     for (int sub = 0; sub < (TWO ? 2 : 1); sub++) {
-        uint8_t* A = img + ((long long)(w.w + sub) * a.ntile + blockIdx.y) * A_BYTES;
+        uint8_t* A = simg;
+        if (sub) __syncthreads();                     // the previous image has been copied out
 #pragma unroll
         for (int jj = 0; jj < KC / 8; jj++) {
             float hv[8], lv[8];
@@ -1134,6 +1139,11 @@ k_slice(const float2* __restrict__ raw, uint8_t* __restrict__ img, TcArgs a)
             }
             put4x8<r0_grid<M2A, S2>()>(A, A_PLANE, t, jj, hv, lv);
         }
+        __syncthreads();
+        uint4* dst = reinterpret_cast<uint4*>(img + ((long long)(w.w + sub) * a.ntile + blockIdx.y) * A_BYTES);
+        const uint4* src = reinterpret_cast<const uint4*>(simg);
+#pragma unroll 4
+        for (int i = t; i < A_BYTES / 16; i += TC_M) dst[i] = src[i];
     }
 }
 
