@@ -992,14 +992,18 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
         tc_fence_before();
         named_bar_sync(2, 256);
         tc_fence_after();
-        const int t = tid & (TC_M - 1);
-        const long long cg = c0 + t;
-        const bool cok = cg < a.ncol;
+        const int t = tid & (TC_M - 1);             // this lane's TMEM lane: real column c0 + t
         const int ce = sh.colexp[t];
         const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         const bool ok = sh.eok != 0;
         const int g0 = (warp >= 4) ? 0 : 2;
-#pragma unroll
+        // each warp's 32 x 32 outputs go through its own 8.25 KB of the (now idle)
+        // stage memory and out by map column: lane = row, one 16-byte store of
+        // (re, im) per lane, so a warp's store spans 1 KB of one map column
+        // instead of 16 columns nalm apart
+        double* tile = reinterpret_cast<double*>(smem) + warp * 32 * 33;   // rows of 33: conflict-free
+        const long long cw = c0 + (warp & 3) * 32;     // the warp's first real column
+#pragma unroll 1
         for (int g = g0; g < g0 + 2; g++) {
             if (g * 32 >= nmma) continue;
             uint32_t v0[32], vr[32];
@@ -1007,29 +1011,42 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 tmem_ld32(tl + g * 32, v0);
                 tmem_ld32(tl + ACC_SM + g * 32, vr);
                 tmem_wait_ld();
-            }
-            if (!ok || !cok) continue;
-            {
-                double* alm = (double*)dst + ((cg >> 1) * a.nalm) * 2 + (cg & 1);
-                const bool zero_im = (m == 0) && (cg & 1);
+            } else {
 #pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    const int r = g * 32 + i;
-                    if (r < nrows) {
-                        // main (exact integer) + the residual as an FP32 pair, times c_l f (hi/lo)
-                        const float x0 = __uint_as_float(v0[i]), x1 = __uint_as_float(vr[i]);
-                        const float sm = x0 + x1;
-                        const float bb = sm - x0;
-                        const float er = (x0 - (sm - bb)) + (x1 - bb);
-                        const float2 F = sh.rfac[r];
-                        const float p1 = __fmul_rn(sm, F.x);
-                        const float lo = fmaf(sm, F.x, -p1) + er * F.x + sm * F.y;
-                        double v = f32_to_f64(p1) + f32_to_f64(lo);            // final FP64 accumulation
-                        v = ldexp_fast(v, sh.rowexp[r] + ce);
-                        alm[(long long)sh.rowidx[r] * 2] = zero_im ? 0.0 : v;
-                    }
+                for (int i = 0; i < 32; i++) v0[i] = vr[i] = 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+                const int r = g * 32 + i;
+                double v = 0.0;
+                if (r < nrows) {
+                    // main (exact integer) + the residual as an FP32 pair, times c_l f (hi/lo)
+                    const float x0 = __uint_as_float(v0[i]), x1 = __uint_as_float(vr[i]);
+                    const float sm = x0 + x1;
+                    const float bb = sm - x0;
+                    const float er = (x0 - (sm - bb)) + (x1 - bb);
+                    const float2 F = sh.rfac[r];
+                    const float p1 = __fmul_rn(sm, F.x);
+                    const float lo = fmaf(sm, F.x, -p1) + er * F.x + sm * F.y;
+                    v = f32_to_f64(p1) + f32_to_f64(lo);                       // final FP64 accumulation
+                    v = ldexp_fast(v, sh.rowexp[r] + ce);
+                }
+                tile[i * 33 + lane] = v;
+            }
+            __syncwarp();
+            const int r = g * 32 + lane;
+            if (ok && r < nrows) {
+                const long long ri = sh.rowidx[r];
+#pragma unroll 4
+                for (int mc = 0; mc < 16; mc++) {
+                    const long long cr = cw + 2 * mc;  // the re column (ncol is even)
+                    if (cr >= a.ncol) break;
+                    const double re = tile[lane * 33 + 2 * mc];
+                    const double im = (m == 0) ? 0.0 : tile[lane * 33 + 2 * mc + 1];
+                    reinterpret_cast<double2*>(dst)[(cr >> 1) * a.nalm + ri] = make_double2(re, im);
                 }
             }
+            __syncwarp();                               // the tile is rewritten for the next g
         }
     }
     __syncwarp();
