@@ -234,7 +234,7 @@ def run_reference(a):
     def step():
         oracle.alm2map(alm, nside, lmax)
         oracle.map2alm(maps, nside, lmax)
-    for _ in range(min(a.warmup, 1)):
+    for _ in range(a.warmup):
         step()
     t0 = time.perf_counter()
     for _ in range(a.steps):
@@ -243,7 +243,7 @@ def run_reference(a):
     value = a.steps / dt
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "maps/s",
-        "n_gpus": a.gpus, "steps": a.steps, "warmup": min(a.warmup, 1), "ms_per_step": 1e3 * dt / a.steps,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": ref_config(a),
         "cpu_baseline": {"value": value, "unit": "maps/s", "cores": oracle.num_threads(), "kind": "oracle",
