@@ -81,7 +81,7 @@ struct FftClass {
     int m;             // FFT size of the class
     int off, cnt;      // its ring pairs: cls_pairs[off .. off + cnt)
     long long tw;      // split form: offset of its twiddles exp(-2 pi i u / m), u < m / 2
-    long long twp;     // split form: offset of its per-pass radix-4 twiddles (float4 units)
+    long long twp;     // split form: offset of its per-pass radix-8 twiddles (float4 units)
     int twp_n;         //   their count
 };
 
@@ -96,7 +96,7 @@ struct CompTables {
     // the split form's FFT recipes (sizes 2^a or 3^b 2^a), per-class twiddles
     // and digit-reversed Bluestein filters, FP32 hi/lo
     FftLen* fft_s = nullptr;
-    float4* twp = nullptr;         // per-pass radix-4 twiddles (hi re, hi im, lo re, lo im)
+    float4* twp = nullptr;         // per-pass radix-8 twiddles (hi re, hi im, lo re, lo im)
     float2* tws_h = nullptr;
     float2* tws_l = nullptr;
     float2* bhs_h = nullptr;

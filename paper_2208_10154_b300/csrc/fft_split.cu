@@ -11,12 +11,13 @@
 // table per ring length.
 //
 // Structure (Sec. 2.1 eq:mm; Appendix A.1 for m -> bin m mod N) is that of
-// fft.cu: one complex FFT of x_north + i x_south per ring pair, power-of-two
-// sizes directly, Bluestein's chirp convolution otherwise. Each CTA transforms
-// one ring pair for two map columns at once (so a T / G row write covers 32
-// contiguous bytes) with radix-4 passes (two radix-2 stages per shared-memory
-// round trip), and the rings are launched in classes of equal FFT size so the
-// shared-memory footprint and thread count fit each size.
+// fft.cu: one complex FFT of x_north + i x_south per ring pair, sizes 2^a and
+// 3^b 2^a directly, Bluestein's chirp convolution otherwise. Each CTA
+// transforms one ring pair for two map columns at once (so a T / G row write
+// covers 32 contiguous bytes) with radix-8 passes (three radix-2 stages per
+// shared-memory round trip), and the rings are launched in classes of equal
+// FFT size so the shared-memory footprint and thread count fit each size; the
+// classes of one call run on the caller's stream and two helper streams.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -231,7 +232,7 @@ __device__ __forceinline__ cx cmul_mi(const cx& a) { cx r; r.hr = a.hi; r.lr = a
 __device__ __forceinline__ cx cmul_pi(const cx& a) { cx r; r.hr = -a.hi; r.lr = -a.li; r.hi = a.hr; r.li = a.lr; return r; }
 
 struct FftTabsF {
-    const float4* twp;            // per size class: per-pass radix-4 twiddles (hi re, hi im, lo re, lo im)
+    const float4* twp;            // per size class: per-pass radix-8 twiddles (hi re, hi im, lo re, lo im)
     const float2 *twh, *twl;      // per size class: exp(-2 pi i u / M), u < M / 2, hi / lo
     const float2 *chh, *chl;      // Bluestein chirp, hi / lo
     const float2 *bhh, *bhl;      // Bluestein filter spectrum / M (digit-reversed), hi / lo
@@ -276,7 +277,7 @@ __device__ __forceinline__ void stage_twiddles(float4* tw, int M, long long ctw,
     }
 }
 
-// the class's per-pass radix-4 twiddles (n float4 at offset ctwp) into shared memory
+// the class's per-pass radix-8 twiddles (n float4 at offset ctwp) into shared memory
 __device__ __forceinline__ void stage_pass_twiddles(float4* twp, int n, long long ctwp, const FftTabsF& t)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) twp[i] = t.twp[ctwp + i];
