@@ -68,6 +68,7 @@ def _load():
             getattr(lib, fn).argtypes = [I, I, I, I, I, P, P]
         lib.oracle_map2alm_iter.argtypes = [I, I, I, I, I, P, P, I]
         lib.oracle_map2alm_immediate.argtypes = [I, I, I, I, P, P, I]
+        lib.oracle_map2alm_immediate2.argtypes = [I, I, I, I, P, P, I]
         lib.oracle_map2alm_msel.argtypes = [I, I, I, I, I, P, I, P, P]
         lib.oracle_alm2map_rings.argtypes = [I, I, I, I, I, P, I, P, P]
         lib.oracle_lambda_scaled.argtypes = [I, I, ctypes.c_double, P, P]
@@ -187,16 +188,20 @@ def map2alm(maps, nside: int, lmax: int, mmax: int | None = None, spin: int = 0,
     return out
 
 
-def map2alm_immediate(maps, nside: int, lmax: int, npass: int, mmax: int | None = None) -> np.ndarray:
-    """Algorithm 3 (immediate / Gauss-Seidel iteration over m), spin 0:
-    ``npass`` >= 1 sweeps from a = 0 on the ring spectra of the residual.
-    map float64 [nmaps, 1, npix] -> alm complex128 [nmaps, 1, nalm]."""
-    mmax = _check(nside, lmax, mmax, 0)
+def map2alm_immediate(maps, nside: int, lmax: int, npass: int, mmax: int | None = None,
+                      spin: int = 0) -> np.ndarray:
+    """Algorithm 3 (immediate / Gauss-Seidel iteration over m): ``npass`` >= 1
+    sweeps from a = 0 on the ring spectra of the residual. spin 0: map float64
+    [nmaps, 1, npix] -> alm complex128 [nmaps, 1, nalm]; spin 2: Q/U maps
+    [nmaps, 2, npix] -> E/B alm [nmaps, 2, nalm]."""
+    mmax = _check(nside, lmax, mmax, spin)
     if npass < 1:
         raise ValueError("npass must be >= 1")
-    x = np.ascontiguousarray(maps, dtype=np.float64).reshape(-1, 1, npix(nside))
-    out = np.zeros((x.shape[0], 1, nalm(lmax, mmax)), dtype=np.complex128)
-    _load().oracle_map2alm_immediate(nside, lmax, mmax, x.shape[0], _ptr(x), _ptr(out), int(npass))
+    nc = 2 if spin else 1
+    x = np.ascontiguousarray(maps, dtype=np.float64).reshape(-1, nc, npix(nside))
+    out = np.zeros((x.shape[0], nc, nalm(lmax, mmax)), dtype=np.complex128)
+    fn = "oracle_map2alm_immediate2" if spin else "oracle_map2alm_immediate"
+    getattr(_load(), fn)(nside, lmax, mmax, x.shape[0], _ptr(x), _ptr(out), int(npass))
     return out
 
 

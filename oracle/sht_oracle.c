@@ -1022,6 +1022,134 @@ void oracle_map2alm_immediate(int nside, int lmax, int mmax, int nmaps, const do
     free(F); free(lam); free(c); free(rg);
 }
 
+/* Immediate iteration, Algorithm 3, spin 2 (Q/U -> E/B). The residual
+ * map's Q and U rings are kept as their full DFTs FQ, FU (bins 0..N-1, no
+ * phase). Each pass walks m = 0..mmax in order:
+ *   TQ, TU     = e^{-i m phi0} FQ_{m mod N}, e^{-i m phi0} FU_{m mod N}   (remap)
+ *   (cE, cB)_l = the spin-2 quadrature of order m from TQ, TU (as in the
+ *                separable map2alm: F(Q +- iU) against +-2 lambda, Sec. 2.3)
+ *   a_E, a_B  += cE, cB                                                  (at once)
+ *   G_m'       = sum_l c_{2,l,m'} 2lambda_{l,m'}, m' = m and -m, with
+ *                c_{2,lm} = -(cE + i cB), c_{X,l,-m} = (-1)^m conj(c_{X,lm})
+ *                (the correction's Q + iU at order m')
+ *   for each m' (once for m = 0), g = N G_m' e^{i m' phi0} (its DFT bin):
+ *     FQ_{m'} -= g / 2,   FQ_{-m'} -= conj(g) / 2      (Q = Re of Q + iU)
+ *     FU_{m'} -= g / 2i,  FU_{-m'} += conj(g) / 2i     (U = Im of Q + iU)
+ * so every later order sharing a bin sees the update. a starts at 0 and the
+ * residual at the map; npass >= 1 passes. map [nmaps][2][npix] (Q, U),
+ * alm [nmaps][2][nalm] (E, B). */
+void oracle_map2alm_immediate2(int nside, int lmax, int mmax, int nmaps, const double* map, double* alm,
+                               int npass)
+{
+    long long npix = oracle_npix(nside);
+    long long nalm = oracle_nalm(lmax, mmax);
+    int nr = 4 * nside - 1;
+    ld dsig = 4.0L * PI_L / (ld)npix;
+    ld* FQ = (ld*)malloc(sizeof(ld) * 2 * (size_t)npix);
+    ld* FU = (ld*)malloc(sizeof(ld) * 2 * (size_t)npix);
+    ld* lpp = (ld*)malloc(sizeof(ld) * (size_t)nr * (lmax + 1));   /* 2lambda_{l,m} per ring */
+    ld* lpm = (ld*)malloc(sizeof(ld) * (size_t)nr * (lmax + 1));   /* -2lambda_{l,m} */
+    ld* lnp = (ld*)malloc(sizeof(ld) * (size_t)nr * (lmax + 1));   /* 2lambda_{l,-m} */
+    ld* acc = (ld*)malloc(sizeof(ld) * 4 * (lmax + 1));
+    ld* ce = (ld*)malloc(sizeof(ld) * 4 * (lmax + 1));             /* cE (re, im), cB (re, im) */
+    ring_t* rg = (ring_t*)malloc(sizeof(ring_t) * nr);
+    for (int i = 1; i <= nr; i++) ring_geom(nside, i, &rg[i - 1]);
+    for (int j = 0; j < nmaps; j++) {
+        const double* xq = map + ((long long)j * 2 + 0) * npix;
+        const double* xu = map + ((long long)j * 2 + 1) * npix;
+        double* oE = alm + ((long long)j * 2 + 0) * nalm * 2;
+        double* oB = alm + ((long long)j * 2 + 1) * nalm * 2;
+        memset(oE, 0, sizeof(double) * 2 * nalm);
+        memset(oB, 0, sizeof(double) * 2 * nalm);
+#pragma omp parallel for schedule(dynamic)
+        for (int i = 0; i < nr; i++) {                      /* FQ, FU = DFT of each ring */
+            const ring_t* r = &rg[i];
+            for (int b = 0; b < r->n; b++) {
+                ld qr = 0.0L, qi = 0.0L, ur = 0.0L, ui = 0.0L;
+                for (int k = 0; k < r->n; k++) {
+                    long long t = ((long long)b * k) % r->n;
+                    ld a = -2.0L * PI_L * (ld)t / r->n, ca = cosl(a), sa = sinl(a);
+                    qr += xq[r->start + k] * ca; qi += xq[r->start + k] * sa;
+                    ur += xu[r->start + k] * ca; ui += xu[r->start + k] * sa;
+                }
+                FQ[2 * (r->start + b)] = qr; FQ[2 * (r->start + b) + 1] = qi;
+                FU[2 * (r->start + b)] = ur; FU[2 * (r->start + b) + 1] = ui;
+            }
+        }
+        for (int pass = 0; pass < npass; pass++) {
+            for (int m = 0; m <= mmax; m++) {
+                int l0 = m > 2 ? m : 2;
+                if (l0 > lmax) continue;                     /* no coefficient of this order */
+                int nl = lmax - l0 + 1;
+#pragma omp parallel for schedule(dynamic)
+                for (int i = 0; i < nr; i++) {
+                    slambda(lmax, m, 2, rg[i].cth, rg[i].chalf, rg[i].shalf, lpp + (long long)i * (lmax + 1));
+                    slambda(lmax, m, -2, rg[i].cth, rg[i].chalf, rg[i].shalf, lpm + (long long)i * (lmax + 1));
+                    slambda(lmax, -m, 2, rg[i].cth, rg[i].chalf, rg[i].shalf, lnp + (long long)i * (lmax + 1));
+                }
+                /* remap and this order's correction */
+                memset(acc, 0, sizeof(ld) * 4 * (lmax + 1));
+                for (int i = 0; i < nr; i++) {
+                    const ring_t* r = &rg[i];
+                    int b = m % r->n;
+                    ld ph = -(ld)m * r->phi0, cph = cosl(ph), sph = sinl(ph);
+                    ld fqr = FQ[2 * (r->start + b)], fqi = FQ[2 * (r->start + b) + 1];
+                    ld fur = FU[2 * (r->start + b)], fui = FU[2 * (r->start + b) + 1];
+                    ld tqr = cph * fqr - sph * fqi, tqi = cph * fqi + sph * fqr;
+                    ld tur = cph * fur - sph * fui, tui = cph * fui + sph * fur;
+                    ld pr = tqr - tui, pi = tqi + tur;           /* F(Q + iU) */
+                    ld mr = tqr + tui, mi = tqi - tur;           /* F(Q - iU) */
+                    const ld* p2 = lpp + (long long)i * (lmax + 1);
+                    const ld* m2 = lpm + (long long)i * (lmax + 1);
+                    for (int l = 0; l < nl; l++) {
+                        acc[4 * l] += p2[l] * pr; acc[4 * l + 1] += p2[l] * pi;
+                        acc[4 * l + 2] += m2[l] * mr; acc[4 * l + 3] += m2[l] * mi;
+                    }
+                }
+                for (int l = 0; l < nl; l++) {
+                    ld pr = dsig * acc[4 * l], pi = dsig * acc[4 * l + 1];
+                    ld mr = dsig * acc[4 * l + 2], mi = dsig * acc[4 * l + 3];
+                    ld er = -0.5L * (pr + mr), ei = (m == 0) ? 0.0L : -0.5L * (pi + mi);
+                    ld br = -0.5L * (pi - mi), bi = (m == 0) ? 0.0L : 0.5L * (pr - mr);
+                    ce[4 * l] = er; ce[4 * l + 1] = ei; ce[4 * l + 2] = br; ce[4 * l + 3] = bi;
+                    long long q = aidx(lmax, l0 + l, m);
+                    oE[2 * q] += (double)er; oE[2 * q + 1] += (double)ei;
+                    oB[2 * q] += (double)br; oB[2 * q + 1] += (double)bi;
+                }
+                /* synthesis of the correction at orders m and -m, removed from
+                 * the residual's Q and U bins */
+                for (int i = 0; i < nr; i++) {
+                    const ring_t* r = &rg[i];
+                    for (int sg = 1; sg >= -1; sg -= 2) {
+                        if (sg < 0 && m == 0) break;
+                        const int mp = sg * m;
+                        const ld* lam = ((sg > 0) ? lpp : lnp) + (long long)i * (lmax + 1);
+                        ld gr = 0.0L, gi = 0.0L;
+                        for (int l = 0; l < nl; l++) {
+                            ld er = ce[4 * l], ei = ce[4 * l + 1], br = ce[4 * l + 2], bi = ce[4 * l + 3];
+                            if (sg < 0) {
+                                ld sgn = (m & 1) ? -1.0L : 1.0L;
+                                er = sgn * er; ei = -sgn * ei; br = sgn * br; bi = -sgn * bi;
+                            }
+                            ld a2r = -(er - bi), a2i = -(ei + br);
+                            gr += lam[l] * a2r; gi += lam[l] * a2i;
+                        }
+                        ld ph = (ld)mp * r->phi0, cph = cosl(ph), sph = sinl(ph);
+                        ld n = (ld)r->n;
+                        ld g_r = n * (cph * gr - sph * gi), g_i = n * (cph * gi + sph * gr);
+                        int b1 = ((mp % r->n) + r->n) % r->n, b2 = (r->n - b1) % r->n;
+                        FQ[2 * (r->start + b1)] -= 0.5L * g_r; FQ[2 * (r->start + b1) + 1] -= 0.5L * g_i;
+                        FQ[2 * (r->start + b2)] -= 0.5L * g_r; FQ[2 * (r->start + b2) + 1] += 0.5L * g_i;
+                        FU[2 * (r->start + b1)] -= 0.5L * g_i; FU[2 * (r->start + b1) + 1] += 0.5L * g_r;
+                        FU[2 * (r->start + b2)] -= 0.5L * g_i; FU[2 * (r->start + b2) + 1] -= 0.5L * g_r;
+                    }
+                }
+            }
+        }
+    }
+    free(FQ); free(FU); free(lpp); free(lpm); free(lnp); free(acc); free(ce); free(rg);
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP
