@@ -168,7 +168,9 @@ size_t     sht_workspace_bytes_eb(const sht_plan* plan, int nmaps);
  * npass >= 1 sweeps (npass = 1 is one sweep; without aliasing it equals the
  * plain quadrature and npass sweeps equal Algorithm 2 with npass - 1
  * refinements). For lmax between 2 nside and 3 nside it converges faster
- * than Algorithm 2. FP64 spin-0 plans only (SHT_EUNSUPPORTED otherwise).
+ * than Algorithm 2. Spin 2 refines a_E and a_B of order m together from the
+ * order-m spectra of Q and U (the orders m and -m of Q + iU). FP64 plans
+ * only (SHT_EUNSUPPORTED for split plans).
  * Three kernel launches per order and pass (the orders depend on each
  * other in sequence). Layouts as sht_map2alm; needs
  * sht_workspace_bytes_immediate(plan, nmaps) bytes of workspace. */

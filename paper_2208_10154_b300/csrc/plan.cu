@@ -1262,9 +1262,11 @@ sht_status sht_alm2map_eb(sht_plan* p, const void* alm, void* map, int nmaps, in
     return do_alm2map(p, (const double*)ws, (double*)map, nmaps, (char*)ws + fb, 1.0, 1.0, st);
 }
 
-// Algorithm 3 (immediate iteration), FP64 spin-0 plans: ring spectra T of
-// the map, the current coefficients' spectra G and the residual D of one
-// order at a time, each [m][q][p][c] in FP64.
+// Algorithm 3 (immediate iteration), FP64 plans: ring spectra T of the map,
+// the current coefficients' spectra G and the residual D of one order at a
+// time, each [m][q][p][c] in FP64. Spin 2 runs on the Q and U columns: the
+// order-m spectra of the two real maps carry the orders m and -m of Q + iU,
+// so one step refines a_E, a_B at order m and resynthesises both.
 size_t sht_workspace_bytes_immediate(const sht_plan* p, int nmaps)
 {
     if (!p || nmaps < 1) return 0;
@@ -1278,8 +1280,8 @@ sht_status sht_map2alm_immediate(sht_plan* p, const void* map, void* alm, int nm
     t_err.clear();
     reset_launches();
     if (!p) { set_error("plan is NULL"); return SHT_EINVAL; }
-    if (p->precision != SHT_FP64 || p->spin != 0) {
-        set_error("the immediate iteration is built for FP64 spin-0 plans");
+    if (p->precision != SHT_FP64) {
+        set_error("the immediate iteration is built for FP64 plans");
         return SHT_EUNSUPPORTED;
     }
     if (nmaps < 1) { set_error("nmaps must be >= 1"); return SHT_EINVAL; }
@@ -1298,7 +1300,8 @@ sht_status sht_map2alm_immediate(sht_plan* p, const void* map, void* alm, int nm
     const double dsig = 4.0 * PI_D / (double)p->npix;
     // a = 0, so the coefficients' spectra G = 0 and the first residual is T
     cudaError_t e = launch_fft_forward_f64(p, (const double*)map, T, nmaps, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(alm, 0, (size_t)nmaps * p->nalm * 2 * sizeof(double), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(alm, 0, (size_t)nmaps * p->ncomp * p->nalm * 2 * sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, tb, st);
     // each order m in turn: its residual from the current G of every order
     // sharing its ring bins, its correction added to a at once, and its G

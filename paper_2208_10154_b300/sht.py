@@ -294,7 +294,7 @@ class Plan:
 
     def map2alm_immediate(self, maps: torch.Tensor, npass: int, out=None) -> torch.Tensor:
         """Algorithm 3 (immediate iteration): npass >= 1 Gauss-Seidel sweeps
-        over m from a = 0 (FP64 spin-0 plans)."""
+        over m from a = 0 (FP64 plans, spin 0 or 2)."""
         maps = self._in(maps, torch.float64, self.npix)
         nmaps = maps.numel() // (self.ncomp * self.npix)
         if out is None:

@@ -637,3 +637,22 @@ def test_immediate_spin2_planted_sign_error_fails_pixel_check(orc):
     y[:, 1] *= -1
     got = orc.map2alm_immediate(y, nside, lmax, 2, spin=2)
     assert rel(got, _gs_pixel(orc, x, nside, lmax, 2, lmax, spin=2)) > 1e-2
+
+
+def test_immediate_pixel_error_at_the_papers_configuration(orc):
+    """Sec. 4's comparison (its figure of pixel-domain errors): nside 128, a
+    sky band-limited to lmax = 383 < 3 nside, 3 rounds. The map resynthesised
+    from the immediate mode's a_lm is much closer to the input than the
+    traditional mode's (about 10x here), and both a_lm errors shrink."""
+    nside, lmax = 128, 383
+    a = inputs.gaussian_alm(1, 1, 1, lmax, cls=inputs.cl_inv_llp1(lmax))
+    x = orc.alm2map(a, nside, lmax)
+
+    def pix(b):
+        return float(np.sqrt(np.mean((orc.alm2map(b, nside, lmax) - x) ** 2) / np.mean(x ** 2)))
+
+    g1 = orc.map2alm_immediate(x, nside, lmax, 1)
+    g = orc.map2alm_immediate(x, nside, lmax, 3)
+    j = orc.map2alm(x, nside, lmax, niter=2)
+    assert pix(g) < pix(j) / 4, (pix(g), pix(j))
+    assert rel(g, a) < rel(j, a) and rel(g, a) < rel(g1, a)
