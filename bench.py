@@ -366,8 +366,9 @@ def run_qu(nside, lmax, npairs, steps, warmup, precision, eb=True):
 
 def run_next_rows(nside, lmax, nmaps, npairs, precision):
     """The widening rows: the compact square a_lm storage (Sec. 5) converted
-    both ways for the benchmark's batch (bytes moved / time against HBM), and
-    the pixel-domain E projection (Sec. 2.3) of npairs Q/U pairs."""
+    both ways for the benchmark's batch (bytes moved / time against HBM), the
+    pixel-domain E projection (Sec. 2.3) of npairs Q/U pairs, and Algorithm 3
+    against Algorithm 2 at the paper's setting of that comparison."""
     import torch
     from paper_2208_10154_b300 import sht
     g = torch.Generator(device="cuda")
@@ -409,7 +410,43 @@ def run_next_rows(nside, lmax, nmaps, npairs, precision):
     status = p2.device_status()
     proj = {"pairs": npairs, "which": "E", "niter": 0, "precision": precision, "ms": ms,
             "pairs_per_s": npairs / (ms / 1e3), "device_status": status}
-    return {"square_storage": layout, "eb_projection": proj}
+    return {"square_storage": layout, "eb_projection": proj, "immediate": time_immediate()}
+
+
+def time_immediate(passes=3):
+    """Algorithm 3 (immediate iteration, Sec. 4) at the paper's setting of that
+    comparison: nside 128, lmax 383 (< 3 nside), 3 passes, FP64 form, 1000
+    maps (spin 0) and 500 Q/U pairs (spin 2), beside Algorithm 2 with the
+    same number of passes (niter = passes - 1). CUDA events, one call each
+    after one untimed call; Gaussian white-noise maps (the cost does not
+    depend on the values)."""
+    import torch
+    from paper_2208_10154_b300 import sht
+    nside, lmax = 128, 383
+    out = {"nside": nside, "lmax": lmax, "passes": passes, "precision": "fp64"}
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    for spin, nmaps in ((0, 1000), (2, 500)):
+        plan = sht.Plan(nside, lmax, None, spin, "fp64")
+        x = torch.randn((nmaps, plan.ncomp, plan.npix), generator=g, dtype=torch.float64, device="cuda")
+        res = {"maps": nmaps}
+        for name, fn in (("immediate_ms", lambda: plan.map2alm_immediate(x, passes)),
+                         ("traditional_ms", lambda: plan.map2alm(x, niter=passes - 1))):
+            fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = e0.elapsed_time(e1)
+            del r
+        plan.device_status()
+        res["immediate_maps_per_s"] = nmaps / (res["immediate_ms"] / 1e3)
+        out["spin%d" % spin] = res
+        del plan, x
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_context(precision, steps=3):
