@@ -212,13 +212,15 @@ cudaError_t expand_component(const sht_plan* p, const void* one, void* full, int
 cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, double* alm, int nmaps,
                                          double scale0, double scale, int csel, cudaStream_t st);
 // one order m only (its work items); map2alm may add into alm
+// the orders m0 .. m0 + nm - 1 (one contiguous range of the work lists)
 cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
-                                          double scale0, double scale, int m, bool accum, cudaStream_t st);
-cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m,
-                                          cudaStream_t st);
-// Fourier-domain residual of order m only: D[m] = T[m] - F(G)[m] (FP64)
+                                          double scale0, double scale, int m0, int nm, bool accum, cudaStream_t st);
+cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m0,
+                                          int nm, cudaStream_t st);
+// Fourier-domain residual of the orders m0 .. m0 + nm - 1 only:
+// D[m] = T[m] - F(G)[m] (FP64)
 cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, const double* G, double* D, int nmaps,
-                                        int m, cudaStream_t st);
+                                        int m0, int nm, cudaStream_t st);
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
 int legendre_f64_row_tile();

@@ -435,15 +435,16 @@ k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const Pa
     }
 }
 
-// The same residual for one order m only (Algorithm 3 updates the
+// The same residual for single orders (Algorithm 3 updates the
 // coefficients order by order): D[m] = T[m] - F(G)[m], with F(G)[m] =
 // f sigma^{k0} [B(j) + sigma_j conj(B(j'))] folded from the current G of
 // every order that shares the ring bin j = m mod N (and its mirror j').
-// FP64. grid = (ring pair, column blocks of 128)
+// FP64. grid = (ring pair, column blocks of 128, order m0 + z)
 __global__ void __launch_bounds__(128)
 k_alias_residual_order(const double2* __restrict__ T, const double2* __restrict__ G, double2* __restrict__ D,
-                       const PairGeom* __restrict__ pairs, int R_, int mmax, long long ncol, int nmc, int m)
+                       const PairGeom* __restrict__ pairs, int R_, int mmax, long long ncol, int nmc, int m0)
 {
+    const int m = m0 + (int)blockIdx.z;
     const int p = blockIdx.x;
     const int mc = blockIdx.y * blockDim.x + threadIdx.x;
     if (mc >= nmc) return;
@@ -488,13 +489,13 @@ k_alias_residual_order(const double2* __restrict__ T, const double2* __restrict_
 }
 
 cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, const double* G, double* D, int nmaps,
-                                        int m, cudaStream_t st)
+                                        int m0, int nm, cudaStream_t st)
 {
     const int nmc = nmaps * p->ncomp;
-    dim3 grid(p->R, (nmc + 127) / 128);
+    dim3 grid(p->R, (nmc + 127) / 128, nm);
     prof_start("k_alias_residual_order", st);
     k_alias_residual_order<<<grid, 128, 0, st>>>((const double2*)T, (const double2*)G, (double2*)D, p->t.pairs,
-                                                 p->R, p->mmax, ncols(p, nmaps), nmc, m);
+                                                 p->R, p->mmax, ncols(p, nmaps), nmc, m0);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

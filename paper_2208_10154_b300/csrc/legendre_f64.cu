@@ -427,10 +427,10 @@ cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, dou
 }
 
 cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
-                                          double scale0, double scale, int m, bool accum, cudaStream_t st)
+                                          double scale0, double scale, int m0, int nm, bool accum, cudaStream_t st)
 {
-    const int w0 = p->m2a_off[m];
-    return launch_m2a_range(p, T, alm, nmaps, scale0, scale, w0, p->m2a_off[m + 1] - w0, accum, st);
+    const int w0 = p->m2a_off[m0];
+    return launch_m2a_range(p, T, alm, nmaps, scale0, scale, w0, p->m2a_off[m0 + nm] - w0, accum, st);
 }
 
 static cudaError_t launch_a2m_range(const sht_plan* p, const double* alm, double* G, int nmaps, double scale0,
@@ -455,11 +455,11 @@ cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double
     return launch_a2m_range(p, alm, G, nmaps, scale0, scale, 0, p->nwork_a2m, st);
 }
 
-cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m,
-                                          cudaStream_t st)
+cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, double* G, int nmaps, int m0,
+                                          int nm, cudaStream_t st)
 {
-    const int w0 = p->a2m_off[m];
-    return launch_a2m_range(p, alm, G, nmaps, 1.0, 1.0, w0, p->a2m_off[m + 1] - w0, st);
+    const int w0 = p->a2m_off[m0];
+    return launch_a2m_range(p, alm, G, nmaps, 1.0, 1.0, w0, p->a2m_off[m0 + nm] - w0, st);
 }
 
 int legendre_f64_row_tile() { return M2A_TL; }

@@ -1305,12 +1305,18 @@ sht_status sht_map2alm_immediate(sht_plan* p, const void* map, void* alm, int nm
     if (e == cudaSuccess) e = cudaMemsetAsync(G, 0, tb, st);
     // each order m in turn: its residual from the current G of every order
     // sharing its ring bins, its correction added to a at once, and its G
-    // recomputed from the updated a, so the orders after it see the update
+    // recomputed from the updated a, so the orders after it see the update.
+    // Orders m and m' share a bin of a ring of N pixels only if m' = +-m
+    // (mod N), and every HEALPix ring has a multiple of 4 pixels, so an even
+    // and an odd order never do: the orders 2t and 2t + 1 run in one step,
+    // each seeing exactly the updates the sequential sweep gives it.
     for (int pass = 0; pass < npass && e == cudaSuccess; pass++)
-        for (int m = 0; m <= p->mmax && e == cudaSuccess; m++) {
-            e = launch_alias_residual_order(p, T, G, D, nmaps, m, st);
-            if (e == cudaSuccess) e = launch_legendre_m2a_f64_order(p, D, (double*)alm, nmaps, dsig, dsig, m, true, st);
-            if (e == cudaSuccess) e = launch_legendre_a2m_f64_order(p, (const double*)alm, G, nmaps, m, st);
+        for (int m0 = 0; m0 <= p->mmax && e == cudaSuccess; m0 += 2) {
+            const int nm = std::min(2, p->mmax + 1 - m0);
+            e = launch_alias_residual_order(p, T, G, D, nmaps, m0, nm, st);
+            if (e == cudaSuccess)
+                e = launch_legendre_m2a_f64_order(p, D, (double*)alm, nmaps, dsig, dsig, m0, nm, true, st);
+            if (e == cudaSuccess) e = launch_legendre_a2m_f64_order(p, (const double*)alm, G, nmaps, m0, nm, st);
         }
     if (e != cudaSuccess) { set_error(std::string("immediate iteration: ") + cudaGetErrorString(e)); return SHT_ECUDA; }
     return SHT_OK;

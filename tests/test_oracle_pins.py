@@ -656,3 +656,14 @@ def test_immediate_pixel_error_at_the_papers_configuration(orc):
     j = orc.map2alm(x, nside, lmax, niter=2)
     assert pix(g) < pix(j) / 4, (pix(g), pix(j))
     assert rel(g, a) < rel(j, a) and rel(g, a) < rel(g1, a)
+
+
+@pytest.mark.parametrize("nside", [1, 2, 3, 8, 13, 64])
+def test_every_ring_has_a_multiple_of_four_pixels(orc, nside):
+    """HEALPix rings hold 4i (caps) or 4 nside (belt) pixels. So orders m, m'
+    share a ring bin (m' = +-m mod N) only if m' = +-m mod 4: an even and an
+    odd order never interact in Algorithm 3's sweep, which is what lets the
+    GPU refine the orders 2t and 2t + 1 in one step."""
+    _, _, _, n, _ = orc.ring_info(nside)
+    assert np.all(np.asarray(n) % 4 == 0)
+    assert len(n) == 4 * nside - 1 and int(np.sum(n)) == 12 * nside * nside
