@@ -73,6 +73,14 @@ struct DevTables {
     double* w_A[2] = {nullptr, nullptr};
     double* w_AB[2] = {nullptr, nullptr};
     double* w_C[2] = {nullptr, nullptr};
+    // FP64 plans: states of the recurrences above where the FP64 map2alm
+    // resumes a chain mid-tile. Spin 0, chain (m, q, p): (value at row 32b,
+    // value at row 32b - 1) and the exponent, b >= 1; spin 2, chain (m, p):
+    // both recurrences (s = +2, then -2) at l = m + 64b, b >= 1.
+    // [off[chain] + b - 1][p] (spin 2: two entries per [..][p]).
+    double2* ck64 = nullptr;
+    int* ck64_exp = nullptr;
+    int* ck64_off = nullptr;       // spin 0: [m][q]; spin 2: [m]
 };
 
 // lo parts of the FP32 FFT tables and hi/lo ring phase tables (compensated FFT)
@@ -221,6 +229,8 @@ cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, 
 // D[m] = T[m] - F(G)[m] (FP64)
 cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, const double* G, double* D, int nmaps,
                                         int m0, int nm, cudaStream_t st);
+// plan-time walk of the FP64 recurrences that stores their checkpoints
+cudaError_t build_f64_checkpoints(sht_plan* p, size_t* acc);
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
 int legendre_f64_row_tile();

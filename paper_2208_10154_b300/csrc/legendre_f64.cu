@@ -8,6 +8,9 @@
 //   map2alm  slot q rows (l-m)%2 == q:  A = F+ T_q + F- perm(T_{1-q})
 //   alm2map  slot q:  G_q = sum_{(l-m)%2==q} F+ a + sum_{(l-m)%2!=q} F- perm(a)
 // with perm(Qr,Qi,Ur,Ui) = (-Ui,Ur,Qi,-Qr) (E/B coupling through i U, Sec. 2.3).
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace sht {
@@ -47,6 +50,10 @@ struct LegArgs {
     // of T. csel = 0: pcol = ncol.
     long long pcol;
     int csel;
+    // checkpoints of the recurrences (FP64 plans; null: walk from the seeds)
+    const double2* ck64;
+    const int* ck64_exp;
+    const int* ck64_off;
 };
 
 __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
@@ -60,13 +67,40 @@ __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
 // grid.x = work item (m, q, row tile), grid.y = column tile
 // ---------------------------------------------------------------------------
 constexpr int M2A_TL = 128, M2A_TN = 32, M2A_TK = 32;
+constexpr int M2A_TLP = M2A_TL + 1;     // padded row stride of the lambda tile: the
+                                        // lanes' stores (one ring pair each) hit distinct banks
+constexpr int M2A_SMEM = (2 * M2A_TK * M2A_TLP + 2 * M2A_TK * M2A_TN) * (int)sizeof(double);
+
+// One step of each recurrence. The checkpoint walk at plan time and the
+// kernels run these same operations, so a chain resumed from a checkpoint
+// gives the values of the serial walk bit for bit.
+// spin 0, row r -> r + 1 of slot q (ci = index of l = m + q + 2r)
+__device__ __forceinline__ void step0(const double* ra, const double* rb, const double* rc, long long ci, double x2,
+                                      double& cur, double& prev, int& E)
+{
+    const double t = fma(ra[ci], x2, rb[ci]);
+    const double nxt = fma(t, cur, rc[ci] * prev);
+    prev = cur;
+    cur = nxt;
+    if (fabs(cur) > RESCALE_UP) { cur *= RESCALE_DN; prev *= RESCALE_DN; E += 500; }
+}
+// spin 2, one of s = +-2: l - 1 -> l (ci = index of l)
+__device__ __forceinline__ void step2(const double* A, const double* AB, const double* C, long long ci, double x,
+                                      double& cur, double& prev, int& E)
+{
+    const double t = fma(A[ci], x, AB[ci]);
+    const double nxt = fma(t, cur, -C[ci] * prev);
+    prev = cur;
+    cur = nxt;
+    if (fabs(cur) > RESCALE_UP) { cur *= RESCALE_DN; prev *= RESCALE_DN; E += 500; }
+}
 
 __global__ void __launch_bounds__(256)
 k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
 {
     extern __shared__ __align__(16) double sm[];
-    double* lam = sm;                                   // [2][TK][TL]
-    double* dat = sm + 2 * M2A_TK * M2A_TL;             // [2][TK][TN]
+    double* lam = sm;                                   // [2][TK][TLP]
+    double* dat = sm + 2 * M2A_TK * M2A_TLP;            // [2][TK][TN]
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, rt = w.z;
     const int tid = threadIdx.x;
@@ -86,72 +120,84 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
         for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
     for (int k0 = 0; k0 < a.R; k0 += M2A_TK) {
-        // ---- lambda tile: warp 0, one ring pair per lane, walk rows ----
-        if (tid < 32) {
-            const int p = k0 + tid;
+        // ---- lambda tile: warp v < 4 holds the rows rb = r0 + 32 v .. rb + 31
+        // of the 32 ring pairs (one per lane), resuming each chain from its
+        // checkpoint at row rb (the seed at row 0) ----
+        if (tid < 128) {
+            const int lane = tid & 31;
+            const int rb = r0 + 32 * (tid >> 5);
+            const int b = rb >> 5;
+            const int p = k0 + lane;
             const bool valid = p < a.R;
+            const bool live = valid && rb < nrows;
             const double x = valid ? a.pairs[p].x : 0.0;
+            double* l0row = lam + (long long)lane * M2A_TLP + (rb - r0);                  // type 0
+            double* l1row = lam + (long long)(M2A_TK + lane) * M2A_TLP + (rb - r0);       // type 1
             if (a.spin == 0) {
                 double cur = 0.0, prev = 0.0;
                 int E = 0;
-                if (valid) {
-                    long long si = ((long long)m * 2 + q) * a.R + p;
-                    cur = a.seed_mant[si];
-                    E = a.seed_exp[si];
-                }
                 const double x2 = x * x;
-                for (int r = 0; r < r0 + M2A_TL; r++) {
-                    if (r >= r0) lam[tid * M2A_TL + (r - r0)] = (r < nrows) ? scale2(cur, E) : 0.0;
-                    if (r + 1 < nrows) {
-                        int l = l_first + 2 * r;
-                        long long ci = d_alm_index(a.lmax, l, m);
-                        double t = fma(a.ra[ci], x2, a.rb[ci]);
-                        double nxt = fma(t, cur, a.rc[ci] * prev);
-                        prev = cur;
-                        cur = nxt;
-                        if (fabs(cur) > RESCALE_UP) { cur *= RESCALE_DN; prev *= RESCALE_DN; E += 500; }
+                if (live) {
+                    if (b > 0 && a.ck64) {
+                        const long long ci = (long long)(a.ck64_off[m * 2 + q] + b - 1) * a.R + p;
+                        const double2 v = a.ck64[ci];
+                        cur = v.x; prev = v.y; E = a.ck64_exp[ci];
+                    } else {
+                        const long long si = ((long long)m * 2 + q) * a.R + p;
+                        cur = a.seed_mant[si];
+                        E = a.seed_exp[si];
+                        for (int r = 0; r < rb; r++)             // (plans without checkpoints)
+                            step0(a.ra, a.rb, a.rc, d_alm_index(a.lmax, l_first + 2 * r, m), x2, cur, prev, E);
                     }
                 }
+                for (int i = 0; i < 32; i++) {
+                    const int r = rb + i;
+                    l0row[i] = (r < nrows) ? scale2(cur, E) : 0.0;
+                    if (i + 1 < 32 && r + 1 < nrows)
+                        step0(a.ra, a.rb, a.rc, d_alm_index(a.lmax, l_first + 2 * r, m), x2, cur, prev, E);
+                }
             } else {
-                // spin 2: walk every l from l0 = max(m,2); rows are l with (l-m)%2 == q
+                // spin 2: walk every l from the start state; rows are l with (l-m)%2 == q
                 const int l0 = m > 2 ? m : 2;
                 double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;   // s=+2: cur, prev; s=-2: cur, prev
                 int E2 = 0, E3 = 0;
-                if (valid) {
-                    long long si = ((long long)m * 2 + 0) * a.R + p;
-                    c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
-                    si = ((long long)m * 2 + 1) * a.R + p;
-                    c3 = a.seed_mant[si]; E3 = a.seed_exp[si];
-                }
-                const int rlast = r0 + M2A_TL - 1;
-                const int lend = min(a.lmax, l_first + 2 * rlast);
-                for (int l = l0; l <= lend; l++) {
-                    if (l > l0) {
-                        long long ci = d_alm_index(a.lmax, l, m);
-                        double t = fma(a.wA0[ci], x, a.wAB0[ci]);
-                        double n2 = fma(t, c2, -a.wC0[ci] * p2);
-                        p2 = c2; c2 = n2;
-                        t = fma(a.wA1[ci], x, a.wAB1[ci]);
-                        double n3 = fma(t, c3, -a.wC1[ci] * p3);
-                        p3 = c3; c3 = n3;
-                        if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
-                        if (fabs(c3) > RESCALE_UP) { c3 *= RESCALE_DN; p3 *= RESCALE_DN; E3 += 500; }
+                int ls = l0;                                     // l of the state
+                if (live) {
+                    if (b > 0 && a.ck64) {
+                        const long long ci = (long long)(a.ck64_off[m] + b - 1) * a.R + p;
+                        const double2 v2 = a.ck64[2 * ci], v3 = a.ck64[2 * ci + 1];
+                        c2 = v2.x; p2 = v2.y; c3 = v3.x; p3 = v3.y;
+                        E2 = a.ck64_exp[2 * ci]; E3 = a.ck64_exp[2 * ci + 1];
+                        ls = m + 64 * b;
+                    } else {
+                        long long si = ((long long)m * 2 + 0) * a.R + p;
+                        c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
+                        si = ((long long)m * 2 + 1) * a.R + p;
+                        c3 = a.seed_mant[si]; E3 = a.seed_exp[si];
                     }
-                    if (((l - m) & 1) == q && l >= l_first) {
-                        int r = (l - l_first) >> 1;
-                        if (r >= r0) {
-                            double v2 = scale2(c2, E2), v3 = scale2(c3, E3);
-                            lam[(0 * M2A_TK + tid) * M2A_TL + (r - r0)] = -0.5 * (v2 + v3);
-                            lam[(1 * M2A_TK + tid) * M2A_TL + (r - r0)] = -0.5 * (v2 - v3);
+                    const int lend = min(a.lmax, l_first + 2 * (rb + 31));
+                    for (int l = ls; l <= lend; l++) {
+                        if (l > ls) {
+                            const long long ci = d_alm_index(a.lmax, l, m);
+                            step2(a.wA0, a.wAB0, a.wC0, ci, x, c2, p2, E2);
+                            step2(a.wA1, a.wAB1, a.wC1, ci, x, c3, p3, E3);
+                        }
+                        if (((l - m) & 1) == q && l >= l_first) {
+                            const int r = (l - l_first) >> 1;
+                            if (r >= rb) {
+                                const double v2 = scale2(c2, E2), v3 = scale2(c3, E3);
+                                l0row[r - rb] = -0.5 * (v2 + v3);
+                                l1row[r - rb] = -0.5 * (v2 - v3);
+                            }
                         }
                     }
                 }
                 // rows not produced above (l < l0 or beyond lmax) are zero
-                for (int r = r0; r < r0 + M2A_TL; r++) {
-                    int l = l_first + 2 * r;
-                    if (l < l0 || l > a.lmax || !valid) {
-                        lam[(0 * M2A_TK + tid) * M2A_TL + (r - r0)] = 0.0;
-                        lam[(1 * M2A_TK + tid) * M2A_TL + (r - r0)] = 0.0;
+                for (int i = 0; i < 32; i++) {
+                    const int l = l_first + 2 * (rb + i);
+                    if (l < l0 || l > a.lmax || !live) {
+                        l0row[i] = 0.0;
+                        l1row[i] = 0.0;
                     }
                 }
             }
@@ -177,13 +223,13 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
         }
         __syncthreads();
         for (int t = 0; t < ntypes; t++) {
-            const double* L = lam + t * M2A_TK * M2A_TL;
+            const double* L = lam + t * M2A_TK * M2A_TLP;
             const double* D = dat + t * M2A_TK * M2A_TN;
 #pragma unroll 4
             for (int k = 0; k < M2A_TK; k++) {
                 double lv[4], dv[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) lv[i] = L[k * M2A_TL + ty + 32 * i];
+                for (int i = 0; i < 4; i++) lv[i] = L[k * M2A_TLP + ty + 32 * i];
 #pragma unroll
                 for (int j = 0; j < 4; j++) dv[j] = D[k * M2A_TN + tx * 4 + j];
 #pragma unroll
@@ -378,6 +424,9 @@ static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double sca
     a.accum = 0;
     a.pcol = a.ncol;
     a.csel = 0;
+    a.ck64 = p->t.ck64;
+    a.ck64_exp = p->t.ck64_exp;
+    a.ck64_off = p->t.ck64_off;
     return a;
 }
 
@@ -387,7 +436,7 @@ static cudaError_t launch_m2a_range(const sht_plan* p, const double* T, double* 
                                     double scale, int w0, int nwork, bool accum, cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
-    size_t sm = (size_t)(2 * M2A_TK * M2A_TL + 2 * M2A_TK * M2A_TN) * sizeof(double);
+    size_t sm = (size_t)M2A_SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     long long nc = ncols(p, nmaps);
@@ -412,7 +461,7 @@ cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, dou
 {
     const int nwork = p->nwork_m2a;
     if (nwork <= 0) return cudaSuccess;
-    size_t sm = (size_t)(2 * M2A_TK * M2A_TL + 2 * M2A_TK * M2A_TN) * sizeof(double);
+    size_t sm = (size_t)M2A_SMEM;
     cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a);
@@ -460,6 +509,92 @@ cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, 
 {
     const int w0 = p->a2m_off[m0];
     return launch_a2m_range(p, alm, G, nmaps, 1.0, 1.0, w0, p->a2m_off[m0 + nm] - w0, st);
+}
+
+// ---------------------------------------------------------------------------
+// plan-time walk of every chain the map2alm kernel resumes mid-tile (the
+// layout of DevTables::ck64): spin 0, thread (p, m, q); spin 2, thread (p, m)
+// ---------------------------------------------------------------------------
+__global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ cke)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y, q = blockIdx.z;
+    if (p >= a.R) return;
+    const double x = a.pairs[p].x;
+    if (a.spin == 0) {
+        const int l_first = m + q;
+        const int nrows = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
+        const long long si = ((long long)m * 2 + q) * a.R + p;
+        double cur = a.seed_mant[si], prev = 0.0;
+        int E = a.seed_exp[si];
+        const double x2 = x * x;
+        const int o = a.ck64_off[m * 2 + q];
+        for (int r = 0; r + 1 < nrows; r++) {
+            step0(a.ra, a.rb, a.rc, d_alm_index(a.lmax, l_first + 2 * r, m), x2, cur, prev, E);
+            if (((r + 1) & 31) == 0) {
+                const long long i = (long long)(o + ((r + 1) >> 5) - 1) * a.R + p;
+                ck[i] = make_double2(cur, prev);
+                cke[i] = E;
+            }
+        }
+    } else {
+        if (q) return;
+        const int l0 = m > 2 ? m : 2;
+        long long si = ((long long)m * 2 + 0) * a.R + p;
+        double c2 = a.seed_mant[si], p2 = 0.0;
+        int E2 = a.seed_exp[si];
+        si = ((long long)m * 2 + 1) * a.R + p;
+        double c3 = a.seed_mant[si], p3 = 0.0;
+        int E3 = a.seed_exp[si];
+        const int o = a.ck64_off[m];
+        for (int l = l0 + 1; l <= a.lmax; l++) {
+            const long long ci = d_alm_index(a.lmax, l, m);
+            step2(a.wA0, a.wAB0, a.wC0, ci, x, c2, p2, E2);
+            step2(a.wA1, a.wAB1, a.wC1, ci, x, c3, p3, E3);
+            if (((l - m) & 63) == 0) {                  // l = m + 64 b, b >= 1 (l > l0 >= m)
+                const long long i = (long long)(o + ((l - m) >> 6) - 1) * a.R + p;
+                ck[2 * i] = make_double2(c2, p2);
+                ck[2 * i + 1] = make_double2(c3, p3);
+                cke[2 * i] = E2;
+                cke[2 * i + 1] = E3;
+            }
+        }
+    }
+}
+
+cudaError_t build_f64_checkpoints(sht_plan* p, size_t* acc)
+{
+    const int lmax = p->lmax, mmax = p->mmax;
+    std::vector<int> off;
+    long long n = 0;                                   // checkpoints per ring pair
+    if (p->spin == 0) {
+        for (int m = 0; m <= mmax; m++)
+            for (int q = 0; q < 2; q++) {
+                const int nrows = (lmax >= m + q) ? (lmax - m - q) / 2 + 1 : 0;
+                off.push_back((int)n);
+                n += std::max(0, (nrows + 31) / 32 - 1);
+            }
+    } else {
+        for (int m = 0; m <= mmax; m++) {
+            off.push_back((int)n);
+            n += (lmax - m) / 64;
+        }
+    }
+    const long long ne = n * p->R * (p->spin ? 2 : 1);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->t.ck64_off, off.size() * sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(p->t.ck64_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    *acc += off.size() * sizeof(int);
+    if (ne == 0) return cudaSuccess;
+    if ((e = cudaMalloc(&p->t.ck64, (size_t)ne * sizeof(double2))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&p->t.ck64_exp, (size_t)ne * sizeof(int))) != cudaSuccess) return e;
+    *acc += (size_t)ne * (sizeof(double2) + sizeof(int));
+    LegArgs a = make_args(p, 1, 1.0, 1.0, nullptr);
+    dim3 grid((unsigned)((p->R + 127) / 128), (unsigned)(mmax + 1), p->spin ? 1u : 2u);
+    k_ck64<<<grid, 128>>>(a, p->t.ck64, p->t.ck64_exp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaDeviceSynchronize();
 }
 
 int legendre_f64_row_tile() { return M2A_TL; }

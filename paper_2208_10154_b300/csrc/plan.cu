@@ -804,7 +804,8 @@ static void free_tables(sht_plan* p)
     void* ptrs[] = {p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp, p->t.bhat, p->t.twiddle_f,
                     p->t.chirp_f, p->t.bhat_f, p->t.seed_mant, p->t.seed_exp, p->t.rec_a, p->t.rec_b,
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
-                    p->t.w_C[1], p->work_m2a, p->work_a2m, p->host_dev_in, p->host_dev_out, p->host_ws};
+                    p->t.w_C[1], p->t.ck64, p->t.ck64_exp, p->t.ck64_off, p->work_m2a, p->work_a2m,
+                    p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
     void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off,
                   p->c.fft_s, p->c.twp, p->c.tws_h, p->c.tws_l, p->c.bhs_h, p->c.bhs_l};
@@ -1025,6 +1026,11 @@ sht_status sht_plan_create(int nside, int lmax, int mmax, int spin, int precisio
     p->nalm = (long long)(mmax + 1) * (2 * lmax + 2 - mmax) / 2;
     p->R = 2 * nside;
     cudaError_t e = build_tables(p);
+    if (e == cudaSuccess && precision == SHT_FP64) {
+        size_t ckb = 0;
+        e = build_f64_checkpoints(p, &ckb);
+        p->table_bytes += ckb;
+    }
     if (e == cudaSuccess && precision == SHT_SPLIT_F16X4) e = build_split_tables(p);
     // the split FFTs' helper streams and events, made here rather than at the
     // first call (which may be under stream capture)
