@@ -69,7 +69,14 @@ __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
 constexpr int M2A_TL = 128, M2A_TN = 32, M2A_TK = 32;
 constexpr int M2A_TLP = M2A_TL + 1;     // padded row stride of the lambda tile: the
                                         // lanes' stores (one ring pair each) hit distinct banks
-constexpr int M2A_SMEM = (2 * M2A_TK * M2A_TLP + 2 * M2A_TK * M2A_TN) * (int)sizeof(double);
+// two buffers of (lambda + data) per type (spin 2: two types)
+__host__ __device__ constexpr int m2a_smem(int spin, int tn)
+{
+    return 2 * (spin ? 2 : 1) * (M2A_TK * M2A_TLP + M2A_TK * tn) * (int)sizeof(double);
+}
+// column tiles: 32 (map2alm) / 64 (alm2map) map columns per CTA, 4 / 8 for
+// batches of at most that many columns (one map or one Q/U pair)
+constexpr int M2A_TN_SMALL = 4, A2M_TN_SMALL = 8;
 
 // One step of each recurrence. The checkpoint walk at plan time and the
 // kernels run these same operations, so a chain resumed from a checkpoint
@@ -95,51 +102,64 @@ __device__ __forceinline__ void step2(const double* A, const double* AB, const d
     if (fabs(cur) > RESCALE_UP) { cur *= RESCALE_DN; prev *= RESCALE_DN; E += 500; }
 }
 
-__global__ void __launch_bounds__(256)
+// Roles: warps 0-3 produce the next K chunk (lambda rows from the
+// checkpoints, the data tile) into one buffer while warps 4-7 run the FMAs of
+// the current chunk from the other, 8 rows x 4 columns per thread, so the
+// recurrence's FP64 latency overlaps the contraction (each output sums its
+// products in the same order as a single-buffered tile would).
+template <int TN>
+__global__ void __launch_bounds__(256, 2)
 k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
 {
     extern __shared__ __align__(16) double sm[];
-    double* lam = sm;                                   // [2][TK][TLP]
-    double* dat = sm + 2 * M2A_TK * M2A_TLP;            // [2][TK][TN]
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, rt = w.z;
     const int tid = threadIdx.x;
-    const int c0 = blockIdx.y * M2A_TN;
+    const int c0 = blockIdx.y * TN;
     const int l_first = m + q;
     const int nrows = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
     const int r0 = rt * M2A_TL;
     const int ntypes = a.spin ? 2 : 1;
+    // buffer b, type t: lambda [TK][TLP], data [TK][TN]
+    double* const lam0 = sm;
+    double* const dat0 = sm + 2 * ntypes * M2A_TK * M2A_TLP;
+    auto lam_buf = [&](int b, int t) { return lam0 + (long long)(b * ntypes + t) * M2A_TK * M2A_TLP; };
+    auto dat_buf = [&](int b, int t) { return dat0 + (long long)(b * ntypes + t) * M2A_TK * TN; };
     const long long qstride = (long long)a.R * a.pcol;     // T holds every data column
     const double* Tq = T + ((long long)m * 2 + q) * qstride;
     const double* To = T + ((long long)m * 2 + (1 - q)) * qstride;
-    const int tx = tid & 7, ty = tid >> 3;
-    double acc[4][4];
+    const bool producer = tid < 128;
+    const int ct = tid - 128;                   // consumer thread
+    // TN / 4 column groups of 4; rows ty + RG i, i < RPT
+    constexpr int CG = TN / 4, RG = 128 / CG, RPT = M2A_TL / RG;
+    const int tx = ct % CG, ty = ct / CG;
+    double acc[RPT][4];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < RPT; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
-    for (int k0 = 0; k0 < a.R; k0 += M2A_TK) {
+    // the producers' part: chunk k0 into buffer b
+    auto produce = [&](int k0, int b) {
         // ---- lambda tile: warp v < 4 holds the rows rb = r0 + 32 v .. rb + 31
         // of the 32 ring pairs (one per lane), resuming each chain from its
         // checkpoint at row rb (the seed at row 0) ----
-        if (tid < 128) {
+        {
             const int lane = tid & 31;
             const int rb = r0 + 32 * (tid >> 5);
-            const int b = rb >> 5;
+            const int bk = rb >> 5;
             const int p = k0 + lane;
             const bool valid = p < a.R;
             const bool live = valid && rb < nrows;
             const double x = valid ? a.pairs[p].x : 0.0;
-            double* l0row = lam + (long long)lane * M2A_TLP + (rb - r0);                  // type 0
-            double* l1row = lam + (long long)(M2A_TK + lane) * M2A_TLP + (rb - r0);       // type 1
+            double* l0row = lam_buf(b, 0) + (long long)lane * M2A_TLP + (rb - r0);
             if (a.spin == 0) {
                 double cur = 0.0, prev = 0.0;
                 int E = 0;
                 const double x2 = x * x;
                 if (live) {
-                    if (b > 0 && a.ck64) {
-                        const long long ci = (long long)(a.ck64_off[m * 2 + q] + b - 1) * a.R + p;
+                    if (bk > 0 && a.ck64) {
+                        const long long ci = (long long)(a.ck64_off[m * 2 + q] + bk - 1) * a.R + p;
                         const double2 v = a.ck64[ci];
                         cur = v.x; prev = v.y; E = a.ck64_exp[ci];
                     } else {
@@ -158,17 +178,18 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
                 }
             } else {
                 // spin 2: walk every l from the start state; rows are l with (l-m)%2 == q
+                double* l1row = lam_buf(b, 1) + (long long)lane * M2A_TLP + (rb - r0);
                 const int l0 = m > 2 ? m : 2;
                 double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;   // s=+2: cur, prev; s=-2: cur, prev
                 int E2 = 0, E3 = 0;
                 int ls = l0;                                     // l of the state
                 if (live) {
-                    if (b > 0 && a.ck64) {
-                        const long long ci = (long long)(a.ck64_off[m] + b - 1) * a.R + p;
+                    if (bk > 0 && a.ck64) {
+                        const long long ci = (long long)(a.ck64_off[m] + bk - 1) * a.R + p;
                         const double2 v2 = a.ck64[2 * ci], v3 = a.ck64[2 * ci + 1];
                         c2 = v2.x; p2 = v2.y; c3 = v3.x; p3 = v3.y;
                         E2 = a.ck64_exp[2 * ci]; E3 = a.ck64_exp[2 * ci + 1];
-                        ls = m + 64 * b;
+                        ls = m + 64 * bk;
                     } else {
                         long long si = ((long long)m * 2 + 0) * a.R + p;
                         c2 = a.seed_mant[si]; E2 = a.seed_exp[si];
@@ -203,8 +224,10 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
             }
         }
         // ---- data tile ----
-        for (int i = tid; i < M2A_TK * M2A_TN; i += blockDim.x) {
-            int k = i / M2A_TN, c = i % M2A_TN;
+        double* d0 = dat_buf(b, 0);
+        double* d1 = a.spin ? dat_buf(b, 1) : nullptr;
+        for (int i = tid; i < M2A_TK * TN; i += 128) {
+            int k = i / TN, c = i % TN;
             int p = k0 + k;
             long long cg = c0 + c;
             double v0 = 0.0, v1 = 0.0;
@@ -218,32 +241,47 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
                     v1 = (wsel == 0) ? -o[3] : (wsel == 1) ? o[2] : (wsel == 2) ? o[1] : -o[0];
                 }
             }
-            dat[k * M2A_TN + c] = v0;
-            dat[(M2A_TK + k) * M2A_TN + c] = v1;
+            d0[k * TN + c] = v0;
+            if (a.spin) d1[k * TN + c] = v1;
         }
-        __syncthreads();
-        for (int t = 0; t < ntypes; t++) {
-            const double* L = lam + t * M2A_TK * M2A_TLP;
-            const double* D = dat + t * M2A_TK * M2A_TN;
+    };
+
+    const int nch = (a.R + M2A_TK - 1) / M2A_TK;
+    if (producer) produce(0, 0);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ch++) {
+        const int cb = ch & 1;
+        if (producer) {
+            if (ch + 1 < nch) produce((ch + 1) * M2A_TK, cb ^ 1);
+        } else {
+            // row groups i with RG i >= nv hold no row of the tile (short last
+            // tiles at high m): skipped, block-uniformly
+            const int nv = nrows - r0;
+            for (int t = 0; t < ntypes; t++) {
+                const double* L = lam_buf(cb, t);
+                const double* D = dat_buf(cb, t);
 #pragma unroll 4
-            for (int k = 0; k < M2A_TK; k++) {
-                double lv[4], dv[4];
+                for (int k = 0; k < M2A_TK; k++) {
+                    double lv[RPT], dv[4];
 #pragma unroll
-                for (int i = 0; i < 4; i++) lv[i] = L[k * M2A_TLP + ty + 32 * i];
+                    for (int i = 0; i < RPT; i++) lv[i] = (RG * i < nv) ? L[k * M2A_TLP + ty + RG * i] : 0.0;
 #pragma unroll
-                for (int j = 0; j < 4; j++) dv[j] = D[k * M2A_TN + tx * 4 + j];
+                    for (int j = 0; j < 4; j++) dv[j] = D[k * TN + tx * 4 + j];
 #pragma unroll
-                for (int i = 0; i < 4; i++)
+                    for (int i = 0; i < RPT; i++)
+                        if (RG * i < nv)
 #pragma unroll
-                    for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+                            for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+                }
             }
         }
         __syncthreads();
     }
+    if (producer) return;
     // ---- write a_lm ----
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        int r = r0 + ty + 32 * i;
+    for (int i = 0; i < RPT; i++) {
+        int r = r0 + ty + RG * i;
         if (r >= nrows) continue;
         int l = l_first + 2 * r;
 #pragma unroll
@@ -267,22 +305,32 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
 // ---------------------------------------------------------------------------
 constexpr int A2M_TP = 64, A2M_TN = 64, A2M_TK = 32;
 
-__global__ void __launch_bounds__(256)
+// Roles as in map2alm: warps 0-3 produce the next chunk (threads 0-63 step
+// the lambda chains of the tile's ring pairs, all four warps load the a_lm
+// tile) while warps 4-7 run the FMAs of the current one, 8 ring pairs x 4
+// columns per thread.
+template <int TN>
+__global__ void __launch_bounds__(256, 2)
 k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
 {
     extern __shared__ __align__(16) double sm[];
-    double* lam = sm;                        // [TK][TP]
-    double* dat = sm + A2M_TK * A2M_TP;      // [TK][TN]
+    // buffer b: lambda [TK][TP] at sm + b * TK * TP, data [TK][TN] after both
+    double* const lam0 = sm;
+    double* const dat0 = sm + 2 * A2M_TK * A2M_TP;
     const int4 w = a.work[blockIdx.x];
     const int m = w.x, q = w.y, pt = w.z;
     const int tid = threadIdx.x;
-    const int c0 = blockIdx.y * A2M_TN;
+    const int c0 = blockIdx.y * TN;
     const int p0 = pt * A2M_TP;
     const long long qstride = (long long)a.R * a.ncol;
-    const int tx = tid & 15, ty = tid >> 4;     // 16 col groups of 4, 16 pair groups of 4
-    double acc[4][4];
+    const bool producer = tid < 128;
+    const int ct = tid - 128;                    // consumer thread
+    // TN / 4 column groups of 4; ring pairs ty + PG i, i < PPT
+    constexpr int CG = TN / 4, PG = 128 / CG, PPT = A2M_TP / PG;
+    const int tx = ct % CG, ty = ct / CG;
+    double acc[PPT][4];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < PPT; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
 
@@ -294,7 +342,7 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
         lk0 = m > 2 ? m : 2; lstep = 1;
         K = (a.lmax >= lk0) ? a.lmax - lk0 + 1 : 0;
     }
-    // chain state (threads 0..63: one ring pair each)
+    // chain state (threads 0..63: one ring pair each, carried across chunks)
     double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;
     int E2 = 0, E3 = 0;
     double x = 0.0;
@@ -312,7 +360,9 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
         }
     }
     const double x2 = x * x;
-    for (int k0 = 0; k0 < K; k0 += A2M_TK) {
+    auto produce = [&](int k0, int b) {
+        double* lam = lam0 + b * A2M_TK * A2M_TP;
+        double* dat = dat0 + b * A2M_TK * TN;
         if (tid < A2M_TP) {
             const bool valid = myp < a.R;
             for (int kk = 0; kk < A2M_TK; kk++) {
@@ -322,24 +372,12 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
                     int l = lk0 + lstep * k;
                     if (a.spin == 0) {
                         v = scale2(c2, E2);
-                        if (k + 1 < K) {
-                            long long ci = d_alm_index(a.lmax, l, m);
-                            double t = fma(a.ra[ci], x2, a.rb[ci]);
-                            double nxt = fma(t, c2, a.rc[ci] * p2);
-                            p2 = c2; c2 = nxt;
-                            if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
-                        }
+                        if (k + 1 < K) step0(a.ra, a.rb, a.rc, d_alm_index(a.lmax, l, m), x2, c2, p2, E2);
                     } else {
                         if (k > 0) {
-                            long long ci = d_alm_index(a.lmax, l, m);
-                            double t = fma(a.wA0[ci], x, a.wAB0[ci]);
-                            double n2 = fma(t, c2, -a.wC0[ci] * p2);
-                            p2 = c2; c2 = n2;
-                            t = fma(a.wA1[ci], x, a.wAB1[ci]);
-                            double n3 = fma(t, c3, -a.wC1[ci] * p3);
-                            p3 = c3; c3 = n3;
-                            if (fabs(c2) > RESCALE_UP) { c2 *= RESCALE_DN; p2 *= RESCALE_DN; E2 += 500; }
-                            if (fabs(c3) > RESCALE_UP) { c3 *= RESCALE_DN; p3 *= RESCALE_DN; E3 += 500; }
+                            const long long ci = d_alm_index(a.lmax, l, m);
+                            step2(a.wA0, a.wAB0, a.wC0, ci, x, c2, p2, E2);
+                            step2(a.wA1, a.wAB1, a.wC1, ci, x, c3, p3, E3);
                         }
                         double v2 = scale2(c2, E2), v3 = scale2(c3, E3);
                         v = (((l - m) & 1) == q) ? -0.5 * (v2 + v3) : -0.5 * (v2 - v3);
@@ -349,8 +387,8 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
             }
         }
         // data tile: a[l][c] (or perm(a) for spin-2 rows of the other parity)
-        for (int i = tid; i < A2M_TK * A2M_TN; i += blockDim.x) {
-            int kk = i / A2M_TN, c = i % A2M_TN;
+        for (int i = tid; i < A2M_TK * TN; i += 128) {
+            int kk = i / TN, c = i % TN;
             int k = k0 + kk;
             long long cg = c0 + c;
             double v = 0.0;
@@ -375,28 +413,42 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
                         : sg * alm[((mp * 2 + comp) * a.nalm + li) * 2 + reim];
                 }
             }
-            dat[kk * A2M_TN + c] = v;
+            dat[kk * TN + c] = v;
         }
-        __syncthreads();
+    };
+
+    const int nch = (K + A2M_TK - 1) / A2M_TK;
+    if (producer && nch > 0) produce(0, 0);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ch++) {
+        const int cb = ch & 1;
+        if (producer) {
+            if (ch + 1 < nch) produce((ch + 1) * A2M_TK, cb ^ 1);
+        } else {
+            const double* lam = lam0 + cb * A2M_TK * A2M_TP;
+            const double* dat = dat0 + cb * A2M_TK * TN;
+            const int kn = min(A2M_TK, K - ch * A2M_TK);     // (the last chunk's rest is zero)
 #pragma unroll 4
-        for (int kk = 0; kk < A2M_TK; kk++) {
-            double lv[4], dv[4];
+            for (int kk = 0; kk < kn; kk++) {
+                double lv[PPT], dv[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) lv[i] = lam[kk * A2M_TP + ty + 16 * i];
+                for (int i = 0; i < PPT; i++) lv[i] = lam[kk * A2M_TP + ty + PG * i];
 #pragma unroll
-            for (int j = 0; j < 4; j++) dv[j] = dat[kk * A2M_TN + tx * 4 + j];
+                for (int j = 0; j < 4; j++) dv[j] = dat[kk * TN + tx * 4 + j];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+                for (int i = 0; i < PPT; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+                    for (int j = 0; j < 4; j++) acc[i][j] = fma(lv[i], dv[j], acc[i][j]);
+            }
         }
         __syncthreads();
     }
+    if (producer) return;
     double* Gq = G + ((long long)m * 2 + q) * qstride;
     const double gs = (m == 0) ? a.scale0 : a.scale;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        int p = p0 + ty + 16 * i;
+    for (int i = 0; i < PPT; i++) {
+        int p = p0 + ty + PG * i;
         if (p >= a.R) continue;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
@@ -432,22 +484,36 @@ static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double sca
 
 // work items [w0, w0 + nwork) of the plan's list (the list runs over m in
 // order, so one order's items are one range); accum adds into alm
-static cudaError_t launch_m2a_range(const sht_plan* p, const double* T, double* alm, int nmaps, double scale0,
-                                    double scale, int w0, int nwork, bool accum, cudaStream_t st)
+// one map2alm launch over work items [w0, w0 + nwork) with the column tile TN
+template <int TN>
+static cudaError_t launch_m2a_tn(const LegArgs& a, const double* T, double* alm, int nwork, int spin,
+                                 cudaStream_t st)
 {
-    if (nwork <= 0) return cudaSuccess;
-    size_t sm = (size_t)M2A_SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = (size_t)m2a_smem(spin, TN);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    long long nc = ncols(p, nmaps);
-    dim3 grid((unsigned)nwork, (unsigned)((nc + M2A_TN - 1) / M2A_TN));
-    LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a + w0);
-    a.accum = accum ? 1 : 0;
+    dim3 grid((unsigned)nwork, (unsigned)((a.ncol + TN - 1) / TN));
     prof_start("k_leg_m2a_f64", st);
-    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, a);
+    k_leg_m2a_f64<TN><<<grid, 256, sm, st>>>(T, alm, a);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();
+}
+static cudaError_t launch_m2a(const LegArgs& a, const double* T, double* alm, int nwork, int spin, cudaStream_t st)
+{
+    if (nwork <= 0) return cudaSuccess;
+    return a.ncol <= M2A_TN_SMALL ? launch_m2a_tn<M2A_TN_SMALL>(a, T, alm, nwork, spin, st)
+                                  : launch_m2a_tn<M2A_TN>(a, T, alm, nwork, spin, st);
+}
+
+// work items [w0, w0 + nwork) of the plan's list (the list runs over m in
+// order, so one order's items are one range); accum adds into alm
+static cudaError_t launch_m2a_range(const sht_plan* p, const double* T, double* alm, int nmaps, double scale0,
+                                    double scale, int w0, int nwork, bool accum, cudaStream_t st)
+{
+    LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a + w0);
+    a.accum = accum ? 1 : 0;
+    return launch_m2a(a, T, alm, nwork, p->spin, st);
 }
 
 cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* alm, int nmaps,
@@ -459,20 +525,10 @@ cudaError_t launch_legendre_m2a_f64(const sht_plan* p, const double* T, double* 
 cudaError_t launch_legendre_m2a_f64_comp(const sht_plan* p, const double* T, double* alm, int nmaps,
                                          double scale0, double scale, int csel, cudaStream_t st)
 {
-    const int nwork = p->nwork_m2a;
-    if (nwork <= 0) return cudaSuccess;
-    size_t sm = (size_t)M2A_SMEM;
-    cudaError_t e = cudaFuncSetAttribute(k_leg_m2a_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
     LegArgs a = make_args(p, nmaps, scale0, scale, p->work_m2a);
     a.csel = csel;
     a.ncol = a.pcol / 2;
-    dim3 grid((unsigned)nwork, (unsigned)((a.ncol + M2A_TN - 1) / M2A_TN));
-    prof_start("k_leg_m2a_f64", st);
-    k_leg_m2a_f64<<<grid, 256, sm, st>>>(T, alm, a);
-    prof_stop(st);
-    count_launch();
-    return cudaGetLastError();
+    return launch_m2a(a, T, alm, p->nwork_m2a, p->spin, st);
 }
 
 cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, double* alm, int nmaps,
@@ -482,20 +538,27 @@ cudaError_t launch_legendre_m2a_f64_order(const sht_plan* p, const double* T, do
     return launch_m2a_range(p, T, alm, nmaps, scale0, scale, w0, p->m2a_off[m0 + nm] - w0, accum, st);
 }
 
+template <int TN>
+static cudaError_t launch_a2m_tn(const LegArgs& a, const double* alm, double* G, int nwork, cudaStream_t st)
+{
+    const size_t sm = (size_t)(2 * (A2M_TK * A2M_TP + A2M_TK * TN)) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_leg_a2m_f64<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)nwork, (unsigned)((a.ncol + TN - 1) / TN));
+    prof_start("k_leg_a2m_f64", st);
+    k_leg_a2m_f64<TN><<<grid, 256, sm, st>>>(alm, G, a);
+    prof_stop(st);
+    count_launch();
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_a2m_range(const sht_plan* p, const double* alm, double* G, int nmaps, double scale0,
                                     double scale, int w0, int nwork, cudaStream_t st)
 {
     if (nwork <= 0) return cudaSuccess;
-    size_t sm = (size_t)(A2M_TK * A2M_TP + A2M_TK * A2M_TN) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_leg_a2m_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    long long nc = ncols(p, nmaps);
-    dim3 grid((unsigned)nwork, (unsigned)((nc + A2M_TN - 1) / A2M_TN));
-    prof_start("k_leg_a2m_f64", st);
-    k_leg_a2m_f64<<<grid, 256, sm, st>>>(alm, G, make_args(p, nmaps, scale0, scale, p->work_a2m + w0));
-    prof_stop(st);
-    count_launch();
-    return cudaGetLastError();
+    const LegArgs a = make_args(p, nmaps, scale0, scale, p->work_a2m + w0);
+    return a.ncol <= A2M_TN_SMALL ? launch_a2m_tn<A2M_TN_SMALL>(a, alm, G, nwork, st)
+                                  : launch_a2m_tn<A2M_TN>(a, alm, G, nwork, st);
 }
 
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
