@@ -41,7 +41,7 @@ SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split
 # kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
 # and lmax it grows in proportion to the map columns. Empty while the kernel
 # has changed since the last capture (the line then reports null).
-TRAFFIC_NCU = {"k_leg_a2m_tc": 5.555e9, "k_leg_m2a_tc": 5.988e9}
+TRAFFIC_NCU = {}
 TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
 
@@ -740,10 +740,13 @@ def main():
                         "avg_launch_ms": avg_ms, "algorithmic_flops_per_launch": flops}
         elif "leg" in name:
             # split form: `achieved` counts the method's own flops (4 per (l, m,
-            # ring pair, map)); the tensor cores execute SPLIT_PRODUCTS FP16
-            # slice products per term (kind::f16 runs at the bf16 rate), which
-            # `executed` reports against the same peak
+            # ring pair, map), every term); the tensor cores execute
+            # SPLIT_PRODUCTS FP16 slice products per term they evaluate
+            # (kind::f16 runs at the bf16 rate), which `executed` reports
+            # against the same peak; the ring optimisation leaves out the
+            # share 1 - kept of the terms (negligible lambda on polar rings)
             ach = flops / (avg_ms / 1e3) / 1e12
+            kept = plan.terms_kept()
             pk = peaks.get("bf16_tflops_sustained", 1400.0)
             traffic = None
             if name in TRAFFIC_NCU and (nside, lmax) == (TRAFFIC_NCU_AT["nside"], TRAFFIC_NCU_AT["lmax"]):
@@ -753,8 +756,10 @@ def main():
                         "traffic_source": "ncu capture at 128 maps, scaled by map columns" if traffic else None,
                         "peak_source": f"bf16 dense sustained ({peak_src}); the kernel runs inside a long step",
                         "algorithmic_flops_per_launch": flops, "avg_launch_ms": avg_ms,
-                        "executed": {"products_per_term": SPLIT_PRODUCTS, "flops_per_launch": SPLIT_PRODUCTS * flops,
-                                     "achieved": SPLIT_PRODUCTS * ach, "frac": SPLIT_PRODUCTS * ach / pk}}
+                        "executed": {"products_per_term": SPLIT_PRODUCTS, "terms_kept": kept,
+                                     "flops_per_launch": SPLIT_PRODUCTS * kept * flops,
+                                     "achieved": SPLIT_PRODUCTS * kept * ach,
+                                     "frac": SPLIT_PRODUCTS * kept * ach / pk}}
         else:
             byts = 8.0 * nmaps * plan.npix * 2
             ach = byts / (avg_ms / 1e3) / 1e9

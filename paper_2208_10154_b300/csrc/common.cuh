@@ -140,7 +140,18 @@ struct SplitTables {
     int4* sunits_m2a = nullptr; int nsunits_m2a = 0;
     int4* sunits_a2m = nullptr; int nsunits_a2m = 0;
     long long img_chunks_m2a = 0, img_chunks_a2m = 0;
+    // ring optimisation (spin 0): orders m are contracted only over the ring
+    // pairs p >= pfirst[m] (a multiple of 32, nondecreasing in m); the polar
+    // pairs before it hold |lambda_lm| < SPLIT_LAMBDA_EPS for every l. mlim[p]:
+    // the highest order whose ring spectra pair p takes part in. Null: no
+    // ring pair is skipped.
+    int* pfirst = nullptr;
+    int* mlim = nullptr;
 };
+
+// |lambda_lm(theta)| below which an (m, ring pair) term of the split form is
+// skipped (lambda peaks at O(1): a dropped term is below 1e-30 of it)
+constexpr float SPLIT_LAMBDA_EPS = 1e-30f;
 
 }  // namespace sht
 
@@ -158,6 +169,8 @@ struct sht_plan {
     std::vector<sht::FftLen> h_fft;
     std::vector<sht::FftLen> h_fft_s;       // split form's FFT recipes
     std::vector<sht::FftClass> h_fcls;
+    std::vector<int> h_pfirst;              // split form: host copy of s.pfirst (empty: none)
+    double terms_kept = 1.0;                // share of the (m, l, ring pair) terms contracted
     size_t table_bytes = 0;
     // Legendre work lists (m, q, tile, 0) for the FP64 kernels
     int4* work_m2a = nullptr; int nwork_m2a = 0;

@@ -316,7 +316,7 @@ __device__ __forceinline__ float2 df_norm(float hi, float lo)
 template <bool SPLIT>
 __global__ void __launch_bounds__(128)
 k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const PairGeom* __restrict__ pairs,
-                 int R_, int mmax, long long ncol, int nmc)
+                 int R_, int mmax, long long ncol, int nmc, const int* __restrict__ mlim)
 {
     const int p = blockIdx.x;
     const int mc = blockIdx.y * blockDim.x + threadIdx.x;
@@ -334,10 +334,13 @@ k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const Pa
         const float2* G = (const float2*)Gv;      // (re, im) of one complex column, FP32
         const float4* T = (const float4*)Tv;      // (re hi, re lo, im hi, im lo)
         float4* D = (float4*)Dv;
+        // G holds the orders m <= ml of this ring pair (the split contraction
+        // skips the others, whose lambda is negligible here)
+        const int ml = mlim ? min(mmax, mlim[p]) : mmax;
         auto fold = [&](int j, int slot) -> float4 {
             float rh = 0.0f, rl = 0.0f, ih = 0.0f, il = 0.0f;
             bool odd = false;
-            for (int m = j; m <= mmax; m += N) {
+            for (int m = j; m <= ml; m += N) {
                 // w = w_m sigma^k: the products w G are exact in FP32
                 const float w = (m ? 2.0f : 1.0f) * ((neg && odd) ? -1.0f : 1.0f);
                 const float2 v = G[idx(m, slot) >> 1];
@@ -361,7 +364,7 @@ k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const Pa
             df_add(xi, xil, -sj * Bc.z);
             xil -= sj * Bc.w;
             bool odd = false;
-            for (int m = j; m <= mmax; m += N) {
+            for (int m = j; m <= ml; m += N) {
                 // f = (N or N / 2) sigma^k0, exact in FP32
                 const float f = (eq ? 0.5f : 1.0f) * (float)N * ((neg && odd) ? -1.0f : 1.0f);
                 const float fr = xr * f, fi = xi * f;
@@ -380,13 +383,14 @@ k_alias_residual(const void* __restrict__ Tv, const void* Gv, void* Dv, const Pa
                 odd = !odd;
             }
         };
+        // (D is written for the orders m <= ml only: the contraction reads no other)
         for (int slot = 0; slot < (eq ? 1 : 2); slot++) {
-            for (int j = 0; j <= jmax; j++) {
+            for (int j = 0; j <= min(jmax, ml); j++) {
                 const int jp = (N - j) % N;
                 const float4 Bj = fold(j, slot);
-                const float4 Bjp = (jp == j) ? Bj : (jp <= mmax ? fold(jp, slot) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+                const float4 Bjp = (jp == j) ? Bj : (jp <= ml ? fold(jp, slot) : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
                 unfold(j, slot, Bj, Bjp, neg && j);
-                if (jp != j && jp <= mmax) unfold(jp, slot, Bjp, Bj, neg && jp);
+                if (jp != j && jp <= ml) unfold(jp, slot, Bjp, Bj, neg && jp);
             }
         }
     } else {
@@ -505,13 +509,15 @@ cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, cons
 // bits: the quanta of the split map2alm. grid = ((mmax + 1) * 2, column
 // blocks of 256)
 __global__ void __launch_bounds__(256)
-k_colmax_T(const float2* __restrict__ T, unsigned int* __restrict__ colmax, int R_, long long ncol)
+k_colmax_T(const float2* __restrict__ T, unsigned int* __restrict__ colmax, int R_, long long ncol,
+           const int* __restrict__ pfirst)
 {
     const long long c = (long long)blockIdx.y * blockDim.x + threadIdx.x;
     if (c >= ncol) return;
     const float2* t = T + (long long)blockIdx.x * R_ * ncol + c;
     float mx = 0.0f;
-    for (int p = 0; p < R_; p++) mx = fmaxf(mx, fabsf(t[(long long)p * ncol].x));
+    // (the ring pairs the order's contraction reads: from pfirst[m])
+    for (int p = pfirst ? pfirst[blockIdx.x >> 1] : 0; p < R_; p++) mx = fmaxf(mx, fabsf(t[(long long)p * ncol].x));
     colmax[(long long)blockIdx.x * ncol + c] = __float_as_uint(mx);
 }
 
@@ -523,9 +529,9 @@ cudaError_t launch_alias_residual(const sht_plan* p, const void* T, const void* 
     dim3 grid(p->R, (nmc + 127) / 128);
     prof_start("k_alias_residual", st);
     if (split)
-        k_alias_residual<true><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc);
+        k_alias_residual<true><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc, p->s.mlim);
     else
-        k_alias_residual<false><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc);
+        k_alias_residual<false><<<grid, 128, 0, st>>>(T, G, D, p->t.pairs, p->R, p->mmax, ncols(p, nmaps), nmc, nullptr);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();
@@ -536,7 +542,7 @@ cudaError_t launch_colmax_T(const sht_plan* p, const float2* T, unsigned int* co
     const long long nc = ncols(p, nmaps);
     dim3 grid((unsigned)((p->mmax + 1) * 2), (unsigned)((nc + 255) / 256));
     prof_start("k_colmax_T", st);
-    k_colmax_T<<<grid, 256, 0, st>>>(T, colmax, p->R, nc);
+    k_colmax_T<<<grid, 256, 0, st>>>(T, colmax, p->R, nc, p->s.pfirst);
     prof_stop(st);
     count_launch();
     return cudaGetLastError();

@@ -694,7 +694,7 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
                const int* __restrict__ cls, int ncls, const PairGeom* __restrict__ pairs,
                const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw, long long ctwp, int ntwp, int M,
                int R_, int mmax,
-               long long npix, long long ncol, int nmc, int mpc, int pf)
+               long long npix, long long ncol, int nmc, int mpc, int pf, const int* __restrict__ mlim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
@@ -726,6 +726,10 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         const PairGeom g = pairs[p];
         const FftLen f = ffts[g.fft];
         const int N = g.n;
+        // the orders this ring pair takes part in (the contraction skips the
+        // others, whose lambda is negligible on this ring): T and the column
+        // maxima are written for m <= ml only
+        const int ml = mlim ? min(mmax, mlim[p]) : mmax;
         // the next ring pair's rows into L2 while this one is transformed (pf:
         // the map is 16-byte aligned; rows start at even pixels, N = 4i)
         if (pf && ip + 1 < iend && threadIdx.x < 2 * nb) {
@@ -779,13 +783,13 @@ k_fftc_forward(const double* __restrict__ map, float2* __restrict__ T, unsigned 
         for (int jj = 0; jj < FWD_MJ; jj++) {
             const int m = et + jj * ent;
             PH[jj] = make_float2(1.0f, 0.0f); PL[jj] = make_float2(0.0f, 0.0f);
-            if (m <= mmax && g.phi0 != 0.0) phase(tb, g.fft, N, m, true, PH[jj], PL[jj]);
+            if (m <= ml && g.phi0 != 0.0) phase(tb, g.fft, N, m, true, PH[jj], PL[jj]);
         }
         const float osc = es ? osc1 : osc0;
 #pragma unroll
         for (int jj = 0; jj < FWD_MJ; jj++) {
             const int m = et + jj * ent;
-            if (m > mmax) break;
+            if (m > ml) break;
             if (es < nb) {
                 const int j = (m < N) ? m : m % N, jm = j ? N - j : 0;
                 const cx a = buf[es * P + fft_pad(j)], b = cconjc(buf[es * P + fft_pad(jm)]);
@@ -840,7 +844,8 @@ __global__ void __launch_bounds__(NT, 512 / NT)
 k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int* __restrict__ cls, int ncls,
                 const PairGeom* __restrict__ pairs, const FftLen* __restrict__ ffts, FftTabsF tb, long long ctw,
                 long long ctwp, int ntwp,
-                int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc)
+                int M, int R_, int mmax, long long npix, long long ncol, int nmc, int mpc,
+                const int* __restrict__ mlim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cx* buf = reinterpret_cast<cx*>(smem_raw);
@@ -863,6 +868,9 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
         const FftLen f = ffts[g.fft];
         const int N = g.n;
         const float* g0 = G + (long long)p * ncol + mc0 * 2;
+        // the orders this ring pair takes part in (the contraction skips the
+        // others: their lambda is negligible on this ring)
+        const int ml = mlim ? min(mmax, mlim[p]) : mmax;
         // E and O of the two columns at order m (16-byte loads when aligned)
         auto load_eo = [&](int m, float4& E4, float4& O4) {
             const float* e = g0 + (long long)m * 2 * qstride;
@@ -930,7 +938,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
                         const int m = t ? (j ? N - j : 0) : j;
                         E[u][t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); O[u][t] = E[u][t];
                         PH[u][t] = make_float2(1.0f, 0.0f); PL[u][t] = make_float2(0.0f, 0.0f);
-                        if (j <= N / 2 && m <= mmax) {
+                        if (j <= N / 2 && m <= ml) {
                             load_eo(m, E[u][t], O[u][t]);
                             if (g.phi0 != 0.0) phase(tb, g.fft, N, m, false, PH[u][t], PL[u][t]);
                         }
@@ -947,7 +955,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
 #pragma unroll
                         for (int s = 0; s < 2; s++) {
                             Bn[t][s] = czero(); Bs[t][s] = czero();
-                            if (m <= mmax) term(m, E[u][t], O[u][t], PH[u][t], PL[u][t], s, Bn[t][s], Bs[t][s]);
+                            if (m <= ml) term(m, E[u][t], O[u][t], PH[u][t], PL[u][t], s, Bn[t][s], Bs[t][s]);
                         }
                     }
                     emit(j, Bn, Bs);
@@ -960,7 +968,7 @@ k_fftc_backward(const float* __restrict__ G, double* __restrict__ map, const int
 #pragma unroll
                 for (int t = 0; t < 2; t++) {
                     cx sn[2] = {czero(), czero()}, ss[2] = {czero(), czero()};
-                    for (int m = jj[t]; m <= mmax; m += N) {
+                    for (int m = jj[t]; m <= ml; m += N) {
                         float4 E4, O4;
                         load_eo(m, E4, O4);
                         float2 ph = make_float2(1.0f, 0.0f), pl = make_float2(0.0f, 0.0f);
@@ -1128,11 +1136,11 @@ cudaError_t launch_fft_forward_split(const sht_plan* p, const double* map, float
         if (k.nt == 512)
             k_fftc_forward<512><<<grid, k.nt, k.sm, ss>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
-                                                          p->npix, nc, nmc, k.mpc, pf);
+                                                          p->npix, nc, nmc, k.mpc, pf, p->s.mlim);
         else
             k_fftc_forward<256><<<grid, k.nt, k.sm, ss>>>(map, T, colmax, p->c.cls_pairs + c.off, c.cnt, p->t.pairs,
                                                           p->c.fft_s, tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax,
-                                                          p->npix, nc, nmc, k.mpc, pf);
+                                                          p->npix, nc, nmc, k.mpc, pf, p->s.mlim);
         count_launch();
     }
     e = cudaGetLastError();
@@ -1160,11 +1168,11 @@ cudaError_t launch_fft_backward_f32(const sht_plan* p, const float* G, double* m
         if (k.nt == 512)
             k_fftc_backward<512><<<grid, k.nt, k.sm, ss>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
                                                            tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
-                                                           ncols(p, nmaps), nmc, k.mpc);
+                                                           ncols(p, nmaps), nmc, k.mpc, p->s.mlim);
         else
             k_fftc_backward<256><<<grid, k.nt, k.sm, ss>>>(G, map, p->c.cls_pairs + c.off, c.cnt, p->t.pairs, p->c.fft_s,
                                                            tabs(p), c.tw, c.twp, ntwp, c.m, p->R, p->mmax, p->npix,
-                                                           ncols(p, nmaps), nmc, k.mpc);
+                                                           ncols(p, nmaps), nmc, k.mpc, p->s.mlim);
         count_launch();
     }
     e = cudaGetLastError();

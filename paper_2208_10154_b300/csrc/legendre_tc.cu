@@ -112,6 +112,7 @@ struct TcArgs {
     const float* rowmax;       // map2alm: max_p |mu_l(theta_p) 2^E| per packed (l, m)
     const float* pairmax;      // alm2map: max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
     const float* colmax;       // data: max |x| per [m][q][col]
+    const int* pfirst;         // spin 0: first ring pair contracted for order m (multiple of 32; null: 0)
     // spin 2: normalised Wigner recurrences, per s = +2 / -2 and packed (l, m):
     //   mu_l = (s2A x + s2B) mu_{l-1} - mu_{l-2},  s lambda_l = d_l mu_l (d_l the same for both s)
     const double* s2A[2];
@@ -445,7 +446,9 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const long long c0 = (long long)blockIdx.y * TC_M;
     const int l_first = m + q;
     const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;   // l rows of slot q
-    const int nrow_all = M2A ? nl : a.R;           // lambda rows of (m, q)
+    // ring pairs before pb hold negligible lambda for this order (spin 0)
+    const int pb = (!S2 && a.pfirst != nullptr) ? a.pfirst[m] : 0;
+    const int nrow_all = M2A ? nl : a.R - pb;      // lambda rows of (m, q) (alm2map: ring pairs from pb)
     // tile t of the CTA: first lambda row, rows, 32-row pieces, MMA N
     auto t_n0 = [&](int t) { return (tile0 + t) * TC_N; };
     auto t_nrows = [&](int t) { return min(TC_N, nrow_all - t_n0(t)); };
@@ -454,7 +457,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const int n0 = t_n0(0), nrows = t_nrows(0);    // map2alm: its only tile
     // contraction length: spin 0 over ring pairs (map2alm) or the l of slot q;
     // spin 2 over ring pairs or all l >= m, each twice (v+ and v- chunks)
-    const int K = M2A ? a.R : (S2 ? a.lmax - m + 1 : nl);
+    const int K = M2A ? a.R - pb : (S2 ? a.lmax - m + 1 : nl);
     const int nunit = (K + KC - 1) / KC;           // 32-wide units of raw data
     const int nch = S2 ? 2 * nunit : nunit;        // MMA chunks (pipeline stages) per tile
     const int nchunk = ntl * nch;                  // chunks of the CTA: chunk g = tile g / nch, kc = g % nch
@@ -541,7 +544,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             auto copy = [&](int c) {                    // c: chunk of the CTA
                 const int s = c % NST;
                 const int t = c / nch, kc = c - t * nch;
-                const long long ci = (S2 && !M2A) ? (kc >> 1) : kc;
+                const long long ci = (S2 && !M2A) ? (kc >> 1) : kc + (M2A ? pb / KC : 0);
                 mbar_arrive_expect_tx(&sh.full[s], A_BYTES + t_npieces(t) * SCR_BYTES);
                 bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
             };
@@ -690,7 +693,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 }
             } else if constexpr (M2A) {
                 // lane = ring pair (k), walking the 32 l rows of piece j
-                const int p = kc * KC + lane;
+                const int p = pb + kc * KC + lane;
                 df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x2 = {0.0f, 0.0f};
                 int E = 0;
                 const bool live = p < a.R;
@@ -779,7 +782,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 // coefficients of those 32 l are loaded once (lane k holds l_k)
                 // and broadcast with shuffles
                 const int r = j * PR + lane;
-                const int p = n0t + r;
+                const int p = pb + n0t + r;
                 const bool live = r < nrt;
                 df cur = {0.0f, 0.0f}, prev = {0.0f, 0.0f}, x2 = {0.0f, 0.0f};
                 int E = 0, pe = 0;
@@ -938,7 +941,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const int nmt = t_nmma(t), nrt = t_nrows(t), n0t = t_n0(t);
                 {   // the tile's row factors; the load overlaps the span drains
                     const int rl = quarter * 32 + lane;
-                    const float pm = (rl < nrt) ? a.pairmax[((long long)m * 2 + q) * a.R + n0t + rl] : 0.0f;
+                    const float pm = (rl < nrt) ? a.pairmax[((long long)m * 2 + q) * a.R + pb + n0t + rl] : 0.0f;
                     for (int j = 0; j < nspan && dok; j++) drain(t * nspan + j, nmt);
                     rsc[(t & 1) * TC_N + rl] = (pm > 0.0f) ? ldexpf(1.0f, quantum_exp(pm, a.Q)) : 0.0f;
                     named_bar_sync(3, 128);    // drain warps only
@@ -967,7 +970,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 // next write to this half is two barriers later)
                 if (cok && dok) {
                     const float4* rs4 = reinterpret_cast<const float4*>(rsc + (t & 1) * TC_N);
-                    float* gp = Gq + (long long)n0t * a.ncol;
+                    float* gp = Gq + (long long)(pb + n0t) * a.ncol;
 #pragma unroll
                     for (int r4 = 0; r4 < TC_N / 4; r4++) {
                         const float4 f = rs4[r4];
@@ -1353,6 +1356,7 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.s2d2 = p->s.s2d2; a.s2d64 = p->s.s2d64;
     a.rowmax = (const float*)p->s.rowmax_bits;
     a.pairmax = p->s.pairmax;
+    a.pfirst = p->spin ? nullptr : p->s.pfirst;
     a.colmax = colmax;
     a.err = p->s.err;
     a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;

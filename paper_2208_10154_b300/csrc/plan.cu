@@ -567,6 +567,73 @@ static float slice_range(double K)
 // spin 2 stores two chunks per unit (T_q + P(T_{1-q}) and T_q - P(T_{1-q})).
 // alm2map: K = the l of slot q (spin 0) or all l >= m (spin 2, one chunk per
 // unit shared by the v+ and v- chunks of the contraction).
+// Ring optimisation (Sec. 3.1, Implementation detail: for each m the rings
+// where P_lm has an extremely low amplitude are left out, in the Legendre
+// step and in the FFT mapping). Near the poles lambda_lm(theta)
+// ~ sin^m(theta) underflows for large m, so for each order m the leading ring
+// pairs p < pfirst[m] (from the north pole) where max_l |lambda_lm| stays below
+// SPLIT_LAMBDA_EPS for both parities are skipped: map2alm contracts only the
+// 32-wide chunks of ring pairs from pfirst[m], alm2map computes G only for
+// those ring pairs, and the ring FFTs and the Fourier-domain residual use the
+// orders m <= mlim[p] of ring pair p. pfirst is made nondecreasing in m (the
+// smallest first pair of this and every higher order) and rounded down to a
+// multiple of 32, so {m : p >= pfirst[m]} = {m <= mlim[p]}. A skipped term is
+// below 1e-30 of lambda's O(1) peak times the data, far below FP64 rounding
+// of the outputs. SHT_RING_SKIP=0 turns it off. Spin-0 split plans only.
+static cudaError_t build_ring_skip(sht_plan* p, size_t* acc)
+{
+    const int mmax = p->mmax, R = p->R, KCH = 32;
+    p->h_pfirst.assign((size_t)mmax + 1, 0);
+    const char* env = std::getenv("SHT_RING_SKIP");
+    if (env && std::atoi(env) == 0) return cudaSuccess;
+    std::vector<float> pm((size_t)(mmax + 1) * 2 * R);
+    cudaError_t e = cudaMemcpy(pm.data(), p->s.pairmax, pm.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    int run = R - 1;                     // the equator pair is never skipped
+    for (int m = mmax; m >= 0; m--) {
+        int p0 = 0;
+        while (p0 < R - 1 && std::max(pm[((size_t)m * 2 + 0) * R + p0], pm[((size_t)m * 2 + 1) * R + p0]) <
+                                 SPLIT_LAMBDA_EPS)
+            p0++;
+        run = std::min(run, p0);
+        p->h_pfirst[m] = run / KCH * KCH;
+    }
+    p->h_pfirst[0] = 0;                  // (lambda_00 is constant: order 0 keeps every pair)
+    double kept = 0.0, all = 0.0;
+    for (int m = 0; m <= mmax; m++) {
+        const double nl = (p->lmax >= m) ? (double)(p->lmax - m + 1) : 0.0;
+        kept += nl * (R - p->h_pfirst[m]);
+        all += nl * R;
+    }
+    p->terms_kept = all > 0.0 ? kept / all : 1.0;
+    std::vector<int> ml((size_t)R, 0);
+    for (int q = 0, m = 0; q < R; q++) {
+        while (m < mmax && p->h_pfirst[m + 1] <= q) m++;
+        ml[q] = m;
+    }
+    if ((e = upload(&p->s.pfirst, p->h_pfirst, acc)) != cudaSuccess) return e;
+    if ((e = upload(&p->s.mlim, ml, acc)) != cudaSuccess) return e;
+    // alm2map work items over the ring pairs [pfirst[m], R) of each order
+    const int TM = split_row_tile(), GA = split_a2m_tiles();
+    std::vector<int4> w2;
+    std::vector<int4> old((size_t)p->s.nwork_a2m);
+    if (!old.empty() &&
+        (e = cudaMemcpy(old.data(), p->s.work_a2m, old.size() * sizeof(int4), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return e;
+    int last = -1;
+    for (const int4& w : old) {          // keep each (m, q)'s checkpoint block, one pass per (m, q)
+        const int mq = w.x * 2 + w.y;
+        if (mq == last) continue;
+        last = mq;
+        const int ntR = (R - p->h_pfirst[w.x] + TM - 1) / TM;
+        for (int t = 0; t < ntR; t += GA) w2.push_back(make_int4(w.x, w.y, t | (std::min(GA, ntR - t) << 16), w.w));
+    }
+    cudaFree(p->s.work_a2m);
+    p->s.work_a2m = nullptr;
+    p->s.nwork_a2m = (int)w2.size();
+    return upload(&p->s.work_a2m, w2, acc);
+}
+
 static cudaError_t build_slice_lists(sht_plan* p, size_t* acc)
 {
     const int lmax = p->lmax, mmax = p->mmax, KCH = 32;
@@ -580,7 +647,9 @@ static cudaError_t build_slice_lists(sht_plan* p, size_t* acc)
             const int nl = (lmax >= m + q) ? (lmax - m - q) / 2 + 1 : 0;
             bm[mq] = (int)cm;
             if (nl > 0) {
-                for (int u = 0; u < nuR; u++) um.push_back(make_int4(m, q, u, (int)(cm + (p->spin ? 2 * u : u))));
+                // (units before the order's first ring pair are never contracted)
+                const int u0 = p->h_pfirst.empty() ? 0 : p->h_pfirst[m] / KCH;
+                for (int u = u0; u < nuR; u++) um.push_back(make_int4(m, q, u, (int)(cm + (p->spin ? 2 * u : u))));
                 cm += p->spin ? 2 * nuR : nuR;
             }
             const int Ka = p->spin ? (lmax >= m ? lmax - m + 1 : 0) : nl;
@@ -792,6 +861,7 @@ static cudaError_t build_split_tables(sht_plan* p)
     e = run_split_tables(p, d_base);
     cudaFree(d_base);
     if (e != cudaSuccess) return e;
+    if ((e = build_ring_skip(p, &acc)) != cudaSuccess) return e;
     p->s.Q_m2a = slice_range((double)R);
     p->s.Q_a2m = slice_range((double)(lmax / 2 + 1));
     if ((e = build_slice_lists(p, &acc)) != cudaSuccess) return e;
@@ -812,7 +882,8 @@ static void free_tables(sht_plan* p)
     for (void* q : cp) if (q) cudaFree(q);
     void* sp[] = {p->s.nA, p->s.nB, p->s.nc, p->s.nc64, p->s.nc2, p->s.ck, p->s.ck_exp, p->s.rowmax_bits, p->s.pairmax, p->s.err,
                   p->s.work_m2a, p->s.work_a2m, p->s.s2A[0], p->s.s2A[1], p->s.s2B[0], p->s.s2B[1], p->s.s2d2,
-                  p->s.s2d64, p->s.img_base_m2a, p->s.img_base_a2m, p->s.sunits_m2a, p->s.sunits_a2m};
+                  p->s.s2d64, p->s.img_base_m2a, p->s.img_base_a2m, p->s.sunits_m2a, p->s.sunits_a2m,
+                  p->s.pfirst, p->s.mlim};
     for (void* q : sp) if (q) cudaFree(q);
     for (cudaEvent_t ev : p->hp_ev) if (ev) cudaEventDestroy(ev);
     if (p->hp_h2d) cudaStreamDestroy(p->hp_h2d);
@@ -1078,6 +1149,7 @@ int sht_plan_spin(const sht_plan* p) { return p ? p->spin : 0; }
 int sht_plan_precision(const sht_plan* p) { return p ? p->precision : 0; }
 long long sht_plan_npix(const sht_plan* p) { return p ? p->npix : 0; }
 long long sht_plan_nalm(const sht_plan* p) { return p ? p->nalm : 0; }
+double sht_plan_terms_kept(const sht_plan* p) { return p ? p->terms_kept : 0.0; }
 size_t sht_plan_device_bytes(const sht_plan* p)
 {
     return p ? p->table_bytes + p->host_dev_in_bytes + p->host_dev_out_bytes + p->host_ws_bytes : 0;

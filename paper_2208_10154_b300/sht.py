@@ -63,6 +63,8 @@ def load() -> ctypes.CDLL:
             f.restype = LL
         lib.sht_plan_device_bytes.argtypes = [P]
         lib.sht_plan_device_bytes.restype = S
+        lib.sht_plan_terms_kept.argtypes = [P]
+        lib.sht_plan_terms_kept.restype = ctypes.c_double
         lib.sht_alm2map.argtypes = [P, P, P, I, P, S, P]
         lib.sht_map2alm.argtypes = [P, P, P, I, I, P, S, P]
         lib.sht_alm2map_adjoint.argtypes = [P, P, P, I, P, S, P]
@@ -220,6 +222,10 @@ class Plan:
     def device_bytes(self) -> int:
         """Device memory held by the plan itself (tables, host-path staging)."""
         return int(load().sht_plan_device_bytes(self.handle))
+
+    def terms_kept(self) -> float:
+        """Share of the (m, l, ring pair) Legendre terms the contraction evaluates."""
+        return float(load().sht_plan_terms_kept(self.handle))
 
     def workspace_bytes(self, nmaps: int, niter: int = 0) -> int:
         return sht_workspace_bytes(self.handle, nmaps, niter)
