@@ -140,7 +140,7 @@ struct SplitTables {
     int4* sunits_m2a = nullptr; int nsunits_m2a = 0;
     int4* sunits_a2m = nullptr; int nsunits_a2m = 0;
     long long img_chunks_m2a = 0, img_chunks_a2m = 0;
-    // ring optimisation (spin 0): orders m are contracted only over the ring
+    // ring optimisation: orders m are contracted only over the ring
     // pairs p >= pfirst[m] (a multiple of 32, nondecreasing in m); the polar
     // pairs before it hold |lambda_lm| < SPLIT_LAMBDA_EPS for every l. mlim[p]:
     // the highest order whose ring spectra pair p takes part in. Null: no

@@ -112,7 +112,7 @@ struct TcArgs {
     const float* rowmax;       // map2alm: max_p |mu_l(theta_p) 2^E| per packed (l, m)
     const float* pairmax;      // alm2map: max_{l in q} |lambda_lm(theta_p)| per [m][q][p]
     const float* colmax;       // data: max |x| per [m][q][col]
-    const int* pfirst;         // spin 0: first ring pair contracted for order m (multiple of 32; null: 0)
+    const int* pfirst;         // first ring pair contracted for order m (multiple of 32; null: 0)
     // spin 2: normalised Wigner recurrences, per s = +2 / -2 and packed (l, m):
     //   mu_l = (s2A x + s2B) mu_{l-1} - mu_{l-2},  s lambda_l = d_l mu_l (d_l the same for both s)
     const double* s2A[2];
@@ -446,8 +446,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
     const long long c0 = (long long)blockIdx.y * TC_M;
     const int l_first = m + q;
     const int nl = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;   // l rows of slot q
-    // ring pairs before pb hold negligible lambda for this order (spin 0)
-    const int pb = (!S2 && a.pfirst != nullptr) ? a.pfirst[m] : 0;
+    // ring pairs before pb hold negligible lambda for this order
+    const int pb = (a.pfirst != nullptr) ? a.pfirst[m] : 0;
     const int nrow_all = M2A ? nl : a.R - pb;      // lambda rows of (m, q) (alm2map: ring pairs from pb)
     // tile t of the CTA: first lambda row, rows, 32-row pieces, MMA N
     auto t_n0 = [&](int t) { return (tile0 + t) * TC_N; };
@@ -544,7 +544,8 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
             auto copy = [&](int c) {                    // c: chunk of the CTA
                 const int s = c % NST;
                 const int t = c / nch, kc = c - t * nch;
-                const long long ci = (S2 && !M2A) ? (kc >> 1) : kc + (M2A ? pb / KC : 0);
+                // (map2alm: K starts at ring pair pb, (S2 ? 2 : 1) image chunks per unit)
+                const long long ci = M2A ? kc + (S2 ? 2 : 1) * (pb / KC) : (S2 ? (kc >> 1) : kc);
                 mbar_arrive_expect_tx(&sh.full[s], A_BYTES + t_npieces(t) * SCR_BYTES);
                 bulk_copy_g2s(smem_base + s * STAGE_BYTES, img0 + ci * a.ntile * A_BYTES, A_BYTES, &sh.full[s]);
             };
@@ -641,7 +642,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 // lane = ring pair (k) of unit kc / 2, walking the 64 l that hold the
                 // 32 rows (slot q) of piece j with the recurrence of s = (kc odd ? -2 : +2)
                 const int sg = kc & 1;
-                const int p = (kc >> 1) * KC + lane;
+                const int p = pb + (kc >> 1) * KC + lane;
                 const int J = (n0t >> 5) + j;            // 32-row block of the slot's rows
                 const int L = m + 64 * J;               // first l of the walk (checkpoint block 2J)
                 const int lck = max(L, l0s);            // l of the checkpointed value
@@ -730,7 +731,7 @@ k_leg_tc(void* __restrict__ dst, TcArgs a)
                 const int sg = kc & 1;
                 const int u = kc >> 1;
                 const int r = j * PR + lane;
-                const int p = n0t + r;
+                const int p = pb + n0t + r;
                 const bool live = r < nrt;
                 const int L = m + KC * u;               // first l of the unit (checkpoint block u)
                 const int lck = max(L, l0s);
@@ -1356,7 +1357,7 @@ static TcArgs make_tc(const sht_plan* p, int nmaps, const float* colmax, float Q
     a.s2d2 = p->s.s2d2; a.s2d64 = p->s.s2d64;
     a.rowmax = (const float*)p->s.rowmax_bits;
     a.pairmax = p->s.pairmax;
-    a.pfirst = p->spin ? nullptr : p->s.pfirst;
+    a.pfirst = p->s.pfirst;
     a.colmax = colmax;
     a.err = p->s.err;
     a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;

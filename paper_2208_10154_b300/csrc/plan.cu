@@ -579,7 +579,8 @@ static float slice_range(double K)
 // smallest first pair of this and every higher order) and rounded down to a
 // multiple of 32, so {m : p >= pfirst[m]} = {m <= mlim[p]}. A skipped term is
 // below 1e-30 of lambda's O(1) peak times the data, far below FP64 rounding
-// of the outputs. SHT_RING_SKIP=0 turns it off. Spin-0 split plans only.
+// of the outputs. SHT_RING_SKIP=0 turns it off. Split plans (spin 2: the
+// maxima over both slots are those of s = +2 and -2).
 static cudaError_t build_ring_skip(sht_plan* p, size_t* acc)
 {
     const int mmax = p->mmax, R = p->R, KCH = 32;
@@ -768,6 +769,7 @@ static cudaError_t build_split_tables_s2(sht_plan* p)
     e = run_split_tables(p, d_base);
     cudaFree(d_base);
     if (e != cudaSuccess) return e;
+    if ((e = build_ring_skip(p, &acc)) != cudaSuccess) return e;
     // each contraction runs twice over its range (v+ and v- chunks)
     p->s.Q_m2a = slice_range(2.0 * R);
     p->s.Q_a2m = slice_range(2.0 * (lmax + 1));

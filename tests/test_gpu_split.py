@@ -194,7 +194,8 @@ def test_split_iteration(orc, sht, nside, lmax, spin, niter):
     assert colerr(got, orc.map2alm(h, nside, lmax, spin=spin, niter=niter)) < TOL
 
 
-def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch):
+@pytest.mark.parametrize("spin", [0, 2])
+def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch, spin):
     """Sec. 3.1 (Implementation detail), the ring optimisation: a spin-0 split
     plan leaves out, per order m, the polar ring pairs where |lambda_lm| <
     1e-30 for every l, in the contraction and in the FFT order mapping. At
@@ -203,18 +204,27 @@ def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch):
     the split form's own error, for alm2map and for map2alm with the
     Fourier-domain iteration (whose residual folds only the kept orders)."""
     nside, lmax, nmaps = 256, 511, 3
-    plan = sht.Plan(nside, lmax, None, 0, "split")
+    plan = sht.Plan(nside, lmax, None, spin, "split")
     monkeypatch.setenv("SHT_RING_SKIP", "0")
-    full = sht.Plan(nside, lmax, None, 0, "split")
+    full = sht.Plan(nside, lmax, None, spin, "split")
     monkeypatch.delenv("SHT_RING_SKIP")
     assert full.terms_kept() == 1.0
     assert 0.5 < plan.terms_kept() < 0.95
-    a = torch.from_numpy(inputs.gaussian_alm(11, nmaps, 1, lmax)).cuda()
+    ncomp = 2 if spin else 1
+    cls = None
+    if spin:
+        cl = inputs.cl_inv_llp1(lmax)
+        cls = np.stack([cl, 0.01 * cl])
+    a = torch.from_numpy(inputs.gaussian_alm(11, nmaps, ncomp, lmax, cls=cls)).cuda()
     m_skip, m_full = plan.alm2map(a), full.alm2map(a)
     assert colerr(m_skip.cpu().numpy(), m_full.cpu().numpy()) < 1e-9
     for niter in (0, 2):
         b_skip = plan.map2alm(m_full, niter=niter).cpu().numpy()
         b_full = full.map2alm(m_full, niter=niter).cpu().numpy()
         assert np.all(np.isfinite(b_skip))
-        assert colerr(b_skip, b_full) < 1e-7
+        assert colerr(b_skip, b_full) < 2e-7
+    if spin:                             # one component: half of the contraction
+        e_skip = plan.map2alm_eb(m_full, "B").cpu().numpy()
+        e_full = full.map2alm_eb(m_full, "B").cpu().numpy()
+        assert colerr(e_skip, e_full) < 2e-7
     plan.device_status()
