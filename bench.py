@@ -41,7 +41,7 @@ SPLIT_PRODUCTS = 10          # tensor-core products per output term in the split
 # kernel build at nside 512, lmax 1023, 128 maps (256 columns); at fixed nside
 # and lmax it grows in proportion to the map columns. Empty while the kernel
 # has changed since the last capture (the line then reports null).
-TRAFFIC_NCU = {}
+TRAFFIC_NCU = {"k_leg_a2m_tc": 4.956e9, "k_leg_m2a_tc": 4.711e9}
 TRAFFIC_NCU_AT = {"nside": 512, "lmax": 1023, "ncol": 256}
 
 
