@@ -1443,21 +1443,23 @@ static cudaError_t launch_grid(int nwork, int C, void* dst, const TcArgs& a, cud
 
 // Filling the SMs that large clusters leave idle. With one 227 KB CTA per SM a
 // cluster of C CTAs needs C free SMs in one GPC, so clusters of 8 occupy only
-// 120 of this GPU's 148 SMs. When the main launch uses clusters of 8 or more,
-// a share of the work items (the last ones: the cheapest alm2map items) goes
+// 120 of this GPU's 148 SMs. When the main launch uses clusters of 4 or more
+// (SHT_FILL_MIN_CLUSTER), a share of the work items (the last ones: the
+// cheapest items) goes
 // to a second launch with small clusters on a low-priority helper stream of
 // the device, forked from and joined back into the caller's stream; the two
 // launches never wait on each other, and each work item computes exactly
 // what it would in one launch. SHT_FILL_FRAC: share of the work items for
 // that launch (default 0.06; 0 turns it off); SHT_FILL_CLUSTER: its cluster
 // size (default 2).
-struct FillCfg { double frac; int cluster; };
+struct FillCfg { double frac; int cluster; int min_main; };
 static FillCfg fill_cfg()
 {
     static FillCfg f = [] {
-        FillCfg c{0.06, 2};
+        FillCfg c{0.06, 2, 4};
         if (const char* e = std::getenv("SHT_FILL_FRAC")) c.frac = std::max(0.0, std::min(0.5, std::atof(e)));
         if (const char* e = std::getenv("SHT_FILL_CLUSTER")) c.cluster = std::max(1, std::min(8, std::atoi(e)));
+        if (const char* e = std::getenv("SHT_FILL_MIN_CLUSTER")) c.min_main = std::max(2, std::min(16, std::atoi(e)));
         return c;
     }();
     return f;
@@ -1498,7 +1500,7 @@ static cudaError_t launch_tc(const sht_plan* p, int nwork, void* dst,
     }
     const FillCfg fc = fill_cfg();
     std::unique_lock<std::mutex> lk(g_fill_mu, std::defer_lock);
-    int nB = (fc.frac > 0.0 && C >= 8 && C > fc.cluster) ? (int)(fc.frac * nwork + 0.5) : 0;
+    int nB = (fc.frac > 0.0 && C >= fc.min_main && C > fc.cluster) ? (int)(fc.frac * nwork + 0.5) : 0;
     if (nB > 0) lk.lock();
     FillStream* fs = (nB > 0) ? fill_stream() : nullptr;
     if (!fs) nB = 0;
