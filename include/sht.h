@@ -123,12 +123,15 @@ size_t    sht_plan_device_bytes(const sht_plan* plan);
 /* Share of the Legendre terms (m, l, ring pair) that the plan's contraction
  * evaluates (Sec. 3.1, Implementation detail: the ring optimisation, which
  * leaves out, for each m, the rings where P_lm has an extremely low
- * amplitude). Split plans skip, for each order m, the leading polar ring
- * pairs on which |lambda_lm| < 1e-30 for every l (spin 2: for s = +2 and -2;
- * in 32-pair steps, the same set for every higher order), in the
- * contraction and in the ring FFTs' order mapping; the skipped terms change
- * no output beyond rounding. 1.0 when nothing is skipped (FP64 plans, or the
- * environment variable SHT_RING_SKIP=0 at plan creation); 0 for a NULL plan. */
+ * amplitude). Plans skip, for each order m, the leading polar ring pairs
+ * on which |lambda_lm| < 1e-30 for every l (spin 2: for s = +2 and -2; in
+ * 32-pair steps, the same set for every higher order): split plans in the
+ * contraction and in the ring FFTs' order mapping, FP64 plans in map2alm's
+ * contraction and in alm2map's ring-pair tiles that lie wholly among them
+ * (their G is written as zeros). The skipped terms change no output beyond
+ * rounding. 1.0 when nothing is skipped (the environment variable
+ * SHT_RING_SKIP=0 at plan creation); 0 for a NULL plan. The value counts
+ * the pairs from each order's first kept one. */
 double    sht_plan_terms_kept(const sht_plan* plan);
 
 /* Backward transform (Sec. 2.1 equ:backward equ, equ:mm backward; spin 2:

@@ -81,6 +81,9 @@ struct DevTables {
     double2* ck64 = nullptr;
     int* ck64_exp = nullptr;
     int* ck64_off = nullptr;       // spin 0: [m][q]; spin 2: [m]
+    // FP64 plans, ring optimisation: the first ring pair each order m
+    // contracts (a multiple of 32, nondecreasing in m; null: every pair)
+    int* pfirst64 = nullptr;
 };
 
 // lo parts of the FP32 FFT tables and hi/lo ring phase tables (compensated FFT)
@@ -244,6 +247,8 @@ cudaError_t launch_alias_residual_order(const sht_plan* p, const double* T, cons
                                         int m0, int nm, cudaStream_t st);
 // plan-time walk of the FP64 recurrences that stores their checkpoints
 cudaError_t build_f64_checkpoints(sht_plan* p, size_t* acc);
+bool ring_skip_enabled();
+void ring_first_pairs(sht_plan* p, const std::vector<char>& live);
 cudaError_t launch_legendre_a2m_f64(const sht_plan* p, const double* alm, double* G, int nmaps,
                                     double scale0, double scale, cudaStream_t st);
 int legendre_f64_row_tile();

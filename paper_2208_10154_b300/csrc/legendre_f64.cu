@@ -54,6 +54,9 @@ struct LegArgs {
     const double2* ck64;
     const int* ck64_exp;
     const int* ck64_off;
+    // ring optimisation: first ring pair of order m with a non-negligible
+    // lambda (a multiple of 32; null: 0)
+    const int* pfirst;
 };
 
 __device__ __forceinline__ long long d_alm_index(int lmax, int l, int m)
@@ -246,13 +249,15 @@ k_leg_m2a_f64(const double* __restrict__ T, double* __restrict__ alm, LegArgs a)
         }
     };
 
-    const int nch = (a.R + M2A_TK - 1) / M2A_TK;
-    if (producer) produce(0, 0);
+    // (ring pairs before pb hold negligible lambda for this order)
+    const int pb = a.pfirst ? a.pfirst[m] : 0;
+    const int nch = (a.R - pb + M2A_TK - 1) / M2A_TK;
+    if (producer) produce(pb, 0);
     __syncthreads();
     for (int ch = 0; ch < nch; ch++) {
         const int cb = ch & 1;
         if (producer) {
-            if (ch + 1 < nch) produce((ch + 1) * M2A_TK, cb ^ 1);
+            if (ch + 1 < nch) produce(pb + (ch + 1) * M2A_TK, cb ^ 1);
         } else {
             // row groups i with RG i >= nv hold no row of the tile (short last
             // tiles at high m): skipped, block-uniformly
@@ -342,6 +347,9 @@ k_leg_a2m_f64(const double* __restrict__ alm, double* __restrict__ G, LegArgs a)
         lk0 = m > 2 ? m : 2; lstep = 1;
         K = (a.lmax >= lk0) ? a.lmax - lk0 + 1 : 0;
     }
+    // a tile of ring pairs that all hold negligible lambda for this order
+    // writes zeros (the ring optimisation)
+    if (a.pfirst && p0 + A2M_TP <= a.pfirst[m]) K = 0;
     // chain state (threads 0..63: one ring pair each, carried across chunks)
     double c2 = 0.0, p2 = 0.0, c3 = 0.0, p3 = 0.0;
     int E2 = 0, E3 = 0;
@@ -468,6 +476,7 @@ static LegArgs make_args(const sht_plan* p, int nmaps, double scale0, double sca
     a.seed_exp = p->t.seed_exp;
     a.ra = p->t.rec_a; a.rb = p->t.rec_b; a.rc = p->t.rec_c;
     a.wA0 = p->t.w_A[0]; a.wAB0 = p->t.w_AB[0]; a.wC0 = p->t.w_C[0];
+    a.pfirst = p->t.pfirst64;
     a.wA1 = p->t.w_A[1]; a.wAB1 = p->t.w_AB[1]; a.wC1 = p->t.w_C[1];
     a.spin = p->spin; a.lmax = p->lmax; a.mmax = p->mmax; a.R = p->R;
     a.ncol = ncols(p, nmaps); a.nalm = p->nalm; a.ncomp = p->ncomp;
@@ -578,12 +587,16 @@ cudaError_t launch_legendre_a2m_f64_order(const sht_plan* p, const double* alm, 
 // plan-time walk of every chain the map2alm kernel resumes mid-tile (the
 // layout of DevTables::ck64): spin 0, thread (p, m, q); spin 2, thread (p, m)
 // ---------------------------------------------------------------------------
-__global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ cke)
+// (and live[(m * 2 + q) * R + p] = 1 where some |lambda| of the chain reaches
+// SPLIT_LAMBDA_EPS: the ring optimisation's first pairs)
+__global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ cke, char* __restrict__ live)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int m = blockIdx.y, q = blockIdx.z;
     if (p >= a.R) return;
     const double x = a.pairs[p].x;
+    const double eps = (double)SPLIT_LAMBDA_EPS;
+    bool lv = false;
     if (a.spin == 0) {
         const int l_first = m + q;
         const int nrows = (a.lmax >= l_first) ? (a.lmax - l_first) / 2 + 1 : 0;
@@ -592,8 +605,10 @@ __global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ ck
         int E = a.seed_exp[si];
         const double x2 = x * x;
         const int o = a.ck64_off[m * 2 + q];
+        if (nrows > 0) lv = fabs(scale2(cur, E)) >= eps;
         for (int r = 0; r + 1 < nrows; r++) {
             step0(a.ra, a.rb, a.rc, d_alm_index(a.lmax, l_first + 2 * r, m), x2, cur, prev, E);
+            lv = lv || fabs(scale2(cur, E)) >= eps;
             if (((r + 1) & 31) == 0) {
                 const long long i = (long long)(o + ((r + 1) >> 5) - 1) * a.R + p;
                 ck[i] = make_double2(cur, prev);
@@ -610,10 +625,12 @@ __global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ ck
         double c3 = a.seed_mant[si], p3 = 0.0;
         int E3 = a.seed_exp[si];
         const int o = a.ck64_off[m];
+        if (a.lmax >= l0) lv = fabs(scale2(c2, E2)) >= eps || fabs(scale2(c3, E3)) >= eps;
         for (int l = l0 + 1; l <= a.lmax; l++) {
             const long long ci = d_alm_index(a.lmax, l, m);
             step2(a.wA0, a.wAB0, a.wC0, ci, x, c2, p2, E2);
             step2(a.wA1, a.wAB1, a.wC1, ci, x, c3, p3, E3);
+            lv = lv || fabs(scale2(c2, E2)) >= eps || fabs(scale2(c3, E3)) >= eps;
             if (((l - m) & 63) == 0) {                  // l = m + 64 b, b >= 1 (l > l0 >= m)
                 const long long i = (long long)(o + ((l - m) >> 6) - 1) * a.R + p;
                 ck[2 * i] = make_double2(c2, p2);
@@ -623,6 +640,7 @@ __global__ void k_ck64(LegArgs a, double2* __restrict__ ck, int* __restrict__ ck
             }
         }
     }
+    live[((long long)m * 2 + q) * a.R + p] = lv ? 1 : 0;
 }
 
 cudaError_t build_f64_checkpoints(sht_plan* p, size_t* acc)
@@ -649,15 +667,35 @@ cudaError_t build_f64_checkpoints(sht_plan* p, size_t* acc)
     if ((e = cudaMemcpy(p->t.ck64_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
         return e;
     *acc += off.size() * sizeof(int);
-    if (ne == 0) return cudaSuccess;
-    if ((e = cudaMalloc(&p->t.ck64, (size_t)ne * sizeof(double2))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&p->t.ck64_exp, (size_t)ne * sizeof(int))) != cudaSuccess) return e;
-    *acc += (size_t)ne * (sizeof(double2) + sizeof(int));
+    if (ne > 0) {
+        if ((e = cudaMalloc(&p->t.ck64, (size_t)ne * sizeof(double2))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&p->t.ck64_exp, (size_t)ne * sizeof(int))) != cudaSuccess) return e;
+        *acc += (size_t)ne * (sizeof(double2) + sizeof(int));
+    }
+    // (with no checkpoints, no chain is long enough to write one)
+    const size_t nlive = (size_t)(mmax + 1) * 2 * p->R;
+    char* d_live = nullptr;
+    if ((e = cudaMalloc(&d_live, nlive)) != cudaSuccess) return e;
+    cudaMemset(d_live, 0, nlive);
     LegArgs a = make_args(p, 1, 1.0, 1.0, nullptr);
     dim3 grid((unsigned)((p->R + 127) / 128), (unsigned)(mmax + 1), p->spin ? 1u : 2u);
-    k_ck64<<<grid, 128>>>(a, p->t.ck64, p->t.ck64_exp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return cudaDeviceSynchronize();
+    k_ck64<<<grid, 128>>>(a, p->t.ck64, p->t.ck64_exp, d_live);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    std::vector<char> lq(nlive);
+    if (e == cudaSuccess) e = cudaMemcpy(lq.data(), d_live, nlive, cudaMemcpyDeviceToHost);
+    cudaFree(d_live);
+    if (e != cudaSuccess || !ring_skip_enabled()) return e;
+    // the ring optimisation: first ring pair of each order (either slot live)
+    const int R = p->R;
+    std::vector<char> live((size_t)(mmax + 1) * R);
+    for (int m = 0; m <= mmax; m++)
+        for (int q = 0; q < R; q++)
+            live[(size_t)m * R + q] = lq[((size_t)m * 2 + 0) * R + q] || lq[((size_t)m * 2 + 1) * R + q];
+    ring_first_pairs(p, live);
+    if ((e = cudaMalloc(&p->t.pfirst64, p->h_pfirst.size() * sizeof(int))) != cudaSuccess) return e;
+    *acc += p->h_pfirst.size() * sizeof(int);
+    return cudaMemcpy(p->t.pfirst64, p->h_pfirst.data(), p->h_pfirst.size() * sizeof(int), cudaMemcpyHostToDevice);
 }
 
 int legendre_f64_row_tile() { return M2A_TL; }

@@ -581,21 +581,25 @@ static float slice_range(double K)
 // below 1e-30 of lambda's O(1) peak times the data, far below FP64 rounding
 // of the outputs. SHT_RING_SKIP=0 turns it off. Split plans (spin 2: the
 // maxima over both slots are those of s = +2 and -2).
-static cudaError_t build_ring_skip(sht_plan* p, size_t* acc)
+// whether ring skipping is on for plans created now (SHT_RING_SKIP=0: off)
+bool ring_skip_enabled()
+{
+    const char* env = std::getenv("SHT_RING_SKIP");
+    return !(env && std::atoi(env) == 0);
+}
+
+// pfirst[m] (host) and the kept share of the (m, l, ring pair) terms from
+// live[m * R + p] = 1 where some |lambda_lm(theta_p)| >= SPLIT_LAMBDA_EPS:
+// the first live pair of each order, made nondecreasing in m from the top
+// and rounded down to 32; order 0 keeps every pair
+void ring_first_pairs(sht_plan* p, const std::vector<char>& live)
 {
     const int mmax = p->mmax, R = p->R, KCH = 32;
     p->h_pfirst.assign((size_t)mmax + 1, 0);
-    const char* env = std::getenv("SHT_RING_SKIP");
-    if (env && std::atoi(env) == 0) return cudaSuccess;
-    std::vector<float> pm((size_t)(mmax + 1) * 2 * R);
-    cudaError_t e = cudaMemcpy(pm.data(), p->s.pairmax, pm.size() * sizeof(float), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return e;
     int run = R - 1;                     // the equator pair is never skipped
     for (int m = mmax; m >= 0; m--) {
         int p0 = 0;
-        while (p0 < R - 1 && std::max(pm[((size_t)m * 2 + 0) * R + p0], pm[((size_t)m * 2 + 1) * R + p0]) <
-                                 SPLIT_LAMBDA_EPS)
-            p0++;
+        while (p0 < R - 1 && !live[(size_t)m * R + p0]) p0++;
         run = std::min(run, p0);
         p->h_pfirst[m] = run / KCH * KCH;
     }
@@ -607,6 +611,22 @@ static cudaError_t build_ring_skip(sht_plan* p, size_t* acc)
         all += nl * R;
     }
     p->terms_kept = all > 0.0 ? kept / all : 1.0;
+}
+
+static cudaError_t build_ring_skip(sht_plan* p, size_t* acc)
+{
+    const int mmax = p->mmax, R = p->R;
+    p->h_pfirst.assign((size_t)mmax + 1, 0);
+    if (!ring_skip_enabled()) return cudaSuccess;
+    std::vector<float> pm((size_t)(mmax + 1) * 2 * R);
+    cudaError_t e = cudaMemcpy(pm.data(), p->s.pairmax, pm.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    std::vector<char> live((size_t)(mmax + 1) * R);
+    for (int m = 0; m <= mmax; m++)
+        for (int q = 0; q < R; q++)
+            live[(size_t)m * R + q] = std::max(pm[((size_t)m * 2 + 0) * R + q], pm[((size_t)m * 2 + 1) * R + q]) >=
+                                      SPLIT_LAMBDA_EPS;
+    ring_first_pairs(p, live);
     std::vector<int> ml((size_t)R, 0);
     for (int q = 0, m = 0; q < R; q++) {
         while (m < mmax && p->h_pfirst[m + 1] <= q) m++;
@@ -876,7 +896,7 @@ static void free_tables(sht_plan* p)
     void* ptrs[] = {p->t.pairs, p->t.fft, p->t.twiddle, p->t.chirp, p->t.bhat, p->t.twiddle_f,
                     p->t.chirp_f, p->t.bhat_f, p->t.seed_mant, p->t.seed_exp, p->t.rec_a, p->t.rec_b,
                     p->t.rec_c, p->t.w_A[0], p->t.w_A[1], p->t.w_AB[0], p->t.w_AB[1], p->t.w_C[0],
-                    p->t.w_C[1], p->t.ck64, p->t.ck64_exp, p->t.ck64_off, p->work_m2a, p->work_a2m,
+                    p->t.w_C[1], p->t.ck64, p->t.ck64_exp, p->t.ck64_off, p->t.pfirst64, p->work_m2a, p->work_a2m,
                     p->host_dev_in, p->host_dev_out, p->host_ws};
     for (void* q : ptrs) if (q) cudaFree(q);
     void* cp[] = {p->c.cls_pairs, p->c.twiddle_l, p->c.chirp_l, p->c.bhat_l, p->c.phase_h, p->c.phase_l, p->c.phase_off,

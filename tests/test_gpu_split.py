@@ -194,19 +194,22 @@ def test_split_iteration(orc, sht, nside, lmax, spin, niter):
     assert colerr(got, orc.map2alm(h, nside, lmax, spin=spin, niter=niter)) < TOL
 
 
-@pytest.mark.parametrize("spin", [0, 2])
-def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch, spin):
+@pytest.mark.parametrize("prec,spin", [("split", 0), ("split", 2), ("fp64", 0), ("fp64", 2)])
+def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch, prec, spin):
     """Sec. 3.1 (Implementation detail), the ring optimisation: a spin-0 split
     plan leaves out, per order m, the polar ring pairs where |lambda_lm| <
     1e-30 for every l, in the contraction and in the FFT order mapping. At
     nside 256 / lmax 511 that is about a tenth of the (m, l, ring pair) terms;
     the results match a plan that skips nothing (SHT_RING_SKIP=0) to far below
-    the split form's own error, for alm2map and for map2alm with the
-    Fourier-domain iteration (whose residual folds only the kept orders)."""
+    the form's own error, for alm2map and for map2alm with the Fourier-domain
+    iteration (whose residual folds only the kept orders). The FP64 form
+    skips the same leading ring pairs in map2alm and writes zeros for
+    alm2map's ring-pair tiles that lie wholly among them."""
     nside, lmax, nmaps = 256, 511, 3
-    plan = sht.Plan(nside, lmax, None, spin, "split")
+    tol_a, tol_b = (1e-9, 2e-7) if prec == "split" else (1e-12, 1e-12)
+    plan = sht.Plan(nside, lmax, None, spin, prec)
     monkeypatch.setenv("SHT_RING_SKIP", "0")
-    full = sht.Plan(nside, lmax, None, spin, "split")
+    full = sht.Plan(nside, lmax, None, spin, prec)
     monkeypatch.delenv("SHT_RING_SKIP")
     assert full.terms_kept() == 1.0
     assert 0.5 < plan.terms_kept() < 0.95
@@ -217,14 +220,14 @@ def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch, spin):
         cls = np.stack([cl, 0.01 * cl])
     a = torch.from_numpy(inputs.gaussian_alm(11, nmaps, ncomp, lmax, cls=cls)).cuda()
     m_skip, m_full = plan.alm2map(a), full.alm2map(a)
-    assert colerr(m_skip.cpu().numpy(), m_full.cpu().numpy()) < 1e-9
+    assert colerr(m_skip.cpu().numpy(), m_full.cpu().numpy()) < tol_a
     for niter in (0, 2):
         b_skip = plan.map2alm(m_full, niter=niter).cpu().numpy()
         b_full = full.map2alm(m_full, niter=niter).cpu().numpy()
         assert np.all(np.isfinite(b_skip))
-        assert colerr(b_skip, b_full) < 2e-7
+        assert colerr(b_skip, b_full) < tol_b
     if spin:                             # one component: half of the contraction
         e_skip = plan.map2alm_eb(m_full, "B").cpu().numpy()
         e_full = full.map2alm_eb(m_full, "B").cpu().numpy()
-        assert colerr(e_skip, e_full) < 2e-7
+        assert colerr(e_skip, e_full) < tol_b
     plan.device_status()
