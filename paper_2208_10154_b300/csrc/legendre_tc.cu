@@ -254,7 +254,7 @@ __device__ __align__(128) uint8_t g_lam_slots[(size_t)LAM_SM * 3 * LAM_SLOTS * S
 struct df { float h, l; };   // double-float value hi + lo
 
 struct TcShared {
-    uint64_t full[NST];        // stage filled: 4 data warps + one arrival per lambda piece
+    uint64_t full[NST];        // stage filled: one arrival with the data copy; every byte completes as tx
     uint64_t empty[NST];       // stage consumed by the MMAs of every CTA of the cluster
     uint64_t accf;             // all MMAs of this CTA done
     uint64_t cdone;            // the correction accumulators hold a finished span
