@@ -134,6 +134,16 @@ size_t    sht_plan_device_bytes(const sht_plan* plan);
  * the pairs from each order's first kept one. */
 double    sht_plan_terms_kept(const sht_plan* plan);
 
+/* The ring optimisation's first ring pair per order (the same passage):
+ * out[m], m = 0..mmax (host memory owned by the caller, mmax + 1 ints) is
+ * the first ring pair, counted from the north pole (pair p holds rings p + 1
+ * and 4 nside - 1 - p), that the plan contracts for order m: the first pair
+ * where some |lambda_lm| (spin 2: of s = +2 or -2) reaches 1e-30, made
+ * nondecreasing in m (the smallest over this and every higher order),
+ * rounded down to a multiple of 32, and 0 for m = 0; all 0 when nothing is
+ * skipped. SHT_EINVAL for a NULL argument. */
+sht_status sht_plan_first_pairs(const sht_plan* plan, int* out);
+
 /* Backward transform (Sec. 2.1 equ:backward equ, equ:mm backward; spin 2:
  * equ:aeab mat form inv). alm [nmaps][ncomp][nalm] (complex double, device)
  * -> map [nmaps][ncomp][npix] (double, device). Real field:

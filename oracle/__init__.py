@@ -148,6 +148,36 @@ def slambda_theta(lmax: int, mmax: int, s: int, theta) -> np.ndarray:
     return out
 
 
+def ring_first_pairs(nside: int, lmax: int, spin: int = 0, eps: float = 1e-30, raw: bool = False):
+    """The ring optimisation (Sec. 3.1, Implementation detail: for a given m
+    the rings where P_lm has an extremely low amplitude are ignored), as the
+    library reads it: for each order m, p0(m) = the first ring pair, counted
+    from the north pole (pair p = north ring p + 1), where |lambda_lm(theta)|
+    reaches eps for some l (spin 2: the theta parts of sY_lm for s = +2 and
+    -2). With raw=False the result is then made nondecreasing in m (the
+    smallest p0 of this and every higher order), rounded down to a multiple
+    of 32, and 0 for m = 0. int array [lmax + 1] (mmax = lmax)."""
+    z, sth, _, _, _ = ring_info(nside)
+    R = 2 * nside
+    theta = np.arctan2(sth[:R], z[:R])
+    if spin == 0:
+        lam = np.abs(lambda_theta(lmax, lmax, theta))                   # [R, nalm]
+        live = np.zeros((lmax + 1, R), dtype=bool)
+        for m in range(lmax + 1):
+            i0 = m * (2 * lmax + 1 - m) // 2
+            live[m] = lam[:, i0 + m:i0 + lmax + 1].max(axis=1) >= eps
+    else:
+        sp = np.abs(slambda_theta(lmax, lmax, 2, theta))[:, lmax:, :]   # [R, m >= 0, l]
+        sm = np.abs(slambda_theta(lmax, lmax, -2, theta))[:, lmax:, :]
+        live = (np.maximum(sp, sm).max(axis=2) >= eps).T                # [m, R]
+    p0 = np.array([int(np.argmax(live[m])) if live[m, :R - 1].any() else R - 1 for m in range(lmax + 1)])
+    if raw:
+        return p0
+    out = np.minimum.accumulate(p0[::-1])[::-1] // 32 * 32
+    out[0] = 0
+    return out.astype(np.int32)
+
+
 def _check(nside, lmax, mmax, spin):
     if spin not in (0, 2):
         raise ValueError("spin must be 0 or 2")

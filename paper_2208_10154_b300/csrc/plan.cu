@@ -1172,6 +1172,12 @@ int sht_plan_precision(const sht_plan* p) { return p ? p->precision : 0; }
 long long sht_plan_npix(const sht_plan* p) { return p ? p->npix : 0; }
 long long sht_plan_nalm(const sht_plan* p) { return p ? p->nalm : 0; }
 double sht_plan_terms_kept(const sht_plan* p) { return p ? p->terms_kept : 0.0; }
+sht_status sht_plan_first_pairs(const sht_plan* p, int* out)
+{
+    if (!p || !out) { set_error("sht_plan_first_pairs: NULL argument"); return SHT_EINVAL; }
+    for (int m = 0; m <= p->mmax; m++) out[m] = p->h_pfirst.empty() ? 0 : p->h_pfirst[m];
+    return SHT_OK;
+}
 size_t sht_plan_device_bytes(const sht_plan* p)
 {
     return p ? p->table_bytes + p->host_dev_in_bytes + p->host_dev_out_bytes + p->host_ws_bytes : 0;

@@ -65,6 +65,8 @@ def load() -> ctypes.CDLL:
         lib.sht_plan_device_bytes.restype = S
         lib.sht_plan_terms_kept.argtypes = [P]
         lib.sht_plan_terms_kept.restype = ctypes.c_double
+        lib.sht_plan_first_pairs.argtypes = [P, P]
+        lib.sht_plan_first_pairs.restype = I
         lib.sht_alm2map.argtypes = [P, P, P, I, P, S, P]
         lib.sht_map2alm.argtypes = [P, P, P, I, I, P, S, P]
         lib.sht_alm2map_adjoint.argtypes = [P, P, P, I, P, S, P]
@@ -222,6 +224,13 @@ class Plan:
     def device_bytes(self) -> int:
         """Device memory held by the plan itself (tables, host-path staging)."""
         return int(load().sht_plan_device_bytes(self.handle))
+
+    def first_pairs(self):
+        """First ring pair contracted for each order m (numpy int32 [mmax + 1])."""
+        import numpy as np
+        out = np.zeros(self.mmax + 1, dtype=np.int32)
+        _check(load().sht_plan_first_pairs(self.handle, ctypes.c_void_p(out.ctypes.data)))
+        return out
 
     def terms_kept(self) -> float:
         """Share of the (m, l, ring pair) Legendre terms the contraction evaluates."""

@@ -231,3 +231,19 @@ def test_ring_optimisation_changes_nothing_measurable(sht, monkeypatch, prec, sp
         e_full = full.map2alm_eb(m_full, "B").cpu().numpy()
         assert colerr(e_skip, e_full) < tol_b
     plan.device_status()
+
+
+@pytest.mark.parametrize("prec,spin,nside", [("split", 0, 128), ("split", 2, 64), ("fp64", 0, 128),
+                                             ("fp64", 2, 64), ("split", 0, 256)])
+def test_ring_first_pairs_match_the_oracle(orc, sht, prec, spin, nside):
+    """The plan's ring-optimisation table (index work: bit-exact) equals the
+    oracle's restatement of the rule: per order, the first ring pair where
+    some |lambda_lm| (spin 2: of s = +2 or -2) reaches 1e-30, made
+    nondecreasing in m, rounded down to 32, 0 for m = 0. The split plan takes
+    its maxima from its double-float lambda walk in FP32, the FP64 plan from
+    its FP64 walk, the oracle from long double."""
+    lmax = 2 * nside - 1
+    plan = sht.Plan(nside, lmax, None, spin, prec)
+    want = orc.ring_first_pairs(nside, lmax, spin)
+    assert want[-1] > 0
+    assert np.array_equal(plan.first_pairs(), want)

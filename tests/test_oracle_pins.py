@@ -667,3 +667,34 @@ def test_every_ring_has_a_multiple_of_four_pixels(orc, nside):
     _, _, _, n, _ = orc.ring_info(nside)
     assert np.all(np.asarray(n) % 4 == 0)
     assert len(n) == 4 * nside - 1 and int(np.sum(n)) == 12 * nside * nside
+
+
+@pytest.mark.parametrize("m", [44, 55, 63])
+def test_ring_first_pair_against_mpmath(orc, m):
+    """The ring optimisation's criterion (Sec. 3.1, Implementation detail)
+    checked with the explicit Rodrigues expansion in mpmath (enough digits
+    for its cancellation), independently of the oracle's recurrence: at
+    nside 32, lmax 63, every ring pair before the
+    oracle's first pair of order m has |lambda_lm| < 1e-30 for all l, and the
+    first pair has some l at or above it. The library's table follows from
+    these by the stated rule (nondecreasing in m, multiples of 32, order 0
+    keeps every pair)."""
+    mp = pytest.importorskip("mpmath")
+    nside, lmax = 32, 63
+    mp.mp.dps = int(0.7 * lmax) + 60
+    eps = mp.mpf("1e-30")
+    p0 = int(orc.ring_first_pairs(nside, lmax, 0, raw=True)[m])
+    assert p0 >= 3
+    z, s, _, _, _ = orc.ring_info(nside)
+
+    def lam_max(p):
+        th = float(np.arctan2(s[p], z[p]))
+        return max(abs(_plm_explicit(mp, l, m, th)) for l in range(m, lmax + 1))
+
+    for p in range(p0):
+        assert lam_max(p) < eps, (m, p)
+    assert lam_max(p0) >= eps
+    full = orc.ring_first_pairs(nside, lmax, 0)
+    raw = orc.ring_first_pairs(nside, lmax, 0, raw=True)
+    assert full[0] == 0 and np.all(np.diff(full) >= 0) and np.all(full % 32 == 0)
+    assert np.all(full <= raw)
