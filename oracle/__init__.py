@@ -17,7 +17,7 @@ Pins that tie each function to something other than itself live in
 orthonormality, brute force vs separable, quadrature identities, adjoint
 identity, iteration convergence, E/B rotation, the compact square storage
 against a worked example, the E/B projection's complementarity and
-idempotence).
+idempotence, the ring optimisation's criterion against mpmath).
 """
 from __future__ import annotations
 
