@@ -1311,14 +1311,26 @@ k_alm_prep(const double* __restrict__ alm, float2* __restrict__ A2, unsigned int
     const int tid = threadIdx.x;
     if (tid < 4 * PREP_M) cmx[tid / (2 * PREP_M)][tid % (2 * PREP_M)] = 0.0f;
     const long long base = a_idx(lmax, l0, m);
-    for (int e = tid; e < PREP_L * PREP_M; e += blockDim.x) {
-        const int j = e / PREP_L, li = e % PREP_L;            // consecutive threads: consecutive l
-        double2 v = make_double2(0.0, 0.0);
-        if (l0 + li <= lmax && mp0 + j < nmc) {
-            v = reinterpret_cast<const double2*>(alm)[(mp0 + j) * nalm + base + li];
-            if (m == 0) v.y = 0.0;
+    // the block's 64 x 32 loads, PREP_UB per thread all in flight before the
+    // first is stored (256 threads: one batch)
+    constexpr int PREP_UB = PREP_L * PREP_M / 256;
+    for (int e0 = tid; e0 < PREP_L * PREP_M; e0 += PREP_UB * blockDim.x) {
+        double2 v[PREP_UB];
+#pragma unroll
+        for (int u = 0; u < PREP_UB; u++) {
+            const int e = e0 + u * (int)blockDim.x;
+            const int j = e / PREP_L, li = e % PREP_L;        // consecutive threads: consecutive l
+            v[u] = make_double2(0.0, 0.0);
+            if (e < PREP_L * PREP_M && l0 + li <= lmax && mp0 + j < nmc)
+                v[u] = reinterpret_cast<const double2*>(alm)[(mp0 + j) * nalm + base + li];
         }
-        tile[li][j] = v;
+#pragma unroll
+        for (int u = 0; u < PREP_UB; u++) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e >= PREP_L * PREP_M) break;
+            if (m == 0) v[u].y = 0.0;
+            tile[e % PREP_L][e / PREP_L] = v[u];
+        }
     }
     __syncthreads();
     const int cc = tid % (2 * PREP_M);                        // column within the block (fixed per thread)

@@ -42,6 +42,7 @@ CASES = [
     (8, 23, 23, 520, "flat"),           # 9 column tiles: clusters of 5, one padded tile
     (96, 200, 200, 6, "inv_llp1"),      # 192 ring pairs: an alm2map CTA walks a full and a 64-row tile
     (560, 100, 100, 3, "flat"),         # 1120 ring pairs: two alm2map groups (8 tiles, then a 96-row tile)
+    (128, 255, 180, 3, "inv_llp1"),     # mmax < lmax with polar ring pairs skipped per order (up to 64)
 ]
 
 
