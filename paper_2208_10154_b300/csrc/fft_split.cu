@@ -18,6 +18,10 @@
 // shared-memory round trip), and the rings are launched in classes of equal
 // FFT size so the shared-memory footprint and thread count fit each size; the
 // classes of one call run on the caller's stream and two helper streams.
+// Ring optimisation (Sec. 3.1): with a per-pair order limit mlim[p] (the
+// orders whose lambda is not negligible on the pair), the forward transform
+// writes T and its column maxima for m <= mlim[p] only and the backward one
+// folds only those orders.
 #include <algorithm>
 #include <cmath>
 #include <mutex>

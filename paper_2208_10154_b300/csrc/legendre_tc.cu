@@ -49,6 +49,10 @@
 // Each CTA's MMA completion is multicast to the "stage free" barriers of all
 // CTAs of the cluster.
 //
+// Ring optimisation (Sec. 3.1). Order m contracts only the ring pairs from
+// pfirst[m] (a multiple of 32; the pairs before it hold |lambda_lm| < 1e-30
+// for every l): map2alm's K and alm2map's ring-pair tiles start there.
+//
 // Data operand. A separate pass (k_slice) writes, per 32-wide chunk of K and
 // column tile, the four slice planes of the data as the exact 32 KB image of
 // the stage's A operand; the contraction fetches it with one bulk copy per
